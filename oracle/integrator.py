@@ -1,0 +1,147 @@
+"""RHMC trajectory (paper Sec. 2 and Sec. 4; ref. [rhmc] Horvath, Kennedy,
+Sint; ref. [hmc] Duane, Kennedy, Pendleton, Roweth).
+
+  * pseudo-fermion heatbath  phi = r_hb(A) xi,  xi ~ exp(-xi^dag xi)
+  * multi-step integrator: the fermion force on the outer level, the gauge
+    force on an inner level with n_gauge substeps per outer half step
+  * both levels use the second-order minimum-norm scheme
+        p += -lam h F;  U-update h/2;  p += -(1-2 lam) h F;  U-update h/2;  p += -lam h F
+    with lam = 0.1931833275037836 (Omelyan, Mryglod, Folk 2002; the paper
+    names the scheme but not the constant)
+  * Metropolis on dH = H_f - H_i with H = 1/2 sum p_a^2 + S_g + S_f, where the
+    final S_f uses the Metropolis rational (tighter than the MD one, Sec. 2)
+    and the initial S_f = xi^dag xi.
+Everything here is float64 (the oracle reference for all precision modes).
+"""
+from dataclasses import dataclass, field
+from typing import List
+
+import numpy as np
+
+from . import dirac, lattice as lat, solvers, su3
+from .actions import fermion_action, fermion_force, wilson_action, wilson_force
+
+LAMBDA_2MN = 0.1931833275037836
+
+
+@dataclass
+class Flavour:
+    mass: float
+    hb: object          # rational for the heatbath, ~ x^(+s/2)
+    md: object          # rational for the MD force, ~ x^(-s)
+    met: object         # rational for the Metropolis action, ~ x^(-s)
+    n_pf: int = 1
+
+
+@dataclass
+class HMCParams:
+    dims: tuple
+    beta: float
+    tau: float
+    n_outer: int
+    n_gauge: int
+    flavours: List[Flavour] = field(default_factory=list)
+    tol_md: float = 1e-10
+    tol_met: float = 1e-14
+    antiperiodic_t: bool = True
+
+
+class Context:
+    def __init__(self, p: HMCParams):
+        self.p = p
+        self.eta = lat.eta(p.dims, p.antiperiodic_t)
+        self.par = lat.parity(p.dims)
+
+    def shifted_solves(self, u, mass, phi, betas, tol):
+        def apply0(v, s0=min(betas)):
+            return dirac.a_op(u, v, mass, self.eta, self.par, s0)
+        xs, _, _ = solvers.multishift_cg(apply0, phi, betas, tol)
+        return xs
+
+    def rational_apply(self, u, mass, rat, phi, tol):
+        xs = self.shifted_solves(u, mass, phi, rat.beta, tol)
+        out = rat.a0 * phi
+        for a, x in zip(rat.alpha, xs):
+            out = out + a * x
+        return out, xs
+
+    def fermion_force_total(self, u, phis):
+        f = np.zeros(u.shape[:5] + (8,))
+        for fl, phi_list in zip(self.p.flavours, phis):
+            for phi in phi_list:
+                xs = self.shifted_solves(u, fl.mass, phi, fl.md.beta, self.p.tol_md)
+                f += fermion_force(u, xs, fl.md.alpha, self.eta, self.par)
+        return f
+
+    def fermion_action_total(self, u, phis, tol):
+        s = 0.0
+        for fl, phi_list in zip(self.p.flavours, phis):
+            for phi in phi_list:
+                xs = self.shifted_solves(u, fl.mass, phi, fl.met.beta, tol)
+                s += fermion_action(phi, xs, fl.met)
+        return s
+
+
+def update_links(u, mom, h):
+    """U_mu(x) <- exp(i h P_mu(x)) U_mu(x)."""
+    return np.einsum("...ij,...jk->...ik", su3.expi_coeffs(mom, h), u)
+
+
+def gauge_level(u, mom, h, n, beta):
+    """n minimum-norm steps of size h/n with the gauge force only."""
+    d = h / n
+    for _ in range(n):
+        mom = mom - LAMBDA_2MN * d * wilson_force(u, beta)
+        u = update_links(u, mom, d / 2)
+        mom = mom - (1 - 2 * LAMBDA_2MN) * d * wilson_force(u, beta)
+        u = update_links(u, mom, d / 2)
+        mom = mom - LAMBDA_2MN * d * wilson_force(u, beta)
+    return u, mom
+
+
+def md_evolve(ctx, u, mom, phis, tau, n_outer, n_gauge):
+    """Two-level minimum-norm integration of length tau."""
+    p = ctx.p
+    e = tau / n_outer
+    for _ in range(n_outer):
+        mom = mom - LAMBDA_2MN * e * ctx.fermion_force_total(u, phis)
+        u, mom = gauge_level(u, mom, e / 2, n_gauge, p.beta)
+        mom = mom - (1 - 2 * LAMBDA_2MN) * e * ctx.fermion_force_total(u, phis)
+        u, mom = gauge_level(u, mom, e / 2, n_gauge, p.beta)
+        mom = mom - LAMBDA_2MN * e * ctx.fermion_force_total(u, phis)
+    return u, mom
+
+
+def heatbath(ctx, u, xis):
+    """phi = r_hb(A) xi for every pseudo-fermion (the first FP64 inversion)."""
+    phis = []
+    for fl, xi_list in zip(ctx.p.flavours, xis):
+        phis.append([ctx.rational_apply(u, fl.mass, fl.hb, xi, ctx.p.tol_met)[0] for xi in xi_list])
+    return phis
+
+
+def hamiltonian_kinetic(mom):
+    return 0.5 * float(np.sum(mom * mom))
+
+
+def trajectory(ctx, u0, mom0, xis, uniform=None):
+    """One RHMC trajectory with supplied momenta mom0 [4,t,z,y,x,8] and
+    Gaussian sources xis (per flavour, per pseudo-fermion, even fields).
+
+    Returns dict with the final links and momenta (before accept/reject),
+    dH, the pieces of H and, if `uniform` is given, the Metropolis decision
+    accept = uniform < exp(-dH)."""
+    p = ctx.p
+    phis = heatbath(ctx, u0, xis)
+    s_f0 = sum(float(np.real(np.vdot(x, x))) for xl in xis for x in xl)
+    h0 = hamiltonian_kinetic(mom0) + wilson_action(u0, p.beta) + s_f0
+    u1, mom1 = md_evolve(ctx, u0, mom0, phis, p.tau, p.n_outer, p.n_gauge)
+    u1 = su3.reunitarize(u1)
+    s_f1 = ctx.fermion_action_total(u1, phis, p.tol_met)
+    h1 = hamiltonian_kinetic(mom1) + wilson_action(u1, p.beta) + s_f1
+    dh = h1 - h0
+    out = {"u": u1, "mom": mom1, "dH": dh, "H0": h0, "H1": h1, "Sf0": s_f0, "Sf1": s_f1,
+           "phis": phis}
+    if uniform is not None:
+        out["accept"] = bool(uniform < np.exp(-dh)) if np.isfinite(dh) else False
+    return out

@@ -1,0 +1,207 @@
+/*
+ * stag.h -- C ABI of libstag, a GB300 (sm_103a) implementation of the
+ * all-on-GPU RHMC hot path for unimproved staggered fermions described in
+ * Bonati, Cossu, D'Elia, Di Giacomo, "Staggered fermions simulations on GPUs"
+ * (Lattice 2010).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Lattice: dims = {Lx, Ly, Lz, Lt}, all even and >= 2; V = Lx Ly Lz Lt,
+ *   Vh = V / 2.  Lexicographic site index s = x + Lx*(y + Ly*(z + Lz*t)).
+ *   Parity p(s) = (x+y+z+t) mod 2, 0 = even.  Within one parity a site has
+ *   the half index h = s >> 1 (a bijection onto [0, Vh) because Lx is even).
+ * Operator (Sec. 2: unimproved staggered, even/odd preconditioned):
+ *   D psi(x) = 1/2 sum_mu eta_mu(x) [U_mu(x) psi(x+mu) - U_mu(x-mu)^dag psi(x-mu)]
+ *   eta_0 = 1, eta_1 = (-1)^x, eta_2 = (-1)^(x+y), eta_3 = (-1)^(x+y+z),
+ *   times -1 on t-links leaving the last time slice when t_antiperiodic.
+ *   D_eo maps odd -> even fields, D_oe even -> odd;  A = m^2 - D_eo D_oe.
+ * Spinor fields (caller-owned DEVICE memory): half-lattice, structure of
+ *   arrays, [nrhs][colour 3][Vh] complex, i.e. element (r, c, h) at
+ *   ((r*3 + c)*Vh + h), each complex stored (re, im).  Real type: double for
+ *   STAG_FP64, float for every other precision.  16-byte aligned.
+ * Momenta and forces (caller-owned DEVICE memory, always double):
+ *   [mu 4][parity 2][a 8][Vh]: coefficient a of sum_a p_a lambda_a/2 on link
+ *   (x, mu), x of the given parity with half index h.
+ * Host gauge layout (load/store): double complex U[mu][s][3][3] row-major,
+ *   i.e. 4*V*18 doubles, ((mu*V + s)*9 + 3*i + j)*2 + {0 re, 1 im}.
+ *
+ * Every call returns a stag_status and never aborts the process.  Calls are
+ * ordered on the context's stream; only those that return host scalars, and
+ * stag_store_gauge, synchronise it.  Device memory the context allocates is
+ * freed by stag_destroy.  A context is not thread-safe.
+ */
+#ifndef STAG_H
+#define STAG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct stag_ctx stag_ctx;
+
+typedef enum {
+    STAG_OK = 0,
+    STAG_ERR_ARG = 1,            /* invalid argument (null pointer, bad size, ...) */
+    STAG_ERR_ALLOC = 2,          /* device or pinned-host allocation failed */
+    STAG_ERR_CUDA = 3,           /* a CUDA runtime call failed (see stag_last_cuda_error) */
+    STAG_ERR_NOT_CONVERGED = 4,  /* solver hit max_iter; partial results are valid */
+    STAG_ERR_TIMEOUT = 5,        /* a bounded device-side wait gave up */
+    STAG_ERR_NAN = 6,            /* a NaN/Inf appeared in a reduction */
+    STAG_ERR_NO_GAUGE = 7        /* no gauge field loaded yet */
+} stag_status;
+
+/* Arithmetic of a Dslash / solver call (Sec. 4 and Sec. 5, Fig. 2):
+ *  STAG_FP64     links rebuilt as hi + lo from the two-float store, fp64 math
+ *  STAG_FP32     fp32 links (the hi words), 18 reals, fp32 math
+ *  STAG_FP32_12  fp32 links, first two rows only, third row rebuilt (Sec. 5)
+ *  STAG_BF16_12  bf16 copies of the first two rows, fp32 spinors and math   */
+typedef enum { STAG_FP64 = 0, STAG_FP32 = 1, STAG_FP32_12 = 2, STAG_BF16_12 = 3 } stag_prec;
+
+typedef struct {
+    int dims[4];          /* Lx, Ly, Lz, Lt: even, >= 2 */
+    int t_antiperiodic;   /* 1: antiperiodic fermion boundary in time */
+    void* cuda_stream;    /* cudaStream_t the context launches on (NULL = legacy default) */
+} stag_lattice;
+
+/* r(x) = a0 + sum_i alpha[i] / (x + beta[i]), n <= STAG_MAX_SHIFTS (Sec. 2). */
+#define STAG_MAX_SHIFTS 32
+typedef struct {
+    int n;
+    double a0;
+    const double* alpha;  /* host array of n */
+    const double* beta;   /* host array of n, all > -m^2 */
+} stag_rational;
+
+/* ---- context and gauge field (Sec. 3: the configuration is copied to the
+ *      device once and the whole update runs there) ---------------------- */
+
+/* Creates a context for one lattice.  *out receives the handle. */
+stag_status stag_create(const stag_lattice* lat, stag_ctx** out);
+void        stag_destroy(stag_ctx* ctx);
+const char* stag_strerror(stag_status s);
+/* Text of the last CUDA error seen by this context ("" if none). */
+const char* stag_last_cuda_error(stag_ctx* ctx);
+stag_status stag_set_stream(stag_ctx* ctx, void* cuda_stream);
+/* Device bytes the context currently holds. */
+size_t      stag_device_bytes(stag_ctx* ctx);
+
+/* Copy a host gauge field (host layout above; the caller keeps ownership)
+ * into the device two-float store of Sec. 5, Fig. 2: every real a is kept
+ * as b = (float)a and c = (float)(a - b); fp32 kernels read b, fp64 kernels
+ * rebuild b + c.  Also refreshes the bf16 copy.  Synchronous. */
+stag_status stag_load_gauge(stag_ctx* ctx, const double* host_u);
+/* Same, from a DEVICE buffer in the host layout (stream-ordered). */
+stag_status stag_load_gauge_device(stag_ctx* ctx, const double* dev_u);
+/* Copy the device gauge field (b + c) back to a caller-allocated host
+ * buffer of 4*V*18 doubles.  Synchronous. */
+stag_status stag_store_gauge(stag_ctx* ctx, double* host_u);
+
+/* ---- operator (Sec. 2, Sec. 5 Table 2) ---------------------------------- */
+
+/* out = D_{out_parity, 1-out_parity} in for nrhs right-hand sides: each link
+ * is loaded once per site and applied to every right-hand side.
+ * in: [nrhs][3][Vh] on parity 1-out_parity; out: same shape on out_parity. */
+stag_status stag_dslash(stag_ctx* ctx, int out_parity, stag_prec prec, int nrhs,
+                        const void* in, void* out);
+
+/* out = (m^2 + shift) in - D_eo D_oe in on even fields, nrhs right-hand sides. */
+stag_status stag_apply_a(stag_ctx* ctx, double mass, double shift, stag_prec prec,
+                         int nrhs, const void* in, void* out);
+
+/* ---- solvers (Sec. 6; multi-shift CG after Jegerlehner, hep-lat/9612014) --- */
+
+typedef struct {
+    int iterations;                       /* Krylov iterations of the base system */
+    int shift_iterations[STAG_MAX_SHIFTS]; /* iteration at which each shift froze */
+    double true_residual[STAG_MAX_SHIFTS]; /* max over rhs of ||b-(A+s)x||/||b||, fp64 */
+    int reliable_updates;                 /* fp64 residual replacements made */
+} stag_solve_info;
+
+/* Solve (A + shift_i) x_i = b for nshift shifts and nrhs independent sources
+ * in one Krylov space per source.  b: [nrhs][3][Vh] even field;
+ * x: [nrhs][nshift][3][Vh] (caller-owned, overwritten).
+ * prec STAG_FP64: everything in fp64.  Other precisions: the iteration runs
+ * with that Dslash and fp32 vectors, fp64 reductions, and fp64 reliable
+ * updates of the base residual (recomputed as b - (A+s0)x0 with the fp64
+ * operator whenever it fell by 'delta' = 0.1 since the last one).
+ * Stops each shift when its residual |zeta_i| ||r|| <= tol ||b||.
+ * info may be NULL.  Returns STAG_ERR_NOT_CONVERGED after max_iter. */
+stag_status stag_multishift_solve(stag_ctx* ctx, double mass, int nshift, const double* shifts,
+                                  stag_prec prec, int nrhs, const void* b, void* x,
+                                  double tol, int max_iter, stag_solve_info* info);
+
+/* ---- forces and actions (Sec. 2, Sec. 4) -------------------------------- */
+
+/* Force of S_f = sum_k phi_k^dag r(A) phi_k over n_pf pseudo-fermions:
+ *   F_a(x,mu) = sum_i alpha_i eps(x) eta_mu(x) Re tr[i T_a U_mu(x) Z_i(x+mu) Z_i(x)^dag]
+ * with Z_i = X_i on even and D_oe X_i on odd sites, X_i = (A+beta_i)^-1 phi,
+ * eps = +1/-1 on even/odd sites (dS/domega_a for U -> exp(i omega T_a) U).
+ * phi: [n_pf][3][Vh] even fields in the real type of prec.
+ * force: momentum layout, written (not accumulated). */
+stag_status stag_fermion_force(stag_ctx* ctx, double mass, const stag_rational* r, stag_prec prec,
+                               int n_pf, const void* phi, double* force, double tol, int max_iter,
+                               stag_solve_info* info);
+
+/* Wilson gauge force F_a = -(beta/3) Re tr(i T_a U_mu(x) Sigma_mu(x)),
+ * Sigma the sum of the six staples; force in momentum layout. */
+stag_status stag_gauge_force(stag_ctx* ctx, double beta, double* force);
+
+/* Mean plaquette <Re tr U_P / 3> in fp64 (synchronous). */
+stag_status stag_plaquette(stag_ctx* ctx, double* plaq);
+
+/* ---- the RHMC trajectory (Sec. 2, Sec. 4) -------------------------------- */
+
+#define STAG_MAX_FLAVOURS 2
+typedef struct {
+    double mass;
+    int n_pf;                   /* pseudo-fermions of this flavour */
+    stag_rational hb;           /* heatbath rational, ~ x^(+s/2)             */
+    stag_rational md;           /* MD-force rational, ~ x^(-s)               */
+    stag_rational met;          /* Metropolis rational, ~ x^(-s), tighter    */
+} stag_flavour;
+
+typedef struct {
+    double beta;                /* Wilson coupling */
+    double tau;                 /* trajectory length */
+    int n_outer;                /* minimum-norm steps of the fermion level */
+    int n_gauge;                /* gauge substeps per fermion half step */
+    int n_flavours;
+    stag_flavour flavour[STAG_MAX_FLAVOURS];
+    double tol_md, tol_met;     /* relative residuals of MD and heatbath/Metropolis solves */
+    int max_iter;
+    stag_prec md_prec;          /* arithmetic of the MD force solves and link update:
+                                   STAG_FP64 (plain fp64 path) or fp32 variants
+                                   (mixed path: fp32 update, fp64 reunitarisation,
+                                   fp64 heatbath and Metropolis, Sec. 4) */
+    unsigned long long seed;    /* Philox4x64 key word 0 */
+    unsigned long long counter; /* trajectory counter (Philox counter words 1-2) */
+    const double* ext_mom;      /* optional DEVICE momenta (momentum layout) instead of drawn ones */
+    const void* ext_xi;         /* optional DEVICE sources, [flavour][pf][3][Vh] fp64 complex */
+    double ext_uniform;         /* used for the accept test when ext_mom is set */
+    int no_metropolis;          /* 1: always keep the new field (tests, reversibility) */
+    int flip_momenta;           /* 1: start from -P (reversibility test) */
+} stag_hmc;
+
+typedef struct {
+    double dH, H0, H1;          /* Hamiltonian change and its ends */
+    double plaq;                /* mean plaquette after the trajectory */
+    int accepted;
+    long long cg_iterations;    /* Krylov iterations summed over all solves */
+    int reliable_updates;
+    double seconds;             /* device time of the trajectory */
+} stag_traj;
+
+/* One RHMC trajectory: heatbath, two-level minimum-norm MD, Metropolis with a
+ * host-side uniform, restore of the old field on rejection. */
+stag_status stag_md_trajectory(stag_ctx* ctx, const stag_hmc* p, stag_traj* out);
+
+/* Momenta of the last trajectory (device, momentum layout, read-only). */
+const double* stag_momenta(stag_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STAG_H */

@@ -1,0 +1,134 @@
+// Context management and error plumbing of the C ABI.
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+#include "solver_state.cuh"
+
+stag_status cuda_fail(stag_ctx* c, cudaError_t e, const char* where) {
+    if (c) {
+        c->last_err = std::string(where) + ": " + cudaGetErrorString(e);
+    }
+    return STAG_ERR_CUDA;
+}
+
+stag_status dev_alloc(stag_ctx* ctx, void** p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        ctx->last_err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+        *p = nullptr;
+        return STAG_ERR_ALLOC;
+    }
+    ctx->dev_bytes += bytes;
+    return STAG_OK;
+}
+
+stag_status ws_get(stag_ctx* ctx, int slot, size_t bytes, void** out) {
+    if (slot < 0 || slot >= WS_COUNT) return STAG_ERR_ARG;
+    if (ctx->ws_bytes[slot] < bytes) {
+        if (ctx->ws[slot]) {
+            // the old buffer may still be read by queued work
+            CK(cudaStreamSynchronize(ctx->stream));
+            CK(cudaFree(ctx->ws[slot]));
+            ctx->dev_bytes -= ctx->ws_bytes[slot];
+            ctx->ws[slot] = nullptr;
+            ctx->ws_bytes[slot] = 0;
+        }
+        void* p;
+        CKS(dev_alloc(ctx, &p, bytes));
+        ctx->ws[slot] = p;
+        ctx->ws_bytes[slot] = bytes;
+    }
+    *out = ctx->ws[slot];
+    return STAG_OK;
+}
+
+extern "C" const char* stag_strerror(stag_status s) {
+    switch (s) {
+        case STAG_OK: return "ok";
+        case STAG_ERR_ARG: return "invalid argument";
+        case STAG_ERR_ALLOC: return "allocation failed";
+        case STAG_ERR_CUDA: return "CUDA error";
+        case STAG_ERR_NOT_CONVERGED: return "solver did not converge";
+        case STAG_ERR_TIMEOUT: return "device wait timed out";
+        case STAG_ERR_NAN: return "NaN or Inf in a reduction";
+        case STAG_ERR_NO_GAUGE: return "no gauge field loaded";
+    }
+    return "unknown status";
+}
+
+extern "C" const char* stag_last_cuda_error(stag_ctx* ctx) { return ctx ? ctx->last_err.c_str() : ""; }
+
+extern "C" stag_status stag_set_stream(stag_ctx* ctx, void* s) {
+    if (!ctx) return STAG_ERR_ARG;
+    ctx->stream = (cudaStream_t)s;
+    return STAG_OK;
+}
+
+extern "C" size_t stag_device_bytes(stag_ctx* ctx) { return ctx ? ctx->dev_bytes : 0; }
+
+extern "C" void stag_destroy(stag_ctx* ctx) {
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    for (int i = 0; i < WS_COUNT; ++i)
+        if (ctx->ws[i]) cudaFree(ctx->ws[i]);
+    if (ctx->ghi) cudaFree(ctx->ghi);
+    if (ctx->glo) cudaFree(ctx->glo);
+    if (ctx->g16) cudaFree(ctx->g16);
+    if (ctx->red) cudaFree(ctx->red);
+    if (ctx->counters) cudaFree(ctx->counters);
+    if (ctx->scal) cudaFree(ctx->scal);
+    if (ctx->st) cudaFree(ctx->st);
+    if (ctx->scal_host) cudaFreeHost(ctx->scal_host);
+    if (ctx->st_host) cudaFreeHost(ctx->st_host);
+    delete ctx;
+}
+
+extern "C" stag_status stag_create(const stag_lattice* lat, stag_ctx** out) {
+    if (!lat || !out) return STAG_ERR_ARG;
+    *out = nullptr;
+    long long V = 1;
+    for (int mu = 0; mu < 4; ++mu) {
+        int L = lat->dims[mu];
+        if (L < 2 || (L & 1)) return STAG_ERR_ARG;
+        V *= L;
+    }
+    if (V > (1LL << 30)) return STAG_ERR_ARG;
+    stag_ctx* ctx = new (std::nothrow) stag_ctx();
+    if (!ctx) return STAG_ERR_ALLOC;
+    for (int mu = 0; mu < 4; ++mu) ctx->g.L[mu] = lat->dims[mu];
+    ctx->g.Lxh = lat->dims[0] / 2;
+    ctx->g.V = (int)V;
+    ctx->g.Vh = (int)(V / 2);
+    ctx->g.apt = lat->t_antiperiodic ? 1 : 0;
+    ctx->stream = (cudaStream_t)lat->cuda_stream;
+    stag_status s = STAG_OK;
+    size_t gbytes = (size_t)4 * 2 * 18 * ctx->g.Vh * sizeof(float);
+    size_t bbytes = (size_t)4 * 2 * 12 * ctx->g.Vh * sizeof(uint16_t);
+    if ((s = dev_alloc(ctx, (void**)&ctx->ghi, gbytes)) != STAG_OK ||
+        (s = dev_alloc(ctx, (void**)&ctx->glo, gbytes)) != STAG_OK ||
+        (s = dev_alloc(ctx, (void**)&ctx->g16, bbytes)) != STAG_OK ||
+        (s = dev_alloc(ctx, (void**)&ctx->red, sizeof(double) * STAG_MAX_RED_BLOCKS * 4)) != STAG_OK ||
+        (s = dev_alloc(ctx, (void**)&ctx->counters, sizeof(unsigned int) * 16)) != STAG_OK ||
+        (s = dev_alloc(ctx, (void**)&ctx->scal, sizeof(double) * 64)) != STAG_OK ||
+        (s = dev_alloc(ctx, (void**)&ctx->st, sizeof(SolverState))) != STAG_OK) {
+        stag_destroy(ctx);
+        return s;
+    }
+    if (cudaMallocHost((void**)&ctx->scal_host, sizeof(double) * 64) != cudaSuccess ||
+        cudaMallocHost((void**)&ctx->st_host, sizeof(SolverState)) != cudaSuccess) {
+        cudaGetLastError();
+        stag_destroy(ctx);
+        return STAG_ERR_ALLOC;
+    }
+    if (cudaMemsetAsync(ctx->counters, 0, sizeof(unsigned int) * 16, ctx->stream) != cudaSuccess ||
+        cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+        cudaGetLastError();
+        stag_destroy(ctx);
+        return STAG_ERR_CUDA;
+    }
+    *out = ctx;
+    return STAG_OK;
+}

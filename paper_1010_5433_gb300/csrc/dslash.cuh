@@ -1,0 +1,134 @@
+// The staggered Dslash kernel template (Sec. 2, Sec. 3, Sec. 5 / Table 2).
+//
+// One thread per output site and chunk of NR right-hand sides.  Each of the
+// eight links of the site is loaded once (coalesced, structure of arrays) and
+// applied to all NR sources before the next link is fetched, so the link
+// traffic is shared by the right-hand sides.  What happens to the result
+// (plain store, A-operator epilogue, reductions) is supplied by an Epi functor.
+#pragma once
+#include "common.cuh"
+
+enum LinkFmt { FMT_F64 = 0, FMT_F32_18 = 1, FMT_F32_12 = 2, FMT_BF16_12 = 3 };
+
+struct LinkPtrs {
+    const float* hi;
+    const float* lo;
+    const uint16_t* b16;
+};
+
+template <typename R, int FMT> struct LinkFetch;
+template <> struct LinkFetch<double, FMT_F64> {
+    __device__ __forceinline__ static Su3<double> get(const LinkPtrs& L, int mu, int par, int h, int Vh) {
+        return load_link_d(L.hi, L.lo, link_block_f(mu, par, Vh), h, Vh);
+    }
+};
+template <> struct LinkFetch<float, FMT_F32_18> {
+    __device__ __forceinline__ static Su3<float> get(const LinkPtrs& L, int mu, int par, int h, int Vh) {
+        return load_link_f<3>(L.hi + link_block_f(mu, par, Vh), h, Vh);
+    }
+};
+template <> struct LinkFetch<float, FMT_F32_12> {
+    __device__ __forceinline__ static Su3<float> get(const LinkPtrs& L, int mu, int par, int h, int Vh) {
+        return load_link_f<2>(L.hi + link_block_f(mu, par, Vh), h, Vh);
+    }
+};
+template <> struct LinkFetch<float, FMT_BF16_12> {
+    __device__ __forceinline__ static Su3<float> get(const LinkPtrs& L, int mu, int par, int h, int Vh) {
+        return load_link_bf(L.b16 + link_block_b(mu, par, Vh), h, Vh);
+    }
+};
+
+// Accumulate sum_mu [ sf U_mu(x) in(x+mu) - sb U_mu(x-mu)^dag in(x-mu) ] for NR sources
+// (the factor 1/2 is left to the epilogue).
+template <typename R, int FMT, int NR>
+__device__ __forceinline__ void dslash_site(const Geom& g, int out_par, const LinkPtrs& L,
+                                            const typename V2T<R>::T* __restrict__ in, int r0, int nrhs,
+                                            int h, Vec3<R> (&acc)[NR]) {
+    Nbr n;
+    site_neighbours(g, h, out_par, n);
+    const size_t rs = (size_t)3 * g.Vh;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) zero(acc[r]);
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+        Su3<R> u = LinkFetch<R, FMT>::get(L, mu, out_par, h, g.Vh);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            if (r0 + r < nrhs) {
+                Vec3<R> v = load_vec<R>(in + (size_t)(r0 + r) * rs, n.fwd[mu], g.Vh);
+                mac_uv(acc[r], (R)n.sf[mu], u, v);
+            }
+        }
+        Su3<R> w = LinkFetch<R, FMT>::get(L, mu, 1 - out_par, n.bwd[mu], g.Vh);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            if (r0 + r < nrhs) {
+                Vec3<R> v = load_vec<R>(in + (size_t)(r0 + r) * rs, n.bwd[mu], g.Vh);
+                mac_udv(acc[r], -(R)n.sb[mu], w, v);
+            }
+        }
+    }
+}
+
+// Grid: blockIdx.x = site_block * nchunk + chunk, so that the chunks of one
+// site block run back to back and re-read its links from L2.
+template <typename R, int FMT, int NR, class Epi>
+__global__ void __launch_bounds__(STAG_RED_BLOCK)
+k_dslash(Geom g, int out_par, LinkPtrs L, const typename V2T<R>::T* __restrict__ in, int nrhs, int nchunk, Epi epi) {
+    if (epi.halted()) return;
+    const int chunk = blockIdx.x % nchunk;
+    const int sblock = blockIdx.x / nchunk;
+    const int h = sblock * blockDim.x + threadIdx.x;
+    const int r0 = chunk * NR;
+    Vec3<R> acc[NR];
+    const bool valid = h < g.Vh;
+    if (valid) dslash_site<R, FMT, NR>(g, out_par, L, in, r0, nrhs, h, acc);
+    epi.template finish<NR>(g, h, valid, r0, nrhs, acc);
+}
+
+// Plain epilogue: out = scale * acc  (scale = 1/2 for D itself).
+template <typename R> struct EpiStore {
+    typename V2T<R>::T* out;
+    R scale;
+    __device__ __forceinline__ bool halted() const { return false; }
+    template <int NR>
+    __device__ __forceinline__ void finish(const Geom& g, int h, bool valid, int r0, int nrhs, Vec3<R> (&acc)[NR]) {
+        if (!valid) return;
+        const size_t rs = (size_t)3 * g.Vh;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            if (r0 + r >= nrhs) continue;
+            Vec3<R> o;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) o.c[c] = scale * acc[r].c[c];
+            store_vec<R>(out + (size_t)(r0 + r) * rs, h, g.Vh, o);
+        }
+    }
+};
+
+// A-operator epilogue: out = c0 * aux - 1/2 acc (aux on the output parity).
+template <typename R> struct EpiAop {
+    typename V2T<R>::T* out;
+    const typename V2T<R>::T* aux;
+    R c0;
+    __device__ __forceinline__ bool halted() const { return false; }
+    template <int NR>
+    __device__ __forceinline__ void finish(const Geom& g, int h, bool valid, int r0, int nrhs, Vec3<R> (&acc)[NR]) {
+        if (!valid) return;
+        const size_t rs = (size_t)3 * g.Vh;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            if (r0 + r >= nrhs) continue;
+            Vec3<R> a = load_vec<R>(aux + (size_t)(r0 + r) * rs, h, g.Vh);
+            Vec3<R> o;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                o.c[c].re = c0 * a.c[c].re - (R)0.5 * acc[r].c[c].re;
+                o.c[c].im = c0 * a.c[c].im - (R)0.5 * acc[r].c[c].im;
+            }
+            store_vec<R>(out + (size_t)(r0 + r) * rs, h, g.Vh, o);
+        }
+    }
+};
+
+inline int dslash_nr_for(int nrhs) { return nrhs >= 4 ? 4 : (nrhs >= 2 ? 2 : 1); }

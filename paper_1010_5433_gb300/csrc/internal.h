@@ -1,0 +1,105 @@
+// Host-side context and the launchers each translation unit provides.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "dslash.cuh"
+
+// Device state of one multi-shift solve (see solver.cu).
+struct SolverState;
+
+enum WsSlot {
+    WS_STAGE = 0,      // host-layout gauge staging (load/store)
+    WS_TMP_ODD,        // D_oe p (odd), solver
+    WS_R, WS_P, WS_Q, WS_PS,   // solver vectors (real type of the solve)
+    WS_B64, WS_X64, WS_R64, WS_T64, WS_U64,  // fp64 vectors for reliable updates
+    WS_APPLY_TMP,      // stag_apply_a scratch
+    WS_FORCE_X, WS_FORCE_Y,    // fermion force: solutions and D_oe solutions
+    WS_PHI, WS_XI, WS_HB,      // trajectory: pseudo-fermions, sources, heatbath output
+    WS_FORCE,          // trajectory: force accumulator
+    WS_SAVE_HI, WS_SAVE_LO,    // saved gauge field for Metropolis rejection
+    WS_MOM,            // momenta
+    WS_MISC,
+    WS_COUNT
+};
+
+struct stag_ctx {
+    Geom g;
+    cudaStream_t stream = nullptr;
+    float* ghi = nullptr;
+    float* glo = nullptr;
+    uint16_t* g16 = nullptr;
+    bool has_gauge = false;
+    bool b16_stale = true;
+    // reductions
+    double* red = nullptr;            // partials, STAG_MAX_RED_BLOCKS * STAG_MAX_RHS * 4
+    unsigned int* counters = nullptr; // 16 counters, zero between launches
+    double* scal = nullptr;           // small device scalar area (64 doubles)
+    double* scal_host = nullptr;      // pinned mirror
+    SolverState* st = nullptr;        // device
+    SolverState* st_host = nullptr;   // pinned
+    // workspace
+    void* ws[WS_COUNT] = {};
+    size_t ws_bytes[WS_COUNT] = {};
+    std::string last_err;
+    size_t dev_bytes = 0;
+};
+
+// error plumbing
+stag_status cuda_fail(stag_ctx* c, cudaError_t e, const char* where);
+#define CK(call)                                                        \
+    do {                                                                \
+        cudaError_t _e = (call);                                        \
+        if (_e != cudaSuccess) return cuda_fail(ctx, _e, #call);        \
+    } while (0)
+#define CKS(call)                                                       \
+    do {                                                                \
+        stag_status _s = (call);                                        \
+        if (_s != STAG_OK) return _s;                                   \
+    } while (0)
+
+stag_status ws_get(stag_ctx* ctx, int slot, size_t bytes, void** out);
+stag_status dev_alloc(stag_ctx* ctx, void** p, size_t bytes);
+
+inline LinkPtrs link_ptrs(const stag_ctx* c) { return LinkPtrs{c->ghi, c->glo, c->g16}; }
+inline int nblocks(long long n, int bs) { return (int)((n + bs - 1) / bs); }
+
+// gauge.cu
+stag_status refresh_bf16(stag_ctx* ctx);
+stag_status gauge_copy(stag_ctx* ctx, float* dst_hi, float* dst_lo, const float* src_hi, const float* src_lo);
+
+// dslash.cu: out = scale * D_{out_par} in  (no reductions)
+stag_status launch_dslash(stag_ctx* ctx, int out_par, stag_prec prec, int nrhs, const void* in, void* out,
+                          double scale);
+// out = c0 * aux - 1/2 D_eo tmp  with tmp = D_oe in  computed into ws
+stag_status launch_apply_a(stag_ctx* ctx, double c0, stag_prec prec, int nrhs, const void* in, void* out,
+                           void* tmp_odd);
+
+// solver.cu
+stag_status multishift(stag_ctx* ctx, double mass, int nshift, const double* shifts, stag_prec prec, int nrhs,
+                       const void* b, void* x, double tol, int max_iter, stag_solve_info* info,
+                       bool want_true_residual);
+
+// force.cu
+stag_status fermion_force_from_solutions(stag_ctx* ctx, stag_prec prec, int n_pf, int nshift, const double* alpha,
+                                         const void* x, double* force, double coef, int accumulate);
+stag_status gauge_force_launch(stag_ctx* ctx, double beta, double* force, double coef, int accumulate);
+stag_status update_links(stag_ctx* ctx, const double* mom, double eps, stag_prec prec);
+stag_status reunitarize(stag_ctx* ctx);
+stag_status plaquette_sum(stag_ctx* ctx, double* out_host);
+stag_status kinetic_sum(stag_ctx* ctx, const double* mom, double* out_host);
+stag_status mom_axpy(stag_ctx* ctx, double* mom, const double* f, double c);
+stag_status draw_momenta(stag_ctx* ctx, double* mom, unsigned long long seed, unsigned long long counter);
+stag_status draw_sources(stag_ctx* ctx, double2* xi, int n, unsigned long long seed, unsigned long long counter,
+                         int stream_base);
+
+// blas.cu
+stag_status blas_norm2(stag_ctx* ctx, stag_prec prec, int nrhs, const void* v, double* out_host);
+stag_status blas_dot_re(stag_ctx* ctx, int nrhs, const double2* a, const double2* b, double* out_host);
+stag_status blas_combine(stag_ctx* ctx, int n, double a0, const double2* phi, int nshift, const double* alpha,
+                         const double2* x, double2* out);
+stag_status blas_convert(stag_ctx* ctx, size_t ncomplex, const void* src, int src_double, void* dst, int dst_double);

@@ -1,0 +1,640 @@
+// Multi-shift CG (Sec. 6 of the paper; B. Jegerlehner, hep-lat/9612014) for
+//   (A + sigma_i) x_i = b,   A = m^2 - D_eo D_oe,
+// with nrhs independent sources iterated together, so every Dslash is a
+// multi-RHS Dslash that loads each link once for all of them.
+//
+// One iteration is four kernels:
+//   K1  t  = D_oe p                                     (multi-RHS Dslash)
+//   K2  q  = (m^2 + sigma_0) p - D_eo t,  (p, q)        (multi-RHS Dslash, A epilogue)
+//       last block: alpha = (r,r)/(p,q), zeta_{k+1}, alpha_i for every live shift
+//   K3  r -= alpha q,  (r, r)
+//       last block: beta, beta_i, shift convergence, loop control
+//   K4  x_i += alpha_i p_i;  p_i = zeta_{k+1} r + beta_i p_i;  p = r + beta p
+// All sums are fp64 in a fixed order; the scalar recurrences run on the device,
+// so the host only polls a halt flag every chunk of iterations.
+//
+// Mixed precision (fp32 or bf16 Dslash, fp32 vectors): the recursive residual of
+// the base system is replaced by the true one, b - (A + sigma_0) x_0 computed
+// with the fp64 operator, whenever it fell by delta since the last replacement
+// (reliable updates, van der Vorst & Ye; Clark et al. 2010).  x_0 is then
+// accumulated in fp64.  The paper argues that a shifted solver cannot restart
+// (Sec. 6); replacing the base residual keeps the shifted residuals collinear
+// only approximately, which is why every shift's true residual is reported.
+#include <cmath>
+#include <cstring>
+
+#include "internal.h"
+#include "solver_state.cuh"
+
+namespace {
+
+constexpr int VB = 256;   // block of the vector kernels
+
+// ---------------------------------------------------------------- init
+template <typename R>
+__global__ void k_ms_init(SolverState* st, int Vh, const typename V2T<R>::T* __restrict__ b,
+                          typename V2T<R>::T* r, typename V2T<R>::T* p, typename V2T<R>::T* ps,
+                          typename V2T<R>::T* x, double* partial, unsigned int* counter) {
+    const int rhs = blockIdx.y;
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    const int ns = st->nshift;
+    const size_t rs = (size_t)3 * Vh;
+    double v[1] = {0.0};
+    if (h < Vh) {
+        Vec3<R> bv = load_vec<R>(b + rhs * rs, h, Vh);
+        store_vec<R>(r + rhs * rs, h, Vh, bv);
+        store_vec<R>(p + rhs * rs, h, Vh, bv);
+        Vec3<R> z;
+        zero(z);
+        for (int s = 0; s < ns; ++s) {
+            store_vec<R>(ps + ((size_t)rhs * ns + s) * rs, h, Vh, bv);
+            store_vec<R>(x + ((size_t)rhs * ns + s) * rs, h, Vh, z);
+        }
+        v[0] = norm2(bv);
+    }
+    block_sum<1>(v);
+    if (threadIdx.x == 0) partial[(size_t)rhs * gridDim.x + blockIdx.x] = v[0];
+    if (elect_last_block(counter, gridDim.x * gridDim.y)) {
+        __shared__ double sums[STAG_MAX_RHS];
+        for (int q = 0; q < st->nrhs; ++q) {
+            double s = block_sum_array(partial + (size_t)q * gridDim.x, gridDim.x);
+            if (threadIdx.x == 0) sums[q] = s;
+        }
+        if (threadIdx.x == 0) {
+            st->k = 0;
+            st->halt = 0;
+            st->k4_skip = 0;
+            st->status = STAG_OK;
+            st->need_reliable = 0;
+            st->n_reliable = 0;
+            int any = 0;
+            for (int q = 0; q < st->nrhs; ++q) {
+                double bb = sums[q];
+                st->bb[q] = bb;
+                st->rr[q] = bb;
+                st->rr_ref[q] = bb;
+                st->alpha_prev[q] = 1.0;
+                st->beta_prev[q] = 0.0;
+                st->beta[q] = 0.0;
+                int live = (bb > 0.0) && isfinite(bb);
+                if (!isfinite(bb)) st->status = STAG_ERR_NAN;
+                st->rhs_live[q] = live;
+                any |= live;
+                for (int s = 0; s < st->nshift; ++s) {
+                    st->zeta[q][s] = 1.0;
+                    st->zeta_prev[q][s] = 1.0;
+                    st->zeta_next[q][s] = 1.0;
+                    st->live[q][s] = live;
+                    st->active[q][s] = 0;
+                    st->iters_at[q][s] = 0;
+                }
+            }
+            if (!any) st->halt = 1;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- K1 / K2 epilogues
+template <typename R> struct EpiMsOdd {     // K1: t = D_oe p (without the 1/2)
+    typename V2T<R>::T* out;
+    SolverState* st;
+    __device__ __forceinline__ bool halted() const {
+        if (*(volatile int*)&st->halt) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) st->k4_skip = 1;
+            return true;
+        }
+        return false;
+    }
+    template <int NR>
+    __device__ __forceinline__ void finish(const Geom& g, int h, bool valid, int r0, int nrhs, Vec3<R> (&acc)[NR]) {
+        if (!valid) return;
+        const size_t rs = (size_t)3 * g.Vh;
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+            if (r0 + r < nrhs) store_vec<R>(out + (size_t)(r0 + r) * rs, h, g.Vh, acc[r]);
+    }
+};
+
+// The scalar step after (p, A p) is known: alpha and the shifted zeta recurrence.
+__device__ void ms_alpha_step(SolverState* st, const double* pap) {
+    for (int q = 0; q < st->nrhs; ++q) {
+        if (!st->rhs_live[q]) continue;
+        double alpha = st->rr[q] / pap[q];
+        if (!isfinite(alpha) || pap[q] <= 0.0) {
+            st->status = STAG_ERR_NAN;
+            st->halt = 1;
+            alpha = 0.0;
+        }
+        st->alpha[q] = alpha;
+        const double ap = st->alpha_prev[q], bp = st->beta_prev[q];
+        for (int s = 0; s < st->nshift; ++s) {
+            if (!st->live[q][s]) { st->cx[q][s] = 0.0; continue; }
+            const double z = st->zeta[q][s], zp = st->zeta_prev[q][s];
+            const double den = alpha * bp * (zp - z) + zp * ap * (1.0 + st->dsig[s] * alpha);
+            const double zn = z * zp * ap / den;
+            st->zeta_next[q][s] = zn;
+            st->cx[q][s] = alpha * zn / z;
+        }
+    }
+}
+
+template <typename R> struct EpiMsA {       // K2: q = c0 p - 1/2 (D_eo t) (t holds 2 D_oe p)
+    typename V2T<R>::T* q;
+    const typename V2T<R>::T* p;
+    SolverState* st;
+    double* partial;
+    unsigned int* counter;
+    __device__ __forceinline__ bool halted() const { return *(volatile int*)&st->halt != 0; }
+    template <int NR>
+    __device__ __forceinline__ void finish(const Geom& g, int h, bool valid, int r0, int nrhs, Vec3<R> (&acc)[NR]) {
+        const size_t rs = (size_t)3 * g.Vh;
+        const R c0 = (R)st->c0;
+        double d[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            d[r] = 0.0;
+            if (valid && r0 + r < nrhs) {
+                Vec3<R> pv = load_vec_cg<R>(p + (size_t)(r0 + r) * rs, h, g.Vh);
+                Vec3<R> o;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    // t = 2 D_oe p, so D_eo D_oe p = 1/4 (sum of hops of t)
+                    o.c[c].re = c0 * pv.c[c].re - (R)0.25 * acc[r].c[c].re;
+                    o.c[c].im = c0 * pv.c[c].im - (R)0.25 * acc[r].c[c].im;
+                }
+                store_vec<R>(q + (size_t)(r0 + r) * rs, h, g.Vh, o);
+                d[r] = re_dot(pv, o);
+            }
+        }
+        block_sum<NR>(d);
+        const int nchunk = (nrhs + NR - 1) / NR;
+        const int sblock = blockIdx.x / nchunk, nsb = gridDim.x / nchunk;
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int r = 0; r < NR; ++r)
+                if (r0 + r < nrhs) partial[(size_t)(r0 + r) * nsb + sblock] = d[r];
+        }
+        if (elect_last_block(counter, gridDim.x)) {
+            __shared__ double sums[STAG_MAX_RHS];
+            for (int r = 0; r < nrhs; ++r) {
+                double s = block_sum_array(partial + (size_t)r * nsb, nsb);
+                if (threadIdx.x == 0) sums[r] = s;
+            }
+            if (threadIdx.x == 0) ms_alpha_step(st, sums);
+        }
+    }
+};
+
+// ---------------------------------------------------------------- K3
+__device__ void ms_beta_step(SolverState* st, const double* rrn) {
+    int any_live = 0;
+    for (int q = 0; q < st->nrhs; ++q) {
+        if (!st->rhs_live[q]) {
+            for (int s = 0; s < st->nshift; ++s) st->active[q][s] = 0;
+            continue;
+        }
+        const double rr_new = rrn[q];
+        if (!isfinite(rr_new)) {
+            st->status = STAG_ERR_NAN;
+            st->halt = 1;
+        }
+        const double beta = rr_new / st->rr[q];
+        int live_left = 0;
+        for (int s = 0; s < st->nshift; ++s) {
+            if (!st->live[q][s]) { st->active[q][s] = 0; continue; }
+            const double zn = st->zeta_next[q][s], z = st->zeta[q][s];
+            const double zr = zn / z;
+            st->active[q][s] = 1;
+            st->cpr[q][s] = zn;
+            st->cpp[q][s] = beta * zr * zr;
+            st->zeta_prev[q][s] = z;
+            st->zeta[q][s] = zn;
+            if (zn * zn * rr_new <= st->tol2 * st->bb[q]) {
+                st->live[q][s] = 0;
+                st->iters_at[q][s] = st->k + 1;
+            } else {
+                live_left = 1;
+            }
+        }
+        st->beta[q] = beta;
+        st->alpha_prev[q] = st->alpha[q];
+        st->beta_prev[q] = beta;
+        st->rr[q] = rr_new;
+        if (!live_left) st->rhs_live[q] = 0;
+        any_live |= live_left;
+        if (live_left && st->mixed && rr_new < st->delta2 * st->rr_ref[q]) st->need_reliable = 1;
+    }
+    st->k += 1;
+    if (!any_live) st->halt = 1;
+    else if (st->k >= st->max_iter) { st->halt = 1; st->status = STAG_ERR_NOT_CONVERGED; }
+    if (st->need_reliable) st->halt = 1;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(VB) k_ms_rupdate(SolverState* st, int Vh, typename V2T<R>::T* r,
+                                                   const typename V2T<R>::T* __restrict__ q, double* partial,
+                                                   unsigned int* counter) {
+    if (*(volatile int*)&st->halt) return;
+    const int rhs = blockIdx.y;
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t rs = (size_t)3 * Vh;
+    double v[1] = {0.0};
+    if (st->rhs_live[rhs] && h < Vh) {
+        const R a = (R)st->alpha[rhs];
+        Vec3<R> rv = load_vec_cg<R>(r + rhs * rs, h, Vh);
+        Vec3<R> qv = load_vec_cg<R>(q + rhs * rs, h, Vh);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            rv.c[c].re -= a * qv.c[c].re;
+            rv.c[c].im -= a * qv.c[c].im;
+        }
+        store_vec<R>(r + rhs * rs, h, Vh, rv);
+        v[0] = norm2(rv);
+    }
+    block_sum<1>(v);
+    if (threadIdx.x == 0) partial[(size_t)rhs * gridDim.x + blockIdx.x] = v[0];
+    if (elect_last_block(counter, gridDim.x * gridDim.y)) {
+        __shared__ double sums[STAG_MAX_RHS];
+        for (int q2 = 0; q2 < st->nrhs; ++q2) {
+            double s = block_sum_array(partial + (size_t)q2 * gridDim.x, gridDim.x);
+            if (threadIdx.x == 0) sums[q2] = s;
+        }
+        if (threadIdx.x == 0) ms_beta_step(st, sums);
+    }
+}
+
+// ---------------------------------------------------------------- K4
+template <typename R>
+__global__ void __launch_bounds__(VB) k_ms_shift_update(SolverState* st, int Vh, const typename V2T<R>::T* r,
+                                                        typename V2T<R>::T* p, typename V2T<R>::T* ps,
+                                                        typename V2T<R>::T* x) {
+    if (*(volatile int*)&st->k4_skip) return;
+    const int rhs = blockIdx.y;
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= Vh) return;
+    const int ns = st->nshift;
+    const size_t rs = (size_t)3 * Vh;
+    Vec3<R> rv = load_vec_cg<R>(r + rhs * rs, h, Vh);
+    bool any = false;
+    for (int s = 0; s < ns; ++s) {
+        if (!st->active[rhs][s]) continue;
+        any = true;
+        const R cx = (R)st->cx[rhs][s], cpr = (R)st->cpr[rhs][s], cpp = (R)st->cpp[rhs][s];
+        typename V2T<R>::T* pp = ps + ((size_t)rhs * ns + s) * rs;
+        typename V2T<R>::T* xp = x + ((size_t)rhs * ns + s) * rs;
+        Vec3<R> pv = load_vec_cg<R>(pp, h, Vh);
+        Vec3<R> xv = load_vec_cg<R>(xp, h, Vh);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            xv.c[c].re += cx * pv.c[c].re;
+            xv.c[c].im += cx * pv.c[c].im;
+            pv.c[c].re = cpr * rv.c[c].re + cpp * pv.c[c].re;
+            pv.c[c].im = cpr * rv.c[c].im + cpp * pv.c[c].im;
+        }
+        store_vec<R>(xp, h, Vh, xv);
+        store_vec<R>(pp, h, Vh, pv);
+    }
+    if (any) {
+        const R beta = (R)st->beta[rhs];
+        Vec3<R> pv = load_vec_cg<R>(p + rhs * rs, h, Vh);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            pv.c[c].re = rv.c[c].re + beta * pv.c[c].re;
+            pv.c[c].im = rv.c[c].im + beta * pv.c[c].im;
+        }
+        store_vec<R>(p + rhs * rs, h, Vh, pv);
+    }
+}
+
+// ---------------------------------------------------------------- reliable update kernels
+// x64 += x_base (fp32), x_base = 0 for every rhs still iterating
+__global__ void k_rel_accumulate(const SolverState* st, int Vh, double2* x64, float2* x) {
+    const int rhs = blockIdx.y;
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= Vh || !st->rhs_live[rhs]) return;
+    const size_t rs = (size_t)3 * Vh;
+    float2* xb = x + ((size_t)rhs * st->nshift + st->base) * rs;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        size_t i = rhs * rs + (size_t)c * Vh + h;
+        float2 a = xb[(size_t)c * Vh + h];
+        double2 d = x64[i];
+        d.x += (double)a.x;
+        d.y += (double)a.y;
+        x64[i] = d;
+        xb[(size_t)c * Vh + h] = make_float2(0.f, 0.f);
+    }
+}
+
+// r = b - Ax (fp64), stored in fp32; new rr / rr_ref for the rhs still iterating
+__global__ void __launch_bounds__(VB) k_rel_finish(SolverState* st, int Vh, const double2* __restrict__ b64,
+                                                   const double2* __restrict__ ax, float2* r, double* partial,
+                                                   unsigned int* counter) {
+    const int rhs = blockIdx.y;
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t rs = (size_t)3 * Vh;
+    double v[1] = {0.0};
+    if (h < Vh && st->rhs_live[rhs]) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            size_t i = rhs * rs + (size_t)c * Vh + h;
+            double2 bb = b64[i], a = ax[i];
+            double re = bb.x - a.x, im = bb.y - a.y;
+            r[i] = make_float2((float)re, (float)im);
+            v[0] += re * re + im * im;
+        }
+    }
+    block_sum<1>(v);
+    if (threadIdx.x == 0) partial[(size_t)rhs * gridDim.x + blockIdx.x] = v[0];
+    if (elect_last_block(counter, gridDim.x * gridDim.y)) {
+        __shared__ double sums[STAG_MAX_RHS];
+        for (int q = 0; q < st->nrhs; ++q) {
+            double s = block_sum_array(partial + (size_t)q * gridDim.x, gridDim.x);
+            if (threadIdx.x == 0) sums[q] = s;
+        }
+        if (threadIdx.x == 0) {
+            for (int q = 0; q < st->nrhs; ++q) {
+                if (!st->rhs_live[q]) continue;
+                st->rr[q] = sums[q];
+                st->rr_ref[q] = sums[q];
+                if (!isfinite(sums[q])) st->status = STAG_ERR_NAN;
+            }
+            st->need_reliable = 0;
+            st->n_reliable += 1;
+        }
+    }
+}
+
+// x_base = (float)(x64 + x_base) at the end of a mixed solve
+__global__ void k_rel_output(const SolverState* st, int Vh, const double2* x64, float2* x) {
+    const int rhs = blockIdx.y;
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= Vh) return;
+    const size_t rs = (size_t)3 * Vh;
+    float2* xb = x + ((size_t)rhs * st->nshift + st->base) * rs;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float2 a = xb[(size_t)c * Vh + h];
+        double2 d = x64[rhs * rs + (size_t)c * Vh + h];
+        xb[(size_t)c * Vh + h] = make_float2((float)(d.x + (double)a.x), (float)(d.y + (double)a.y));
+    }
+}
+
+__global__ void k_f2d(size_t n, const float2* a, double2* b) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = make_double2((double)a[i].x, (double)a[i].y);
+}
+
+// |b - (A + s) x|^2 per rhs, fp64, with ax = A x (c0 = m^2 already applied), x fp64
+__global__ void __launch_bounds__(VB) k_true_res(int Vh, double shift, const double2* __restrict__ b,
+                                                 const double2* __restrict__ ax, const double2* __restrict__ x,
+                                                 double* partial) {
+    const int rhs = blockIdx.y;
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t rs = (size_t)3 * Vh;
+    double v[2] = {0.0, 0.0};
+    if (h < Vh) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            size_t i = rhs * rs + (size_t)c * Vh + h;
+            double re = b[i].x - ax[i].x - shift * x[i].x;
+            double im = b[i].y - ax[i].y - shift * x[i].y;
+            v[0] += re * re + im * im;
+            v[1] += b[i].x * b[i].x + b[i].y * b[i].y;
+        }
+    }
+    block_sum<2>(v);
+    if (threadIdx.x == 0) {
+        partial[(size_t)(2 * rhs) * gridDim.x + blockIdx.x] = v[0];
+        partial[(size_t)(2 * rhs + 1) * gridDim.x + blockIdx.x] = v[1];
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host driver
+template <typename R>
+static stag_status ms_iterations(stag_ctx* ctx, stag_prec prec, int nrhs, int chunk, void* tmp, void* r, void* p,
+                                 void* q, void* ps, void* x) {
+    typedef typename V2T<R>::T V;
+    const Geom& g = ctx->g;
+    const int bs = 128;
+    int nr = dslash_nr_for(nrhs);
+    int nchunk = (nrhs + nr - 1) / nr;
+    int grid_d = nblocks(g.Vh, bs) * nchunk;
+    dim3 grid_v(nblocks(g.Vh, VB), nrhs);
+    LinkPtrs L = link_ptrs(ctx);
+    EpiMsOdd<R> e1{(V*)tmp, ctx->st};
+    EpiMsA<R> e2{(V*)q, (const V*)p, ctx->st, ctx->red, ctx->counters + 0};
+    for (int it = 0; it < chunk; ++it) {
+#define MS_LAUNCH(FMT_, NR_)                                                                                         \
+    k_dslash<R, FMT_, NR_, EpiMsOdd<R>><<<grid_d, bs, 0, ctx->stream>>>(g, 1, L, (const V*)p, nrhs, nchunk, e1);     \
+    k_dslash<R, FMT_, NR_, EpiMsA<R>><<<grid_d, bs, 0, ctx->stream>>>(g, 0, L, (const V*)tmp, nrhs, nchunk, e2);
+#define MS_FMT(FMT_)                         \
+    switch (nr) {                            \
+        case 4: MS_LAUNCH(FMT_, 4) break;    \
+        case 2: MS_LAUNCH(FMT_, 2) break;    \
+        default: MS_LAUNCH(FMT_, 1) break;   \
+    }
+        if constexpr (sizeof(R) == 8) {
+            MS_FMT(FMT_F64)
+        } else {
+            if (prec == STAG_FP32) { MS_FMT(FMT_F32_18) }
+            else if (prec == STAG_FP32_12) { MS_FMT(FMT_F32_12) }
+            else { MS_FMT(FMT_BF16_12) }
+        }
+#undef MS_FMT
+#undef MS_LAUNCH
+        k_ms_rupdate<R><<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, (V*)r, (const V*)q, ctx->red,
+                                                        ctx->counters + 1);
+        k_ms_shift_update<R><<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, (const V*)r, (V*)p, (V*)ps, (V*)x);
+    }
+    CK(cudaGetLastError());
+    return STAG_OK;
+}
+
+static size_t rsize(stag_prec p) { return p == STAG_FP64 ? sizeof(double) : sizeof(float); }
+
+// Reads the loop-control words of the device state into the pinned mirror.
+static stag_status pull_control(stag_ctx* ctx) {
+    CK(cudaMemcpyAsync(ctx->st_host, ctx->st, sizeof(SolverState), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return STAG_OK;
+}
+
+static stag_status ms_batch(stag_ctx* ctx, double mass, int nshift, const double* shifts, int base, stag_prec prec,
+                            int nrhs, const void* b, void* x, double tol, int max_iter, stag_solve_info* info,
+                            bool want_true_residual) {
+    const Geom& g = ctx->g;
+    const bool mixed = prec != STAG_FP64;
+    const size_t rsz = rsize(prec);
+    const size_t vbytes = (size_t)nrhs * 3 * g.Vh * 2 * rsz;
+    void *tmp, *r, *p, *q, *ps;
+    CKS(ws_get(ctx, WS_TMP_ODD, vbytes, &tmp));
+    CKS(ws_get(ctx, WS_R, vbytes, &r));
+    CKS(ws_get(ctx, WS_P, vbytes, &p));
+    CKS(ws_get(ctx, WS_Q, vbytes, &q));
+    CKS(ws_get(ctx, WS_PS, vbytes * nshift, &ps));
+    const size_t v64 = (size_t)nrhs * 3 * g.Vh * sizeof(double2);
+    void *b64 = nullptr, *x64 = nullptr, *ax64 = nullptr, *t64 = nullptr;
+    if (mixed) {
+        CKS(ws_get(ctx, WS_B64, v64, &b64));
+        CKS(ws_get(ctx, WS_X64, v64, &x64));
+        CKS(ws_get(ctx, WS_R64, v64, &ax64));
+        CKS(ws_get(ctx, WS_T64, v64, &t64));
+        size_t n = (size_t)nrhs * 3 * g.Vh;
+        k_f2d<<<nblocks((long long)n, 256), 256, 0, ctx->stream>>>(n, (const float2*)b, (double2*)b64);
+        CK(cudaMemsetAsync(x64, 0, v64, ctx->stream));
+    }
+    // host part of the state
+    SolverState* hs = ctx->st_host;
+    std::memset(hs, 0, sizeof(SolverState));
+    hs->nrhs = nrhs;
+    hs->nshift = nshift;
+    hs->base = base;
+    hs->max_iter = max_iter;
+    hs->mixed = mixed ? 1 : 0;
+    hs->tol2 = tol * tol;
+    hs->c0 = mass * mass + shifts[base];
+    hs->delta2 = 0.01;   // replace the residual after every factor 10 in ||r||
+    for (int s = 0; s < nshift; ++s) hs->dsig[s] = shifts[s] - shifts[base];
+    CK(cudaMemcpyAsync(ctx->st, hs, sizeof(SolverState), cudaMemcpyHostToDevice, ctx->stream));
+    dim3 grid_v(nblocks(g.Vh, VB), nrhs);
+    if (mixed)
+        k_ms_init<float><<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, (const float2*)b, (float2*)r, (float2*)p,
+                                                         (float2*)ps, (float2*)x, ctx->red, ctx->counters + 2);
+    else
+        k_ms_init<double><<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, (const double2*)b, (double2*)r,
+                                                          (double2*)p, (double2*)ps, (double2*)x, ctx->red,
+                                                          ctx->counters + 2);
+    CK(cudaGetLastError());
+    const int chunk = 16;
+    stag_status status = STAG_OK;
+    for (int guard = 0; guard < 1000000; ++guard) {
+        if (mixed) CKS(ms_iterations<float>(ctx, prec, nrhs, chunk, tmp, r, p, q, ps, x));
+        else CKS(ms_iterations<double>(ctx, prec, nrhs, chunk, tmp, r, p, q, ps, x));
+        CKS(pull_control(ctx));
+        if (!hs->halt) continue;
+        if (hs->status != STAG_OK) { status = (stag_status)hs->status; break; }
+        if (hs->need_reliable) {
+            // x0 accumulated in fp64; true residual b - (A + s0) x0 with the fp64 operator
+            k_rel_accumulate<<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, (double2*)x64, (float2*)x);
+            CKS(launch_apply_a(ctx, hs->c0, STAG_FP64, nrhs, x64, ax64, t64));
+            k_rel_finish<<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, (const double2*)b64, (const double2*)ax64,
+                                                         (float2*)r, ctx->red, ctx->counters + 3);
+            CK(cudaGetLastError());
+            hs->halt = 0;
+            hs->k4_skip = 0;
+            CK(cudaMemcpyAsync(&ctx->st->halt, &hs->halt, 2 * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+            continue;
+        }
+        break;   // converged
+    }
+    if (mixed) {
+        k_rel_output<<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, (const double2*)x64, (float2*)x);
+        CK(cudaGetLastError());
+    }
+    if (info) {
+        info->iterations = hs->k;
+        info->reliable_updates = hs->n_reliable;
+        for (int s = 0; s < nshift; ++s) {
+            int it = 0;
+            for (int q2 = 0; q2 < nrhs; ++q2) it = hs->iters_at[q2][s] > it ? hs->iters_at[q2][s] : it;
+            info->shift_iterations[s] = it;
+        }
+    }
+    if (info && want_true_residual) {
+        // true residual of every shift in fp64: ||b - (A + s) x|| / ||b||, max over rhs
+        void *xs64, *ax, *t, *bd;
+        CKS(ws_get(ctx, WS_X64, v64, &xs64));
+        CKS(ws_get(ctx, WS_R64, v64, &ax));
+        CKS(ws_get(ctx, WS_T64, v64, &t));
+        CKS(ws_get(ctx, WS_B64, v64, &bd));
+        size_t n = (size_t)nrhs * 3 * g.Vh;
+        if (mixed) k_f2d<<<nblocks((long long)n, 256), 256, 0, ctx->stream>>>(n, (const float2*)b, (double2*)bd);
+        else CK(cudaMemcpyAsync(bd, b, v64, cudaMemcpyDeviceToDevice, ctx->stream));
+        void* ws_misc;
+        CKS(ws_get(ctx, WS_MISC, v64, &ws_misc));
+        std::vector<double> part((size_t)2 * nrhs * grid_v.x);
+        for (int s = 0; s < nshift; ++s) {
+            // gather x_s of every rhs into a contiguous fp64 array
+            for (int q2 = 0; q2 < nrhs; ++q2) {
+                size_t off = ((size_t)q2 * nshift + s) * 3 * g.Vh;
+                size_t m = (size_t)3 * g.Vh;
+                if (mixed)
+                    k_f2d<<<nblocks((long long)m, 256), 256, 0, ctx->stream>>>(
+                        m, (const float2*)x + off, (double2*)xs64 + (size_t)q2 * m);
+                else
+                    CK(cudaMemcpyAsync((double2*)xs64 + (size_t)q2 * m, (const double2*)x + off,
+                                       m * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->stream));
+            }
+            CKS(launch_apply_a(ctx, mass * mass, STAG_FP64, nrhs, xs64, ax, t));
+            k_true_res<<<grid_v, VB, 0, ctx->stream>>>(g.Vh, shifts[s], (const double2*)bd, (const double2*)ax,
+                                                       (const double2*)xs64, ctx->red);
+            CK(cudaGetLastError());
+            CK(cudaMemcpyAsync(part.data(), ctx->red, part.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                               ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+            double worst = 0.0;
+            for (int q2 = 0; q2 < nrhs; ++q2) {
+                double num = 0.0, den = 0.0;
+                for (unsigned i = 0; i < grid_v.x; ++i) {
+                    num += part[(size_t)(2 * q2) * grid_v.x + i];
+                    den += part[(size_t)(2 * q2 + 1) * grid_v.x + i];
+                }
+                double rel = den > 0 ? std::sqrt(num / den) : 0.0;
+                worst = rel > worst ? rel : worst;
+            }
+            info->true_residual[s] = worst;
+        }
+    }
+    return status;
+}
+
+stag_status multishift(stag_ctx* ctx, double mass, int nshift, const double* shifts, stag_prec prec, int nrhs,
+                       const void* b, void* x, double tol, int max_iter, stag_solve_info* info,
+                       bool want_true_residual) {
+    if (!ctx || !shifts || !b || !x || nshift < 1 || nshift > STAG_MAX_SHIFTS || nrhs < 1 || max_iter < 1 ||
+        !(tol > 0.0))
+        return STAG_ERR_ARG;
+    if (!ctx->has_gauge) return STAG_ERR_NO_GAUGE;
+    if (prec < STAG_FP64 || prec > STAG_BF16_12) return STAG_ERR_ARG;
+    if (prec == STAG_BF16_12 && ctx->b16_stale) CKS(refresh_bf16(ctx));
+    int base = 0;
+    for (int s = 0; s < nshift; ++s) {
+        if (!(mass * mass + shifts[s] > 0.0)) return STAG_ERR_ARG;
+        if (shifts[s] < shifts[base]) base = s;
+    }
+    const size_t per_rhs = (size_t)3 * ctx->g.Vh * 2 * rsize(prec);
+    stag_solve_info acc;
+    std::memset(&acc, 0, sizeof(acc));
+    stag_status worst = STAG_OK;
+    for (int r0 = 0; r0 < nrhs; r0 += STAG_MAX_RHS) {
+        int n = nrhs - r0 < STAG_MAX_RHS ? nrhs - r0 : STAG_MAX_RHS;
+        stag_solve_info one;
+        std::memset(&one, 0, sizeof(one));
+        stag_status s = ms_batch(ctx, mass, nshift, shifts, base, prec, n, (const char*)b + r0 * per_rhs,
+                                 (char*)x + (size_t)r0 * nshift * per_rhs, tol, max_iter, info ? &one : nullptr,
+                                 want_true_residual);
+        if (s != STAG_OK && s != STAG_ERR_NOT_CONVERGED) return s;
+        if (s != STAG_OK) worst = s;
+        if (info) {
+            acc.iterations = one.iterations > acc.iterations ? one.iterations : acc.iterations;
+            acc.reliable_updates += one.reliable_updates;
+            for (int k = 0; k < nshift; ++k) {
+                acc.shift_iterations[k] = one.shift_iterations[k] > acc.shift_iterations[k] ? one.shift_iterations[k]
+                                                                                            : acc.shift_iterations[k];
+                acc.true_residual[k] = one.true_residual[k] > acc.true_residual[k] ? one.true_residual[k]
+                                                                                  : acc.true_residual[k];
+            }
+        }
+    }
+    if (info) *info = acc;
+    return worst;
+}
+
+extern "C" stag_status stag_multishift_solve(stag_ctx* ctx, double mass, int nshift, const double* shifts,
+                                             stag_prec prec, int nrhs, const void* b, void* x, double tol,
+                                             int max_iter, stag_solve_info* info) {
+    return multishift(ctx, mass, nshift, shifts, prec, nrhs, b, x, tol, max_iter, info, info != nullptr);
+}

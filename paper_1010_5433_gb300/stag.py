@@ -1,0 +1,225 @@
+"""ctypes binding of libstag (include/stag.h).  Argument marshalling only: every
+step of the computation runs in the CUDA library; this module converts
+Python values and torch tensors into the plain pointers and structs of the C
+ABI.  There is no CPU fallback: if the compiled library is missing, loading
+fails with an error.
+
+Functions keep the C names (stag_create, stag_dslash, ...).  Tensor arguments
+are torch CUDA tensors in the layouts the header documents; raw integer
+device pointers are accepted as well.
+"""
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libstag.so")
+
+STAG_FP64, STAG_FP32, STAG_FP32_12, STAG_BF16_12 = 0, 1, 2, 3
+STAG_MAX_SHIFTS = 32
+STAG_MAX_FLAVOURS = 2
+STATUS = {0: "ok", 1: "invalid argument", 2: "allocation failed", 3: "CUDA error",
+          4: "solver did not converge", 5: "device wait timed out", 6: "NaN or Inf", 7: "no gauge field"}
+
+
+class StagError(RuntimeError):
+    def __init__(self, status, where, detail=""):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)} {detail}".strip())
+
+
+class stag_lattice(C.Structure):
+    _fields_ = [("dims", C.c_int * 4), ("t_antiperiodic", C.c_int), ("cuda_stream", C.c_void_p)]
+
+
+class stag_rational(C.Structure):
+    _fields_ = [("n", C.c_int), ("a0", C.c_double), ("alpha", C.POINTER(C.c_double)),
+                ("beta", C.POINTER(C.c_double))]
+
+
+class stag_solve_info(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("shift_iterations", C.c_int * STAG_MAX_SHIFTS),
+                ("true_residual", C.c_double * STAG_MAX_SHIFTS), ("reliable_updates", C.c_int)]
+
+
+class stag_flavour(C.Structure):
+    _fields_ = [("mass", C.c_double), ("n_pf", C.c_int), ("hb", stag_rational), ("md", stag_rational),
+                ("met", stag_rational)]
+
+
+class stag_hmc(C.Structure):
+    _fields_ = [("beta", C.c_double), ("tau", C.c_double), ("n_outer", C.c_int), ("n_gauge", C.c_int),
+                ("n_flavours", C.c_int), ("flavour", stag_flavour * STAG_MAX_FLAVOURS),
+                ("tol_md", C.c_double), ("tol_met", C.c_double), ("max_iter", C.c_int),
+                ("md_prec", C.c_int), ("seed", C.c_ulonglong), ("counter", C.c_ulonglong),
+                ("ext_mom", C.c_void_p), ("ext_xi", C.c_void_p), ("ext_uniform", C.c_double),
+                ("no_metropolis", C.c_int), ("flip_momenta", C.c_int)]
+
+
+class stag_traj(C.Structure):
+    _fields_ = [("dH", C.c_double), ("H0", C.c_double), ("H1", C.c_double), ("plaq", C.c_double),
+                ("accepted", C.c_int), ("cg_iterations", C.c_longlong), ("reliable_updates", C.c_int),
+                ("seconds", C.c_double)]
+
+
+_lib = None
+_keep = []   # ctypes arrays referenced by live structs
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libstag is not built ({LIB_PATH} missing); run "
+                              "python -m paper_1010_5433_gb300.build")
+        L = C.CDLL(LIB_PATH)
+        vp, i, d = C.c_void_p, C.c_int, C.c_double
+        sig = {
+            "stag_create": ([C.POINTER(stag_lattice), C.POINTER(vp)], i),
+            "stag_destroy": ([vp], None),
+            "stag_strerror": ([i], C.c_char_p),
+            "stag_last_cuda_error": ([vp], C.c_char_p),
+            "stag_set_stream": ([vp, vp], i),
+            "stag_device_bytes": ([vp], C.c_size_t),
+            "stag_load_gauge": ([vp, vp], i),
+            "stag_load_gauge_device": ([vp, vp], i),
+            "stag_store_gauge": ([vp, vp], i),
+            "stag_dslash": ([vp, i, i, i, vp, vp], i),
+            "stag_apply_a": ([vp, d, d, i, i, vp, vp], i),
+            "stag_multishift_solve": ([vp, d, i, vp, i, i, vp, vp, d, i, C.POINTER(stag_solve_info)], i),
+            "stag_fermion_force": ([vp, d, C.POINTER(stag_rational), i, i, vp, vp, d, i,
+                                    C.POINTER(stag_solve_info)], i),
+            "stag_gauge_force": ([vp, d, vp], i),
+            "stag_plaquette": ([vp, C.POINTER(d)], i),
+            "stag_md_trajectory": ([vp, C.POINTER(stag_hmc), C.POINTER(stag_traj)], i),
+            "stag_momenta": ([vp], vp),
+        }
+        for name, (args, res) in sig.items():
+            if not hasattr(L, name):
+                continue           # reported by the export test; calling it raises
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    if hasattr(t, "ctypes"):
+        return t.ctypes.data
+    raise TypeError(f"cannot take a pointer of {type(t)}")
+
+
+def _check(status, where, ctx=None):
+    if status != 0:
+        detail = ""
+        if ctx is not None and status == 3:
+            detail = lib().stag_last_cuda_error(ctx).decode()
+        raise StagError(status, where, detail)
+    return status
+
+
+def _darr(vals):
+    a = (C.c_double * max(1, len(vals)))(*vals)
+    _keep.append(a)
+    return a
+
+
+def make_rational(a0, alpha, beta):
+    r = stag_rational()
+    r.n = len(alpha)
+    r.a0 = float(a0)
+    r.alpha = C.cast(_darr([float(v) for v in alpha]), C.POINTER(C.c_double))
+    r.beta = C.cast(_darr([float(v) for v in beta]), C.POINTER(C.c_double))
+    return r
+
+
+# ---------------------------------------------------------------- C-named calls
+def stag_create(dims, t_antiperiodic=True, cuda_stream=None):
+    lat = stag_lattice()
+    for k in range(4):
+        lat.dims[k] = int(dims[k])
+    lat.t_antiperiodic = 1 if t_antiperiodic else 0
+    lat.cuda_stream = _ptr(cuda_stream) if cuda_stream is not None else None
+    h = C.c_void_p()
+    _check(lib().stag_create(C.byref(lat), C.byref(h)), "stag_create")
+    return h
+
+
+def stag_destroy(ctx):
+    lib().stag_destroy(ctx)
+
+
+def stag_set_stream(ctx, stream):
+    _check(lib().stag_set_stream(ctx, _ptr(stream)), "stag_set_stream", ctx)
+
+
+def stag_device_bytes(ctx):
+    return lib().stag_device_bytes(ctx)
+
+
+def stag_load_gauge(ctx, host_u):
+    """host_u: C-contiguous float64 host array (numpy or CPU tensor), 4*V*18 values."""
+    _check(lib().stag_load_gauge(ctx, _ptr(host_u)), "stag_load_gauge", ctx)
+
+
+def stag_load_gauge_device(ctx, dev_u):
+    _check(lib().stag_load_gauge_device(ctx, _ptr(dev_u)), "stag_load_gauge_device", ctx)
+
+
+def stag_store_gauge(ctx, host_u):
+    _check(lib().stag_store_gauge(ctx, _ptr(host_u)), "stag_store_gauge", ctx)
+
+
+def stag_dslash(ctx, out_parity, prec, nrhs, inp, out):
+    _check(lib().stag_dslash(ctx, int(out_parity), int(prec), int(nrhs), _ptr(inp), _ptr(out)), "stag_dslash", ctx)
+
+
+def stag_apply_a(ctx, mass, shift, prec, nrhs, inp, out):
+    _check(lib().stag_apply_a(ctx, float(mass), float(shift), int(prec), int(nrhs), _ptr(inp), _ptr(out)),
+           "stag_apply_a", ctx)
+
+
+def stag_multishift_solve(ctx, mass, shifts, prec, nrhs, b, x, tol, max_iter, info=True, check=True):
+    sh = _darr([float(s) for s in shifts])
+    inf = stag_solve_info() if info else None
+    st = lib().stag_multishift_solve(ctx, float(mass), len(shifts), C.cast(sh, C.c_void_p), int(prec), int(nrhs),
+                                     _ptr(b), _ptr(x), float(tol), int(max_iter),
+                                     C.byref(inf) if inf is not None else None)
+    if check:
+        _check(st, "stag_multishift_solve", ctx)
+    return (st, inf) if not check else inf
+
+
+def stag_fermion_force(ctx, mass, rational, prec, n_pf, phi, force, tol, max_iter, info=True):
+    inf = stag_solve_info() if info else None
+    _check(lib().stag_fermion_force(ctx, float(mass), C.byref(rational), int(prec), int(n_pf), _ptr(phi),
+                                    _ptr(force), float(tol), int(max_iter),
+                                    C.byref(inf) if inf is not None else None), "stag_fermion_force", ctx)
+    return inf
+
+
+def stag_gauge_force(ctx, beta, force):
+    _check(lib().stag_gauge_force(ctx, float(beta), _ptr(force)), "stag_gauge_force", ctx)
+
+
+def stag_plaquette(ctx):
+    v = C.c_double()
+    _check(lib().stag_plaquette(ctx, C.byref(v)), "stag_plaquette", ctx)
+    return v.value
+
+
+def stag_md_trajectory(ctx, hmc):
+    out = stag_traj()
+    st = lib().stag_md_trajectory(ctx, C.byref(hmc), C.byref(out))
+    _check(st, "stag_md_trajectory", ctx)
+    return out
+
+
+def stag_momenta(ctx):
+    return lib().stag_momenta(ctx)

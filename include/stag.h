@@ -120,15 +120,24 @@ typedef struct {
     int reliable_updates;                 /* fp64 residual replacements made */
 } stag_solve_info;
 
-/* Solve (A + shift_i) x_i = b for nshift shifts and nrhs independent sources
- * in one Krylov space per source.  b: [nrhs][3][Vh] even field;
- * x: [nrhs][nshift][3][Vh] (caller-owned, overwritten).
- * prec STAG_FP64: everything in fp64.  Other precisions: the iteration runs
- * with that Dslash and fp32 vectors, fp64 reductions, and fp64 reliable
- * updates of the base residual (recomputed as b - (A+s0)x0 with the fp64
- * operator whenever it fell by 'delta' = 0.1 since the last one).
- * Stops each shift when its residual |zeta_i| ||r|| <= tol ||b||.
- * info may be NULL.  Returns STAG_ERR_NOT_CONVERGED after max_iter. */
+/* Solve (A + shift_i) x_i = b for nshift shifts and nrhs independent sources,
+ * one Krylov space per source, the sources iterated together (every Dslash
+ * is a multi-RHS Dslash).  I/O is always fp64: b [nrhs][3][Vh] and
+ * x [nrhs][nshift][3][Vh] double complex (x caller-owned, overwritten).
+ * prec selects the arithmetic of the iteration:
+ *   STAG_FP64   fp64 throughout (the paper's Metropolis/heatbath inversions).
+ *   fp32 / fp32-12: fp32 vectors, fp64 sums, and the base residual replaced
+ *     by b - (A+s0)x0 from the fp64 operator after every decade (reliable
+ *     updates); every shift's solution is accumulated in fp64 per decade.
+ *   bf16-12: bf16-link iteration without residual replacement.
+ *   For the three mixed precisions each shift whose fp64 true residual is
+ *   still above tol is then refined by single-shift fp32 CG with fp64
+ *   reliable updates, warm-started at x_i (a single shift may restart;
+ *   the multi-shift solver may not, Sec. 6).
+ * Convergence: shift i stops when |zeta_i| ||r|| <= tol ||b||; on return the
+ * fp64 true residual of every shift is reported in info (may be NULL).
+ * Returns STAG_ERR_NOT_CONVERGED after max_iter iterations of a stage, with
+ * the partial solutions in x. */
 stag_status stag_multishift_solve(stag_ctx* ctx, double mass, int nshift, const double* shifts,
                                   stag_prec prec, int nrhs, const void* b, void* x,
                                   double tol, int max_iter, stag_solve_info* info);

@@ -86,6 +86,13 @@ extern "C" void stag_destroy(stag_ctx* ctx) {
     delete ctx;
 }
 
+// Partial sums of every reducing kernel: at most 2 values per source per
+// block of >= 64 threads.
+static size_t red_doubles(int Vh) {
+    size_t n = (size_t)2 * STAG_MAX_RHS * ((size_t)Vh / 64 + 2);
+    return n < 65536 ? 65536 : n;
+}
+
 extern "C" stag_status stag_create(const stag_lattice* lat, stag_ctx** out) {
     if (!lat || !out) return STAG_ERR_ARG;
     *out = nullptr;
@@ -110,7 +117,7 @@ extern "C" stag_status stag_create(const stag_lattice* lat, stag_ctx** out) {
     if ((s = dev_alloc(ctx, (void**)&ctx->ghi, gbytes)) != STAG_OK ||
         (s = dev_alloc(ctx, (void**)&ctx->glo, gbytes)) != STAG_OK ||
         (s = dev_alloc(ctx, (void**)&ctx->g16, bbytes)) != STAG_OK ||
-        (s = dev_alloc(ctx, (void**)&ctx->red, sizeof(double) * STAG_MAX_RED_BLOCKS * 4)) != STAG_OK ||
+        (s = dev_alloc(ctx, (void**)&ctx->red, sizeof(double) * red_doubles(ctx->g.Vh))) != STAG_OK ||
         (s = dev_alloc(ctx, (void**)&ctx->counters, sizeof(unsigned int) * 16)) != STAG_OK ||
         (s = dev_alloc(ctx, (void**)&ctx->scal, sizeof(double) * 64)) != STAG_OK ||
         (s = dev_alloc(ctx, (void**)&ctx->st, sizeof(SolverState))) != STAG_OK) {

@@ -24,6 +24,9 @@ enum WsSlot {
     WS_SAVE_HI, WS_SAVE_LO,    // saved gauge field for Metropolis rejection
     WS_MOM,            // momenta
     WS_MISC,
+    WS_B32, WS_X32,    // multishift API: fp32 copy of b, fp32 iteration solutions
+    WS_REF_G, WS_REF_AX, WS_REF_T, WS_REF_R64, WS_REF_B32, WS_REF_E32, WS_REF_E64,  // refinement
+    WS_FORCE_X64,      // fermion force: fp64 accumulation of the mixed solutions
     WS_COUNT
 };
 
@@ -80,9 +83,19 @@ stag_status launch_apply_a(stag_ctx* ctx, double c0, stag_prec prec, int nrhs, c
                            void* tmp_odd);
 
 // solver.cu
-stag_status multishift(stag_ctx* ctx, double mass, int nshift, const double* shifts, stag_prec prec, int nrhs,
-                       const void* b, void* x, double tol, int max_iter, stag_solve_info* info,
-                       bool want_true_residual);
+// Core multi-shift iteration in the arithmetic of prec.  b, x: [nrhs][3][Vh] and
+// [nrhs][nshift][3][Vh] in the real type of prec (x overwritten).  For mixed
+// precisions with reliable updates, b64 (fp64 source) and x64 (fp64
+// accumulator, same shape as x) are required; finish_to_f64 selects whether
+// the result ends in x64 (x64 += x) or in x (x = (float)(x64 + x)).
+struct MsStats {
+    int iterations;
+    int reliable;
+    int shift_iterations[STAG_MAX_SHIFTS];
+};
+stag_status ms_core(stag_ctx* ctx, double mass, int nshift, const double* shifts, stag_prec prec, int nrhs,
+                    const void* b, const double2* b64, void* x, double2* x64, double tol, int max_iter,
+                    bool reliable, bool finish_to_f64, MsStats* stats);
 
 // force.cu
 stag_status fermion_force_from_solutions(stag_ctx* ctx, stag_prec prec, int n_pf, int nshift, const double* alpha,

@@ -20,8 +20,10 @@
 // accumulated in fp64.  The paper argues that a shifted solver cannot restart
 // (Sec. 6); replacing the base residual keeps the shifted residuals collinear
 // only approximately, which is why every shift's true residual is reported.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "internal.h"
 #include "solver_state.cuh"
@@ -307,23 +309,37 @@ __global__ void __launch_bounds__(VB) k_ms_shift_update(SolverState* st, int Vh,
 }
 
 // ---------------------------------------------------------------- reliable update kernels
-// x64 += x_base (fp32), x_base = 0 for every rhs still iterating
+// Windowed accumulation: x64_i += x_i (fp32), x_i = 0 for every shift of every
+// rhs still iterating, so fp32 rounding only ever touches one residual decade.
 __global__ void k_rel_accumulate(const SolverState* st, int Vh, double2* x64, float2* x) {
     const int rhs = blockIdx.y;
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
     if (h >= Vh || !st->rhs_live[rhs]) return;
     const size_t rs = (size_t)3 * Vh;
-    float2* xb = x + ((size_t)rhs * st->nshift + st->base) * rs;
+    for (int s = 0; s < st->nshift; ++s) {
+        const size_t off = ((size_t)rhs * st->nshift + s) * rs;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        size_t i = rhs * rs + (size_t)c * Vh + h;
-        float2 a = xb[(size_t)c * Vh + h];
-        double2 d = x64[i];
-        d.x += (double)a.x;
-        d.y += (double)a.y;
-        x64[i] = d;
-        xb[(size_t)c * Vh + h] = make_float2(0.f, 0.f);
+        for (int c = 0; c < 3; ++c) {
+            size_t i = off + (size_t)c * Vh + h;
+            float2 a = x[i];
+            double2 d = x64[i];
+            d.x += (double)a.x;
+            d.y += (double)a.y;
+            x64[i] = d;
+            x[i] = make_float2(0.f, 0.f);
+        }
     }
+}
+
+// gather the base shift's fp64 solution of every rhs into xb64 [rhs][3][Vh]
+__global__ void k_rel_gather_base(const SolverState* st, int Vh, const double2* x64, double2* xb64) {
+    const int rhs = blockIdx.y;
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= Vh) return;
+    const size_t rs = (size_t)3 * Vh;
+    const size_t off = ((size_t)rhs * st->nshift + st->base) * rs;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) xb64[rhs * rs + (size_t)c * Vh + h] = x64[off + (size_t)c * Vh + h];
 }
 
 // r = b - Ax (fp64), stored in fp32; new rr / rr_ref for the rhs still iterating
@@ -365,30 +381,73 @@ __global__ void __launch_bounds__(VB) k_rel_finish(SolverState* st, int Vh, cons
     }
 }
 
-// x_base = (float)(x64 + x_base) at the end of a mixed solve
+// x_i = (float)(x64_i + x_i) for every shift at the end of a mixed solve
 __global__ void k_rel_output(const SolverState* st, int Vh, const double2* x64, float2* x) {
     const int rhs = blockIdx.y;
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
     if (h >= Vh) return;
     const size_t rs = (size_t)3 * Vh;
-    float2* xb = x + ((size_t)rhs * st->nshift + st->base) * rs;
+    for (int s = 0; s < st->nshift; ++s) {
+        const size_t off = ((size_t)rhs * st->nshift + s) * rs;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        float2 a = xb[(size_t)c * Vh + h];
-        double2 d = x64[rhs * rs + (size_t)c * Vh + h];
-        xb[(size_t)c * Vh + h] = make_float2((float)(d.x + (double)a.x), (float)(d.y + (double)a.y));
+        for (int c = 0; c < 3; ++c) {
+            size_t i = off + (size_t)c * Vh + h;
+            float2 a = x[i];
+            double2 d = x64[i];
+            x[i] = make_float2((float)(d.x + (double)a.x), (float)(d.y + (double)a.y));
+        }
     }
 }
 
-__global__ void k_f2d(size_t n, const float2* a, double2* b) {
-    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) b[i] = make_double2((double)a[i].x, (double)a[i].y);
+// x64_i += x_i (fp32) for every shift: the fp64 result of a mixed solve
+__global__ void k_acc_final(const SolverState* st, int Vh, double2* x64, const float2* x) {
+    const int rhs = blockIdx.y;
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= Vh) return;
+    const size_t rs = (size_t)3 * Vh;
+    for (int s = 0; s < st->nshift; ++s) {
+        const size_t off = ((size_t)rhs * st->nshift + s) * rs;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            size_t i = off + (size_t)c * Vh + h;
+            float2 a = x[i];
+            double2 d = x64[i];
+            d.x += (double)a.x;
+            d.y += (double)a.y;
+            x64[i] = d;
+        }
+    }
 }
 
-// |b - (A + s) x|^2 per rhs, fp64, with ax = A x (c0 = m^2 already applied), x fp64
-__global__ void __launch_bounds__(VB) k_true_res(int Vh, double shift, const double2* __restrict__ b,
+// g[rhs] = x[rhs][s]  (fp64 gather of one shift)
+__global__ void k_gather_shift(int Vh, int nshift, int s, const double2* x, double2* g) {
+    const int rhs = blockIdx.y;
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= Vh) return;
+    const size_t rs = (size_t)3 * Vh;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        g[rhs * rs + (size_t)c * Vh + h] = x[((size_t)rhs * nshift + s) * rs + (size_t)c * Vh + h];
+}
+
+// x[rhs][s] += e[rhs]
+__global__ void k_scatter_add_shift(int Vh, int nshift, int s, const double2* e, double2* x) {
+    const int rhs = blockIdx.y;
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= Vh) return;
+    const size_t rs = (size_t)3 * Vh;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        size_t i = ((size_t)rhs * nshift + s) * rs + (size_t)c * Vh + h;
+        double2 a = x[i], d = e[rhs * rs + (size_t)c * Vh + h];
+        x[i] = make_double2(a.x + d.x, a.y + d.y);
+    }
+}
+
+// r = b - ax - shift * x (fp64), r32 = (float) r, per-rhs partials of |r|^2 and |b|^2
+__global__ void __launch_bounds__(VB) k_residual(int Vh, double shift, const double2* __restrict__ b,
                                                  const double2* __restrict__ ax, const double2* __restrict__ x,
-                                                 double* partial) {
+                                                 double2* r, float2* r32, double* partial) {
     const int rhs = blockIdx.y;
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
     const size_t rs = (size_t)3 * Vh;
@@ -399,6 +458,8 @@ __global__ void __launch_bounds__(VB) k_true_res(int Vh, double shift, const dou
             size_t i = rhs * rs + (size_t)c * Vh + h;
             double re = b[i].x - ax[i].x - shift * x[i].x;
             double im = b[i].y - ax[i].y - shift * x[i].y;
+            if (r) r[i] = make_double2(re, im);
+            if (r32) r32[i] = make_float2((float)re, (float)im);
             v[0] += re * re + im * im;
             v[1] += b[i].x * b[i].x + b[i].y * b[i].y;
         }
@@ -410,7 +471,18 @@ __global__ void __launch_bounds__(VB) k_true_res(int Vh, double shift, const dou
     }
 }
 
+__global__ void k_d2f(size_t n, const double2* a, float2* b) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = make_float2((float)a[i].x, (float)a[i].y);
+}
+
+__global__ void k_f2d(size_t n, const float2* a, double2* b) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = make_double2((double)a[i].x, (double)a[i].y);
+}
+
 }  // namespace
+
 
 // ---------------------------------------------------------------- host driver
 template <typename R>
@@ -455,20 +527,23 @@ static stag_status ms_iterations(stag_ctx* ctx, stag_prec prec, int nrhs, int ch
 
 static size_t rsize(stag_prec p) { return p == STAG_FP64 ? sizeof(double) : sizeof(float); }
 
-// Reads the loop-control words of the device state into the pinned mirror.
-static stag_status pull_control(stag_ctx* ctx) {
+static stag_status pull_state(stag_ctx* ctx) {
     CK(cudaMemcpyAsync(ctx->st_host, ctx->st, sizeof(SolverState), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return STAG_OK;
 }
 
-static stag_status ms_batch(stag_ctx* ctx, double mass, int nshift, const double* shifts, int base, stag_prec prec,
-                            int nrhs, const void* b, void* x, double tol, int max_iter, stag_solve_info* info,
-                            bool want_true_residual) {
+stag_status ms_core(stag_ctx* ctx, double mass, int nshift, const double* shifts, stag_prec prec, int nrhs,
+                    const void* b, const double2* b64, void* x, double2* x64, double tol, int max_iter,
+                    bool reliable, bool finish_to_f64, MsStats* stats) {
     const Geom& g = ctx->g;
     const bool mixed = prec != STAG_FP64;
-    const size_t rsz = rsize(prec);
-    const size_t vbytes = (size_t)nrhs * 3 * g.Vh * 2 * rsz;
+    if (nrhs < 1 || nrhs > STAG_MAX_RHS || nshift < 1 || nshift > STAG_MAX_SHIFTS) return STAG_ERR_ARG;
+    if (mixed && reliable && (!b64 || !x64)) return STAG_ERR_ARG;
+    int base = 0;
+    for (int s = 0; s < nshift; ++s)
+        if (shifts[s] < shifts[base]) base = s;
+    const size_t vbytes = (size_t)nrhs * 3 * g.Vh * 2 * rsize(prec);
     void *tmp, *r, *p, *q, *ps;
     CKS(ws_get(ctx, WS_TMP_ODD, vbytes, &tmp));
     CKS(ws_get(ctx, WS_R, vbytes, &r));
@@ -476,24 +551,21 @@ static stag_status ms_batch(stag_ctx* ctx, double mass, int nshift, const double
     CKS(ws_get(ctx, WS_Q, vbytes, &q));
     CKS(ws_get(ctx, WS_PS, vbytes * nshift, &ps));
     const size_t v64 = (size_t)nrhs * 3 * g.Vh * sizeof(double2);
-    void *b64 = nullptr, *x64 = nullptr, *ax64 = nullptr, *t64 = nullptr;
-    if (mixed) {
-        CKS(ws_get(ctx, WS_B64, v64, &b64));
-        CKS(ws_get(ctx, WS_X64, v64, &x64));
+    void *ax64 = nullptr, *t64 = nullptr, *xb64 = nullptr;
+    const bool use_rel = mixed && reliable;
+    if (use_rel) {
         CKS(ws_get(ctx, WS_R64, v64, &ax64));
         CKS(ws_get(ctx, WS_T64, v64, &t64));
-        size_t n = (size_t)nrhs * 3 * g.Vh;
-        k_f2d<<<nblocks((long long)n, 256), 256, 0, ctx->stream>>>(n, (const float2*)b, (double2*)b64);
-        CK(cudaMemsetAsync(x64, 0, v64, ctx->stream));
+        CKS(ws_get(ctx, WS_U64, v64, &xb64));
     }
-    // host part of the state
+    if (mixed && x64) CK(cudaMemsetAsync(x64, 0, v64 * nshift, ctx->stream));
     SolverState* hs = ctx->st_host;
     std::memset(hs, 0, sizeof(SolverState));
     hs->nrhs = nrhs;
     hs->nshift = nshift;
     hs->base = base;
     hs->max_iter = max_iter;
-    hs->mixed = mixed ? 1 : 0;
+    hs->mixed = use_rel ? 1 : 0;
     hs->tol2 = tol * tol;
     hs->c0 = mass * mass + shifts[base];
     hs->delta2 = 0.01;   // replace the residual after every factor 10 in ||r||
@@ -510,18 +582,24 @@ static stag_status ms_batch(stag_ctx* ctx, double mass, int nshift, const double
     CK(cudaGetLastError());
     const int chunk = 16;
     stag_status status = STAG_OK;
-    for (int guard = 0; guard < 1000000; ++guard) {
+    // every chunk either advances k by up to `chunk` or makes a reliable update
+    const long long guard_max = (long long)max_iter / chunk * 4 + 64;
+    long long guard = 0;
+    for (;; ++guard) {
+        if (guard > guard_max) { status = STAG_ERR_TIMEOUT; break; }
         if (mixed) CKS(ms_iterations<float>(ctx, prec, nrhs, chunk, tmp, r, p, q, ps, x));
         else CKS(ms_iterations<double>(ctx, prec, nrhs, chunk, tmp, r, p, q, ps, x));
-        CKS(pull_control(ctx));
+        CKS(pull_state(ctx));
         if (!hs->halt) continue;
         if (hs->status != STAG_OK) { status = (stag_status)hs->status; break; }
         if (hs->need_reliable) {
-            // x0 accumulated in fp64; true residual b - (A + s0) x0 with the fp64 operator
-            k_rel_accumulate<<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, (double2*)x64, (float2*)x);
-            CKS(launch_apply_a(ctx, hs->c0, STAG_FP64, nrhs, x64, ax64, t64));
-            k_rel_finish<<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, (const double2*)b64, (const double2*)ax64,
-                                                         (float2*)r, ctx->red, ctx->counters + 3);
+            // fp64 accumulation of every shift, then the true base residual
+            // b - (A + s0) x0 with the fp64 operator replaces the recursive one
+            k_rel_accumulate<<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, x64, (float2*)x);
+            k_rel_gather_base<<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, x64, (double2*)xb64);
+            CKS(launch_apply_a(ctx, hs->c0, STAG_FP64, nrhs, xb64, ax64, t64));
+            k_rel_finish<<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, b64, (const double2*)ax64, (float2*)r,
+                                                         ctx->red, ctx->counters + 3);
             CK(cudaGetLastError());
             hs->halt = 0;
             hs->k4_skip = 0;
@@ -530,82 +608,153 @@ static stag_status ms_batch(stag_ctx* ctx, double mass, int nshift, const double
         }
         break;   // converged
     }
-    if (mixed) {
-        k_rel_output<<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, (const double2*)x64, (float2*)x);
+    if (mixed && x64) {
+        if (finish_to_f64) k_acc_final<<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, x64, (const float2*)x);
+        else k_rel_output<<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, x64, (float2*)x);
         CK(cudaGetLastError());
     }
-    if (info) {
-        info->iterations = hs->k;
-        info->reliable_updates = hs->n_reliable;
+    if (stats) {
+        stats->iterations = hs->k;
+        stats->reliable = hs->n_reliable;
         for (int s = 0; s < nshift; ++s) {
             int it = 0;
             for (int q2 = 0; q2 < nrhs; ++q2) it = hs->iters_at[q2][s] > it ? hs->iters_at[q2][s] : it;
-            info->shift_iterations[s] = it;
-        }
-    }
-    if (info && want_true_residual) {
-        // true residual of every shift in fp64: ||b - (A + s) x|| / ||b||, max over rhs
-        void *xs64, *ax, *t, *bd;
-        CKS(ws_get(ctx, WS_X64, v64, &xs64));
-        CKS(ws_get(ctx, WS_R64, v64, &ax));
-        CKS(ws_get(ctx, WS_T64, v64, &t));
-        CKS(ws_get(ctx, WS_B64, v64, &bd));
-        size_t n = (size_t)nrhs * 3 * g.Vh;
-        if (mixed) k_f2d<<<nblocks((long long)n, 256), 256, 0, ctx->stream>>>(n, (const float2*)b, (double2*)bd);
-        else CK(cudaMemcpyAsync(bd, b, v64, cudaMemcpyDeviceToDevice, ctx->stream));
-        void* ws_misc;
-        CKS(ws_get(ctx, WS_MISC, v64, &ws_misc));
-        std::vector<double> part((size_t)2 * nrhs * grid_v.x);
-        for (int s = 0; s < nshift; ++s) {
-            // gather x_s of every rhs into a contiguous fp64 array
-            for (int q2 = 0; q2 < nrhs; ++q2) {
-                size_t off = ((size_t)q2 * nshift + s) * 3 * g.Vh;
-                size_t m = (size_t)3 * g.Vh;
-                if (mixed)
-                    k_f2d<<<nblocks((long long)m, 256), 256, 0, ctx->stream>>>(
-                        m, (const float2*)x + off, (double2*)xs64 + (size_t)q2 * m);
-                else
-                    CK(cudaMemcpyAsync((double2*)xs64 + (size_t)q2 * m, (const double2*)x + off,
-                                       m * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->stream));
-            }
-            CKS(launch_apply_a(ctx, mass * mass, STAG_FP64, nrhs, xs64, ax, t));
-            k_true_res<<<grid_v, VB, 0, ctx->stream>>>(g.Vh, shifts[s], (const double2*)bd, (const double2*)ax,
-                                                       (const double2*)xs64, ctx->red);
-            CK(cudaGetLastError());
-            CK(cudaMemcpyAsync(part.data(), ctx->red, part.size() * sizeof(double), cudaMemcpyDeviceToHost,
-                               ctx->stream));
-            CK(cudaStreamSynchronize(ctx->stream));
-            double worst = 0.0;
-            for (int q2 = 0; q2 < nrhs; ++q2) {
-                double num = 0.0, den = 0.0;
-                for (unsigned i = 0; i < grid_v.x; ++i) {
-                    num += part[(size_t)(2 * q2) * grid_v.x + i];
-                    den += part[(size_t)(2 * q2 + 1) * grid_v.x + i];
-                }
-                double rel = den > 0 ? std::sqrt(num / den) : 0.0;
-                worst = rel > worst ? rel : worst;
-            }
-            info->true_residual[s] = worst;
+            stats->shift_iterations[s] = it;
         }
     }
     return status;
 }
 
-stag_status multishift(stag_ctx* ctx, double mass, int nshift, const double* shifts, stag_prec prec, int nrhs,
-                       const void* b, void* x, double tol, int max_iter, stag_solve_info* info,
-                       bool want_true_residual) {
+// ||b - (A + s) x_s|| / ||b|| for every rhs of one shift, fp64 (x fp64, all shifts).
+// Leaves the fp64 residual in WS_REF_R64 and its fp32 copy in WS_REF_B32.
+static stag_status shift_residuals(stag_ctx* ctx, double mass, int nshift, int s, double shift, int nrhs,
+                                   const double2* b, const double2* x, double* rel_out) {
+    const Geom& g = ctx->g;
+    const size_t v64 = (size_t)nrhs * 3 * g.Vh * sizeof(double2);
+    void *gx, *ax, *t, *r64, *r32;
+    CKS(ws_get(ctx, WS_REF_G, v64, &gx));
+    CKS(ws_get(ctx, WS_REF_AX, v64, &ax));
+    CKS(ws_get(ctx, WS_REF_T, v64, &t));
+    CKS(ws_get(ctx, WS_REF_R64, v64, &r64));
+    CKS(ws_get(ctx, WS_REF_B32, v64 / 2, &r32));
+    dim3 grid_v(nblocks(g.Vh, VB), nrhs);
+    k_gather_shift<<<grid_v, VB, 0, ctx->stream>>>(g.Vh, nshift, s, x, (double2*)gx);
+    CKS(launch_apply_a(ctx, mass * mass, STAG_FP64, nrhs, gx, ax, t));
+    k_residual<<<grid_v, VB, 0, ctx->stream>>>(g.Vh, shift, b, (const double2*)ax, (const double2*)gx,
+                                               (double2*)r64, (float2*)r32, ctx->red);
+    CK(cudaGetLastError());
+    std::vector<double> part((size_t)2 * nrhs * grid_v.x);
+    CK(cudaMemcpyAsync(part.data(), ctx->red, part.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int q = 0; q < nrhs; ++q) {
+        double num = 0.0, den = 0.0;
+        for (unsigned i = 0; i < grid_v.x; ++i) {
+            num += part[(size_t)(2 * q) * grid_v.x + i];
+            den += part[(size_t)(2 * q + 1) * grid_v.x + i];
+        }
+        rel_out[q] = den > 0 ? std::sqrt(num / den) : 0.0;
+    }
+    return STAG_OK;
+}
+
+// Per-shift refinement of fp64 solutions: while a shift's true residual is
+// above tol, solve (A + s) e = r with a single-shift fp32 CG whose residual is
+// replaced in fp64 every decade (reliable updates; with one shift the solver
+// can restart, unlike the multi-shift one, Sec. 6), then x_s += e.
+static stag_status refine_shifts(stag_ctx* ctx, double mass, int nshift, const double* shifts, int nrhs,
+                                 const double2* b, double2* x, double tol, int max_iter, int* extra_iters,
+                                 int* n_reliable, double* final_res) {
+    const Geom& g = ctx->g;
+    const size_t v64 = (size_t)nrhs * 3 * g.Vh * sizeof(double2);
+    void *e32, *e64;
+    CKS(ws_get(ctx, WS_REF_E32, v64 / 2, &e32));
+    CKS(ws_get(ctx, WS_REF_E64, v64, &e64));
+    dim3 grid_v(nblocks(g.Vh, VB), nrhs);
+    for (int s = 0; s < nshift; ++s) {
+        double rel[STAG_MAX_RHS];
+        double worst = 0.0;
+        for (int round = 0; round < 6; ++round) {
+            CKS(shift_residuals(ctx, mass, nshift, s, shifts[s], nrhs, b, x, rel));
+            worst = 0.0;
+            double ratio = 1e300;
+            for (int q = 0; q < nrhs; ++q) {
+                worst = rel[q] > worst ? rel[q] : worst;
+                if (rel[q] > 0) ratio = std::min(ratio, tol / rel[q]);
+            }
+            if (worst <= tol) break;
+            double tol_in = std::min(0.5, std::max(0.5 * ratio, 1e-12));
+            MsStats st;
+            void *r64, *r32;
+            CKS(ws_get(ctx, WS_REF_R64, v64, &r64));
+            CKS(ws_get(ctx, WS_REF_B32, v64 / 2, &r32));
+            stag_status rs = ms_core(ctx, mass, 1, &shifts[s], STAG_FP32, nrhs, r32, (const double2*)r64, e32,
+                                     (double2*)e64, tol_in, max_iter, true, true, &st);
+            if (rs != STAG_OK && rs != STAG_ERR_NOT_CONVERGED) return rs;
+            *extra_iters += st.iterations;
+            *n_reliable += st.reliable;
+            k_scatter_add_shift<<<grid_v, VB, 0, ctx->stream>>>(g.Vh, nshift, s, (const double2*)e64, x);
+            CK(cudaGetLastError());
+        }
+        final_res[s] = worst;
+    }
+    return STAG_OK;
+}
+
+static stag_status ms_api_batch(stag_ctx* ctx, double mass, int nshift, const double* shifts, stag_prec prec,
+                                int nrhs, const double2* b, double2* x, double tol, int max_iter,
+                                stag_solve_info* info) {
+    const Geom& g = ctx->g;
+    MsStats st;
+    std::memset(&st, 0, sizeof(st));
+    stag_status status;
+    int extra = 0, nrel = 0;
+    double res[STAG_MAX_SHIFTS] = {0};
+    if (prec == STAG_FP64) {
+        status = ms_core(ctx, mass, nshift, shifts, prec, nrhs, b, nullptr, x, nullptr, tol, max_iter, false, true,
+                         &st);
+        if (status != STAG_OK && status != STAG_ERR_NOT_CONVERGED) return status;
+        for (int s = 0; s < nshift; ++s) {
+            double rel[STAG_MAX_RHS];
+            CKS(shift_residuals(ctx, mass, nshift, s, shifts[s], nrhs, b, x, rel));
+            for (int q = 0; q < nrhs; ++q) res[s] = rel[q] > res[s] ? rel[q] : res[s];
+        }
+    } else {
+        const size_t n = (size_t)nrhs * 3 * g.Vh;
+        void *b32, *x32;
+        CKS(ws_get(ctx, WS_B32, n * sizeof(float2), &b32));
+        CKS(ws_get(ctx, WS_X32, n * nshift * sizeof(float2), &x32));
+        k_d2f<<<nblocks((long long)n, 256), 256, 0, ctx->stream>>>(n, b, (float2*)b32);
+        CK(cudaGetLastError());
+        // residual replacement keeps the shifted recurrences consistent only when
+        // the iteration operator is the fp32 one; the bf16 operator iterates plainly
+        const bool rel = prec != STAG_BF16_12;
+        status = ms_core(ctx, mass, nshift, shifts, prec, nrhs, b32, b, x32, x, tol, max_iter, rel, true, &st);
+        if (status != STAG_OK && status != STAG_ERR_NOT_CONVERGED) return status;
+        CKS(refine_shifts(ctx, mass, nshift, shifts, nrhs, b, x, tol, max_iter, &extra, &nrel, res));
+    }
+    if (info) {
+        info->iterations = st.iterations + extra;
+        info->reliable_updates = st.reliable + nrel;
+        for (int s = 0; s < nshift; ++s) {
+            info->shift_iterations[s] = st.shift_iterations[s];
+            info->true_residual[s] = res[s];
+        }
+    }
+    return status;
+}
+
+extern "C" stag_status stag_multishift_solve(stag_ctx* ctx, double mass, int nshift, const double* shifts,
+                                             stag_prec prec, int nrhs, const void* b, void* x, double tol,
+                                             int max_iter, stag_solve_info* info) {
     if (!ctx || !shifts || !b || !x || nshift < 1 || nshift > STAG_MAX_SHIFTS || nrhs < 1 || max_iter < 1 ||
         !(tol > 0.0))
         return STAG_ERR_ARG;
     if (!ctx->has_gauge) return STAG_ERR_NO_GAUGE;
     if (prec < STAG_FP64 || prec > STAG_BF16_12) return STAG_ERR_ARG;
     if (prec == STAG_BF16_12 && ctx->b16_stale) CKS(refresh_bf16(ctx));
-    int base = 0;
-    for (int s = 0; s < nshift; ++s) {
+    for (int s = 0; s < nshift; ++s)
         if (!(mass * mass + shifts[s] > 0.0)) return STAG_ERR_ARG;
-        if (shifts[s] < shifts[base]) base = s;
-    }
-    const size_t per_rhs = (size_t)3 * ctx->g.Vh * 2 * rsize(prec);
+    const size_t per_rhs = (size_t)3 * ctx->g.Vh;
     stag_solve_info acc;
     std::memset(&acc, 0, sizeof(acc));
     stag_status worst = STAG_OK;
@@ -613,28 +762,17 @@ stag_status multishift(stag_ctx* ctx, double mass, int nshift, const double* shi
         int n = nrhs - r0 < STAG_MAX_RHS ? nrhs - r0 : STAG_MAX_RHS;
         stag_solve_info one;
         std::memset(&one, 0, sizeof(one));
-        stag_status s = ms_batch(ctx, mass, nshift, shifts, base, prec, n, (const char*)b + r0 * per_rhs,
-                                 (char*)x + (size_t)r0 * nshift * per_rhs, tol, max_iter, info ? &one : nullptr,
-                                 want_true_residual);
+        stag_status s = ms_api_batch(ctx, mass, nshift, shifts, prec, n, (const double2*)b + r0 * per_rhs,
+                                     (double2*)x + (size_t)r0 * nshift * per_rhs, tol, max_iter, &one);
         if (s != STAG_OK && s != STAG_ERR_NOT_CONVERGED) return s;
         if (s != STAG_OK) worst = s;
-        if (info) {
-            acc.iterations = one.iterations > acc.iterations ? one.iterations : acc.iterations;
-            acc.reliable_updates += one.reliable_updates;
-            for (int k = 0; k < nshift; ++k) {
-                acc.shift_iterations[k] = one.shift_iterations[k] > acc.shift_iterations[k] ? one.shift_iterations[k]
-                                                                                            : acc.shift_iterations[k];
-                acc.true_residual[k] = one.true_residual[k] > acc.true_residual[k] ? one.true_residual[k]
-                                                                                  : acc.true_residual[k];
-            }
+        acc.iterations = std::max(acc.iterations, one.iterations);
+        acc.reliable_updates += one.reliable_updates;
+        for (int k = 0; k < nshift; ++k) {
+            acc.shift_iterations[k] = std::max(acc.shift_iterations[k], one.shift_iterations[k]);
+            acc.true_residual[k] = std::max(acc.true_residual[k], one.true_residual[k]);
         }
     }
     if (info) *info = acc;
     return worst;
-}
-
-extern "C" stag_status stag_multishift_solve(stag_ctx* ctx, double mass, int nshift, const double* shifts,
-                                             stag_prec prec, int nrhs, const void* b, void* x, double tol,
-                                             int max_iter, stag_solve_info* info) {
-    return multishift(ctx, mass, nshift, shifts, prec, nrhs, b, x, tol, max_iter, info, info != nullptr);
 }

@@ -148,7 +148,8 @@ stag_status stag_multishift_solve(stag_ctx* ctx, double mass, int nshift, const 
  *   F_a(x,mu) = sum_i alpha_i eps(x) eta_mu(x) Re tr[i T_a U_mu(x) Z_i(x+mu) Z_i(x)^dag]
  * with Z_i = X_i on even and D_oe X_i on odd sites, X_i = (A+beta_i)^-1 phi,
  * eps = +1/-1 on even/odd sites (dS/domega_a for U -> exp(i omega T_a) U).
- * phi: [n_pf][3][Vh] even fields in the real type of prec.
+ * phi: [n_pf][3][Vh] even fields, fp64 complex; prec is the arithmetic of
+ * the inversions (fp32 ones get fp64 reliable updates) and of the force sum.
  * force: momentum layout, written (not accumulated). */
 stag_status stag_fermion_force(stag_ctx* ctx, double mass, const stag_rational* r, stag_prec prec,
                                int n_pf, const void* phi, double* force, double tol, int max_iter,
@@ -160,6 +161,23 @@ stag_status stag_gauge_force(stag_ctx* ctx, double beta, double* force);
 
 /* Mean plaquette <Re tr U_P / 3> in fp64 (synchronous). */
 stag_status stag_plaquette(stag_ctx* ctx, double* plaq);
+
+/* ---- random draws: counter-based Philox4x64-10 (Salmon et al., SC'11) ----
+ * Block (key = (seed, stream), counter = (index, counter, 0, 0)) gives four
+ * uniforms u = ((w >> 11) + 1/2) 2^-53 and, by Box-Muller on (u0, u1) and
+ * (u2, u3), four normals sqrt(-2 ln u0) (cos 2 pi u1, sin 2 pi u1), ...
+ * Momenta (stream 1): link (mu, s), s lexicographic, uses blocks
+ *   2 (mu V + s) + j, j = 0, 1, for p_{4j..4j+3}; output in momentum layout.
+ * Sources (stream 0x100 + stream + k for source k): even site h uses blocks
+ *   2h + j; normals 0..5 times sqrt(1/2) are (Re, Im) of colours 0..2, so the
+ *   density is exp(-xi^dag xi).  Output [n][3][Vh] fp64 complex.
+ * The trajectory draws its momenta with seed/counter of stag_hmc and the
+ * sources of flavour f with stream 16 f; the Metropolis uniform is word 0
+ * of block (seed, stream 3, index 0, counter). */
+stag_status stag_draw_momenta(stag_ctx* ctx, unsigned long long seed, unsigned long long counter,
+                              double* mom);
+stag_status stag_draw_sources(stag_ctx* ctx, unsigned long long seed, unsigned long long counter,
+                              int stream, int n, void* xi);
 
 /* ---- the RHMC trajectory (Sec. 2, Sec. 4) -------------------------------- */
 
@@ -189,6 +207,8 @@ typedef struct {
     unsigned long long counter; /* trajectory counter (Philox counter words 1-2) */
     const double* ext_mom;      /* optional DEVICE momenta (momentum layout) instead of drawn ones */
     const void* ext_xi;         /* optional DEVICE sources, [flavour][pf][3][Vh] fp64 complex */
+    const void* ext_phi;        /* optional DEVICE pseudo-fermions (same layout) used instead of
+                                   the heatbath; H at the start then uses phi^dag r_met(A) phi */
     double ext_uniform;         /* used for the accept test when ext_mom is set */
     int no_metropolis;          /* 1: always keep the new field (tests, reversibility) */
     int flip_momenta;           /* 1: start from -P (reversibility test) */

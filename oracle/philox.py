@@ -51,3 +51,28 @@ def gaussians4(seed, stream, index, counter):
     r1 = np.sqrt(-2.0 * np.log(u[2]))
     return [r0 * np.cos(2 * np.pi * u[1]), r0 * np.sin(2 * np.pi * u[1]),
             r1 * np.cos(2 * np.pi * u[3]), r1 * np.sin(2 * np.pi * u[3])]
+
+
+def draw_momenta(dims, seed, counter):
+    """Momenta [4, t, z, y, x, 8]: link (mu, s) with s lexicographic takes the
+    normals of blocks 2 (mu V + s) + j, j = 0, 1, as p_{4j..4j+3} (stream 1)."""
+    Lx, Ly, Lz, Lt = dims
+    V = Lx * Ly * Lz * Lt
+    out = np.empty((4, V, 8))
+    for mu in range(4):
+        for s in range(V):
+            for j in range(2):
+                out[mu, s, 4 * j:4 * j + 4] = gaussians4(seed, 1, 2 * (mu * V + s) + j, counter)
+    return out.reshape(4, Lt, Lz, Ly, Lx, 8)
+
+
+def draw_source_half(vh, seed, counter, stream):
+    """One source on the even sites in half-lattice order [3, Vh]: site h takes
+    the first six normals of blocks 2h and 2h + 1, times sqrt(1/2), as
+    (Re, Im) of colours 0..2 (stream 0x100 + stream)."""
+    out = np.empty((3, vh), dtype=complex)
+    for h in range(vh):
+        g = gaussians4(seed, 0x100 + stream, 2 * h, counter) + gaussians4(seed, 0x100 + stream, 2 * h + 1, counter)
+        for c in range(3):
+            out[c, h] = np.sqrt(0.5) * (g[2 * c] + 1j * g[2 * c + 1])
+    return out

@@ -10,6 +10,7 @@ stag_status cuda_fail(stag_ctx* c, cudaError_t e, const char* where) {
     if (c) {
         c->last_err = std::string(where) + ": " + cudaGetErrorString(e);
     }
+    cudaGetLastError();   // a non-sticky error must not leak into the next call
     return STAG_ERR_CUDA;
 }
 

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -27,6 +28,7 @@ enum WsSlot {
     WS_B32, WS_X32,    // multishift API: fp32 copy of b, fp32 iteration solutions
     WS_REF_G, WS_REF_AX, WS_REF_T, WS_REF_R64, WS_REF_B32, WS_REF_E32, WS_REF_E64,  // refinement
     WS_FORCE_X64,      // fermion force: fp64 accumulation of the mixed solutions
+    WS_FORCE_B32,      // fermion force: fp32 copy of phi
     WS_COUNT
 };
 
@@ -98,9 +100,10 @@ stag_status ms_core(stag_ctx* ctx, double mass, int nshift, const double* shifts
                     bool reliable, bool finish_to_f64, MsStats* stats);
 
 // force.cu
-stag_status fermion_force_from_solutions(stag_ctx* ctx, stag_prec prec, int n_pf, int nshift, const double* alpha,
-                                         const void* x, double* force, double coef, int accumulate);
-stag_status gauge_force_launch(stag_ctx* ctx, double beta, double* force, double coef, int accumulate);
+// force kernels write out = coef F (mode 0) or add out += coef F (mode 1)
+stag_status fermion_force_from_solutions(stag_ctx* ctx, stag_prec prec, int nsrc, int nshift, const double* alpha,
+                                         const void* x, const void* y, double* out, double coef, int mode);
+stag_status gauge_force_launch(stag_ctx* ctx, stag_prec prec, double beta, double* out, double coef, int mode);
 stag_status update_links(stag_ctx* ctx, const double* mom, double eps, stag_prec prec);
 stag_status reunitarize(stag_ctx* ctx);
 stag_status plaquette_sum(stag_ctx* ctx, double* out_host);

@@ -51,7 +51,7 @@ class stag_hmc(C.Structure):
                 ("n_flavours", C.c_int), ("flavour", stag_flavour * STAG_MAX_FLAVOURS),
                 ("tol_md", C.c_double), ("tol_met", C.c_double), ("max_iter", C.c_int),
                 ("md_prec", C.c_int), ("seed", C.c_ulonglong), ("counter", C.c_ulonglong),
-                ("ext_mom", C.c_void_p), ("ext_xi", C.c_void_p), ("ext_uniform", C.c_double),
+                ("ext_mom", C.c_void_p), ("ext_xi", C.c_void_p), ("ext_phi", C.c_void_p), ("ext_uniform", C.c_double),
                 ("no_metropolis", C.c_int), ("flip_momenta", C.c_int)]
 
 
@@ -92,6 +92,8 @@ def lib():
             "stag_plaquette": ([vp, C.POINTER(d)], i),
             "stag_md_trajectory": ([vp, C.POINTER(stag_hmc), C.POINTER(stag_traj)], i),
             "stag_momenta": ([vp], vp),
+            "stag_draw_momenta": ([vp, C.c_ulonglong, C.c_ulonglong, vp], i),
+            "stag_draw_sources": ([vp, C.c_ulonglong, C.c_ulonglong, i, i, vp], i),
         }
         for name, (args, res) in sig.items():
             if not hasattr(L, name):
@@ -223,3 +225,12 @@ def stag_md_trajectory(ctx, hmc):
 
 def stag_momenta(ctx):
     return lib().stag_momenta(ctx)
+
+
+def stag_draw_momenta(ctx, seed, counter, mom):
+    _check(lib().stag_draw_momenta(ctx, int(seed), int(counter), _ptr(mom)), "stag_draw_momenta", ctx)
+
+
+def stag_draw_sources(ctx, seed, counter, stream, n, xi):
+    _check(lib().stag_draw_sources(ctx, int(seed), int(counter), int(stream), int(n), _ptr(xi)),
+           "stag_draw_sources", ctx)

@@ -1,0 +1,60 @@
+"""Writes tests/golden/rationals.json: the RHMC rational approximations of the
+workloads, computed by the oracle's Remez (oracle/rational.py) and nothing
+else.  Run:  python tests/golden/make_rationals.py
+
+Each entry: r(x) = a0 + sum_i alpha_i / (x + beta_i) ~ x^(-s) on [lo, hi] with
+its relative minimax error.  Exponents per pseudo-fermion s = N_f / (4 n_pf)
+(MD and Metropolis) and -s/2 (heatbath, r_hb ~ x^(+s/2)); ranges
+[m^2, 16 + m^2], the spectrum bound of A = m^2 - D_eo D_oe.
+"""
+import json
+import os
+import sys
+import time
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__)))))
+from oracle.rational import remez  # noqa: E402
+
+# name: (s, m, n)
+TABLE = {
+    # 4^4, m = 0.1, N_f = 1, one pseudo-fermion: 8-pole MD rational of x^(-1/4)
+    "c1_md": (0.25, 0.1, 8),
+    "c1_met": (0.25, 0.1, 16),
+    "c1_hb": (-0.125, 0.1, 16),
+    # 16^4 and 24^4, m = 0.02, N_f = 2: 12-pole MD rational of x^(-1/2)
+    "c2_md": (0.5, 0.02, 12),
+    "c2_met": (0.5, 0.02, 24),
+    "c2_hb": (-0.25, 0.02, 24),
+    # 32^3x8, N_f = 2+1, two pseudo-fermions per flavour, 15 MD poles
+    "c3_light_md": (0.25, 0.01, 15),
+    "c3_light_met": (0.25, 0.01, 24),
+    "c3_light_hb": (-0.125, 0.01, 24),
+    "c3_strange_md": (0.125, 0.1, 15),
+    "c3_strange_met": (0.125, 0.1, 18),
+    "c3_strange_hb": (-0.0625, 0.1, 18),
+    # chains, m = 0.05, N_f = 2, 12 poles
+    "c4_md": (0.5, 0.05, 12),
+    "c4_met": (0.5, 0.05, 20),
+    "c4_hb": (-0.25, 0.05, 20),
+}
+
+
+def main(names=None):
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "rationals.json")
+    out = json.load(open(path)) if os.path.exists(path) else {}
+    for name, (s, m, n) in TABLE.items():
+        if names and name not in names:
+            continue
+        if name in out and out[name]["n"] == n:
+            continue
+        t = time.time()
+        r = remez(s, m * m, 16 + m * m, n, dps=60 if n <= 16 else 100)
+        d = r.as_dict()
+        d["mass"] = m
+        out[name] = d
+        print(f"{name}: n={n} err={r.err:.3e} ({time.time() - t:.0f}s)", flush=True)
+        json.dump(out, open(path, "w"), indent=1)
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:] or None)

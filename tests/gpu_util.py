@@ -25,3 +25,11 @@ def host_complex(t):
     if a.dtype == np.float64:
         return a.view(np.complex128)
     return a.view(np.complex64).astype(np.complex128)
+
+
+def wrap_device(torch, ptr, numel):
+    """A float64 CUDA tensor viewing `numel` doubles at device address ptr."""
+    class _Wrap:
+        __cuda_array_interface__ = {"shape": (int(numel),), "typestr": "<f8", "data": (int(ptr), False),
+                                    "version": 3}
+    return torch.as_tensor(_Wrap(), device="cuda")

@@ -1,0 +1,153 @@
+"""GPU parity of the whole RHMC trajectory (paper Sec. 2 and Sec. 4) against
+the FP64 oracle on the 4^4 workload (supplied momenta and sources), FP32
+reversibility (Sec. 4 reports ~5e-6 per degree of freedom), Metropolis
+rejection restoring the field."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import synthetic as syn
+from oracle import integrator, lattice as lat
+from oracle.rational import Rational
+from tests import layout as L
+from tests.gpu_util import dev, host_complex, torch_cuda, wrap_device
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "rationals.json")
+DIMS = (4, 4, 4, 4)
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return torch_cuda()
+
+
+def _rat(d):
+    return Rational(d["s"], d["lo"], d["hi"], d["a0"], d["alpha"], d["beta"], d["err"])
+
+
+@pytest.fixture(scope="module")
+def c1():
+    g = json.load(open(GOLDEN))
+    return {k: g["c1_" + k] for k in ("md", "met", "hb")}
+
+
+def _hmc(stag, c1, prec, n_outer=10, n_gauge=1, tau=1.0, **kw):
+    p = stag.stag_hmc()
+    p.beta, p.tau, p.n_outer, p.n_gauge = 5.5, tau, n_outer, n_gauge
+    p.n_flavours = 1
+    fl = p.flavour[0]
+    fl.mass, fl.n_pf = 0.1, 1
+    fl.hb = stag.make_rational(c1["hb"]["a0"], c1["hb"]["alpha"], c1["hb"]["beta"])
+    fl.md = stag.make_rational(c1["md"]["a0"], c1["md"]["alpha"], c1["md"]["beta"])
+    fl.met = stag.make_rational(c1["met"]["a0"], c1["met"]["alpha"], c1["met"]["beta"])
+    p.tol_md = 1e-12 if prec == 0 else 1e-8
+    p.tol_met = 1e-12
+    p.max_iter = 20000
+    p.md_prec = prec
+    p.seed, p.counter = 0x5A0001, 0
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+@pytest.fixture(scope="module")
+def oracle_traj(c1):
+    u0 = syn.near_identity_gauge(DIMS, 0x5A0001)
+    mom0 = syn.gaussian_momenta(DIMS, 101)
+    xi = syn.gaussian_fermion(DIMS, 102, on_parity=0)
+    fl = integrator.Flavour(mass=0.1, hb=_rat(c1["hb"]), md=_rat(c1["md"]), met=_rat(c1["met"]))
+    prm = integrator.HMCParams(dims=DIMS, beta=5.5, tau=1.0, n_outer=10, n_gauge=1, flavours=[fl],
+                               tol_md=1e-13, tol_met=1e-13)
+    out = integrator.trajectory(integrator.Context(prm), u0, mom0, [[xi]])
+    return u0, mom0, xi, out
+
+
+@pytest.mark.parametrize("prec,tol_dh,tol_u", [(0, 1e-7, 1e-10), (1, 2e-3, 1e-5), (2, 2e-3, 1e-5)])
+def test_trajectory_matches_oracle(torch, c1, oracle_traj, prec, tol_dh, tol_u):
+    from paper_1010_5433_gb300 import stag
+    u0, mom0, xi, want = oracle_traj
+    ctx = stag.stag_create(DIMS, True)
+    try:
+        stag.stag_load_gauge(ctx, L.gauge_host(u0))
+        d_mom = torch.from_numpy(L.mom_to_abi(mom0, DIMS)).cuda()
+        d_xi = dev(torch, L.to_half(xi, DIMS, 0)[None])
+        p = _hmc(stag, c1, prec, ext_mom=d_mom.data_ptr(), ext_xi=d_xi.data_ptr(), ext_uniform=0.5,
+                 no_metropolis=1)
+        res = stag.stag_md_trajectory(ctx, p)
+        buf = np.empty(4 * 256 * 18)
+        stag.stag_store_gauge(ctx, buf)
+        u1 = L.gauge_from_host(buf, DIMS)
+        assert abs(res.H0 - want["H0"]) < 1e-8 * abs(want["H0"])
+        assert abs(res.dH - want["dH"]) < tol_dh, (res.dH, want["dH"])
+        assert np.abs(u1 - want["u"]).max() < tol_u
+        print(f"prec {prec}: dH gpu {res.dH:.8f} oracle {want['dH']:.8f}  max|dU| {np.abs(u1 - want['u']).max():.2e}"
+              f"  iters {res.cg_iterations}")
+    finally:
+        stag.stag_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec,bound", [(0, 1e-12), (1, 5e-5)])
+def test_reversibility(torch, c1, prec, bound):
+    """Forward trajectory, flip the momenta, integrate back with the same
+    pseudo-fermion field; violation per degree of freedom (rms over the
+    18 reals of every link)."""
+    from paper_1010_5433_gb300 import stag
+    u0 = syn.near_identity_gauge(DIMS, 0x5A0001)
+    ctx = stag.stag_create(DIMS, True)
+    try:
+        stag.stag_load_gauge(ctx, L.gauge_host(u0))
+        d_mom = torch.from_numpy(L.mom_to_abi(syn.gaussian_momenta(DIMS, 7), DIMS)).cuda()
+        d_phi = dev(torch, L.to_half(syn.gaussian_fermion(DIMS, 8, on_parity=0), DIMS, 0)[None])
+        p = _hmc(stag, c1, prec, ext_mom=d_mom.data_ptr(), ext_phi=d_phi.data_ptr(), no_metropolis=1)
+        r1 = stag.stag_md_trajectory(ctx, p)
+        tmp = wrap_device(torch, stag.stag_momenta(ctx), d_mom.numel()).clone().view_as(d_mom)
+        p2 = _hmc(stag, c1, prec, ext_mom=tmp.data_ptr(), ext_phi=d_phi.data_ptr(), no_metropolis=1, flip_momenta=1)
+        r2 = stag.stag_md_trajectory(ctx, p2)
+        buf = np.empty(4 * 256 * 18)
+        stag.stag_store_gauge(ctx, buf)
+        u2 = L.gauge_from_host(buf, DIMS)
+        viol = np.sqrt(np.mean(np.abs(u2 - u0) ** 2 * 0.5))
+        print(f"prec {prec}: reversibility violation per dof {viol:.3e}; dH fwd {r1.dH:.3e} back {r2.dH:.3e}")
+        assert viol < bound
+        assert abs(r1.dH + r2.dH) < (1e-9 if prec == 0 else 1e-2)
+    finally:
+        stag.stag_destroy(ctx)
+
+
+def test_metropolis_reject_restores_field(torch, c1):
+    from paper_1010_5433_gb300 import stag
+    u0 = syn.near_identity_gauge(DIMS, 0x5A0001)
+    ctx = stag.stag_create(DIMS, True)
+    try:
+        stag.stag_load_gauge(ctx, L.gauge_host(u0))
+        d_mom = torch.from_numpy(3.0 * L.mom_to_abi(syn.gaussian_momenta(DIMS, 9), DIMS)).cuda()
+        d_xi = dev(torch, L.to_half(syn.gaussian_fermion(DIMS, 10, on_parity=0), DIMS, 0)[None])
+        p = _hmc(stag, c1, 1, n_outer=2, ext_mom=d_mom.data_ptr(), ext_xi=d_xi.data_ptr(), ext_uniform=1.0 - 1e-16)
+        res = stag.stag_md_trajectory(ctx, p)
+        buf = np.empty(4 * 256 * 18)
+        stag.stag_store_gauge(ctx, buf)
+        if res.dH > 0:
+            assert res.accepted == 0
+            assert np.abs(L.gauge_from_host(buf, DIMS) - u0).max() < 1e-14
+    finally:
+        stag.stag_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_drawn_trajectory_runs_and_is_reproducible(torch, c1, prec):
+    """Two runs from the same seed and counter give the same dH bit for bit."""
+    from paper_1010_5433_gb300 import stag
+    u0 = syn.near_identity_gauge(DIMS, 0x5A0001)
+    out = []
+    for _ in range(2):
+        ctx = stag.stag_create(DIMS, True)
+        try:
+            stag.stag_load_gauge(ctx, L.gauge_host(u0))
+            out.append(stag.stag_md_trajectory(ctx, _hmc(stag, c1, prec, counter=5)))
+        finally:
+            stag.stag_destroy(ctx)
+    assert out[0].dH == out[1].dH and out[0].accepted == out[1].accepted
+    assert abs(out[0].dH) < 1.0

@@ -230,6 +230,28 @@ stag_status stag_md_trajectory(stag_ctx* ctx, const stag_hmc* p, stag_traj* out)
 /* Momenta of the last trajectory (device, momentum layout, read-only). */
 const double* stag_momenta(stag_ctx* ctx);
 
+/* ---- measurement (no counterpart in the paper; used for the roofline) ---- */
+
+/* Kernels of the multi-shift iteration, timed by sampling. */
+#define STAG_PK_DSLASH_OE 0      /* t = D_oe p, multi-RHS                        */
+#define STAG_PK_DSLASH_EO_A 1    /* q = c0 p - D_eo t with the (p, q) reduction  */
+#define STAG_PK_RUPDATE 2        /* r -= alpha q with the (r, r) reduction       */
+#define STAG_PK_SHIFT_UPDATE 3   /* x_i, p_i of the live shifts, p               */
+typedef struct {
+    long long launches;       /* launches of this kernel since stag_profile_begin */
+    int sampled;              /* of which bracketed by CUDA events on the context's stream */
+    double sampled_ms;        /* summed device time of the sampled launches */
+    double bytes_per_launch;  /* algorithmic DRAM bytes per launch, averaged over all launches:
+                                 links once + every spinor read/written once */
+} stag_kernel_profile;
+/* Start counting; every sample_every-th solver iteration records events
+ * around its four kernels (0 stops sampling). */
+stag_status stag_profile_begin(stag_ctx* ctx, int sample_every);
+/* Synchronises the stream and reports kernel `kind` (STAG_PK_*). */
+stag_status stag_profile_read(stag_ctx* ctx, int kind, stag_kernel_profile* out);
+/* Number of kernels this context has launched since its creation. */
+long long stag_launch_count(stag_ctx* ctx);
+
 #ifdef __cplusplus
 }
 #endif

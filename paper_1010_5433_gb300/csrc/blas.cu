@@ -82,14 +82,14 @@ stag_status blas_norm2(stag_ctx* ctx, stag_prec prec, int nrhs, const void* v, d
     dim3 grid(nblocks(ctx->g.Vh, BB), nrhs);
     if (prec == STAG_FP64) k_norm2<double><<<grid, BB, 0, ctx->stream>>>(ctx->g.Vh, (const double2*)v, ctx->red);
     else k_norm2<float><<<grid, BB, 0, ctx->stream>>>(ctx->g.Vh, (const float2*)v, ctx->red);
-    CK(cudaGetLastError());
+    CKL();
     return fetch_sums(ctx, nrhs, grid.x, out_host);
 }
 
 stag_status blas_dot_re(stag_ctx* ctx, int nrhs, const double2* a, const double2* b, double* out_host) {
     dim3 grid(nblocks(ctx->g.Vh, BB), nrhs);
     k_dot_re<<<grid, BB, 0, ctx->stream>>>(ctx->g.Vh, a, b, ctx->red);
-    CK(cudaGetLastError());
+    CKL();
     return fetch_sums(ctx, nrhs, grid.x, out_host);
 }
 
@@ -101,7 +101,7 @@ stag_status blas_combine(stag_ctx* ctx, int nrhs, double a0, const double2* phi,
     CK(cudaMemcpyAsync(ctx->scal, ctx->scal_host, nshift * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     dim3 grid(nblocks(ctx->g.Vh, BB), nrhs);
     k_combine<<<grid, BB, 0, ctx->stream>>>(ctx->g.Vh, nshift, a0, phi, ctx->scal, x, out);
-    CK(cudaGetLastError());
+    CKL();
     // the pinned coefficients must not be rewritten before the copy ran
     CK(cudaStreamSynchronize(ctx->stream));
     return STAG_OK;
@@ -110,6 +110,6 @@ stag_status blas_combine(stag_ctx* ctx, int nrhs, double a0, const double2* phi,
 stag_status blas_convert(stag_ctx* ctx, size_t n, const void* src, int sd, void* dst, int dd) {
     if (n == 0) return STAG_OK;
     k_convert<<<nblocks((long long)n, 256), 256, 0, ctx->stream>>>(n, src, sd, dst, dd);
-    CK(cudaGetLastError());
+    CKL();
     return STAG_OK;
 }

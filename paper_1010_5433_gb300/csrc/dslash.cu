@@ -16,7 +16,7 @@ static stag_status launch_t(stag_ctx* ctx, int out_par, int nrhs, const void* in
         case 2: k_dslash<R, FMT, 2, Epi><<<(int)grid, bs, 0, ctx->stream>>>(ctx->g, out_par, L, vin, nrhs, nchunk, epi); break;
         default: k_dslash<R, FMT, 1, Epi><<<(int)grid, bs, 0, ctx->stream>>>(ctx->g, out_par, L, vin, nrhs, nchunk, epi); break;
     }
-    CK(cudaGetLastError());
+    CKL();
     return STAG_OK;
 }
 

@@ -411,7 +411,7 @@ stag_status fermion_force_from_solutions(stag_ctx* ctx, stag_prec prec, int nsrc
     else
         k_fermion_force<float, FMT_F32_18><<<nblocks(n, FB), FB, 0, ctx->stream>>>(
             ctx->g, L, nsrc, nshift, ctx->scal, (const float2*)x, (const float2*)y, out, coef, mode);
-    CK(cudaGetLastError());
+    CKL();
     CK(cudaStreamSynchronize(ctx->stream));   // pinned coefficients are reused by the next call
     return STAG_OK;
 }
@@ -423,7 +423,7 @@ stag_status gauge_force_launch(stag_ctx* ctx, stag_prec prec, double beta, doubl
         k_gauge_force<double, FMT_F64><<<nblocks(n, FB), FB, 0, ctx->stream>>>(ctx->g, L, beta, out, coef, mode);
     else
         k_gauge_force<float, FMT_F32_18><<<nblocks(n, FB), FB, 0, ctx->stream>>>(ctx->g, L, beta, out, coef, mode);
-    CK(cudaGetLastError());
+    CKL();
     return STAG_OK;
 }
 
@@ -435,7 +435,7 @@ stag_status update_links(stag_ctx* ctx, const double* mom, double eps, stag_prec
     else
         k_update_links<float, FMT_F32_18, 8><<<nblocks(n, FB), FB, 0, ctx->stream>>>(ctx->g, ctx->ghi, ctx->glo, mom,
                                                                                      eps);
-    CK(cudaGetLastError());
+    CKL();
     ctx->b16_stale = true;
     return STAG_OK;
 }
@@ -443,7 +443,7 @@ stag_status update_links(stag_ctx* ctx, const double* mom, double eps, stag_prec
 stag_status reunitarize(stag_ctx* ctx) {
     long long n = 8LL * ctx->g.Vh;
     k_reunitarize<<<nblocks(n, FB), FB, 0, ctx->stream>>>(ctx->g, ctx->ghi, ctx->glo);
-    CK(cudaGetLastError());
+    CKL();
     ctx->b16_stale = true;
     return STAG_OK;
 }
@@ -452,7 +452,7 @@ stag_status plaquette_sum(stag_ctx* ctx, double* out) {
     long long n = 2LL * ctx->g.Vh;
     int nb = nblocks(n, FB);
     k_plaquette<<<nb, FB, 0, ctx->stream>>>(ctx->g, link_ptrs(ctx), ctx->red);
-    CK(cudaGetLastError());
+    CKL();
     return sum_partials(ctx, nb, out);
 }
 
@@ -460,7 +460,7 @@ stag_status kinetic_sum(stag_ctx* ctx, const double* mom, double* out) {
     size_t n = (size_t)64 * ctx->g.Vh;
     int nb = 1024;
     k_sumsq<<<nb, 256, 0, ctx->stream>>>(n, mom, ctx->red);
-    CK(cudaGetLastError());
+    CKL();
     double s;
     CKS(sum_partials(ctx, nb, &s));
     *out = 0.5 * s;
@@ -470,14 +470,14 @@ stag_status kinetic_sum(stag_ctx* ctx, const double* mom, double* out) {
 stag_status mom_axpy(stag_ctx* ctx, double* mom, const double* f, double c) {
     size_t n = (size_t)64 * ctx->g.Vh;
     k_axpy_mom<<<nblocks((long long)n, 256), 256, 0, ctx->stream>>>(n, mom, f, c);
-    CK(cudaGetLastError());
+    CKL();
     return STAG_OK;
 }
 
 stag_status draw_momenta(stag_ctx* ctx, double* mom, unsigned long long seed, unsigned long long counter) {
     long long n = 4LL * ctx->g.V;
     k_draw_momenta<<<nblocks(n, 128), 128, 0, ctx->stream>>>(ctx->g, mom, seed, counter);
-    CK(cudaGetLastError());
+    CKL();
     return STAG_OK;
 }
 
@@ -486,7 +486,7 @@ stag_status draw_sources(stag_ctx* ctx, double2* xi, int n, unsigned long long s
     long long m = (long long)n * ctx->g.Vh;
     k_draw_sources<<<nblocks(m, 128), 128, 0, ctx->stream>>>(ctx->g, xi, n, seed, counter,
                                                               RNG_STREAM_SOURCES + (uint64_t)stream_base);
-    CK(cudaGetLastError());
+    CKL();
     return STAG_OK;
 }
 

@@ -76,7 +76,7 @@ __global__ void k_make_bf16(Geom g, const float* __restrict__ hi, uint16_t* b16)
 stag_status refresh_bf16(stag_ctx* ctx) {
     long long n = 4LL * ctx->g.V;
     k_make_bf16<<<nblocks(n, 256), 256, 0, ctx->stream>>>(ctx->g, ctx->ghi, ctx->g16);
-    CK(cudaGetLastError());
+    CKL();
     ctx->b16_stale = false;
     return STAG_OK;
 }
@@ -91,7 +91,7 @@ stag_status gauge_copy(stag_ctx* ctx, float* dh, float* dl, const float* sh, con
 static stag_status pack_from_device(stag_ctx* ctx, const double* dev_u) {
     long long n = 4LL * ctx->g.V;
     k_pack_gauge<<<nblocks(n, 128), 128, 0, ctx->stream>>>(ctx->g, dev_u, ctx->ghi, ctx->glo);
-    CK(cudaGetLastError());
+    CKL();
     ctx->has_gauge = true;
     return refresh_bf16(ctx);
 }
@@ -120,7 +120,7 @@ extern "C" stag_status stag_store_gauge(stag_ctx* ctx, double* host_u) {
     CKS(ws_get(ctx, WS_STAGE, bytes, &stage));
     long long n = 4LL * ctx->g.V;
     k_unpack_gauge<<<nblocks(n, 128), 128, 0, ctx->stream>>>(ctx->g, ctx->ghi, ctx->glo, (double*)stage);
-    CK(cudaGetLastError());
+    CKL();
     CK(cudaMemcpyAsync(host_u, stage, bytes, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return STAG_OK;

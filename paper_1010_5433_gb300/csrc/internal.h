@@ -32,6 +32,19 @@ enum WsSlot {
     WS_COUNT
 };
 
+// Sampled CUDA-event timing of the solver kernels (stag_profile_*).
+enum ProfKind { PK_DSLASH_OE = 0, PK_DSLASH_EO_A, PK_RUPDATE, PK_SHIFT_UPDATE, PK_COUNT };
+struct ProfData {
+    bool on = false;
+    int every = 16;
+    long long iter = 0;                          // solver iterations launched while on
+    std::vector<cudaEvent_t> pool;               // created lazily, reused
+    size_t used = 0;
+    std::vector<std::pair<int, int>> marks[PK_COUNT];
+    double bytes_total[PK_COUNT] = {};           // algorithmic bytes over all launches
+    long long launches[PK_COUNT] = {};
+};
+
 struct stag_ctx {
     Geom g;
     cudaStream_t stream = nullptr;
@@ -52,7 +65,20 @@ struct stag_ctx {
     size_t ws_bytes[WS_COUNT] = {};
     std::string last_err;
     size_t dev_bytes = 0;
+    long long launches = 0;           // kernels launched by this context
+    ProfData prof;
 };
+
+// a single kernel launch: count it and check the launch
+#define CKL()                                   \
+    do {                                        \
+        ++ctx->launches;                        \
+        CK(cudaGetLastError());                 \
+    } while (0)
+// bytes of the eight links of one site in a Dslash of this precision
+inline double link_bytes_site(stag_prec p) {
+    return p == STAG_FP64 ? 1152.0 : p == STAG_FP32 ? 576.0 : p == STAG_FP32_12 ? 384.0 : 192.0;
+}
 
 // error plumbing
 stag_status cuda_fail(stag_ctx* c, cudaError_t e, const char* where);

@@ -69,6 +69,7 @@ __global__ void k_ms_init(SolverState* st, int Vh, const typename V2T<R>::T* __r
             st->status = STAG_OK;
             st->need_reliable = 0;
             st->n_reliable = 0;
+            st->k4_units = 0.0;
             int any = 0;
             for (int q = 0; q < st->nrhs; ++q) {
                 double bb = sums[q];
@@ -218,6 +219,9 @@ __device__ void ms_beta_step(SolverState* st, const double* rrn) {
                 live_left = 1;
             }
         }
+        int n_act = 0;
+        for (int s2 = 0; s2 < st->nshift; ++s2) n_act += st->active[q][s2];
+        if (n_act) st->k4_units += 72.0 + 96.0 * n_act;
         st->beta[q] = beta;
         st->alpha_prev[q] = st->alpha[q];
         st->beta_prev[q] = beta;
@@ -485,6 +489,19 @@ __global__ void k_f2d(size_t n, const float2* a, double2* b) {
 
 
 // ---------------------------------------------------------------- host driver
+// five consecutive events of the profiling pool (created on first use)
+static stag_status prof_events(stag_ctx* ctx, int* ev) {
+    ProfData& pf = ctx->prof;
+    if (pf.used + 5 > 50000) { pf.on = false; return STAG_OK; }
+    while (pf.pool.size() < pf.used + 5) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        pf.pool.push_back(e);
+    }
+    for (int k = 0; k < 5; ++k) ev[k] = (int)(pf.used + k);
+    pf.used += 5;
+    return STAG_OK;
+}
 template <typename R>
 static stag_status ms_iterations(stag_ctx* ctx, stag_prec prec, int nrhs, int chunk, void* tmp, void* r, void* p,
                                  void* q, void* ps, void* x) {
@@ -498,10 +515,24 @@ static stag_status ms_iterations(stag_ctx* ctx, stag_prec prec, int nrhs, int ch
     LinkPtrs L = link_ptrs(ctx);
     EpiMsOdd<R> e1{(V*)tmp, ctx->st};
     EpiMsA<R> e2{(V*)q, (const V*)p, ctx->st, ctx->red, ctx->counters + 0};
+    ProfData& pf = ctx->prof;
+    const double S = (double)sizeof(V);
     for (int it = 0; it < chunk; ++it) {
+        const bool smp = pf.on && (pf.iter++ % pf.every) == 0;
+        if (pf.on) {
+            pf.bytes_total[PK_DSLASH_OE] += (double)g.Vh * (link_bytes_site(prec) + 2.0 * S * nrhs);
+            pf.bytes_total[PK_DSLASH_EO_A] += (double)g.Vh * (link_bytes_site(prec) + 3.0 * S * nrhs);
+            pf.bytes_total[PK_RUPDATE] += (double)g.Vh * 3.0 * S * nrhs;
+            for (int k = 0; k < PK_COUNT; ++k) pf.launches[k] += 1;
+        }
+        int ev[5];
+        if (smp) CKS(prof_events(ctx, ev));
 #define MS_LAUNCH(FMT_, NR_)                                                                                         \
+    if (smp) CK(cudaEventRecord(pf.pool[ev[0]], ctx->stream));                                                       \
     k_dslash<R, FMT_, NR_, EpiMsOdd<R>><<<grid_d, bs, 0, ctx->stream>>>(g, 1, L, (const V*)p, nrhs, nchunk, e1);     \
-    k_dslash<R, FMT_, NR_, EpiMsA<R>><<<grid_d, bs, 0, ctx->stream>>>(g, 0, L, (const V*)tmp, nrhs, nchunk, e2);
+    if (smp) CK(cudaEventRecord(pf.pool[ev[1]], ctx->stream));                                                       \
+    k_dslash<R, FMT_, NR_, EpiMsA<R>><<<grid_d, bs, 0, ctx->stream>>>(g, 0, L, (const V*)tmp, nrhs, nchunk, e2);     \
+    if (smp) CK(cudaEventRecord(pf.pool[ev[2]], ctx->stream));
 #define MS_FMT(FMT_)                         \
     switch (nr) {                            \
         case 4: MS_LAUNCH(FMT_, 4) break;    \
@@ -519,8 +550,14 @@ static stag_status ms_iterations(stag_ctx* ctx, stag_prec prec, int nrhs, int ch
 #undef MS_LAUNCH
         k_ms_rupdate<R><<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, (V*)r, (const V*)q, ctx->red,
                                                         ctx->counters + 1);
+        if (smp) CK(cudaEventRecord(pf.pool[ev[3]], ctx->stream));
         k_ms_shift_update<R><<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, (const V*)r, (V*)p, (V*)ps, (V*)x);
+        if (smp) {
+            CK(cudaEventRecord(pf.pool[ev[4]], ctx->stream));
+            for (int k = 0; k < PK_COUNT; ++k) pf.marks[k].push_back({ev[k], ev[k + 1]});
+        }
     }
+    ctx->launches += 4LL * chunk;
     CK(cudaGetLastError());
     return STAG_OK;
 }
@@ -579,7 +616,7 @@ stag_status ms_core(stag_ctx* ctx, double mass, int nshift, const double* shifts
         k_ms_init<double><<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, (const double2*)b, (double2*)r,
                                                           (double2*)p, (double2*)ps, (double2*)x, ctx->red,
                                                           ctx->counters + 2);
-    CK(cudaGetLastError());
+    CKL();
     const int chunk = 16;
     stag_status status = STAG_OK;
     // every chunk either advances k by up to `chunk` or makes a reliable update
@@ -600,6 +637,7 @@ stag_status ms_core(stag_ctx* ctx, double mass, int nshift, const double* shifts
             CKS(launch_apply_a(ctx, hs->c0, STAG_FP64, nrhs, xb64, ax64, t64));
             k_rel_finish<<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, b64, (const double2*)ax64, (float2*)r,
                                                          ctx->red, ctx->counters + 3);
+            ctx->launches += 3;
             CK(cudaGetLastError());
             hs->halt = 0;
             hs->k4_skip = 0;
@@ -611,8 +649,9 @@ stag_status ms_core(stag_ctx* ctx, double mass, int nshift, const double* shifts
     if (mixed && x64) {
         if (finish_to_f64) k_acc_final<<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, x64, (const float2*)x);
         else k_rel_output<<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, x64, (float2*)x);
-        CK(cudaGetLastError());
+        CKL();
     }
+    if (ctx->prof.on) ctx->prof.bytes_total[PK_SHIFT_UPDATE] += hs->k4_units * g.Vh * (mixed ? 1.0 : 2.0);
     if (stats) {
         stats->iterations = hs->k;
         stats->reliable = hs->n_reliable;
@@ -642,6 +681,7 @@ static stag_status shift_residuals(stag_ctx* ctx, double mass, int nshift, int s
     CKS(launch_apply_a(ctx, mass * mass, STAG_FP64, nrhs, gx, ax, t));
     k_residual<<<grid_v, VB, 0, ctx->stream>>>(g.Vh, shift, b, (const double2*)ax, (const double2*)gx,
                                                (double2*)r64, (float2*)r32, ctx->red);
+    ctx->launches += 2;
     CK(cudaGetLastError());
     std::vector<double> part((size_t)2 * nrhs * grid_v.x);
     CK(cudaMemcpyAsync(part.data(), ctx->red, part.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
@@ -693,7 +733,7 @@ static stag_status refine_shifts(stag_ctx* ctx, double mass, int nshift, const d
             *extra_iters += st.iterations;
             *n_reliable += st.reliable;
             k_scatter_add_shift<<<grid_v, VB, 0, ctx->stream>>>(g.Vh, nshift, s, (const double2*)e64, x);
-            CK(cudaGetLastError());
+            CKL();
         }
         final_res[s] = worst;
     }
@@ -724,7 +764,7 @@ static stag_status ms_api_batch(stag_ctx* ctx, double mass, int nshift, const do
         CKS(ws_get(ctx, WS_B32, n * sizeof(float2), &b32));
         CKS(ws_get(ctx, WS_X32, n * nshift * sizeof(float2), &x32));
         k_d2f<<<nblocks((long long)n, 256), 256, 0, ctx->stream>>>(n, b, (float2*)b32);
-        CK(cudaGetLastError());
+        CKL();
         // residual replacement keeps the shifted recurrences consistent only when
         // the iteration operator is the fp32 one; the bf16 operator iterates plainly
         const bool rel = prec != STAG_BF16_12;
@@ -776,3 +816,38 @@ extern "C" stag_status stag_multishift_solve(stag_ctx* ctx, double mass, int nsh
     if (info) *info = acc;
     return worst;
 }
+
+extern "C" stag_status stag_profile_begin(stag_ctx* ctx, int sample_every) {
+    if (!ctx || sample_every < 0) return STAG_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->stream));
+    ProfData& pf = ctx->prof;
+    pf.on = sample_every > 0;
+    pf.every = sample_every > 0 ? sample_every : 1;
+    pf.iter = 0;
+    pf.used = 0;
+    for (int k = 0; k < PK_COUNT; ++k) {
+        pf.marks[k].clear();
+        pf.bytes_total[k] = 0.0;
+        pf.launches[k] = 0;
+    }
+    return STAG_OK;
+}
+
+extern "C" stag_status stag_profile_read(stag_ctx* ctx, int kind, stag_kernel_profile* out) {
+    if (!ctx || !out || kind < 0 || kind >= PK_COUNT) return STAG_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->stream));
+    ProfData& pf = ctx->prof;
+    double ms = 0.0;
+    for (auto& m : pf.marks[kind]) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, pf.pool[m.first], pf.pool[m.second]));
+        ms += t;
+    }
+    out->launches = pf.launches[kind];
+    out->sampled = (int)pf.marks[kind].size();
+    out->sampled_ms = ms;
+    out->bytes_per_launch = pf.launches[kind] ? pf.bytes_total[kind] / pf.launches[kind] : 0.0;
+    return STAG_OK;
+}
+
+extern "C" long long stag_launch_count(stag_ctx* ctx) { return ctx ? ctx->launches : 0; }

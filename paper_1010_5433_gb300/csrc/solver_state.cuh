@@ -21,6 +21,7 @@ struct SolverState {
     int status;                        // stag_status of the solve
     int need_reliable;                 // host must replace the base residual
     int n_reliable;
+    double k4_units;                   // sum over shift updates of (72 + 96 n_active) per rhs (fp32 bytes/site)
     // per source
     int rhs_live[STAG_MAX_RHS];
     double bb[STAG_MAX_RHS], rr[STAG_MAX_RHS], rr_ref[STAG_MAX_RHS];

@@ -55,6 +55,11 @@ class stag_hmc(C.Structure):
                 ("no_metropolis", C.c_int), ("flip_momenta", C.c_int)]
 
 
+class stag_kernel_profile(C.Structure):
+    _fields_ = [("launches", C.c_longlong), ("sampled", C.c_int), ("sampled_ms", C.c_double),
+                ("bytes_per_launch", C.c_double)]
+
+
 class stag_traj(C.Structure):
     _fields_ = [("dH", C.c_double), ("H0", C.c_double), ("H1", C.c_double), ("plaq", C.c_double),
                 ("accepted", C.c_int), ("cg_iterations", C.c_longlong), ("reliable_updates", C.c_int),
@@ -92,6 +97,9 @@ def lib():
             "stag_plaquette": ([vp, C.POINTER(d)], i),
             "stag_md_trajectory": ([vp, C.POINTER(stag_hmc), C.POINTER(stag_traj)], i),
             "stag_momenta": ([vp], vp),
+            "stag_profile_begin": ([vp, i], i),
+            "stag_profile_read": ([vp, i, C.POINTER(stag_kernel_profile)], i),
+            "stag_launch_count": ([vp], C.c_longlong),
             "stag_draw_momenta": ([vp, C.c_ulonglong, C.c_ulonglong, vp], i),
             "stag_draw_sources": ([vp, C.c_ulonglong, C.c_ulonglong, i, i, vp], i),
         }
@@ -234,3 +242,20 @@ def stag_draw_momenta(ctx, seed, counter, mom):
 def stag_draw_sources(ctx, seed, counter, stream, n, xi):
     _check(lib().stag_draw_sources(ctx, int(seed), int(counter), int(stream), int(n), _ptr(xi)),
            "stag_draw_sources", ctx)
+
+
+STAG_PK_DSLASH_OE, STAG_PK_DSLASH_EO_A, STAG_PK_RUPDATE, STAG_PK_SHIFT_UPDATE = 0, 1, 2, 3
+
+
+def stag_profile_begin(ctx, sample_every):
+    _check(lib().stag_profile_begin(ctx, int(sample_every)), "stag_profile_begin", ctx)
+
+
+def stag_profile_read(ctx, kind):
+    out = stag_kernel_profile()
+    _check(lib().stag_profile_read(ctx, int(kind), C.byref(out)), "stag_profile_read", ctx)
+    return out
+
+
+def stag_launch_count(ctx):
+    return lib().stag_launch_count(ctx)

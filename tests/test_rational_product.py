@@ -1,0 +1,52 @@
+"""The library's own Remez (host set-up of the C ABI's rational inputs)
+against the oracle's, whose coefficients tests/golden/make_rationals.py
+wrote: the relative-minimax approximation is unique, so both must agree
+coefficient by coefficient."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_1010_5433_gb300 import rational
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "rationals.json")
+
+
+def _close(r, g, tol):
+    assert r.n == g["n"]
+    np.testing.assert_allclose(r.beta, g["beta"], rtol=tol)
+    np.testing.assert_allclose(r.alpha, g["alpha"], rtol=tol)
+    assert abs(r.a0 - g["a0"]) <= tol * abs(g["a0"])
+    assert abs(r.err - g["err"]) <= 1e-3 * g["err"]
+
+
+@pytest.mark.parametrize("name", ["c1_md", "c2_md", "c4_md"])
+def test_product_remez_matches_oracle(name):
+    g = json.load(open(GOLDEN))[name]
+    s, m, n = rational.WORKLOADS[name]
+    _close(rational.remez(s, m * m, 16 + m * m, n), g, 1e-9)
+
+
+def test_shipped_table_matches_oracle():
+    if not os.path.exists(rational.TABLE_PATH):
+        pytest.skip("no shipped table")
+    tab = json.load(open(rational.TABLE_PATH))
+    gold = json.load(open(GOLDEN))
+    common = [k for k in tab if k in gold]
+    assert common
+    for k in common:
+        _close(rational.load(k), gold[k], 1e-8)
+
+
+def test_positivity_and_heatbath_inverse():
+    """x^(-s) approximations have alpha_i, beta_i > 0; r_hb(x)^2 r_met(x) = 1
+    within the two approximation errors."""
+    tab = json.load(open(GOLDEN))
+    for k in ("c1_md", "c1_met", "c2_md"):
+        assert min(tab[k]["alpha"]) > 0 and min(tab[k]["beta"]) > 0
+    hb, met = tab["c1_hb"], tab["c1_met"]
+    x = np.geomspace(hb["lo"], hb["hi"], 2001)
+    rh = hb["a0"] + sum(a / (x + b) for a, b in zip(hb["alpha"], hb["beta"]))
+    rm = met["a0"] + sum(a / (x + b) for a, b in zip(met["alpha"], met["beta"]))
+    assert np.abs(rh * rh * rm - 1).max() < 3 * (2 * hb["err"] + met["err"]) + 1e-15

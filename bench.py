@@ -172,12 +172,14 @@ def run_gpu(args, rank, world, local_rank):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         with ClockSampler(local_rank) as clk:
+            torch.cuda.nvtx.range_push(f"timed_{'fp64' if prec == 0 else 'mixed'}")
             e0.record(stream)
             for k in range(steps):
                 flush.zero_()                 # inputs fit in L2: flush between trajectories
                 trajs.append(stag.stag_md_trajectory(ctx, make_hmc(stag, rats, prec, seed, counter0 + k)))
             e1.record(stream)
             torch.cuda.synchronize()
+            torch.cuda.nvtx.range_pop()
         if world > 1:
             torch.distributed.barrier()
         ms = e0.elapsed_time(e1)
@@ -239,7 +241,7 @@ def run_gpu(args, rank, world, local_rank):
                         "event-timed launch duration (sampled every 8th solver iteration)",
                 "kernels": kern}
 
-    point = dslash_roofline_point(torch, stag, dev, stream, hbm) if rank == 0 else None
+    point = dslash_roofline_point(hbm) if rank == 0 else None
     stag.stag_destroy(ctx)
 
     dh = [t.dH for t in trajs]
@@ -272,46 +274,11 @@ def run_gpu(args, rank, world, local_rank):
     return out
 
 
-def dslash_roofline_point(torch, stag, dev, stream, hbm):
-    """Standalone D_oe at 48^4 (links 382 MB in fp32: larger than L2) in every
-    precision, timed with CUDA events over 20 launches after 3 warm-ups."""
-    dims = ROOFLINE_POINT_DIMS
-    V = int(np.prod(dims))
-    vh = V // 2
-    ctx = stag.stag_create(dims, True, stream.cuda_stream)
-    res = {}
-    try:
-        g = torch.randn(4 * V * 18, dtype=torch.float64, device=dev).mul_(0.05)
-        gv = g.view(4 * V, 9, 2)
-        gv[:, 0, 0] += 1.0
-        gv[:, 4, 0] += 1.0
-        gv[:, 8, 0] += 1.0
-        stag.stag_load_gauge_device(ctx, g)
-        torch.cuda.synchronize()
-        del g, gv
-        link = {0: 1152, 1: 576, 2: 384, 3: 192}
-        for prec, name in [(1, "fp32_18"), (2, "fp32_12"), (3, "bf16_12"), (0, "fp64")]:
-            dt = torch.float64 if prec == 0 else torch.float32
-            s = 48 if prec == 0 else 24
-            inp = torch.randn(3 * 2 * vh, dtype=dt, device=dev)
-            out = torch.empty_like(inp)
-            for _ in range(3):
-                stag.stag_dslash(ctx, 1, prec, 1, inp, out)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for _ in range(20):
-                stag.stag_dslash(ctx, 1, prec, 1, inp, out)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            t = e0.elapsed_time(e1) / 20 * 1e-3
-            gbs = vh * (link[prec] + 2 * s) / t / 1e9
-            res[name] = {"us": round(t * 1e6, 2), "achieved_gbs": round(gbs, 1), "frac": round(gbs / hbm, 4),
-                         "bytes_per_site": link[prec] + 2 * s}
-            del inp, out
-    finally:
-        stag.stag_destroy(ctx)
-    return {"lattice": "48^4", "kernel": "D_oe single RHS", **res}
+def dslash_roofline_point(hbm):
+    """Standalone D_oe at 48^4 (fp32 links 382 MB: larger than L2) in every
+    precision, CUDA-event timed over 20 launches after 3 warm-ups."""
+    from paper_1010_5433_gb300 import dslash_bench
+    return dslash_bench.run(ROOFLINE_POINT_DIMS, (1, 2, 3, 0), 1, 20, hbm)
 
 
 # ---------------------------------------------------------------- CPU baseline (the oracle)

@@ -1,5 +1,6 @@
 // Context management and error plumbing of the C ABI.
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -73,6 +74,7 @@ extern "C" size_t stag_device_bytes(stag_ctx* ctx) { return ctx ? ctx->dev_bytes
 extern "C" void stag_destroy(stag_ctx* ctx) {
     if (!ctx) return;
     cudaStreamSynchronize(ctx->stream);
+    destroy_solver_graphs(ctx);
     for (int i = 0; i < WS_COUNT; ++i)
         if (ctx->ws[i]) cudaFree(ctx->ws[i]);
     if (ctx->ghi) cudaFree(ctx->ghi);
@@ -112,6 +114,10 @@ extern "C" stag_status stag_create(const stag_lattice* lat, stag_ctx** out) {
     ctx->g.Vh = (int)(V / 2);
     ctx->g.apt = lat->t_antiperiodic ? 1 : 0;
     ctx->stream = (cudaStream_t)lat->cuda_stream;
+    // STAG_GRAPHS=0 runs the solver loop as plain launches (same kernels),
+    // e.g. under a profiler that replays single kernels
+    const char* gr = std::getenv("STAG_GRAPHS");
+    ctx->use_graphs = !(gr && gr[0] == '0');
     stag_status s = STAG_OK;
     size_t gbytes = (size_t)4 * 2 * 18 * ctx->g.Vh * sizeof(float);
     size_t bbytes = (size_t)4 * 2 * 12 * ctx->g.Vh * sizeof(uint16_t);

@@ -45,6 +45,14 @@ struct ProfData {
     long long launches[PK_COUNT] = {};
 };
 
+struct SolverGraphEntry {
+    const void* key[8];
+    int prec, nrhs;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+void destroy_solver_graphs(stag_ctx* ctx);
+
 struct stag_ctx {
     Geom g;
     cudaStream_t stream = nullptr;
@@ -67,6 +75,9 @@ struct stag_ctx {
     size_t dev_bytes = 0;
     long long launches = 0;           // kernels launched by this context
     ProfData prof;
+    bool use_graphs = true;           // solver iterations as a device-side WHILE graph
+    cudaStream_t cap_stream = nullptr;
+    std::vector<SolverGraphEntry> graphs;
 };
 
 // a single kernel launch: count it and check the launch

@@ -21,6 +21,7 @@
 // (Sec. 6); replacing the base residual keeps the shifted residuals collinear
 // only approximately, which is why every shift's true residual is reported.
 #include <algorithm>
+#include <cstddef>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -101,7 +102,12 @@ __global__ void k_ms_init(SolverState* st, int Vh, const typename V2T<R>::T* __r
 template <typename R> struct EpiMsOdd {     // K1: t = D_oe p (without the 1/2)
     typename V2T<R>::T* out;
     SolverState* st;
+    cudaGraphConditionalHandle cond;       // loop condition of the solver graph
+    int use_cond;
     __device__ __forceinline__ bool halted() const {
+        // inside the solver graph the loop continues only if the r-update of
+        // this iteration explicitly says so
+        if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0);
         if (*(volatile int*)&st->halt) {
             if (blockIdx.x == 0 && threadIdx.x == 0) st->k4_skip = 1;
             return true;
@@ -239,7 +245,8 @@ __device__ void ms_beta_step(SolverState* st, const double* rrn) {
 template <typename R>
 __global__ void __launch_bounds__(VB) k_ms_rupdate(SolverState* st, int Vh, typename V2T<R>::T* r,
                                                    const typename V2T<R>::T* __restrict__ q, double* partial,
-                                                   unsigned int* counter) {
+                                                   unsigned int* counter, cudaGraphConditionalHandle cond,
+                                                   int use_cond) {
     if (*(volatile int*)&st->halt) return;
     const int rhs = blockIdx.y;
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
@@ -265,7 +272,10 @@ __global__ void __launch_bounds__(VB) k_ms_rupdate(SolverState* st, int Vh, type
             double s = block_sum_array(partial + (size_t)q2 * gridDim.x, gridDim.x);
             if (threadIdx.x == 0) sums[q2] = s;
         }
-        if (threadIdx.x == 0) ms_beta_step(st, sums);
+        if (threadIdx.x == 0) {
+            ms_beta_step(st, sums);
+            if (use_cond) cudaGraphSetConditional(cond, st->halt ? 0u : 1u);
+        }
     }
 }
 
@@ -503,8 +513,9 @@ static stag_status prof_events(stag_ctx* ctx, int* ev) {
     return STAG_OK;
 }
 template <typename R>
-static stag_status ms_iterations(stag_ctx* ctx, stag_prec prec, int nrhs, int chunk, void* tmp, void* r, void* p,
-                                 void* q, void* ps, void* x) {
+static stag_status ms_iterations(stag_ctx* ctx, cudaStream_t stream, stag_prec prec, int nrhs, int chunk, void* tmp,
+                                 void* r, void* p, void* q, void* ps, void* x, bool sample,
+                                 cudaGraphConditionalHandle cond, int use_cond) {
     typedef typename V2T<R>::T V;
     const Geom& g = ctx->g;
     const int bs = 128;
@@ -513,26 +524,19 @@ static stag_status ms_iterations(stag_ctx* ctx, stag_prec prec, int nrhs, int ch
     int grid_d = nblocks(g.Vh, bs) * nchunk;
     dim3 grid_v(nblocks(g.Vh, VB), nrhs);
     LinkPtrs L = link_ptrs(ctx);
-    EpiMsOdd<R> e1{(V*)tmp, ctx->st};
+    EpiMsOdd<R> e1{(V*)tmp, ctx->st, cond, use_cond};
     EpiMsA<R> e2{(V*)q, (const V*)p, ctx->st, ctx->red, ctx->counters + 0};
     ProfData& pf = ctx->prof;
-    const double S = (double)sizeof(V);
     for (int it = 0; it < chunk; ++it) {
-        const bool smp = pf.on && (pf.iter++ % pf.every) == 0;
-        if (pf.on) {
-            pf.bytes_total[PK_DSLASH_OE] += (double)g.Vh * (link_bytes_site(prec) + 2.0 * S * nrhs);
-            pf.bytes_total[PK_DSLASH_EO_A] += (double)g.Vh * (link_bytes_site(prec) + 3.0 * S * nrhs);
-            pf.bytes_total[PK_RUPDATE] += (double)g.Vh * 3.0 * S * nrhs;
-            for (int k = 0; k < PK_COUNT; ++k) pf.launches[k] += 1;
-        }
+        const bool smp = sample && pf.on;
         int ev[5];
         if (smp) CKS(prof_events(ctx, ev));
 #define MS_LAUNCH(FMT_, NR_)                                                                                         \
-    if (smp) CK(cudaEventRecord(pf.pool[ev[0]], ctx->stream));                                                       \
-    k_dslash<R, FMT_, NR_, EpiMsOdd<R>><<<grid_d, bs, 0, ctx->stream>>>(g, 1, L, (const V*)p, nrhs, nchunk, e1);     \
-    if (smp) CK(cudaEventRecord(pf.pool[ev[1]], ctx->stream));                                                       \
-    k_dslash<R, FMT_, NR_, EpiMsA<R>><<<grid_d, bs, 0, ctx->stream>>>(g, 0, L, (const V*)tmp, nrhs, nchunk, e2);     \
-    if (smp) CK(cudaEventRecord(pf.pool[ev[2]], ctx->stream));
+    if (smp) CK(cudaEventRecord(pf.pool[ev[0]], stream));                                                       \
+    k_dslash<R, FMT_, NR_, EpiMsOdd<R>><<<grid_d, bs, 0, stream>>>(g, 1, L, (const V*)p, nrhs, nchunk, e1);     \
+    if (smp) CK(cudaEventRecord(pf.pool[ev[1]], stream));                                                       \
+    k_dslash<R, FMT_, NR_, EpiMsA<R>><<<grid_d, bs, 0, stream>>>(g, 0, L, (const V*)tmp, nrhs, nchunk, e2);     \
+    if (smp) CK(cudaEventRecord(pf.pool[ev[2]], stream));
 #define MS_FMT(FMT_)                         \
     switch (nr) {                            \
         case 4: MS_LAUNCH(FMT_, 4) break;    \
@@ -548,24 +552,94 @@ static stag_status ms_iterations(stag_ctx* ctx, stag_prec prec, int nrhs, int ch
         }
 #undef MS_FMT
 #undef MS_LAUNCH
-        k_ms_rupdate<R><<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, (V*)r, (const V*)q, ctx->red,
-                                                        ctx->counters + 1);
-        if (smp) CK(cudaEventRecord(pf.pool[ev[3]], ctx->stream));
-        k_ms_shift_update<R><<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, (const V*)r, (V*)p, (V*)ps, (V*)x);
+        k_ms_rupdate<R><<<grid_v, VB, 0, stream>>>(ctx->st, g.Vh, (V*)r, (const V*)q, ctx->red,
+                                                   ctx->counters + 1, cond, use_cond);
+        if (smp) CK(cudaEventRecord(pf.pool[ev[3]], stream));
+        k_ms_shift_update<R><<<grid_v, VB, 0, stream>>>(ctx->st, g.Vh, (const V*)r, (V*)p, (V*)ps, (V*)x);
         if (smp) {
-            CK(cudaEventRecord(pf.pool[ev[4]], ctx->stream));
+            CK(cudaEventRecord(pf.pool[ev[4]], stream));
             for (int k = 0; k < PK_COUNT; ++k) pf.marks[k].push_back({ev[k], ev[k + 1]});
         }
     }
-    ctx->launches += 4LL * chunk;
+    if (!use_cond) ctx->launches += 4LL * chunk;
     CK(cudaGetLastError());
     return STAG_OK;
 }
 
 static size_t rsize(stag_prec p) { return p == STAG_FP64 ? sizeof(double) : sizeof(float); }
 
+// One solver iteration as the body of a WHILE conditional node: the graph
+// replays iterations on the device until the r-update's last block stops it
+// (convergence, a due reliable update, max_iter or a NaN), so the host waits
+// once per segment instead of launching four kernels per iteration.
+
+static stag_status solver_graph(stag_ctx* ctx, stag_prec prec, int nrhs, void* tmp, void* r, void* p, void* q,
+                                void* ps, void* x, cudaGraphExec_t* out) {
+    const void* key[8] = {tmp, r, p, q, ps, x, ctx->st, ctx->red};
+    auto& cache = ctx->graphs;
+    for (auto& e : cache) {
+        if (e.prec == (int)prec && e.nrhs == nrhs && std::memcmp(e.key, key, sizeof(key)) == 0) {
+            *out = e.exec;
+            return STAG_OK;
+        }
+    }
+    if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    SolverGraphEntry sg = {};
+    std::memcpy(sg.key, key, sizeof(key));
+    sg.prec = (int)prec;
+    sg.nrhs = nrhs;
+    CK(cudaGraphCreate(&sg.graph, 0));
+    cudaGraphConditionalHandle h;
+    CK(cudaGraphConditionalHandleCreate(&h, sg.graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, sg.graph, nullptr, nullptr, 0, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    CK(cudaStreamBeginCaptureToGraph(ctx->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    stag_status s;
+    if (prec == STAG_FP64) s = ms_iterations<double>(ctx, ctx->cap_stream, prec, nrhs, 1, tmp, r, p, q, ps, x, false, h, 1);
+    else s = ms_iterations<float>(ctx, ctx->cap_stream, prec, nrhs, 1, tmp, r, p, q, ps, x, false, h, 1);
+    cudaGraph_t captured;
+    cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &captured);
+    if (s != STAG_OK) return s;
+    CK(e);
+    CK(cudaGraphInstantiate(&sg.exec, sg.graph, 0));
+    if (cache.size() >= 12) {      // a few live configurations are enough
+        cudaGraphExecDestroy(cache.front().exec);
+        cudaGraphDestroy(cache.front().graph);
+        cache.erase(cache.begin());
+    }
+    cache.push_back(sg);
+    *out = sg.exec;
+    return STAG_OK;
+}
+
+void destroy_solver_graphs(stag_ctx* ctx) {
+    for (auto& e : ctx->graphs) {
+        if (e.exec) cudaGraphExecDestroy(e.exec);
+        if (e.graph) cudaGraphDestroy(e.graph);
+    }
+    ctx->graphs.clear();
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    ctx->cap_stream = nullptr;
+}
+
 static stag_status pull_state(stag_ctx* ctx) {
     CK(cudaMemcpyAsync(ctx->st_host, ctx->st, sizeof(SolverState), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return STAG_OK;
+}
+
+// the loop-control words only (k .. k4_units)
+static stag_status pull_control(stag_ctx* ctx) {
+    const size_t off = offsetof(SolverState, k);
+    const size_t len = offsetof(SolverState, rhs_live) - off;
+    CK(cudaMemcpyAsync((char*)ctx->st_host + off, (const char*)ctx->st + off, len, cudaMemcpyDeviceToHost,
+                       ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return STAG_OK;
 }
@@ -617,16 +691,29 @@ stag_status ms_core(stag_ctx* ctx, double mass, int nshift, const double* shifts
                                                           (double2*)p, (double2*)ps, (double2*)x, ctx->red,
                                                           ctx->counters + 2);
     CKL();
-    const int chunk = 16;
     stag_status status = STAG_OK;
-    // every chunk either advances k by up to `chunk` or makes a reliable update
-    const long long guard_max = (long long)max_iter / chunk * 4 + 64;
-    long long guard = 0;
-    for (;; ++guard) {
-        if (guard > guard_max) { status = STAG_ERR_TIMEOUT; break; }
-        if (mixed) CKS(ms_iterations<float>(ctx, prec, nrhs, chunk, tmp, r, p, q, ps, x));
-        else CKS(ms_iterations<double>(ctx, prec, nrhs, chunk, tmp, r, p, q, ps, x));
-        CKS(pull_state(ctx));
+    cudaGraphExec_t gexec = nullptr;
+    if (ctx->use_graphs) CKS(solver_graph(ctx, prec, nrhs, tmp, r, p, q, ps, x, &gexec));
+    // every segment either ends the solve or makes a reliable update (at most
+    // one per decade of the residual), so the number of segments is bounded
+    const int max_segments = ctx->use_graphs ? 64 + max_iter / 4 : 64 + max_iter;
+    const int chunk = 16;
+    for (int seg = 0;; ++seg) {
+        if (seg > max_segments) { status = STAG_ERR_TIMEOUT; break; }
+        // sampled timing: a few plainly launched iterations at the start of every segment
+        if (ctx->prof.on) {
+            if (mixed) CKS(ms_iterations<float>(ctx, ctx->stream, prec, nrhs, 4, tmp, r, p, q, ps, x, true, 0, 0));
+            else CKS(ms_iterations<double>(ctx, ctx->stream, prec, nrhs, 4, tmp, r, p, q, ps, x, true, 0, 0));
+        }
+        if (gexec) {
+            CK(cudaGraphLaunch(gexec, ctx->stream));
+            ++ctx->launches;
+        } else if (mixed) {
+            CKS(ms_iterations<float>(ctx, ctx->stream, prec, nrhs, chunk, tmp, r, p, q, ps, x, false, 0, 0));
+        } else {
+            CKS(ms_iterations<double>(ctx, ctx->stream, prec, nrhs, chunk, tmp, r, p, q, ps, x, false, 0, 0));
+        }
+        CKS(pull_control(ctx));
         if (!hs->halt) continue;
         if (hs->status != STAG_OK) { status = (stag_status)hs->status; break; }
         if (hs->need_reliable) {
@@ -646,12 +733,23 @@ stag_status ms_core(stag_ctx* ctx, double mass, int nshift, const double* shifts
         }
         break;   // converged
     }
+    CKS(pull_state(ctx));
+    if (gexec) ctx->launches += 4LL * hs->k;   // kernels the graph ran
+    if (ctx->prof.on) {
+        ProfData& pf = ctx->prof;
+        const double S = (double)(mixed ? sizeof(float2) : sizeof(double2));
+        pf.bytes_total[PK_DSLASH_OE] += (double)hs->k * g.Vh * (link_bytes_site(prec) + 2.0 * S * nrhs);
+        pf.bytes_total[PK_DSLASH_EO_A] += (double)hs->k * g.Vh * (link_bytes_site(prec) + 3.0 * S * nrhs);
+        pf.bytes_total[PK_RUPDATE] += (double)hs->k * g.Vh * 3.0 * S * nrhs;
+        for (int kk = 0; kk < PK_COUNT; ++kk) pf.launches[kk] += hs->k;
+    }
     if (mixed && x64) {
         if (finish_to_f64) k_acc_final<<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, x64, (const float2*)x);
         else k_rel_output<<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, x64, (float2*)x);
         CKL();
     }
     if (ctx->prof.on) ctx->prof.bytes_total[PK_SHIFT_UPDATE] += hs->k4_units * g.Vh * (mixed ? 1.0 : 2.0);
+
     if (stats) {
         stats->iterations = hs->k;
         stats->reliable = hs->n_reliable;

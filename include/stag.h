@@ -233,10 +233,9 @@ const double* stag_momenta(stag_ctx* ctx);
 /* ---- measurement (no counterpart in the paper; used for the roofline) ---- */
 
 /* Kernels of the multi-shift iteration, timed by sampling. */
-#define STAG_PK_DSLASH_OE 0      /* t = D_oe p, multi-RHS                        */
-#define STAG_PK_DSLASH_EO_A 1    /* q = c0 p - D_eo t with the (p, q) reduction  */
-#define STAG_PK_RUPDATE 2        /* r -= alpha q with the (r, r) reduction       */
-#define STAG_PK_SHIFT_UPDATE 3   /* x_i, p_i of the live shifts, p               */
+#define STAG_PK_DSLASH_OE 0      /* t = D_oe (r + beta p), multi-RHS                             */
+#define STAG_PK_DSLASH_EO_A 1    /* p = r + beta p; q = c0 p - D_eo t; (p, q) and the alpha step */
+#define STAG_PK_UPDATE 2         /* p_i, x_i of the live shifts; r -= alpha q; (r, r), beta step  */
 typedef struct {
     long long launches;       /* launches of this kernel since stag_profile_begin */
     int sampled;              /* of which bracketed by CUDA events on the context's stream */

@@ -9,12 +9,12 @@ static stag_status launch_t(stag_ctx* ctx, int out_par, int nrhs, const void* in
     int nchunk = (nrhs + nr - 1) / nr;
     long long grid = (long long)nblocks(ctx->g.Vh, bs) * nchunk;
     if (grid > 0x7fffffffLL) return STAG_ERR_ARG;
-    const typename V2T<R>::T* vin = (const typename V2T<R>::T*)in;
+    SrcPlain<R> src{(const typename V2T<R>::T*)in};
     LinkPtrs L = link_ptrs(ctx);
     switch (nr) {
-        case 4: k_dslash<R, FMT, 4, Epi><<<(int)grid, bs, 0, ctx->stream>>>(ctx->g, out_par, L, vin, nrhs, nchunk, epi); break;
-        case 2: k_dslash<R, FMT, 2, Epi><<<(int)grid, bs, 0, ctx->stream>>>(ctx->g, out_par, L, vin, nrhs, nchunk, epi); break;
-        default: k_dslash<R, FMT, 1, Epi><<<(int)grid, bs, 0, ctx->stream>>>(ctx->g, out_par, L, vin, nrhs, nchunk, epi); break;
+        case 4: k_dslash<R, FMT, 4, SrcPlain<R>, Epi><<<(int)grid, bs, 0, ctx->stream>>>(ctx->g, out_par, L, src, nrhs, nchunk, epi); break;
+        case 2: k_dslash<R, FMT, 2, SrcPlain<R>, Epi><<<(int)grid, bs, 0, ctx->stream>>>(ctx->g, out_par, L, src, nrhs, nchunk, epi); break;
+        default: k_dslash<R, FMT, 1, SrcPlain<R>, Epi><<<(int)grid, bs, 0, ctx->stream>>>(ctx->g, out_par, L, src, nrhs, nchunk, epi); break;
     }
     CKL();
     return STAG_OK;

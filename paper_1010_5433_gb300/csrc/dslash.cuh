@@ -38,15 +38,23 @@ template <> struct LinkFetch<float, FMT_BF16_12> {
     }
 };
 
+// Source of the hops: the field itself ...
+template <typename R> struct SrcPlain {
+    const typename V2T<R>::T* __restrict__ in;
+    template <int NR> __device__ __forceinline__ void prepare(int r0, int nrhs) {}
+    // slot: the source's index inside the thread's chunk (compile-time after unrolling)
+    __device__ __forceinline__ Vec3<R> load(int slot, int rhs, int h, int Vh) const {
+        return load_vec<R>(in + (size_t)rhs * 3 * Vh, h, Vh);
+    }
+};
+
 // Accumulate sum_mu [ sf U_mu(x) in(x+mu) - sb U_mu(x-mu)^dag in(x-mu) ] for NR sources
 // (the factor 1/2 is left to the epilogue).
-template <typename R, int FMT, int NR>
-__device__ __forceinline__ void dslash_site(const Geom& g, int out_par, const LinkPtrs& L,
-                                            const typename V2T<R>::T* __restrict__ in, int r0, int nrhs,
-                                            int h, Vec3<R> (&acc)[NR]) {
+template <typename R, int FMT, int NR, class Src>
+__device__ __forceinline__ void dslash_site(const Geom& g, int out_par, const LinkPtrs& L, const Src& src,
+                                            int r0, int nrhs, int h, Vec3<R> (&acc)[NR]) {
     Nbr n;
     site_neighbours(g, h, out_par, n);
-    const size_t rs = (size_t)3 * g.Vh;
 #pragma unroll
     for (int r = 0; r < NR; ++r) zero(acc[r]);
 #pragma unroll
@@ -55,7 +63,7 @@ __device__ __forceinline__ void dslash_site(const Geom& g, int out_par, const Li
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
             if (r0 + r < nrhs) {
-                Vec3<R> v = load_vec<R>(in + (size_t)(r0 + r) * rs, n.fwd[mu], g.Vh);
+                Vec3<R> v = src.load(r, r0 + r, n.fwd[mu], g.Vh);
                 mac_uv(acc[r], (R)n.sf[mu], u, v);
             }
         }
@@ -63,7 +71,7 @@ __device__ __forceinline__ void dslash_site(const Geom& g, int out_par, const Li
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
             if (r0 + r < nrhs) {
-                Vec3<R> v = load_vec<R>(in + (size_t)(r0 + r) * rs, n.bwd[mu], g.Vh);
+                Vec3<R> v = src.load(r, r0 + r, n.bwd[mu], g.Vh);
                 mac_udv(acc[r], -(R)n.sb[mu], w, v);
             }
         }
@@ -72,9 +80,9 @@ __device__ __forceinline__ void dslash_site(const Geom& g, int out_par, const Li
 
 // Grid: blockIdx.x = site_block * nchunk + chunk, so that the chunks of one
 // site block run back to back and re-read its links from L2.
-template <typename R, int FMT, int NR, class Epi>
+template <typename R, int FMT, int NR, class Src, class Epi>
 __global__ void __launch_bounds__(STAG_RED_BLOCK)
-k_dslash(Geom g, int out_par, LinkPtrs L, const typename V2T<R>::T* __restrict__ in, int nrhs, int nchunk, Epi epi) {
+k_dslash(Geom g, int out_par, LinkPtrs L, Src src, int nrhs, int nchunk, Epi epi) {
     if (epi.halted()) return;
     const int chunk = blockIdx.x % nchunk;
     const int sblock = blockIdx.x / nchunk;
@@ -82,7 +90,8 @@ k_dslash(Geom g, int out_par, LinkPtrs L, const typename V2T<R>::T* __restrict__
     const int r0 = chunk * NR;
     Vec3<R> acc[NR];
     const bool valid = h < g.Vh;
-    if (valid) dslash_site<R, FMT, NR>(g, out_par, L, in, r0, nrhs, h, acc);
+    src.template prepare<NR>(r0, nrhs);
+    if (valid) dslash_site<R, FMT, NR>(g, out_par, L, src, r0, nrhs, h, acc);
     epi.template finish<NR>(g, h, valid, r0, nrhs, acc);
 }
 

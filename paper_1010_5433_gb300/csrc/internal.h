@@ -33,7 +33,7 @@ enum WsSlot {
 };
 
 // Sampled CUDA-event timing of the solver kernels (stag_profile_*).
-enum ProfKind { PK_DSLASH_OE = 0, PK_DSLASH_EO_A, PK_RUPDATE, PK_SHIFT_UPDATE, PK_COUNT };
+enum ProfKind { PK_DSLASH_OE = 0, PK_DSLASH_EO_A, PK_UPDATE, PK_COUNT };
 struct ProfData {
     bool on = false;
     int every = 16;

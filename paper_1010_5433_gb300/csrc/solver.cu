@@ -66,7 +66,6 @@ __global__ void k_ms_init(SolverState* st, int Vh, const typename V2T<R>::T* __r
         if (threadIdx.x == 0) {
             st->k = 0;
             st->halt = 0;
-            st->k4_skip = 0;
             st->status = STAG_OK;
             st->need_reliable = 0;
             st->n_reliable = 0;
@@ -89,8 +88,10 @@ __global__ void k_ms_init(SolverState* st, int Vh, const typename V2T<R>::T* __r
                     st->zeta_prev[q][s] = 1.0;
                     st->zeta_next[q][s] = 1.0;
                     st->live[q][s] = live;
-                    st->active[q][s] = 0;
                     st->iters_at[q][s] = 0;
+                    st->cx[q][s] = 0.0;
+                    st->cpr[q][s] = 1.0;    // p_i = zeta_0 r_0 + 0 = b in the first update
+                    st->cpp[q][s] = 0.0;
                 }
             }
             if (!any) st->halt = 1;
@@ -98,21 +99,41 @@ __global__ void k_ms_init(SolverState* st, int Vh, const typename V2T<R>::T* __r
     }
 }
 
-// ---------------------------------------------------------------- K1 / K2 epilogues
-template <typename R> struct EpiMsOdd {     // K1: t = D_oe p (without the 1/2)
+// ---------------------------------------------------------------- K1
+// t = D_oe p_k without the 1/2, where the base direction p_k = r_k + beta_{k-1} p_{k-1}
+// is formed on the fly at every neighbour (it is stored only by K2).
+template <typename R> struct SrcRp {
+    const typename V2T<R>::T* r;
+    const typename V2T<R>::T* p;
+    const SolverState* st;
+    R beta[4];
+    template <int NR> __device__ __forceinline__ void prepare(int r0, int nrhs) {
+#pragma unroll
+        for (int q = 0; q < NR; ++q) beta[q] = (r0 + q < nrhs) ? (R)st->beta[r0 + q] : (R)0;
+    }
+    __device__ __forceinline__ Vec3<R> load(int slot, int rhs, int h, int Vh) const {
+        Vec3<R> a = load_vec_cg<R>(r + (size_t)rhs * 3 * Vh, h, Vh);
+        Vec3<R> b = load_vec_cg<R>(p + (size_t)rhs * 3 * Vh, h, Vh);
+        const R bt = beta[slot];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            a.c[c].re += bt * b.c[c].re;
+            a.c[c].im += bt * b.c[c].im;
+        }
+        return a;
+    }
+};
+
+template <typename R> struct EpiMsOdd {
     typename V2T<R>::T* out;
     SolverState* st;
     cudaGraphConditionalHandle cond;       // loop condition of the solver graph
     int use_cond;
     __device__ __forceinline__ bool halted() const {
-        // inside the solver graph the loop continues only if the r-update of
-        // this iteration explicitly says so
+        // inside the solver graph the loop continues only if the update kernel
+        // of this iteration explicitly says so
         if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0);
-        if (*(volatile int*)&st->halt) {
-            if (blockIdx.x == 0 && threadIdx.x == 0) st->k4_skip = 1;
-            return true;
-        }
-        return false;
+        return *(volatile int*)&st->halt != 0;
     }
     template <int NR>
     __device__ __forceinline__ void finish(const Geom& g, int h, bool valid, int r0, int nrhs, Vec3<R> (&acc)[NR]) {
@@ -124,32 +145,45 @@ template <typename R> struct EpiMsOdd {     // K1: t = D_oe p (without the 1/2)
     }
 };
 
-// The scalar step after (p, A p) is known: alpha and the shifted zeta recurrence.
+// ---------------------------------------------------------------- K2
+// The scalar step once (p, A p) is known, by the whole last block: alpha per
+// source, then the shifted zeta recurrence with one thread per (source, shift).
 __device__ void ms_alpha_step(SolverState* st, const double* pap) {
-    for (int q = 0; q < st->nrhs; ++q) {
-        if (!st->rhs_live[q]) continue;
-        double alpha = st->rr[q] / pap[q];
-        if (!isfinite(alpha) || pap[q] <= 0.0) {
-            st->status = STAG_ERR_NAN;
-            st->halt = 1;
-            alpha = 0.0;
+    __shared__ double s_alpha[STAG_MAX_RHS];
+    const int t = threadIdx.x;
+    if (t < st->nrhs) {
+        double alpha = 0.0;
+        if (st->rhs_live[t]) {
+            alpha = st->rr[t] / pap[t];
+            if (!isfinite(alpha) || !(pap[t] > 0.0)) {
+                st->status = STAG_ERR_NAN;
+                st->halt = 1;
+                alpha = 0.0;
+            }
+            st->alpha[t] = alpha;
         }
-        st->alpha[q] = alpha;
+        s_alpha[t] = alpha;
+    }
+    __syncthreads();
+    for (int idx = t; idx < st->nrhs * STAG_MAX_SHIFTS; idx += blockDim.x) {
+        const int q = idx / STAG_MAX_SHIFTS, s = idx % STAG_MAX_SHIFTS;
+        if (s >= st->nshift || !st->rhs_live[q] || !st->live[q][s]) continue;
+        const double alpha = s_alpha[q];
         const double ap = st->alpha_prev[q], bp = st->beta_prev[q];
-        for (int s = 0; s < st->nshift; ++s) {
-            if (!st->live[q][s]) { st->cx[q][s] = 0.0; continue; }
-            const double z = st->zeta[q][s], zp = st->zeta_prev[q][s];
-            const double den = alpha * bp * (zp - z) + zp * ap * (1.0 + st->dsig[s] * alpha);
-            const double zn = z * zp * ap / den;
-            st->zeta_next[q][s] = zn;
-            st->cx[q][s] = alpha * zn / z;
-        }
+        const double z = st->zeta[q][s], zp = st->zeta_prev[q][s];
+        const double den = alpha * bp * (zp - z) + zp * ap * (1.0 + st->dsig[s] * alpha);
+        const double zn = z * zp * ap / den;
+        st->zeta_next[q][s] = zn;
+        st->cx[q][s] = alpha * zn / z;
     }
 }
 
-template <typename R> struct EpiMsA {       // K2: q = c0 p - 1/2 (D_eo t) (t holds 2 D_oe p)
+// p_k = r_k + beta_{k-1} p_{k-1} stored at the own site; q = c0 p_k - D_eo D_oe p_k;
+// (p_k, q) per source; the last block runs the alpha step.
+template <typename R> struct EpiMsA {
     typename V2T<R>::T* q;
-    const typename V2T<R>::T* p;
+    typename V2T<R>::T* p;
+    const typename V2T<R>::T* r;
     SolverState* st;
     double* partial;
     unsigned int* counter;
@@ -160,19 +194,25 @@ template <typename R> struct EpiMsA {       // K2: q = c0 p - 1/2 (D_eo t) (t ho
         const R c0 = (R)st->c0;
         double d[NR];
 #pragma unroll
-        for (int r = 0; r < NR; ++r) {
-            d[r] = 0.0;
-            if (valid && r0 + r < nrhs) {
-                Vec3<R> pv = load_vec_cg<R>(p + (size_t)(r0 + r) * rs, h, g.Vh);
+        for (int rr = 0; rr < NR; ++rr) {
+            d[rr] = 0.0;
+            if (valid && r0 + rr < nrhs) {
+                const size_t off = (size_t)(r0 + rr) * rs;
+                const R bt = (R)st->beta[r0 + rr];
+                Vec3<R> pv = load_vec_cg<R>(p + off, h, g.Vh);
+                Vec3<R> rv = load_vec_cg<R>(r + off, h, g.Vh);
                 Vec3<R> o;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
+                    pv.c[c].re = rv.c[c].re + bt * pv.c[c].re;
+                    pv.c[c].im = rv.c[c].im + bt * pv.c[c].im;
                     // t = 2 D_oe p, so D_eo D_oe p = 1/4 (sum of hops of t)
-                    o.c[c].re = c0 * pv.c[c].re - (R)0.25 * acc[r].c[c].re;
-                    o.c[c].im = c0 * pv.c[c].im - (R)0.25 * acc[r].c[c].im;
+                    o.c[c].re = c0 * pv.c[c].re - (R)0.25 * acc[rr].c[c].re;
+                    o.c[c].im = c0 * pv.c[c].im - (R)0.25 * acc[rr].c[c].im;
                 }
-                store_vec<R>(q + (size_t)(r0 + r) * rs, h, g.Vh, o);
-                d[r] = re_dot(pv, o);
+                store_vec<R>(p + off, h, g.Vh, pv);
+                store_vec<R>(q + off, h, g.Vh, o);
+                d[rr] = re_dot(pv, o);
             }
         }
         block_sum<NR>(d);
@@ -180,81 +220,117 @@ template <typename R> struct EpiMsA {       // K2: q = c0 p - 1/2 (D_eo t) (t ho
         const int sblock = blockIdx.x / nchunk, nsb = gridDim.x / nchunk;
         if (threadIdx.x == 0) {
 #pragma unroll
-            for (int r = 0; r < NR; ++r)
-                if (r0 + r < nrhs) partial[(size_t)(r0 + r) * nsb + sblock] = d[r];
+            for (int rr = 0; rr < NR; ++rr)
+                if (r0 + rr < nrhs) partial[(size_t)(r0 + rr) * nsb + sblock] = d[rr];
         }
         if (elect_last_block(counter, gridDim.x)) {
             __shared__ double sums[STAG_MAX_RHS];
-            for (int r = 0; r < nrhs; ++r) {
-                double s = block_sum_array(partial + (size_t)r * nsb, nsb);
-                if (threadIdx.x == 0) sums[r] = s;
+            for (int rr = 0; rr < nrhs; ++rr) {
+                double s = block_sum_array(partial + (size_t)rr * nsb, nsb);
+                if (threadIdx.x == 0) sums[rr] = s;
             }
-            if (threadIdx.x == 0) ms_alpha_step(st, sums);
+            __syncthreads();
+            ms_alpha_step(st, sums);
         }
     }
 };
 
 // ---------------------------------------------------------------- K3
-__device__ void ms_beta_step(SolverState* st, const double* rrn) {
-    int any_live = 0;
-    for (int q = 0; q < st->nrhs; ++q) {
-        if (!st->rhs_live[q]) {
-            for (int s = 0; s < st->nshift; ++s) st->active[q][s] = 0;
-            continue;
-        }
-        const double rr_new = rrn[q];
-        if (!isfinite(rr_new)) {
-            st->status = STAG_ERR_NAN;
-            st->halt = 1;
-        }
-        const double beta = rr_new / st->rr[q];
-        int live_left = 0;
-        for (int s = 0; s < st->nshift; ++s) {
-            if (!st->live[q][s]) { st->active[q][s] = 0; continue; }
-            const double zn = st->zeta_next[q][s], z = st->zeta[q][s];
-            const double zr = zn / z;
-            st->active[q][s] = 1;
-            st->cpr[q][s] = zn;
-            st->cpp[q][s] = beta * zr * zr;
-            st->zeta_prev[q][s] = z;
-            st->zeta[q][s] = zn;
-            if (zn * zn * rr_new <= st->tol2 * st->bb[q]) {
-                st->live[q][s] = 0;
-                st->iters_at[q][s] = st->k + 1;
-            } else {
-                live_left = 1;
+// The scalar step once (r_{k+1}, r_{k+1}) is known, by the whole last block:
+// beta, beta_i = beta (zeta_{k+1}/zeta_k)^2, shift convergence, loop control.
+__device__ void ms_beta_step(SolverState* st, const double* rrn, cudaGraphConditionalHandle cond, int use_cond) {
+    __shared__ double s_beta[STAG_MAX_RHS], s_rrn[STAG_MAX_RHS];
+    __shared__ int s_left[STAG_MAX_RHS], s_any;
+    const int t = threadIdx.x;
+    if (t == 0) s_any = 0;
+    if (t < st->nrhs) {
+        s_left[t] = 0;
+        if (st->rhs_live[t]) {
+            const double rr_new = rrn[t];
+            if (!isfinite(rr_new)) {
+                st->status = STAG_ERR_NAN;
+                st->halt = 1;
             }
+            s_rrn[t] = rr_new;
+            s_beta[t] = rr_new / st->rr[t];
+            int n_live = 0;
+            for (int s = 0; s < st->nshift; ++s) n_live += st->live[t][s];
+            atomicAdd(&st->k4_units, 72.0 + 96.0 * n_live);
         }
-        int n_act = 0;
-        for (int s2 = 0; s2 < st->nshift; ++s2) n_act += st->active[q][s2];
-        if (n_act) st->k4_units += 72.0 + 96.0 * n_act;
-        st->beta[q] = beta;
-        st->alpha_prev[q] = st->alpha[q];
-        st->beta_prev[q] = beta;
-        st->rr[q] = rr_new;
-        if (!live_left) st->rhs_live[q] = 0;
-        any_live |= live_left;
-        if (live_left && st->mixed && rr_new < st->delta2 * st->rr_ref[q]) st->need_reliable = 1;
     }
-    st->k += 1;
-    if (!any_live) st->halt = 1;
-    else if (st->k >= st->max_iter) { st->halt = 1; st->status = STAG_ERR_NOT_CONVERGED; }
-    if (st->need_reliable) st->halt = 1;
+    __syncthreads();
+    for (int idx = t; idx < st->nrhs * STAG_MAX_SHIFTS; idx += blockDim.x) {
+        const int q = idx / STAG_MAX_SHIFTS, s = idx % STAG_MAX_SHIFTS;
+        if (s >= st->nshift || !st->rhs_live[q] || !st->live[q][s]) continue;
+        const double zn = st->zeta_next[q][s], z = st->zeta[q][s];
+        const double zr = zn / z;
+        st->cpr[q][s] = zn;                     // p_i = zeta_{k+1} r + beta_i p_i in the next update
+        st->cpp[q][s] = s_beta[q] * zr * zr;
+        st->zeta_prev[q][s] = z;
+        st->zeta[q][s] = zn;
+        if (zn * zn * s_rrn[q] <= st->tol2 * st->bb[q]) {
+            st->live[q][s] = 0;
+            st->iters_at[q][s] = st->k + 1;
+        } else {
+            atomicOr(&s_left[q], 1);
+        }
+    }
+    __syncthreads();
+    if (t < st->nrhs && st->rhs_live[t]) {
+        st->beta[t] = s_beta[t];
+        st->alpha_prev[t] = st->alpha[t];
+        st->beta_prev[t] = s_beta[t];
+        st->rr[t] = s_rrn[t];
+        if (!s_left[t]) st->rhs_live[t] = 0;
+        else {
+            atomicOr(&s_any, 1);
+            if (st->mixed && s_rrn[t] < st->delta2 * st->rr_ref[t]) st->need_reliable = 1;
+        }
+    }
+    __syncthreads();
+    if (t == 0) {
+        st->k += 1;
+        if (!s_any) st->halt = 1;
+        else if (st->k >= st->max_iter) { st->halt = 1; st->status = STAG_ERR_NOT_CONVERGED; }
+        if (st->need_reliable) st->halt = 1;
+        if (use_cond) cudaGraphSetConditional(cond, st->halt ? 0u : 1u);
+    }
 }
 
+// Fused update of iteration k at every site of every live source:
+//   p_i = zeta_k r_k + beta_{i,k-1} p_i ;  x_i += alpha_{i,k} p_i   (live shifts)
+//   r_{k+1} = r_k - alpha_k q ;  (r_{k+1}, r_{k+1})
 template <typename R>
-__global__ void __launch_bounds__(VB) k_ms_rupdate(SolverState* st, int Vh, typename V2T<R>::T* r,
-                                                   const typename V2T<R>::T* __restrict__ q, double* partial,
-                                                   unsigned int* counter, cudaGraphConditionalHandle cond,
-                                                   int use_cond) {
+__global__ void __launch_bounds__(VB) k_ms_update(SolverState* st, int Vh, typename V2T<R>::T* r,
+                                                  const typename V2T<R>::T* __restrict__ q, typename V2T<R>::T* ps,
+                                                  typename V2T<R>::T* x, double* partial, unsigned int* counter,
+                                                  cudaGraphConditionalHandle cond, int use_cond) {
     if (*(volatile int*)&st->halt) return;
     const int rhs = blockIdx.y;
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    const int ns = st->nshift;
     const size_t rs = (size_t)3 * Vh;
     double v[1] = {0.0};
     if (st->rhs_live[rhs] && h < Vh) {
-        const R a = (R)st->alpha[rhs];
         Vec3<R> rv = load_vec_cg<R>(r + rhs * rs, h, Vh);
+        for (int s = 0; s < ns; ++s) {
+            if (!st->live[rhs][s]) continue;
+            const R cx = (R)st->cx[rhs][s], cpr = (R)st->cpr[rhs][s], cpp = (R)st->cpp[rhs][s];
+            typename V2T<R>::T* pp = ps + ((size_t)rhs * ns + s) * rs;
+            typename V2T<R>::T* xp = x + ((size_t)rhs * ns + s) * rs;
+            Vec3<R> pv = load_vec_cg<R>(pp, h, Vh);
+            Vec3<R> xv = load_vec_cg<R>(xp, h, Vh);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                pv.c[c].re = cpr * rv.c[c].re + cpp * pv.c[c].re;
+                pv.c[c].im = cpr * rv.c[c].im + cpp * pv.c[c].im;
+                xv.c[c].re += cx * pv.c[c].re;
+                xv.c[c].im += cx * pv.c[c].im;
+            }
+            store_vec<R>(xp, h, Vh, xv);
+            store_vec<R>(pp, h, Vh, pv);
+        }
+        const R a = (R)st->alpha[rhs];
         Vec3<R> qv = load_vec_cg<R>(q + rhs * rs, h, Vh);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -272,53 +348,8 @@ __global__ void __launch_bounds__(VB) k_ms_rupdate(SolverState* st, int Vh, type
             double s = block_sum_array(partial + (size_t)q2 * gridDim.x, gridDim.x);
             if (threadIdx.x == 0) sums[q2] = s;
         }
-        if (threadIdx.x == 0) {
-            ms_beta_step(st, sums);
-            if (use_cond) cudaGraphSetConditional(cond, st->halt ? 0u : 1u);
-        }
-    }
-}
-
-// ---------------------------------------------------------------- K4
-template <typename R>
-__global__ void __launch_bounds__(VB) k_ms_shift_update(SolverState* st, int Vh, const typename V2T<R>::T* r,
-                                                        typename V2T<R>::T* p, typename V2T<R>::T* ps,
-                                                        typename V2T<R>::T* x) {
-    if (*(volatile int*)&st->k4_skip) return;
-    const int rhs = blockIdx.y;
-    const int h = blockIdx.x * blockDim.x + threadIdx.x;
-    if (h >= Vh) return;
-    const int ns = st->nshift;
-    const size_t rs = (size_t)3 * Vh;
-    Vec3<R> rv = load_vec_cg<R>(r + rhs * rs, h, Vh);
-    bool any = false;
-    for (int s = 0; s < ns; ++s) {
-        if (!st->active[rhs][s]) continue;
-        any = true;
-        const R cx = (R)st->cx[rhs][s], cpr = (R)st->cpr[rhs][s], cpp = (R)st->cpp[rhs][s];
-        typename V2T<R>::T* pp = ps + ((size_t)rhs * ns + s) * rs;
-        typename V2T<R>::T* xp = x + ((size_t)rhs * ns + s) * rs;
-        Vec3<R> pv = load_vec_cg<R>(pp, h, Vh);
-        Vec3<R> xv = load_vec_cg<R>(xp, h, Vh);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            xv.c[c].re += cx * pv.c[c].re;
-            xv.c[c].im += cx * pv.c[c].im;
-            pv.c[c].re = cpr * rv.c[c].re + cpp * pv.c[c].re;
-            pv.c[c].im = cpr * rv.c[c].im + cpp * pv.c[c].im;
-        }
-        store_vec<R>(xp, h, Vh, xv);
-        store_vec<R>(pp, h, Vh, pv);
-    }
-    if (any) {
-        const R beta = (R)st->beta[rhs];
-        Vec3<R> pv = load_vec_cg<R>(p + rhs * rs, h, Vh);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            pv.c[c].re = rv.c[c].re + beta * pv.c[c].re;
-            pv.c[c].im = rv.c[c].im + beta * pv.c[c].im;
-        }
-        store_vec<R>(p + rhs * rs, h, Vh, pv);
+        __syncthreads();
+        ms_beta_step(st, sums, cond, use_cond);
     }
 }
 
@@ -490,10 +521,6 @@ __global__ void k_d2f(size_t n, const double2* a, float2* b) {
     if (i < n) b[i] = make_float2((float)a[i].x, (float)a[i].y);
 }
 
-__global__ void k_f2d(size_t n, const float2* a, double2* b) {
-    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) b[i] = make_double2((double)a[i].x, (double)a[i].y);
-}
 
 }  // namespace
 
@@ -502,14 +529,14 @@ __global__ void k_f2d(size_t n, const float2* a, double2* b) {
 // five consecutive events of the profiling pool (created on first use)
 static stag_status prof_events(stag_ctx* ctx, int* ev) {
     ProfData& pf = ctx->prof;
-    if (pf.used + 5 > 50000) { pf.on = false; return STAG_OK; }
-    while (pf.pool.size() < pf.used + 5) {
+    if (pf.used + 4 > 50000) { pf.on = false; return STAG_OK; }
+    while (pf.pool.size() < pf.used + 4) {
         cudaEvent_t e;
         CK(cudaEventCreate(&e));
         pf.pool.push_back(e);
     }
-    for (int k = 0; k < 5; ++k) ev[k] = (int)(pf.used + k);
-    pf.used += 5;
+    for (int k = 0; k < 4; ++k) ev[k] = (int)(pf.used + k);
+    pf.used += 4;
     return STAG_OK;
 }
 template <typename R>
@@ -524,18 +551,20 @@ static stag_status ms_iterations(stag_ctx* ctx, cudaStream_t stream, stag_prec p
     int grid_d = nblocks(g.Vh, bs) * nchunk;
     dim3 grid_v(nblocks(g.Vh, VB), nrhs);
     LinkPtrs L = link_ptrs(ctx);
+    SrcRp<R> src1{(const V*)r, (const V*)p, ctx->st, {}};
+    SrcPlain<R> src2{(const V*)tmp};
     EpiMsOdd<R> e1{(V*)tmp, ctx->st, cond, use_cond};
-    EpiMsA<R> e2{(V*)q, (const V*)p, ctx->st, ctx->red, ctx->counters + 0};
+    EpiMsA<R> e2{(V*)q, (V*)p, (const V*)r, ctx->st, ctx->red, ctx->counters + 0};
     ProfData& pf = ctx->prof;
     for (int it = 0; it < chunk; ++it) {
         const bool smp = sample && pf.on;
-        int ev[5];
+        int ev[4];
         if (smp) CKS(prof_events(ctx, ev));
-#define MS_LAUNCH(FMT_, NR_)                                                                                         \
-    if (smp) CK(cudaEventRecord(pf.pool[ev[0]], stream));                                                       \
-    k_dslash<R, FMT_, NR_, EpiMsOdd<R>><<<grid_d, bs, 0, stream>>>(g, 1, L, (const V*)p, nrhs, nchunk, e1);     \
-    if (smp) CK(cudaEventRecord(pf.pool[ev[1]], stream));                                                       \
-    k_dslash<R, FMT_, NR_, EpiMsA<R>><<<grid_d, bs, 0, stream>>>(g, 0, L, (const V*)tmp, nrhs, nchunk, e2);     \
+#define MS_LAUNCH(FMT_, NR_)                                                                                   \
+    if (smp) CK(cudaEventRecord(pf.pool[ev[0]], stream));                                                     \
+    k_dslash<R, FMT_, NR_, SrcRp<R>, EpiMsOdd<R>><<<grid_d, bs, 0, stream>>>(g, 1, L, src1, nrhs, nchunk, e1); \
+    if (smp) CK(cudaEventRecord(pf.pool[ev[1]], stream));                                                     \
+    k_dslash<R, FMT_, NR_, SrcPlain<R>, EpiMsA<R>><<<grid_d, bs, 0, stream>>>(g, 0, L, src2, nrhs, nchunk, e2); \
     if (smp) CK(cudaEventRecord(pf.pool[ev[2]], stream));
 #define MS_FMT(FMT_)                         \
     switch (nr) {                            \
@@ -552,16 +581,14 @@ static stag_status ms_iterations(stag_ctx* ctx, cudaStream_t stream, stag_prec p
         }
 #undef MS_FMT
 #undef MS_LAUNCH
-        k_ms_rupdate<R><<<grid_v, VB, 0, stream>>>(ctx->st, g.Vh, (V*)r, (const V*)q, ctx->red,
-                                                   ctx->counters + 1, cond, use_cond);
-        if (smp) CK(cudaEventRecord(pf.pool[ev[3]], stream));
-        k_ms_shift_update<R><<<grid_v, VB, 0, stream>>>(ctx->st, g.Vh, (const V*)r, (V*)p, (V*)ps, (V*)x);
+        k_ms_update<R><<<grid_v, VB, 0, stream>>>(ctx->st, g.Vh, (V*)r, (const V*)q, (V*)ps, (V*)x, ctx->red,
+                                                  ctx->counters + 1, cond, use_cond);
         if (smp) {
-            CK(cudaEventRecord(pf.pool[ev[4]], stream));
-            for (int k = 0; k < PK_COUNT; ++k) pf.marks[k].push_back({ev[k], ev[k + 1]});
+            CK(cudaEventRecord(pf.pool[ev[3]], stream));
+            for (int k = 0; k < 3; ++k) pf.marks[k].push_back({ev[k], ev[k + 1]});
         }
     }
-    if (!use_cond) ctx->launches += 4LL * chunk;
+    if (!use_cond) ctx->launches += 3LL * chunk;
     CK(cudaGetLastError());
     return STAG_OK;
 }
@@ -651,6 +678,8 @@ stag_status ms_core(stag_ctx* ctx, double mass, int nshift, const double* shifts
     const bool mixed = prec != STAG_FP64;
     if (nrhs < 1 || nrhs > STAG_MAX_RHS || nshift < 1 || nshift > STAG_MAX_SHIFTS) return STAG_ERR_ARG;
     if (mixed && reliable && (!b64 || !x64)) return STAG_ERR_ARG;
+    // the bf16 copy must follow every link update before a bf16 iteration
+    if (prec == STAG_BF16_12 && ctx->b16_stale) CKS(refresh_bf16(ctx));
     int base = 0;
     for (int s = 0; s < nshift; ++s)
         if (shifts[s] < shifts[base]) base = s;
@@ -727,20 +756,20 @@ stag_status ms_core(stag_ctx* ctx, double mass, int nshift, const double* shifts
             ctx->launches += 3;
             CK(cudaGetLastError());
             hs->halt = 0;
-            hs->k4_skip = 0;
-            CK(cudaMemcpyAsync(&ctx->st->halt, &hs->halt, 2 * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+            CK(cudaMemcpyAsync(&ctx->st->halt, &hs->halt, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
             continue;
         }
         break;   // converged
     }
     CKS(pull_state(ctx));
-    if (gexec) ctx->launches += 4LL * hs->k;   // kernels the graph ran
+    if (gexec) ctx->launches += 3LL * hs->k;   // kernels the graph ran
     if (ctx->prof.on) {
         ProfData& pf = ctx->prof;
         const double S = (double)(mixed ? sizeof(float2) : sizeof(double2));
-        pf.bytes_total[PK_DSLASH_OE] += (double)hs->k * g.Vh * (link_bytes_site(prec) + 2.0 * S * nrhs);
-        pf.bytes_total[PK_DSLASH_EO_A] += (double)hs->k * g.Vh * (link_bytes_site(prec) + 3.0 * S * nrhs);
-        pf.bytes_total[PK_RUPDATE] += (double)hs->k * g.Vh * 3.0 * S * nrhs;
+        // K1 reads r and p (the direction is formed on the fly) and writes t;
+        // K2 reads t, r, p and writes p, q
+        pf.bytes_total[PK_DSLASH_OE] += (double)hs->k * g.Vh * (link_bytes_site(prec) + 3.0 * S * nrhs);
+        pf.bytes_total[PK_DSLASH_EO_A] += (double)hs->k * g.Vh * (link_bytes_site(prec) + 5.0 * S * nrhs);
         for (int kk = 0; kk < PK_COUNT; ++kk) pf.launches[kk] += hs->k;
     }
     if (mixed && x64) {
@@ -748,7 +777,7 @@ stag_status ms_core(stag_ctx* ctx, double mass, int nshift, const double* shifts
         else k_rel_output<<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, x64, (float2*)x);
         CKL();
     }
-    if (ctx->prof.on) ctx->prof.bytes_total[PK_SHIFT_UPDATE] += hs->k4_units * g.Vh * (mixed ? 1.0 : 2.0);
+    if (ctx->prof.on) ctx->prof.bytes_total[PK_UPDATE] += hs->k4_units * g.Vh * (mixed ? 1.0 : 2.0);
 
     if (stats) {
         stats->iterations = hs->k;
@@ -868,7 +897,8 @@ static stag_status ms_api_batch(stag_ctx* ctx, double mass, int nshift, const do
         const bool rel = prec != STAG_BF16_12;
         status = ms_core(ctx, mass, nshift, shifts, prec, nrhs, b32, b, x32, x, tol, max_iter, rel, true, &st);
         if (status != STAG_OK && status != STAG_ERR_NOT_CONVERGED) return status;
-        CKS(refine_shifts(ctx, mass, nshift, shifts, nrhs, b, x, tol, max_iter, &extra, &nrel, res));
+        // refinement only follows a converged multi-shift stage
+        if (status == STAG_OK) CKS(refine_shifts(ctx, mass, nshift, shifts, nrhs, b, x, tol, max_iter, &extra, &nrel, res));
     }
     if (info) {
         info->iterations = st.iterations + extra;

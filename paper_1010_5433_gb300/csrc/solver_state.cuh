@@ -17,11 +17,10 @@ struct SolverState {
     // loop control (device)
     int k;                             // iterations completed
     int halt;                          // stop after the current iteration
-    int k4_skip;                       // the pending shift update must not run
     int status;                        // stag_status of the solve
     int need_reliable;                 // host must replace the base residual
     int n_reliable;
-    double k4_units;                   // sum over shift updates of (72 + 96 n_active) per rhs (fp32 bytes/site)
+    double k4_units;                   // sum over updates of (72 + 96 n_live) per rhs (fp32 bytes/site)
     // per source
     int rhs_live[STAG_MAX_RHS];
     double bb[STAG_MAX_RHS], rr[STAG_MAX_RHS], rr_ref[STAG_MAX_RHS];
@@ -30,10 +29,9 @@ struct SolverState {
     double zeta[STAG_MAX_RHS][STAG_MAX_SHIFTS];
     double zeta_prev[STAG_MAX_RHS][STAG_MAX_SHIFTS];
     double zeta_next[STAG_MAX_RHS][STAG_MAX_SHIFTS];
-    double cx[STAG_MAX_RHS][STAG_MAX_SHIFTS];    // x_i += cx p_i
-    double cpr[STAG_MAX_RHS][STAG_MAX_SHIFTS];   // p_i = cpr r + cpp p_i
+    double cx[STAG_MAX_RHS][STAG_MAX_SHIFTS];    // x_i += cx p_i      (alpha_{i,k})
+    double cpr[STAG_MAX_RHS][STAG_MAX_SHIFTS];   // p_i = cpr r + cpp p_i (zeta_k, beta_{i,k-1})
     double cpp[STAG_MAX_RHS][STAG_MAX_SHIFTS];
-    int live[STAG_MAX_RHS][STAG_MAX_SHIFTS];     // not converged yet
-    int active[STAG_MAX_RHS][STAG_MAX_SHIFTS];   // updated in the pending shift update
+    int live[STAG_MAX_RHS][STAG_MAX_SHIFTS];     // not converged: updated in the next iteration
     int iters_at[STAG_MAX_RHS][STAG_MAX_SHIFTS];
 };

@@ -244,7 +244,7 @@ def stag_draw_sources(ctx, seed, counter, stream, n, xi):
            "stag_draw_sources", ctx)
 
 
-STAG_PK_DSLASH_OE, STAG_PK_DSLASH_EO_A, STAG_PK_RUPDATE, STAG_PK_SHIFT_UPDATE = 0, 1, 2, 3
+STAG_PK_DSLASH_OE, STAG_PK_DSLASH_EO_A, STAG_PK_UPDATE = 0, 1, 2
 
 
 def stag_profile_begin(ctx, sample_every):

@@ -65,7 +65,7 @@ def oracle_traj(c1):
     return u0, mom0, xi, out
 
 
-@pytest.mark.parametrize("prec,tol_dh,tol_u", [(0, 1e-7, 1e-10), (1, 2e-3, 1e-5), (2, 2e-3, 1e-5)])
+@pytest.mark.parametrize("prec,tol_dh,tol_u", [(0, 1e-7, 1e-10), (1, 2e-3, 1e-5), (2, 2e-3, 1e-5), (3, 2e-2, 1e-4)])
 def test_trajectory_matches_oracle(torch, c1, oracle_traj, prec, tol_dh, tol_u):
     from paper_1010_5433_gb300 import stag
     u0, mom0, xi, want = oracle_traj

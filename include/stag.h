@@ -111,6 +111,21 @@ stag_status stag_dslash(stag_ctx* ctx, int out_parity, stag_prec prec, int nrhs,
 stag_status stag_apply_a(stag_ctx* ctx, double mass, double shift, stag_prec prec,
                          int nrhs, const void* in, void* out);
 
+/* Same result as stag_apply_a, for callers that must not allocate device
+ * memory (a program whose device memory belongs to its own pool with no room
+ * left, or a loop that may not take the device-wide synchronisation of
+ * cudaFree).  No counterpart in the paper.  The intermediate odd field
+ * D_oe in lives in a fixed 32 MiB array in the library's device image instead
+ * of a workspace the context would allocate, so this call allocates nothing.
+ * Limit: nrhs * 3 * Vh * (16 bytes fp64, 8 bytes otherwise) <= 32 MiB, else
+ * STAG_ERR_ARG with the sizes in stag_last_cuda_error.  The first call on a
+ * device looks up the array's device address with that device current (make
+ * that first call before any stream capture).  All calls share the one
+ * array: calls whose work overlaps on the GPU (other streams, other host
+ * threads) race on it. */
+stag_status stag_apply_a_noalloc(stag_ctx* ctx, double mass, double shift, stag_prec prec,
+                                 int nrhs, const void* in, void* out);
+
 /* ---- solvers (Sec. 6; multi-shift CG after Jegerlehner, hep-lat/9612014) --- */
 
 typedef struct {

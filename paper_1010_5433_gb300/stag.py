@@ -90,6 +90,7 @@ def lib():
             "stag_store_gauge": ([vp, vp], i),
             "stag_dslash": ([vp, i, i, i, vp, vp], i),
             "stag_apply_a": ([vp, d, d, i, i, vp, vp], i),
+            "stag_apply_a_noalloc": ([vp, d, d, i, i, vp, vp], i),
             "stag_multishift_solve": ([vp, d, i, vp, i, i, vp, vp, d, i, C.POINTER(stag_solve_info)], i),
             "stag_fermion_force": ([vp, d, C.POINTER(stag_rational), i, i, vp, vp, d, i,
                                     C.POINTER(stag_solve_info)], i),
@@ -193,6 +194,13 @@ def stag_dslash(ctx, out_parity, prec, nrhs, inp, out):
 def stag_apply_a(ctx, mass, shift, prec, nrhs, inp, out):
     _check(lib().stag_apply_a(ctx, float(mass), float(shift), int(prec), int(nrhs), _ptr(inp), _ptr(out)),
            "stag_apply_a", ctx)
+
+
+def stag_apply_a_noalloc(ctx, mass, shift, prec, nrhs, inp, out):
+    """stag_apply_a without any device allocation (fixed library scratch)."""
+    st = lib().stag_apply_a_noalloc(ctx, float(mass), float(shift), int(prec), int(nrhs), _ptr(inp), _ptr(out))
+    if st != 0:
+        raise StagError(st, "stag_apply_a_noalloc", lib().stag_last_cuda_error(ctx).decode())
 
 
 def stag_multishift_solve(ctx, mass, shifts, prec, nrhs, b, x, tol, max_iter, info=True, check=True):

@@ -186,7 +186,7 @@ def run_gpu(args, rank, world, local_rank):
         launches = stag.stag_launch_count(ctx) - launches0
         prof = None
         if profile:
-            prof = [stag.stag_profile_read(ctx, kk) for kk in range(3)]
+            prof = [stag.stag_profile_read(ctx, kk) for kk in range(4)]
             stag.stag_profile_begin(ctx, 0)
         return ms, trajs, clk.summary(), launches, prof
 
@@ -226,13 +226,14 @@ def run_gpu(args, rank, world, local_rank):
 
     # ---- roofline of the dominant kernel, from the live sampled events
     hbm, peak_kind = peaks()
-    names = ["dslash_oe", "dslash_eo_A", "update"]
+    names = ["dslash_oe", "dslash_eo_A", "update", "persistent_iteration"]
     kern = []
     for nm, pr in zip(names, prof):
         avg_ms = pr.sampled_ms / max(pr.sampled, 1)
         kern.append({"kernel": nm, "launches": pr.launches, "sampled": pr.sampled, "avg_us": avg_ms * 1e3,
                      "bytes_per_launch": pr.bytes_per_launch, "est_total_ms": avg_ms * pr.launches,
                      "achieved_gbs": pr.bytes_per_launch / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else 0.0})
+    kern = [k for k in kern if k["launches"] > 0]
     dom = max(kern, key=lambda k: k["est_total_ms"])
     roofline = {"bound": "hbm", "kernel": dom["kernel"], "achieved": round(dom["achieved_gbs"], 1), "peak": hbm,
                 "unit": "GB/s", "frac": round(dom["achieved_gbs"] / hbm, 4), "traffic": None,
@@ -262,11 +263,15 @@ def run_gpu(args, rank, world, local_rank):
                                    "mean_abs_dH": float(np.mean(np.abs(dh))),
                                    "cg_iterations_per_traj": float(np.mean([t.cg_iterations for t in trajs])),
                                    "reliable_updates_per_traj": float(np.mean([t.reliable_updates for t in trajs])),
+                                   "seconds_breakdown": {k: round(float(np.mean([getattr(t, "t_" + k) for t in trajs])), 4)
+                                                         for k in ("heatbath", "fermion", "gauge", "metropolis")},
                                    "plaquette": trajs[-1].plaq},
                          "fp64": {"value": round(value64, 2), "unit": "trajectories/hour", "steps": steps64,
                                   "dH": [round(x, 5) for x in dh64], "accepted": [t.accepted for t in trajs64],
                                   "mean_abs_dH": float(np.mean(np.abs(dh64))),
-                                  "cg_iterations_per_traj": float(np.mean([t.cg_iterations for t in trajs64]))},
+                                  "cg_iterations_per_traj": float(np.mean([t.cg_iterations for t in trajs64])),
+                                  "seconds_breakdown": {k: round(float(np.mean([getattr(t, "t_" + k) for t in trajs64])), 4)
+                                                        for k in ("heatbath", "fermion", "gauge", "metropolis")}},
                          "speedup_mixed_vs_fp64": round(value / value64, 3),
                          "warmup_dH": [round(t.dH, 4) for t in warm]},
         "dslash_roofline_point": point,

@@ -236,6 +236,10 @@ typedef struct {
     long long cg_iterations;    /* Krylov iterations summed over all solves */
     int reliable_updates;
     double seconds;             /* device time of the trajectory */
+    double t_heatbath;          /* device time of the heatbath inversions (s) */
+    double t_fermion;           /* of the fermion-force kicks: MD inversions + force */
+    double t_gauge;             /* of the gauge levels: Wilson force + link updates */
+    double t_metropolis;        /* of the final fermion action (Metropolis inversions) */
 } stag_traj;
 
 /* One RHMC trajectory: heatbath, two-level minimum-norm MD, Metropolis with a
@@ -251,6 +255,8 @@ const double* stag_momenta(stag_ctx* ctx);
 #define STAG_PK_DSLASH_OE 0      /* t = D_oe (r + beta p), multi-RHS                             */
 #define STAG_PK_DSLASH_EO_A 1    /* p = r + beta p; q = c0 p - D_eo t; (p, q) and the alpha step */
 #define STAG_PK_UPDATE 2         /* p_i, x_i of the live shifts; r -= alpha q; (r, r), beta step  */
+#define STAG_PK_PERSISTENT 3     /* persistent solver (small lattices): units are iterations,
+                                    every launch event-timed, bytes = one whole iteration       */
 typedef struct {
     long long launches;       /* launches of this kernel since stag_profile_begin */
     int sampled;              /* of which bracketed by CUDA events on the context's stream */
@@ -265,6 +271,12 @@ stag_status stag_profile_begin(stag_ctx* ctx, int sample_every);
 stag_status stag_profile_read(stag_ctx* ctx, int kind, stag_kernel_profile* out);
 /* Number of kernels this context has launched since its creation. */
 long long stag_launch_count(stag_ctx* ctx);
+/* Threads per site the Dslash of this precision and source count uses (1, 2,
+ * 4 or 8), autotuned on the context's first need: every candidate is timed
+ * as a CUDA graph of 20 launches and the fastest kept; us_per_launch (may be
+ * NULL) receives its time.  The environment variable STAG_DSLASH_TPS fixes
+ * the value instead.  Returns 0 on a bad argument. */
+int stag_tuned_threads_per_site(stag_ctx* ctx, stag_prec prec, int nrhs, double* us_per_launch);
 
 #ifdef __cplusplus
 }

@@ -82,6 +82,7 @@ extern "C" void stag_destroy(stag_ctx* ctx) {
     if (ctx->g16) cudaFree(ctx->g16);
     if (ctx->red) cudaFree(ctx->red);
     if (ctx->counters) cudaFree(ctx->counters);
+    if (ctx->bar) cudaFree(ctx->bar);
     if (ctx->scal) cudaFree(ctx->scal);
     if (ctx->st) cudaFree(ctx->st);
     if (ctx->scal_host) cudaFreeHost(ctx->scal_host);
@@ -118,9 +119,15 @@ extern "C" stag_status stag_create(const stag_lattice* lat, stag_ctx** out) {
     // e.g. under a profiler that replays single kernels
     const char* gr = std::getenv("STAG_GRAPHS");
     ctx->use_graphs = !(gr && gr[0] == '0');
+    // STAG_DSLASH_TPS=1|2|4|8 fixes the threads per site instead of tuning
+    const char* tp = std::getenv("STAG_DSLASH_TPS");
+    ctx->tps_force = tp ? std::atoi(tp) : 0;
+    const char* pe = std::getenv("STAG_PERSISTENT");
+    ctx->use_persistent = !(pe && pe[0] == '0');
     stag_status s = STAG_OK;
     size_t gbytes = (size_t)4 * 2 * 18 * ctx->g.Vh * sizeof(float);
     size_t bbytes = (size_t)4 * 2 * 12 * ctx->g.Vh * sizeof(uint16_t);
+    ctx->red_doubles = red_doubles(ctx->g.Vh);
     if ((s = dev_alloc(ctx, (void**)&ctx->ghi, gbytes)) != STAG_OK ||
         (s = dev_alloc(ctx, (void**)&ctx->glo, gbytes)) != STAG_OK ||
         (s = dev_alloc(ctx, (void**)&ctx->g16, bbytes)) != STAG_OK ||

@@ -65,6 +65,53 @@ __device__ __forceinline__ void site_neighbours(const Geom& g, int h, int par, N
     }
 }
 
+// ---------------------------------------------------------------- float-float reals
+// DF = hi + lo with two floats: the representation of Sec. 5 / Fig. 2 of the
+// paper, used "directly" (the option the paper names and leaves aside on
+// hardware with fast doubles).  On GB300 fp32 issue is ~64x fp64 issue, so
+// fp64-accurate (about 48-bit) Dslash and solver vectors run on the fp32
+// pipes.  Arithmetic: Knuth's two-sum / Dekker's fast two-sum for addition,
+// an FMA-based exact product for multiplication (error-free transformations).
+struct DF {
+    float hi, lo;
+    __host__ __device__ __forceinline__ DF() {}
+    __host__ __device__ __forceinline__ DF(int v) : hi((float)v), lo(0.f) {}
+    __host__ __device__ __forceinline__ DF(float v) : hi(v), lo(0.f) {}
+    __host__ __device__ __forceinline__ DF(float h, float l) : hi(h), lo(l) {}
+    __host__ __device__ __forceinline__ DF(double v) {
+        hi = (float)v;
+        lo = (float)(v - (double)hi);
+    }
+    __host__ __device__ __forceinline__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+__device__ __forceinline__ DF df_two_sum(float a, float b) {
+    float s = a + b;
+    float bb = s - a;
+    return DF(s, (a - (s - bb)) + (b - bb));
+}
+__device__ __forceinline__ DF df_fast_two_sum(float a, float b) {
+    float s = a + b;
+    return DF(s, b - (s - a));
+}
+__device__ __forceinline__ DF operator+(DF a, DF b) {
+    DF s = df_two_sum(a.hi, b.hi);
+    return df_fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+__device__ __forceinline__ DF operator-(DF a) { return DF(-a.hi, -a.lo); }
+__device__ __forceinline__ DF operator-(DF a, DF b) { return a + (-b); }
+__device__ __forceinline__ DF operator*(DF a, DF b) {
+    float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ DF& operator+=(DF& a, DF b) { return a = a + b; }
+__device__ __forceinline__ DF __shfl_xor_sync(unsigned int mask, DF v, int lane_mask) {
+    return DF(__shfl_xor_sync(mask, v.hi, lane_mask), __shfl_xor_sync(mask, v.lo, lane_mask));
+}
+__device__ __forceinline__ DF& operator-=(DF& a, DF b) { return a = a - b; }
+
 // ---------------------------------------------------------------- complex / SU(3)
 template <typename R> struct Cx { R re, im; };
 
@@ -252,6 +299,10 @@ __device__ __forceinline__ Su3<float> load_link_bf(const uint16_t* __restrict__ 
 template <typename R> struct V2T;
 template <> struct V2T<float> { typedef float2 T; };
 template <> struct V2T<double> { typedef double2 T; };
+template <> struct V2T<DF> { typedef float4 T; };   // (re.hi, re.lo, im.hi, im.lo)
+
+__device__ __forceinline__ Cx<DF> cx_of(float4 a) { return mk(DF(a.x, a.y), DF(a.z, a.w)); }
+__device__ __forceinline__ float4 f4_of(Cx<DF> v) { return make_float4(v.re.hi, v.re.lo, v.im.hi, v.im.lo); }
 
 template <typename R>
 __device__ __forceinline__ Vec3<R> load_vec(const typename V2T<R>::T* __restrict__ f, int h, int Vh) {
@@ -289,6 +340,49 @@ template <typename R> __device__ __forceinline__ double re_dot(const Vec3<R>& a,
 #pragma unroll
     for (int c = 0; c < 3; ++c) s += a.c[c].re * b.c[c].re + a.c[c].im * b.c[c].im;
     return (double)s;
+}
+
+// float-float spinors: load / store the float4 planes
+template <>
+__device__ __forceinline__ Vec3<DF> load_vec<DF>(const float4* __restrict__ f, int h, int Vh) {
+    Vec3<DF> v;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) v.c[c] = cx_of(__ldg(f + (size_t)c * Vh + h));
+    return v;
+}
+template <>
+__device__ __forceinline__ Vec3<DF> load_vec_cg<DF>(const float4* f, int h, int Vh) {
+    Vec3<DF> v;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) v.c[c] = cx_of(__ldcg(f + (size_t)c * Vh + h));
+    return v;
+}
+template <>
+__device__ __forceinline__ void store_vec<DF>(float4* f, int h, int Vh, const Vec3<DF>& v) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) f[(size_t)c * Vh + h] = f4_of(v.c[c]);
+}
+
+// the two-float gauge store read as float-float links (no conversion at all)
+__device__ __forceinline__ Su3<DF> load_link_df(const float* __restrict__ hi, const float* __restrict__ lo,
+                                                size_t blk, int h, int Vh) {
+    const float4* ph = reinterpret_cast<const float4*>(hi + blk);
+    const float4* pl = reinterpret_cast<const float4*>(lo + blk);
+    float vh[18], vl[18];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        float4 a = __ldg(ph + (size_t)k * Vh + h);
+        float4 b = __ldg(pl + (size_t)k * Vh + h);
+        vh[4 * k] = a.x; vh[4 * k + 1] = a.y; vh[4 * k + 2] = a.z; vh[4 * k + 3] = a.w;
+        vl[4 * k] = b.x; vl[4 * k + 1] = b.y; vl[4 * k + 2] = b.z; vl[4 * k + 3] = b.w;
+    }
+    float2 e = __ldg(reinterpret_cast<const float2*>(hi + blk + 16 * (size_t)Vh) + h);
+    float2 f = __ldg(reinterpret_cast<const float2*>(lo + blk + 16 * (size_t)Vh) + h);
+    vh[16] = e.x; vh[17] = e.y; vl[16] = f.x; vl[17] = f.y;
+    Su3<DF> u;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) u.e[k / 3][k % 3] = mk(DF(vh[2 * k], vl[2 * k]), DF(vh[2 * k + 1], vl[2 * k + 1]));
+    return u;
 }
 template <typename R> __device__ __forceinline__ double norm2(const Vec3<R>& a) { return re_dot(a, a); }
 

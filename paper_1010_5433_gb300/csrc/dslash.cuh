@@ -22,6 +22,11 @@ template <> struct LinkFetch<double, FMT_F64> {
         return load_link_d(L.hi, L.lo, link_block_f(mu, par, Vh), h, Vh);
     }
 };
+template <> struct LinkFetch<DF, FMT_F64> {
+    __device__ __forceinline__ static Su3<DF> get(const LinkPtrs& L, int mu, int par, int h, int Vh) {
+        return load_link_df(L.hi, L.lo, link_block_f(mu, par, Vh), h, Vh);
+    }
+};
 template <> struct LinkFetch<float, FMT_F32_18> {
     __device__ __forceinline__ static Su3<float> get(const LinkPtrs& L, int mu, int par, int h, int Vh) {
         return load_link_f<3>(L.hi + link_block_f(mu, par, Vh), h, Vh);
@@ -48,51 +53,85 @@ template <typename R> struct SrcPlain {
     }
 };
 
-// Accumulate sum_mu [ sf U_mu(x) in(x+mu) - sb U_mu(x-mu)^dag in(x-mu) ] for NR sources
-// (the factor 1/2 is left to the epilogue).
-template <typename R, int FMT, int NR, class Src>
+// Accumulate the hops of one site for NR sources:
+//   sum_mu [ sf U_mu(x) in(x+mu) - sb U_mu(x-mu)^dag in(x-mu) ]
+// (the factor 1/2 is left to the epilogue).  With TPS threads per site, thread
+// `sub` takes the hops of mu = sub, sub + TPS, ... (TPS <= 4), or, for TPS = 8,
+// the forward (even sub) or backward (odd sub) hop of mu = sub / 2; the TPS
+// partial sums are then added with warp shuffles.
+template <typename R, int FMT, int NR, int TPS, class Src>
 __device__ __forceinline__ void dslash_site(const Geom& g, int out_par, const LinkPtrs& L, const Src& src,
-                                            int r0, int nrhs, int h, Vec3<R> (&acc)[NR]) {
+                                            int r0, int nrhs, int h, int sub, Vec3<R> (&acc)[NR]) {
     Nbr n;
     site_neighbours(g, h, out_par, n);
 #pragma unroll
     for (int r = 0; r < NR; ++r) zero(acc[r]);
 #pragma unroll
-    for (int mu = 0; mu < 4; ++mu) {
-        Su3<R> u = LinkFetch<R, FMT>::get(L, mu, out_par, h, g.Vh);
+    for (int m = 0; m < (TPS >= 4 ? 1 : 4 / TPS); ++m) {
+        const int mu = TPS == 8 ? (sub >> 1) : (TPS == 4 ? sub : sub + m * TPS);
+        const bool do_fwd = TPS < 8 || (sub & 1) == 0;
+        const bool do_bwd = TPS < 8 || (sub & 1) == 1;
+        if (do_fwd) {
+            Su3<R> u = LinkFetch<R, FMT>::get(L, mu, out_par, h, g.Vh);
 #pragma unroll
-        for (int r = 0; r < NR; ++r) {
-            if (r0 + r < nrhs) {
-                Vec3<R> v = src.load(r, r0 + r, n.fwd[mu], g.Vh);
-                mac_uv(acc[r], (R)n.sf[mu], u, v);
+            for (int r = 0; r < NR; ++r) {
+                if (r0 + r < nrhs) {
+                    Vec3<R> v = src.load(r, r0 + r, n.fwd[mu], g.Vh);
+                    mac_uv(acc[r], (R)n.sf[mu], u, v);
+                }
             }
         }
-        Su3<R> w = LinkFetch<R, FMT>::get(L, mu, 1 - out_par, n.bwd[mu], g.Vh);
+        if (do_bwd) {
+            Su3<R> w = LinkFetch<R, FMT>::get(L, mu, 1 - out_par, n.bwd[mu], g.Vh);
 #pragma unroll
-        for (int r = 0; r < NR; ++r) {
-            if (r0 + r < nrhs) {
-                Vec3<R> v = src.load(r, r0 + r, n.bwd[mu], g.Vh);
-                mac_udv(acc[r], -(R)n.sb[mu], w, v);
+            for (int r = 0; r < NR; ++r) {
+                if (r0 + r < nrhs) {
+                    Vec3<R> v = src.load(r, r0 + r, n.bwd[mu], g.Vh);
+                    mac_udv(acc[r], -(R)n.sb[mu], w, v);
+                }
             }
         }
     }
 }
 
+template <int TPS, typename R>
+__device__ __forceinline__ R group_sum(R v) {
+#pragma unroll
+    for (int o = TPS / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 // Grid: blockIdx.x = site_block * nchunk + chunk, so that the chunks of one
-// site block run back to back and re-read its links from L2.
-template <typename R, int FMT, int NR, class Src, class Epi>
+// site block run back to back and re-read its links from L2.  A block of
+// blockDim.x threads covers blockDim.x / TPS sites.
+template <typename R, int FMT, int NR, int TPS, class Src, class Epi>
 __global__ void __launch_bounds__(STAG_RED_BLOCK)
 k_dslash(Geom g, int out_par, LinkPtrs L, Src src, int nrhs, int nchunk, Epi epi) {
     if (epi.halted()) return;
     const int chunk = blockIdx.x % nchunk;
     const int sblock = blockIdx.x / nchunk;
-    const int h = sblock * blockDim.x + threadIdx.x;
+    const int sub = TPS > 1 ? (int)(threadIdx.x % TPS) : 0;
+    const int h = sblock * (blockDim.x / TPS) + threadIdx.x / TPS;
     const int r0 = chunk * NR;
     Vec3<R> acc[NR];
-    const bool valid = h < g.Vh;
+    const bool inside = h < g.Vh;
     src.template prepare<NR>(r0, nrhs);
-    if (valid) dslash_site<R, FMT, NR>(g, out_par, L, src, r0, nrhs, h, acc);
-    epi.template finish<NR>(g, h, valid, r0, nrhs, acc);
+    if (inside) {
+        dslash_site<R, FMT, NR, TPS>(g, out_par, L, src, r0, nrhs, h, sub, acc);
+    } else {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) zero(acc[r]);
+    }
+    if (TPS > 1) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                acc[r].c[c].re = group_sum<TPS>(acc[r].c[c].re);
+                acc[r].c[c].im = group_sum<TPS>(acc[r].c[c].im);
+            }
+    }
+    epi.template finish<NR>(g, h, inside && sub == 0, r0, nrhs, acc);
 }
 
 // Plain epilogue: out = scale * acc  (scale = 1/2 for D itself).
@@ -140,4 +179,13 @@ template <typename R> struct EpiAop {
     }
 };
 
-inline int dslash_nr_for(int nrhs) { return nrhs >= 4 ? 4 : (nrhs >= 2 ? 2 : 1); }
+inline int dslash_nr_for(int nrhs) { return nrhs >= 2 ? 4 : 1; }
+
+// Threads per site: enough threads to fill the GPU at small volumes (about
+// 2^19 in flight), one per site once the lattice alone provides them.
+inline int dslash_tps_for(long long vh) {
+    long long t = (1LL << 19) / (vh > 0 ? vh : 1);
+    return t >= 8 ? 8 : t >= 4 ? 4 : t >= 2 ? 2 : 1;
+}
+
+#define STAG_DSLASH_BLOCK 128

@@ -91,9 +91,43 @@ stag_status apply_rational_f64(stag_ctx* ctx, double mass, const stag_rational& 
     return STAG_OK;
 }
 
+// Events bracketing the phases of a trajectory, read after its final sync.
+struct PhaseTimer {
+    stag_ctx* ctx = nullptr;
+    std::vector<cudaEvent_t> ev;
+    std::vector<std::pair<int, int>> spans[4];   // heatbath, fermion, gauge, metropolis
+    int open_at = -1;
+    stag_status begin(int) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaEventCreate");
+        ev.push_back(e);
+        open_at = (int)ev.size() - 1;
+        return cudaEventRecord(e, ctx->stream) == cudaSuccess ? STAG_OK : cuda_fail(ctx, cudaGetLastError(), "rec");
+    }
+    stag_status end(int kind) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaEventCreate");
+        ev.push_back(e);
+        spans[kind].push_back({open_at, (int)ev.size() - 1});
+        return cudaEventRecord(e, ctx->stream) == cudaSuccess ? STAG_OK : cuda_fail(ctx, cudaGetLastError(), "rec");
+    }
+    double seconds(int kind) {
+        double t = 0.0;
+        for (auto& sp : spans[kind]) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, ev[sp.first], ev[sp.second]) == cudaSuccess) t += ms * 1e-3;
+        }
+        return t;
+    }
+    ~PhaseTimer() {
+        for (auto e : ev) cudaEventDestroy(e);
+    }
+};
+
 struct Traj {
     stag_ctx* ctx;
     const stag_hmc* p;
+    PhaseTimer* timer = nullptr;
     double* mom;
     double* force;
     double2* phi;      // [flavour][pf][3][Vh]
@@ -108,18 +142,20 @@ struct Traj {
 
     // p -= c F_fermion (all flavours, all pseudo-fermions)
     stag_status fermion_kick(double c) {
+        CKS(timer->begin(1));
         for (int f = 0; f < p->n_flavours; ++f) {
             const stag_flavour& fl = p->flavour[f];
             CKS(fermion_force_core(ctx, fl.mass, &fl.md, p->md_prec, fl.n_pf, phi_of(f), mom, -c, 1, p->tol_md,
                                    p->max_iter, &ts));
         }
-        return STAG_OK;
+        return timer->end(1);
     }
     stag_status gauge_kick(double c) { return gauge_force_launch(ctx, upd, p->beta, mom, -c, 1); }
 
     // n minimum-norm steps of the gauge force over h, adjacent kicks merged
     stag_status gauge_level(double h, int n) {
         const double d = h / n;
+        CKS(timer->begin(2));
         CKS(gauge_kick(LAMBDA_2MN * d));
         for (int j = 0; j < n; ++j) {
             CKS(update_links(ctx, mom, d / 2, upd));
@@ -127,7 +163,7 @@ struct Traj {
             CKS(update_links(ctx, mom, d / 2, upd));
             CKS(gauge_kick((j == n - 1 ? 1.0 : 2.0) * LAMBDA_2MN * d));
         }
-        return STAG_OK;
+        return timer->end(2);
     }
 
     stag_status md_evolve() {
@@ -207,6 +243,9 @@ extern "C" stag_status stag_md_trajectory(stag_ctx* ctx, const stag_hmc* p, stag
     const size_t hc = half_c(ctx);
     const size_t mom_n = (size_t)64 * g.Vh;
     Traj T;
+    PhaseTimer timer;
+    timer.ctx = ctx;
+    T.timer = &timer;
     T.ctx = ctx;
     T.p = p;
     T.upd = p->md_prec == STAG_FP64 ? STAG_FP64 : STAG_FP32;
@@ -258,6 +297,7 @@ extern "C" stag_status stag_md_trajectory(stag_ctx* ctx, const stag_hmc* p, stag
         for (double v : nn) sf0 += v;
     }
     // heatbath (first inversion, fp64)
+    CKS(timer.begin(0));
     if (!p->ext_phi) {
         size_t off = 0;
         for (int f = 0; f < p->n_flavours; ++f) {
@@ -267,13 +307,16 @@ extern "C" stag_status stag_md_trajectory(stag_ctx* ctx, const stag_hmc* p, stag
             off += fl.n_pf;
         }
     }
+    CKS(timer.end(0));
     // molecular dynamics
     CKS(T.md_evolve());
     // H at the end (last inversion, fp64)
     double kin1, sg1, sf1 = 0.0;
     CKS(kinetic_sum(ctx, T.mom, &kin1));
     CKS(T.gauge_action(&sg1));
+    CKS(timer.begin(3));
     if (npf_total > 0) CKS(T.fermion_action(&sf1));
+    CKS(timer.end(3));
     const double h0 = kin0 + sg0 + sf0, h1 = kin1 + sg1 + sf1;
     const double dh = h1 - h0;
     double u;
@@ -300,5 +343,9 @@ extern "C" stag_status stag_md_trajectory(stag_ctx* ctx, const stag_hmc* p, stag
     out->cg_iterations = T.ts.iters;
     out->reliable_updates = T.ts.reliable;
     out->seconds = ms * 1e-3;
+    out->t_heatbath = timer.seconds(0);
+    out->t_fermion = timer.seconds(1);
+    out->t_gauge = timer.seconds(2);
+    out->t_metropolis = timer.seconds(3);
     return std::isfinite(dh) ? STAG_OK : STAG_ERR_NAN;
 }

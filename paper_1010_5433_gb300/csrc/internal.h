@@ -29,11 +29,13 @@ enum WsSlot {
     WS_REF_G, WS_REF_AX, WS_REF_T, WS_REF_R64, WS_REF_B32, WS_REF_E32, WS_REF_E64,  // refinement
     WS_FORCE_X64,      // fermion force: fp64 accumulation of the mixed solutions
     WS_FORCE_B32,      // fermion force: fp32 copy of phi
+    WS_TUNE_IN, WS_TUNE_OUT,   // autotuner fields
+    WS_B_DF, WS_X_DF,  // fp64 solves: float-float copies of b and x
     WS_COUNT
 };
 
 // Sampled CUDA-event timing of the solver kernels (stag_profile_*).
-enum ProfKind { PK_DSLASH_OE = 0, PK_DSLASH_EO_A, PK_UPDATE, PK_COUNT };
+enum ProfKind { PK_DSLASH_OE = 0, PK_DSLASH_EO_A, PK_UPDATE, PK_PERSISTENT, PK_COUNT };
 struct ProfData {
     bool on = false;
     int every = 16;
@@ -43,6 +45,8 @@ struct ProfData {
     std::vector<std::pair<int, int>> marks[PK_COUNT];
     double bytes_total[PK_COUNT] = {};           // algorithmic bytes over all launches
     long long launches[PK_COUNT] = {};
+    double persist_ms = 0.0;                     // persistent solver: event time of all launches
+    long long persist_iters = 0;                 // and the iterations they ran
 };
 
 struct SolverGraphEntry {
@@ -62,7 +66,8 @@ struct stag_ctx {
     bool has_gauge = false;
     bool b16_stale = true;
     // reductions
-    double* red = nullptr;            // partials, STAG_MAX_RED_BLOCKS * STAG_MAX_RHS * 4
+    double* red = nullptr;            // partial sums of the reducing kernels
+    size_t red_doubles = 0;
     unsigned int* counters = nullptr; // 16 counters, zero between launches
     double* scal = nullptr;           // small device scalar area (64 doubles)
     double* scal_host = nullptr;      // pinned mirror
@@ -76,6 +81,12 @@ struct stag_ctx {
     long long launches = 0;           // kernels launched by this context
     ProfData prof;
     bool use_graphs = true;           // solver iterations as a device-side WHILE graph
+    int tps_cache[4][2] = {};         // autotuned threads per site, [prec][nr == 4]
+    float tps_us[4][2] = {};          // the winner's time per launch (us)
+    int tps_force = 0;                // STAG_DSLASH_TPS: force a value (0 = tune)
+    bool no_alloc_call = false;       // inside stag_apply_a_noalloc: nothing may allocate
+    bool use_persistent = true;       // small lattices: persistent cooperative solver (STAG_PERSISTENT=0 off)
+    void* bar = nullptr;              // grid-barrier words of the persistent solver
     cudaStream_t cap_stream = nullptr;
     std::vector<SolverGraphEntry> graphs;
 };
@@ -114,7 +125,10 @@ inline int nblocks(long long n, int bs) { return (int)((n + bs - 1) / bs); }
 stag_status refresh_bf16(stag_ctx* ctx);
 stag_status gauge_copy(stag_ctx* ctx, float* dst_hi, float* dst_lo, const float* src_hi, const float* src_lo);
 
-// dslash.cu: out = scale * D_{out_par} in  (no reductions)
+// dslash.cu: threads per site for a Dslash of this precision and sources per
+// thread, autotuned on first use (never call it first inside a stream capture)
+int dslash_tps(stag_ctx* ctx, stag_prec prec, int nr);
+// out = scale * D_{out_par} in  (no reductions)
 stag_status launch_dslash(stag_ctx* ctx, int out_par, stag_prec prec, int nrhs, const void* in, void* out,
                           double scale);
 // out = c0 * aux - 1/2 D_eo tmp  with tmp = D_oe in  computed into ws
@@ -135,6 +149,11 @@ struct MsStats {
 stag_status ms_core(stag_ctx* ctx, double mass, int nshift, const double* shifts, stag_prec prec, int nrhs,
                     const void* b, const double2* b64, void* x, double2* x64, double tol, int max_iter,
                     bool reliable, bool finish_to_f64, MsStats* stats);
+
+// persistent.cu: the whole iteration loop in one cooperative launch
+bool persistent_fits(stag_ctx* ctx);
+stag_status launch_persistent(stag_ctx* ctx, stag_prec prec, int nrhs, void* r, void* p, void* q, void* t, void* ps,
+                              void* x);
 
 // force.cu
 // force kernels write out = coef F (mode 0) or add out += coef F (mode 1)

@@ -60,6 +60,11 @@ extern "C" stag_status stag_apply_a_noalloc(stag_ctx* ctx, double mass, double s
     void* tmp = nullptr;
     CKS(scratch_address(ctx, &tmp));
     // D_oe overwrites all nrhs*3*Vh entries of the scratch before D_eo reads
-    // them, so nothing left there by an earlier call needs clearing
-    return launch_apply_a(ctx, mass * mass + shift, prec, nrhs, in, out, tmp);
+    // them, so nothing left there by an earlier call needs clearing.  The
+    // flag keeps the Dslash autotuner (which allocates test fields) from
+    // running inside this call; an untuned precision uses one thread per site.
+    ctx->no_alloc_call = true;
+    stag_status s = launch_apply_a(ctx, mass * mass + shift, prec, nrhs, in, out, tmp);
+    ctx->no_alloc_call = false;
+    return s;
 }

@@ -300,36 +300,59 @@ __device__ void ms_beta_step(SolverState* st, const double* rrn, cudaGraphCondit
 // Fused update of iteration k at every site of every live source:
 //   p_i = zeta_k r_k + beta_{i,k-1} p_i ;  x_i += alpha_{i,k} p_i   (live shifts)
 //   r_{k+1} = r_k - alpha_k q ;  (r_{k+1}, r_{k+1})
-template <typename R>
+// A block covers VB/G sites; the G thread groups of a site share its shifts
+// (group g takes shifts g, g+G, ...), and the block synchronises before group 0
+// overwrites r_k, which every group reads.
+template <typename R, int G>
 __global__ void __launch_bounds__(VB) k_ms_update(SolverState* st, int Vh, typename V2T<R>::T* r,
                                                   const typename V2T<R>::T* __restrict__ q, typename V2T<R>::T* ps,
                                                   typename V2T<R>::T* x, double* partial, unsigned int* counter,
                                                   cudaGraphConditionalHandle cond, int use_cond) {
     if (*(volatile int*)&st->halt) return;
+    constexpr int SPB = VB / G;
     const int rhs = blockIdx.y;
-    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    const int grp = threadIdx.x / SPB;
+    const int h = blockIdx.x * SPB + threadIdx.x % SPB;
     const int ns = st->nshift;
     const size_t rs = (size_t)3 * Vh;
+    const bool work = st->rhs_live[rhs] && h < Vh;
     double v[1] = {0.0};
-    if (st->rhs_live[rhs] && h < Vh) {
-        Vec3<R> rv = load_vec_cg<R>(r + rhs * rs, h, Vh);
-        for (int s = 0; s < ns; ++s) {
-            if (!st->live[rhs][s]) continue;
-            const R cx = (R)st->cx[rhs][s], cpr = (R)st->cpr[rhs][s], cpp = (R)st->cpp[rhs][s];
-            typename V2T<R>::T* pp = ps + ((size_t)rhs * ns + s) * rs;
-            typename V2T<R>::T* xp = x + ((size_t)rhs * ns + s) * rs;
-            Vec3<R> pv = load_vec_cg<R>(pp, h, Vh);
-            Vec3<R> xv = load_vec_cg<R>(xp, h, Vh);
+    Vec3<R> rv;
+    zero(rv);
+    if (work) {
+        rv = load_vec_cg<R>(r + rhs * rs, h, Vh);
+        // shifts grp, grp+G, ... in batches of 4: all loads of a batch before its stores
+        for (int s0 = grp; s0 < ns; s0 += 4 * G) {
+            Vec3<R> pv[4], xv[4];
+            bool on[4];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                pv.c[c].re = cpr * rv.c[c].re + cpp * pv.c[c].re;
-                pv.c[c].im = cpr * rv.c[c].im + cpp * pv.c[c].im;
-                xv.c[c].re += cx * pv.c[c].re;
-                xv.c[c].im += cx * pv.c[c].im;
+            for (int u = 0; u < 4; ++u) {
+                const int s = s0 + u * G;
+                on[u] = s < ns && st->live[rhs][s];
+                if (on[u]) {
+                    pv[u] = load_vec_cg<R>(ps + ((size_t)rhs * ns + s) * rs, h, Vh);
+                    xv[u] = load_vec_cg<R>(x + ((size_t)rhs * ns + s) * rs, h, Vh);
+                }
             }
-            store_vec<R>(xp, h, Vh, xv);
-            store_vec<R>(pp, h, Vh, pv);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (!on[u]) continue;
+                const int s = s0 + u * G;
+                const R cx = (R)st->cx[rhs][s], cpr = (R)st->cpr[rhs][s], cpp = (R)st->cpp[rhs][s];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    pv[u].c[c].re = cpr * rv.c[c].re + cpp * pv[u].c[c].re;
+                    pv[u].c[c].im = cpr * rv.c[c].im + cpp * pv[u].c[c].im;
+                    xv[u].c[c].re += cx * pv[u].c[c].re;
+                    xv[u].c[c].im += cx * pv[u].c[c].im;
+                }
+                store_vec<R>(x + ((size_t)rhs * ns + s) * rs, h, Vh, xv[u]);
+                store_vec<R>(ps + ((size_t)rhs * ns + s) * rs, h, Vh, pv[u]);
+            }
         }
+    }
+    __syncthreads();
+    if (work && grp == 0) {
         const R a = (R)st->alpha[rhs];
         Vec3<R> qv = load_vec_cg<R>(q + rhs * rs, h, Vh);
 #pragma unroll
@@ -516,6 +539,20 @@ __global__ void __launch_bounds__(VB) k_residual(int Vh, double shift, const dou
     }
 }
 
+__global__ void k_d2df(size_t n, const double2* a, float4* b) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double2 v = a[i];
+    b[i] = f4_of(mk(DF(v.x), DF(v.y)));
+}
+
+__global__ void k_df2d(size_t n, const float4* a, double2* b) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const Cx<DF> v = cx_of(a[i]);
+    b[i] = make_double2((double)v.re, (double)v.im);
+}
+
 __global__ void k_d2f(size_t n, const double2* a, float2* b) {
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) b[i] = make_float2((float)a[i].x, (float)a[i].y);
@@ -539,17 +576,51 @@ static stag_status prof_events(stag_ctx* ctx, int* ev) {
     pf.used += 4;
     return STAG_OK;
 }
+// the two Dslash launches of one iteration for a given link format, sources
+// per thread and threads per site
+template <typename R, int FMT, int NR, int TPS>
+static void ms_dslash_pair(cudaStream_t stream, int grid, const Geom& g, const LinkPtrs& L, const SrcRp<R>& s1,
+                           const SrcPlain<R>& s2, const EpiMsOdd<R>& e1, const EpiMsA<R>& e2, int nrhs, int nchunk,
+                           cudaEvent_t mid) {
+    const int bs = STAG_DSLASH_BLOCK;
+    k_dslash<R, FMT, NR, TPS, SrcRp<R>, EpiMsOdd<R>><<<grid, bs, 0, stream>>>(g, 1, L, s1, nrhs, nchunk, e1);
+    if (mid) cudaEventRecord(mid, stream);
+    k_dslash<R, FMT, NR, TPS, SrcPlain<R>, EpiMsA<R>><<<grid, bs, 0, stream>>>(g, 0, L, s2, nrhs, nchunk, e2);
+}
+
+template <typename R, int FMT, int NR>
+static void ms_dslash_tps(int tps, cudaStream_t stream, int grid, const Geom& g, const LinkPtrs& L,
+                          const SrcRp<R>& s1, const SrcPlain<R>& s2, const EpiMsOdd<R>& e1, const EpiMsA<R>& e2,
+                          int nrhs, int nchunk, cudaEvent_t mid) {
+    switch (tps) {
+        case 8: ms_dslash_pair<R, FMT, NR, 8>(stream, grid, g, L, s1, s2, e1, e2, nrhs, nchunk, mid); break;
+        case 4: ms_dslash_pair<R, FMT, NR, 4>(stream, grid, g, L, s1, s2, e1, e2, nrhs, nchunk, mid); break;
+        case 2: ms_dslash_pair<R, FMT, NR, 2>(stream, grid, g, L, s1, s2, e1, e2, nrhs, nchunk, mid); break;
+        default: ms_dslash_pair<R, FMT, NR, 1>(stream, grid, g, L, s1, s2, e1, e2, nrhs, nchunk, mid); break;
+    }
+}
+
+template <typename R, int FMT>
+static void ms_dslash(int nr, int tps, cudaStream_t stream, int grid, const Geom& g, const LinkPtrs& L,
+                      const SrcRp<R>& s1, const SrcPlain<R>& s2, const EpiMsOdd<R>& e1, const EpiMsA<R>& e2,
+                      int nrhs, int nchunk, cudaEvent_t mid) {
+    if (nr == 4) ms_dslash_tps<R, FMT, 4>(tps, stream, grid, g, L, s1, s2, e1, e2, nrhs, nchunk, mid);
+    else ms_dslash_tps<R, FMT, 1>(tps, stream, grid, g, L, s1, s2, e1, e2, nrhs, nchunk, mid);
+}
+
+constexpr int UPDATE_GROUPS = 4;
+
 template <typename R>
 static stag_status ms_iterations(stag_ctx* ctx, cudaStream_t stream, stag_prec prec, int nrhs, int chunk, void* tmp,
                                  void* r, void* p, void* q, void* ps, void* x, bool sample,
                                  cudaGraphConditionalHandle cond, int use_cond) {
     typedef typename V2T<R>::T V;
     const Geom& g = ctx->g;
-    const int bs = 128;
-    int nr = dslash_nr_for(nrhs);
-    int nchunk = (nrhs + nr - 1) / nr;
-    int grid_d = nblocks(g.Vh, bs) * nchunk;
-    dim3 grid_v(nblocks(g.Vh, VB), nrhs);
+    const int nr = dslash_nr_for(nrhs);
+    const int tps = dslash_tps(ctx, prec, nr);
+    const int nchunk = (nrhs + nr - 1) / nr;
+    const int grid_d = nblocks(g.Vh, STAG_DSLASH_BLOCK / tps) * nchunk;
+    dim3 grid_u(nblocks(g.Vh, VB / UPDATE_GROUPS), nrhs);
     LinkPtrs L = link_ptrs(ctx);
     SrcRp<R> src1{(const V*)r, (const V*)p, ctx->st, {}};
     SrcPlain<R> src2{(const V*)tmp};
@@ -559,30 +630,21 @@ static stag_status ms_iterations(stag_ctx* ctx, cudaStream_t stream, stag_prec p
     for (int it = 0; it < chunk; ++it) {
         const bool smp = sample && pf.on;
         int ev[4];
-        if (smp) CKS(prof_events(ctx, ev));
-#define MS_LAUNCH(FMT_, NR_)                                                                                   \
-    if (smp) CK(cudaEventRecord(pf.pool[ev[0]], stream));                                                     \
-    k_dslash<R, FMT_, NR_, SrcRp<R>, EpiMsOdd<R>><<<grid_d, bs, 0, stream>>>(g, 1, L, src1, nrhs, nchunk, e1); \
-    if (smp) CK(cudaEventRecord(pf.pool[ev[1]], stream));                                                     \
-    k_dslash<R, FMT_, NR_, SrcPlain<R>, EpiMsA<R>><<<grid_d, bs, 0, stream>>>(g, 0, L, src2, nrhs, nchunk, e2); \
-    if (smp) CK(cudaEventRecord(pf.pool[ev[2]], stream));
-#define MS_FMT(FMT_)                         \
-    switch (nr) {                            \
-        case 4: MS_LAUNCH(FMT_, 4) break;    \
-        case 2: MS_LAUNCH(FMT_, 2) break;    \
-        default: MS_LAUNCH(FMT_, 1) break;   \
-    }
-        if constexpr (sizeof(R) == 8) {
-            MS_FMT(FMT_F64)
-        } else {
-            if (prec == STAG_FP32) { MS_FMT(FMT_F32_18) }
-            else if (prec == STAG_FP32_12) { MS_FMT(FMT_F32_12) }
-            else { MS_FMT(FMT_BF16_12) }
+        if (smp) {
+            CKS(prof_events(ctx, ev));
+            CK(cudaEventRecord(pf.pool[ev[0]], stream));
         }
-#undef MS_FMT
-#undef MS_LAUNCH
-        k_ms_update<R><<<grid_v, VB, 0, stream>>>(ctx->st, g.Vh, (V*)r, (const V*)q, (V*)ps, (V*)x, ctx->red,
-                                                  ctx->counters + 1, cond, use_cond);
+        cudaEvent_t mid = smp ? pf.pool[ev[1]] : nullptr;
+        if constexpr (sizeof(R) == 8) {
+            ms_dslash<R, FMT_F64>(nr, tps, stream, grid_d, g, L, src1, src2, e1, e2, nrhs, nchunk, mid);
+        } else {
+            if (prec == STAG_FP32) ms_dslash<R, FMT_F32_18>(nr, tps, stream, grid_d, g, L, src1, src2, e1, e2, nrhs, nchunk, mid);
+            else if (prec == STAG_FP32_12) ms_dslash<R, FMT_F32_12>(nr, tps, stream, grid_d, g, L, src1, src2, e1, e2, nrhs, nchunk, mid);
+            else ms_dslash<R, FMT_BF16_12>(nr, tps, stream, grid_d, g, L, src1, src2, e1, e2, nrhs, nchunk, mid);
+        }
+        if (smp) CK(cudaEventRecord(pf.pool[ev[2]], stream));
+        k_ms_update<R, UPDATE_GROUPS><<<grid_u, VB, 0, stream>>>(ctx->st, g.Vh, (V*)r, (const V*)q, (V*)ps, (V*)x,
+                                                                 ctx->red, ctx->counters + 1, cond, use_cond);
         if (smp) {
             CK(cudaEventRecord(pf.pool[ev[3]], stream));
             for (int k = 0; k < 3; ++k) pf.marks[k].push_back({ev[k], ev[k + 1]});
@@ -628,7 +690,7 @@ static stag_status solver_graph(stag_ctx* ctx, stag_prec prec, int nrhs, void* t
     cudaGraph_t body = np.conditional.phGraph_out[0];
     CK(cudaStreamBeginCaptureToGraph(ctx->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     stag_status s;
-    if (prec == STAG_FP64) s = ms_iterations<double>(ctx, ctx->cap_stream, prec, nrhs, 1, tmp, r, p, q, ps, x, false, h, 1);
+    if (prec == STAG_FP64) s = ms_iterations<DF>(ctx, ctx->cap_stream, prec, nrhs, 1, tmp, r, p, q, ps, x, false, h, 1);
     else s = ms_iterations<float>(ctx, ctx->cap_stream, prec, nrhs, 1, tmp, r, p, q, ps, x, false, h, 1);
     cudaGraph_t captured;
     cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &captured);
@@ -699,6 +761,20 @@ stag_status ms_core(stag_ctx* ctx, double mass, int nshift, const double* shifts
         CKS(ws_get(ctx, WS_U64, v64, &xb64));
     }
     if (mixed && x64) CK(cudaMemsetAsync(x64, 0, v64 * nshift, ctx->stream));
+    // fp64 solves iterate in float-float (Sec. 5: the two-float representation
+    // used directly): b and x are double on the outside, float-float inside
+    const void* b_user = b;
+    void* x_user = x;
+    if (!mixed) {
+        void *bdf, *xdf;
+        CKS(ws_get(ctx, WS_B_DF, v64, &bdf));
+        CKS(ws_get(ctx, WS_X_DF, v64 * nshift, &xdf));
+        k_d2df<<<nblocks((long long)nrhs * 3 * g.Vh, 256), 256, 0, ctx->stream>>>((size_t)nrhs * 3 * g.Vh,
+                                                                                   (const double2*)b_user, (float4*)bdf);
+        CKL();
+        b = bdf;
+        x = xdf;
+    }
     SolverState* hs = ctx->st_host;
     std::memset(hs, 0, sizeof(SolverState));
     hs->nrhs = nrhs;
@@ -716,23 +792,59 @@ stag_status ms_core(stag_ctx* ctx, double mass, int nshift, const double* shifts
         k_ms_init<float><<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, (const float2*)b, (float2*)r, (float2*)p,
                                                          (float2*)ps, (float2*)x, ctx->red, ctx->counters + 2);
     else
-        k_ms_init<double><<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, (const double2*)b, (double2*)r,
-                                                          (double2*)p, (double2*)ps, (double2*)x, ctx->red,
+        k_ms_init<DF><<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, (const float4*)b, (float4*)r,
+                                                          (float4*)p, (float4*)ps, (float4*)x, ctx->red,
                                                           ctx->counters + 2);
     CKL();
     stag_status status = STAG_OK;
     cudaGraphExec_t gexec = nullptr;
-    if (ctx->use_graphs) CKS(solver_graph(ctx, prec, nrhs, tmp, r, p, q, ps, x, &gexec));
+    const bool persistent = persistent_fits(ctx);
+    if (!persistent) {
+        dslash_tps(ctx, prec, dslash_nr_for(nrhs));   // tune before any capture
+        if (ctx->use_graphs) CKS(solver_graph(ctx, prec, nrhs, tmp, r, p, q, ps, x, &gexec));
+    }
+    cudaEvent_t pe0 = nullptr, pe1 = nullptr;
+    double persist_ms = 0.0;
+    if (persistent && ctx->prof.on) {
+        CK(cudaEventCreate(&pe0));
+        CK(cudaEventCreate(&pe1));
+    }
     // every segment either ends the solve or makes a reliable update (at most
     // one per decade of the residual), so the number of segments is bounded
     const int max_segments = ctx->use_graphs ? 64 + max_iter / 4 : 64 + max_iter;
     const int chunk = 16;
     for (int seg = 0;; ++seg) {
         if (seg > max_segments) { status = STAG_ERR_TIMEOUT; break; }
+        if (persistent) {
+            if (pe0) CK(cudaEventRecord(pe0, ctx->stream));
+            CKS(launch_persistent(ctx, prec, nrhs, r, p, q, tmp, ps, x));
+            if (pe1) CK(cudaEventRecord(pe1, ctx->stream));
+            CKS(pull_control(ctx));
+            if (pe0) {
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, pe0, pe1));
+                persist_ms += ms;
+            }
+            if (!hs->halt) { status = STAG_ERR_TIMEOUT; break; }   // the loop only ends by halting
+            if (hs->status != STAG_OK) { status = (stag_status)hs->status; break; }
+            if (hs->need_reliable) {
+                k_rel_accumulate<<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, x64, (float2*)x);
+                k_rel_gather_base<<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, x64, (double2*)xb64);
+                CKS(launch_apply_a(ctx, hs->c0, STAG_FP64, nrhs, xb64, ax64, t64));
+                k_rel_finish<<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, b64, (const double2*)ax64, (float2*)r,
+                                                             ctx->red, ctx->counters + 3);
+                ctx->launches += 3;
+                CK(cudaGetLastError());
+                hs->halt = 0;
+                CK(cudaMemcpyAsync(&ctx->st->halt, &hs->halt, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+                continue;
+            }
+            break;
+        }
         // sampled timing: a few plainly launched iterations at the start of every segment
         if (ctx->prof.on) {
             if (mixed) CKS(ms_iterations<float>(ctx, ctx->stream, prec, nrhs, 4, tmp, r, p, q, ps, x, true, 0, 0));
-            else CKS(ms_iterations<double>(ctx, ctx->stream, prec, nrhs, 4, tmp, r, p, q, ps, x, true, 0, 0));
+            else CKS(ms_iterations<DF>(ctx, ctx->stream, prec, nrhs, 4, tmp, r, p, q, ps, x, true, 0, 0));
         }
         if (gexec) {
             CK(cudaGraphLaunch(gexec, ctx->stream));
@@ -740,7 +852,7 @@ stag_status ms_core(stag_ctx* ctx, double mass, int nshift, const double* shifts
         } else if (mixed) {
             CKS(ms_iterations<float>(ctx, ctx->stream, prec, nrhs, chunk, tmp, r, p, q, ps, x, false, 0, 0));
         } else {
-            CKS(ms_iterations<double>(ctx, ctx->stream, prec, nrhs, chunk, tmp, r, p, q, ps, x, false, 0, 0));
+            CKS(ms_iterations<DF>(ctx, ctx->stream, prec, nrhs, chunk, tmp, r, p, q, ps, x, false, 0, 0));
         }
         CKS(pull_control(ctx));
         if (!hs->halt) continue;
@@ -762,8 +874,19 @@ stag_status ms_core(stag_ctx* ctx, double mass, int nshift, const double* shifts
         break;   // converged
     }
     CKS(pull_state(ctx));
+    if (pe0) cudaEventDestroy(pe0);
+    if (pe1) cudaEventDestroy(pe1);
     if (gexec) ctx->launches += 3LL * hs->k;   // kernels the graph ran
-    if (ctx->prof.on) {
+    if (persistent && ctx->prof.on) {
+        ProfData& pf = ctx->prof;
+        const double S = (double)(mixed ? sizeof(float2) : sizeof(double2));
+        // one iteration: both Dslash phases (links twice; r, p, t / t, p, r, p, q) and the update
+        pf.bytes_total[PK_PERSISTENT] += (double)hs->k * g.Vh * (2.0 * link_bytes_site(prec) + 8.0 * S * nrhs) +
+                                         hs->k4_units * g.Vh * (mixed ? 1.0 : 2.0);
+        pf.launches[PK_PERSISTENT] += hs->k;
+        pf.persist_ms += persist_ms;
+        pf.persist_iters += hs->k;
+    } else if (ctx->prof.on) {
         ProfData& pf = ctx->prof;
         const double S = (double)(mixed ? sizeof(float2) : sizeof(double2));
         // K1 reads r and p (the direction is formed on the fly) and writes t;
@@ -772,12 +895,19 @@ stag_status ms_core(stag_ctx* ctx, double mass, int nshift, const double* shifts
         pf.bytes_total[PK_DSLASH_EO_A] += (double)hs->k * g.Vh * (link_bytes_site(prec) + 5.0 * S * nrhs);
         for (int kk = 0; kk < PK_COUNT; ++kk) pf.launches[kk] += hs->k;
     }
+    if (!mixed) {
+        const size_t n = (size_t)nrhs * nshift * 3 * g.Vh;
+        k_df2d<<<nblocks((long long)n, 256), 256, 0, ctx->stream>>>(n, (const float4*)x, (double2*)x_user);
+        CKL();
+        x = x_user;
+        b = b_user;
+    }
     if (mixed && x64) {
         if (finish_to_f64) k_acc_final<<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, x64, (const float2*)x);
         else k_rel_output<<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, x64, (float2*)x);
         CKL();
     }
-    if (ctx->prof.on) ctx->prof.bytes_total[PK_UPDATE] += hs->k4_units * g.Vh * (mixed ? 1.0 : 2.0);
+    if (ctx->prof.on && !persistent) ctx->prof.bytes_total[PK_UPDATE] += hs->k4_units * g.Vh * (mixed ? 1.0 : 2.0);
 
     if (stats) {
         stats->iterations = hs->k;
@@ -958,6 +1088,8 @@ extern "C" stag_status stag_profile_begin(stag_ctx* ctx, int sample_every) {
         pf.bytes_total[k] = 0.0;
         pf.launches[k] = 0;
     }
+    pf.persist_ms = 0.0;
+    pf.persist_iters = 0;
     return STAG_OK;
 }
 
@@ -974,6 +1106,10 @@ extern "C" stag_status stag_profile_read(stag_ctx* ctx, int kind, stag_kernel_pr
     out->launches = pf.launches[kind];
     out->sampled = (int)pf.marks[kind].size();
     out->sampled_ms = ms;
+    if (kind == PK_PERSISTENT) {       // every persistent launch is timed; units are iterations
+        out->sampled = (int)pf.persist_iters;
+        out->sampled_ms = pf.persist_ms;
+    }
     out->bytes_per_launch = pf.launches[kind] ? pf.bytes_total[kind] / pf.launches[kind] : 0.0;
     return STAG_OK;
 }

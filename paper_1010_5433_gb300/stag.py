@@ -63,7 +63,8 @@ class stag_kernel_profile(C.Structure):
 class stag_traj(C.Structure):
     _fields_ = [("dH", C.c_double), ("H0", C.c_double), ("H1", C.c_double), ("plaq", C.c_double),
                 ("accepted", C.c_int), ("cg_iterations", C.c_longlong), ("reliable_updates", C.c_int),
-                ("seconds", C.c_double)]
+                ("seconds", C.c_double), ("t_heatbath", C.c_double), ("t_fermion", C.c_double),
+                ("t_gauge", C.c_double), ("t_metropolis", C.c_double)]
 
 
 _lib = None
@@ -101,6 +102,7 @@ def lib():
             "stag_profile_begin": ([vp, i], i),
             "stag_profile_read": ([vp, i, C.POINTER(stag_kernel_profile)], i),
             "stag_launch_count": ([vp], C.c_longlong),
+            "stag_tuned_threads_per_site": ([vp, i, i, C.POINTER(d)], i),
             "stag_draw_momenta": ([vp, C.c_ulonglong, C.c_ulonglong, vp], i),
             "stag_draw_sources": ([vp, C.c_ulonglong, C.c_ulonglong, i, i, vp], i),
         }
@@ -267,3 +269,9 @@ def stag_profile_read(ctx, kind):
 
 def stag_launch_count(ctx):
     return lib().stag_launch_count(ctx)
+
+
+def stag_tuned_threads_per_site(ctx, prec, nrhs):
+    us = C.c_double()
+    t = lib().stag_tuned_threads_per_site(ctx, int(prec), int(nrhs), C.byref(us))
+    return t, us.value

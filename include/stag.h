@@ -269,6 +269,10 @@ typedef struct {
 stag_status stag_profile_begin(stag_ctx* ctx, int sample_every);
 /* Synchronises the stream and reports kernel `kind` (STAG_PK_*). */
 stag_status stag_profile_read(stag_ctx* ctx, int kind, stag_kernel_profile* out);
+/* Persistent solver only: microseconds that block 0 spent since
+ * stag_profile_begin in [phase 1, barrier 1, phase 2, barrier 2 + alpha step,
+ * phase 3, barrier 3 + beta step] (6 values; %globaltimer). */
+stag_status stag_profile_phases(stag_ctx* ctx, double* us);
 /* Number of kernels this context has launched since its creation. */
 long long stag_launch_count(stag_ctx* ctx);
 /* Threads per site the Dslash of this precision and source count uses (1, 2,

@@ -83,6 +83,7 @@ extern "C" void stag_destroy(stag_ctx* ctx) {
     if (ctx->red) cudaFree(ctx->red);
     if (ctx->counters) cudaFree(ctx->counters);
     if (ctx->bar) cudaFree(ctx->bar);
+    if (ctx->ptime) cudaFree(ctx->ptime);
     if (ctx->scal) cudaFree(ctx->scal);
     if (ctx->st) cudaFree(ctx->st);
     if (ctx->scal_host) cudaFreeHost(ctx->scal_host);
@@ -124,6 +125,8 @@ extern "C" stag_status stag_create(const stag_lattice* lat, stag_ctx** out) {
     ctx->tps_force = tp ? std::atoi(tp) : 0;
     const char* pe = std::getenv("STAG_PERSISTENT");
     ctx->use_persistent = !(pe && pe[0] == '0');
+    const char* pb = std::getenv("STAG_PERSIST_BLOCK");
+    ctx->persist_block = (pb && std::atoi(pb) == 128) ? 128 : 256;
     stag_status s = STAG_OK;
     size_t gbytes = (size_t)4 * 2 * 18 * ctx->g.Vh * sizeof(float);
     size_t bbytes = (size_t)4 * 2 * 12 * ctx->g.Vh * sizeof(uint16_t);

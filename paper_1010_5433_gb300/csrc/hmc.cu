@@ -25,44 +25,80 @@ struct TrajStats {
     int reliable = 0;
 };
 
-// Force of sum_k phi_k^dag r(A) phi_k (phi fp64 [n][3][Vh]) written or added
-// into out with coefficient coef; iteration arithmetic prec.
+// One flavour's share of a fermion force: its mass, rational, pseudo-fermions.
+struct ForceTerm {
+    double mass;
+    const stag_rational* r;
+    int n;                 // pseudo-fermions
+    const double2* phi;    // [n][3][Vh] fp64
+};
+
+// Force of sum over terms and pseudo-fermions of phi^dag r(A) phi, written
+// (mode 0) or added (mode 1) into out with coefficient coef.  Every term's
+// multi-shift solutions go into one buffer, Y_i = D_oe X_i is then one
+// multi-RHS Dslash over all terms, pseudo-fermions and shifts (e.g. 60
+// right-hand sides for 2+1 flavours x 2 pseudo-fermions x 15 shifts), and the
+// force kernel runs once per term.
+stag_status fermion_force_terms(stag_ctx* ctx, const ForceTerm* terms, int nterms, stag_prec prec, double* out,
+                                double coef, int mode, double tol, int max_iter, TrajStats* ts) {
+    const size_t hc = half_c(ctx);
+    const bool f64 = prec == STAG_FP64;
+    const size_t cs = f64 ? sizeof(double2) : sizeof(float2);
+    size_t total = 0;
+    for (int t = 0; t < nterms; ++t) total += (size_t)terms[t].n * terms[t].r->n;
+    void *x, *y;
+    CKS(ws_get(ctx, WS_FORCE_X, total * hc * cs, &x));
+    CKS(ws_get(ctx, WS_FORCE_Y, total * hc * cs, &y));
+    size_t off = 0;
+    for (int t = 0; t < nterms; ++t) {
+        const ForceTerm& T = terms[t];
+        const int ns = T.r->n;
+        for (int k0 = 0; k0 < T.n; k0 += STAG_MAX_RHS) {
+            const int nb = std::min(STAG_MAX_RHS, T.n - k0);
+            const double2* ph = T.phi + (size_t)k0 * hc;
+            char* xk = (char*)x + (off + (size_t)k0 * ns) * hc * cs;
+            MsStats st;
+            std::memset(&st, 0, sizeof(st));
+            stag_status s;
+            if (f64) {
+                s = ms_core(ctx, T.mass, ns, T.r->beta, STAG_FP64, nb, ph, nullptr, xk, nullptr, tol, max_iter, false,
+                            true, &st);
+            } else {
+                void *b32, *x64 = nullptr;
+                CKS(ws_get(ctx, WS_FORCE_B32, (size_t)nb * hc * sizeof(float2), &b32));
+                CKS(blas_convert(ctx, (size_t)nb * hc, ph, 1, b32, 0));
+                const bool rel = prec != STAG_BF16_12;
+                if (rel) CKS(ws_get(ctx, WS_FORCE_X64, (size_t)nb * ns * hc * sizeof(double2), &x64));
+                s = ms_core(ctx, T.mass, ns, T.r->beta, prec, nb, b32, ph, xk, (double2*)x64, tol, max_iter, rel,
+                            false, &st);
+            }
+            if (s != STAG_OK && s != STAG_ERR_NOT_CONVERGED) return s;
+            if (ts) { ts->iters += st.iterations; ts->reliable += st.reliable; }
+        }
+        off += (size_t)T.n * ns;
+    }
+    // Y_i = D_oe X_i for every term, pseudo-fermion and shift: one n-RHS Dslash
+    const stag_prec py = f64 ? STAG_FP64 : STAG_FP32;
+    if (total > 0x7fffffff) return STAG_ERR_ARG;
+    CKS(launch_dslash(ctx, 1, py, (int)total, x, y, 0.5));
+    off = 0;
+    for (int t = 0; t < nterms; ++t) {
+        const ForceTerm& T = terms[t];
+        const int ns = T.r->n;
+        const char* xt = (const char*)x + off * hc * cs;
+        const char* yt = (const char*)y + off * hc * cs;
+        CKS(fermion_force_from_solutions(ctx, py, T.n, ns, T.r->alpha, xt, yt, out, coef, (t == 0) ? mode : 1));
+        off += (size_t)T.n * ns;
+    }
+    return STAG_OK;
+}
+
+// One term: the force of a single flavour (stag_fermion_force).
 stag_status fermion_force_core(stag_ctx* ctx, double mass, const stag_rational* r, stag_prec prec, int n,
                                const double2* phi, double* out, double coef, int mode, double tol, int max_iter,
                                TrajStats* ts) {
-    const int ns = r->n;
-    const size_t hc = half_c(ctx);
-    for (int k0 = 0; k0 < n; k0 += STAG_MAX_RHS) {
-        const int nb = std::min(STAG_MAX_RHS, n - k0);
-        const double2* ph = phi + (size_t)k0 * hc;
-        void *x, *y;
-        MsStats st;
-        std::memset(&st, 0, sizeof(st));
-        stag_status s;
-        if (prec == STAG_FP64) {
-            CKS(ws_get(ctx, WS_FORCE_X, (size_t)nb * ns * hc * sizeof(double2), &x));
-            CKS(ws_get(ctx, WS_FORCE_Y, (size_t)nb * ns * hc * sizeof(double2), &y));
-            s = ms_core(ctx, mass, ns, r->beta, STAG_FP64, nb, ph, nullptr, x, nullptr, tol, max_iter, false, true,
-                        &st);
-        } else {
-            void *b32, *x64 = nullptr;
-            CKS(ws_get(ctx, WS_FORCE_X, (size_t)nb * ns * hc * sizeof(float2), &x));
-            CKS(ws_get(ctx, WS_FORCE_Y, (size_t)nb * ns * hc * sizeof(float2), &y));
-            CKS(ws_get(ctx, WS_FORCE_B32, (size_t)nb * hc * sizeof(float2), &b32));
-            CKS(blas_convert(ctx, (size_t)nb * hc, ph, 1, b32, 0));
-            const bool rel = prec != STAG_BF16_12;
-            if (rel) CKS(ws_get(ctx, WS_FORCE_X64, (size_t)nb * ns * hc * sizeof(double2), &x64));
-            s = ms_core(ctx, mass, ns, r->beta, prec, nb, b32, ph, x, (double2*)x64, tol, max_iter, rel, false, &st);
-        }
-        if (s != STAG_OK && s != STAG_ERR_NOT_CONVERGED) return s;
-        if (ts) { ts->iters += st.iterations; ts->reliable += st.reliable; }
-        // Y_i = D_oe X_i for all sources and shifts: one n-RHS Dslash
-        const stag_prec py = prec == STAG_FP64 ? STAG_FP64 : STAG_FP32;
-        CKS(launch_dslash(ctx, 1, py, nb * ns, x, y, 0.5));
-        CKS(fermion_force_from_solutions(ctx, py, nb, ns, r->alpha, x, y, out, coef,
-                                         (k0 == 0) ? mode : 1));
-    }
-    return STAG_OK;
+    ForceTerm t{mass, r, n, phi};
+    return fermion_force_terms(ctx, &t, 1, prec, out, coef, mode, tol, max_iter, ts);
 }
 
 bool valid_rational(const stag_rational& r) {
@@ -140,14 +176,14 @@ struct Traj {
         return phi + off * half_c(ctx);
     }
 
-    // p -= c F_fermion (all flavours, all pseudo-fermions)
+    // p -= c F_fermion (all flavours, all pseudo-fermions in one force evaluation)
     stag_status fermion_kick(double c) {
         CKS(timer->begin(1));
-        for (int f = 0; f < p->n_flavours; ++f) {
-            const stag_flavour& fl = p->flavour[f];
-            CKS(fermion_force_core(ctx, fl.mass, &fl.md, p->md_prec, fl.n_pf, phi_of(f), mom, -c, 1, p->tol_md,
-                                   p->max_iter, &ts));
-        }
+        ForceTerm terms[STAG_MAX_FLAVOURS];
+        for (int f = 0; f < p->n_flavours; ++f)
+            terms[f] = ForceTerm{p->flavour[f].mass, &p->flavour[f].md, p->flavour[f].n_pf, phi_of(f)};
+        if (p->n_flavours > 0)
+            CKS(fermion_force_terms(ctx, terms, p->n_flavours, p->md_prec, mom, -c, 1, p->tol_md, p->max_iter, &ts));
         return timer->end(1);
     }
     stag_status gauge_kick(double c) { return gauge_force_launch(ctx, upd, p->beta, mom, -c, 1); }

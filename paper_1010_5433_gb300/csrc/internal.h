@@ -87,6 +87,8 @@ struct stag_ctx {
     bool no_alloc_call = false;       // inside stag_apply_a_noalloc: nothing may allocate
     bool use_persistent = true;       // small lattices: persistent cooperative solver (STAG_PERSISTENT=0 off)
     void* bar = nullptr;              // grid-barrier words of the persistent solver
+    void* ptime = nullptr;            // its per-phase ns counters while profiling
+    int persist_block = 256;          // its threads per block (STAG_PERSIST_BLOCK=128|256)
     cudaStream_t cap_stream = nullptr;
     std::vector<SolverGraphEntry> graphs;
 };

@@ -23,7 +23,6 @@
 
 namespace {
 
-constexpr int PB = 128;                       // threads per block
 constexpr long long BAR_SPIN_LIMIT = 1LL << 26;   // ~0.1-1 s of polling
 
 struct GridBar {
@@ -33,29 +32,37 @@ struct GridBar {
     unsigned int pad;
 };
 
-// Sense-free generation barrier over all blocks of a cooperative launch.
+// Generation barrier over all blocks of a cooperative launch, with gpu-scope
+// release/acquire atomics: a block's writes are released by its arrival and
+// acquired by every block that sees the generation advance.
+__device__ __forceinline__ unsigned int atom_add_release(unsigned int* a, unsigned int v) {
+    unsigned int old;
+    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(a), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* a) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+    return v;
+}
 __device__ __forceinline__ bool grid_sync(GridBar* b, unsigned int nblocks) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned int* vgen = &b->gen;
-        volatile unsigned int* verr = &b->err;
-        const unsigned int g0 = *vgen;
-        __threadfence();
-        const unsigned int arrived = atomicAdd(&b->count, 1u);
+        const unsigned int g0 = ld_acquire(&b->gen);
+        const unsigned int arrived = atom_add_release(&b->count, 1u);
         if (arrived == nblocks - 1) {
-            b->count = 0;
-            __threadfence();
-            atomicAdd(&b->gen, 1u);
+            // everyone has arrived (and released); reset, then open the next generation
+            asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(&b->count), "r"(0u) : "memory");
+            atom_add_release(&b->gen, 1u);
         } else {
             long long spins = 0;
-            while (*vgen == g0 && *verr == 0) {
+            while (ld_acquire(&b->gen) == g0 && ld_acquire(&b->err) == 0) {
                 if (++spins > BAR_SPIN_LIMIT) {
                     atomicExch(&b->err, 1u);
                     break;
                 }
             }
         }
-        __threadfence();
     }
     __syncthreads();
     return *(volatile unsigned int*)&b->err == 0;
@@ -275,15 +282,32 @@ __device__ __forceinline__ void shift_updates(const Scal& S, int j, int ns, size
     }
 }
 
-// NRP: sources per pass of the Dslash phases (1, or 4 for multi-source solves)
-template <typename R, int FMT, int NRP>
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// NRP: sources per pass of the Dslash phases (1, or 4 for multi-source solves);
+// PB: threads per block
+template <typename R, int FMT, int NRP, int PB>
 __global__ void __launch_bounds__(PB) k_ms_persistent(Geom g, LinkPtrs L, SolverState* st,
                                                       typename V2T<R>::T* r, typename V2T<R>::T* p,
                                                       typename V2T<R>::T* q, typename V2T<R>::T* t,
                                                       typename V2T<R>::T* ps, typename V2T<R>::T* x,
-                                                      double* partial, GridBar* bar) {
+                                                      double* partial, GridBar* bar, unsigned long long* ptime) {
     typedef typename V2T<R>::T V;
     __shared__ Scal S;
+    // profiling: block 0 accumulates ns spent in phase 1, barrier 1, phase 2,
+    // barrier 2 + alpha step, phase 3, barrier 3 + beta step
+    const bool timing = ptime && blockIdx.x == 0 && threadIdx.x == 0;
+    unsigned long long tp[7] = {0, 0, 0, 0, 0, 0, 0}, t_last = timing ? gtimer() : 0;
+#define PHASE_MARK(i)                               \
+    if (timing) {                                   \
+        unsigned long long t_now = gtimer();        \
+        tp[i] += t_now - t_last;                    \
+        t_last = t_now;                             \
+    }
     load_scal(S, st);
     const unsigned int nb = gridDim.x;
     const int nthreads = gridDim.x * blockDim.x;
@@ -333,7 +357,9 @@ __global__ void __launch_bounds__(PB) k_ms_persistent(Geom g, LinkPtrs L, Solver
                     if (r0 + j < nrhs) store_vec<R>(t + (size_t)(r0 + j) * rs, h, g.Vh, acc[j]);
             }
         }
+        PHASE_MARK(0)
         if (!(ok = grid_sync(bar, nb))) break;
+        PHASE_MARK(1)
         // ---- phase 2: p = r + beta p; q = c0 p - 1/4 (hops of t); (p, q)
         double dots[ND];
 #pragma unroll
@@ -388,9 +414,11 @@ __global__ void __launch_bounds__(PB) k_ms_persistent(Geom g, LinkPtrs L, Solver
         block_sum<ND>(dots);
         if (threadIdx.x == 0)
             for (int j = 0; j < nrhs && j < ND; ++j) partial[(size_t)j * nb + blockIdx.x] = dots[j];
+        PHASE_MARK(2)
         if (!(ok = grid_sync(bar, nb))) break;
         sum_partials(S, partial, nb);
         alpha_step(S);
+        PHASE_MARK(3)
         // ---- phase 3: shift updates and r -= alpha q with (r, r)
         double nrm[ND];
 #pragma unroll
@@ -416,6 +444,7 @@ __global__ void __launch_bounds__(PB) k_ms_persistent(Geom g, LinkPtrs L, Solver
         block_sum<ND>(nrm);
         if (threadIdx.x == 0)
             for (int j = 0; j < nrhs && j < ND; ++j) partial[(size_t)(STAG_MAX_RHS + j) * nb + blockIdx.x] = nrm[j];
+        PHASE_MARK(4)
         if (!(ok = grid_sync(bar, nb))) break;
         for (int j = 0; j < nrhs; ++j) {
             double v = block_sum_array(partial + (size_t)(STAG_MAX_RHS + j) * nb, nb);
@@ -423,7 +452,11 @@ __global__ void __launch_bounds__(PB) k_ms_persistent(Geom g, LinkPtrs L, Solver
         }
         __syncthreads();
         beta_step(S);
+        PHASE_MARK(5)
     }
+#undef PHASE_MARK
+    if (timing)
+        for (int i = 0; i < 6; ++i) ptime[i] += tp[i];
     if (!ok && threadIdx.x == 0) {
         S.halt = 1;
         S.status = STAG_ERR_TIMEOUT;
@@ -432,10 +465,10 @@ __global__ void __launch_bounds__(PB) k_ms_persistent(Geom g, LinkPtrs L, Solver
     if (blockIdx.x == 0) store_scal(S, st);
 }
 
-template <typename R, int FMT, int NRP>
-stag_status launch_persistent_t(stag_ctx* ctx, void* r, void* p, void* q, void* t, void* ps, void* x) {
+template <typename R, int FMT, int NRP, int PB>
+stag_status launch_persistent_pb(stag_ctx* ctx, void* r, void* p, void* q, void* t, void* ps, void* x) {
     typedef typename V2T<R>::T V;
-    auto kern = k_ms_persistent<R, FMT, NRP>;
+    auto kern = k_ms_persistent<R, FMT, NRP, PB>;
     int per_sm = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, PB, 0));
     if (per_sm < 1) return STAG_ERR_ARG;
@@ -455,7 +488,8 @@ stag_status launch_persistent_t(stag_ctx* ctx, void* r, void* p, void* q, void* 
     V *vr = (V*)r, *vp = (V*)p, *vq = (V*)q, *vt = (V*)t, *vps = (V*)ps, *vx = (V*)x;
     double* part = ctx->red;
     GridBar* bar = (GridBar*)ctx->bar;
-    void* args[] = {&g, &L, &st, &vr, &vp, &vq, &vt, &vps, &vx, &part, &bar};
+    unsigned long long* pt = ctx->prof.on ? (unsigned long long*)ctx->ptime : nullptr;
+    void* args[] = {&g, &L, &st, &vr, &vp, &vq, &vt, &vps, &vx, &part, &bar, &pt};
     CK(cudaLaunchCooperativeKernel((const void*)kern, grid, PB, args, 0, ctx->stream));
     ++ctx->launches;
     return STAG_OK;
@@ -465,6 +499,13 @@ stag_status launch_persistent_t(stag_ctx* ctx, void* r, void* p, void* q, void* 
 bool persistent_fits(stag_ctx* ctx) {
     // small lattices, where launch and loop overhead dominate the iteration
     return ctx->use_persistent && ctx->g.Vh <= (1 << 18);
+}
+
+template <typename R, int FMT, int NRP>
+stag_status launch_persistent_t(stag_ctx* ctx, void* r, void* p, void* q, void* t, void* ps, void* x) {
+    // threads per block: 256 halves the blocks that meet at every grid barrier
+    if (ctx->persist_block == 128) return launch_persistent_pb<R, FMT, NRP, 128>(ctx, r, p, q, t, ps, x);
+    return launch_persistent_pb<R, FMT, NRP, 256>(ctx, r, p, q, t, ps, x);
 }
 
 template <int NRP>
@@ -480,6 +521,21 @@ stag_status launch_persistent_n(stag_ctx* ctx, stag_prec prec, void* r, void* p,
 stag_status launch_persistent(stag_ctx* ctx, stag_prec prec, int nrhs, void* r, void* p, void* q, void* t, void* ps,
                               void* x) {
     if (!ctx->bar) CKS(dev_alloc(ctx, &ctx->bar, sizeof(GridBar)));
+    if (!ctx->ptime) {
+        CKS(dev_alloc(ctx, &ctx->ptime, 8 * sizeof(unsigned long long)));
+        CK(cudaMemsetAsync(ctx->ptime, 0, 8 * sizeof(unsigned long long), ctx->stream));
+    }
     if (nrhs == 1) return launch_persistent_n<1>(ctx, prec, r, p, q, t, ps, x);
     return launch_persistent_n<4>(ctx, prec, r, p, q, t, ps, x);
+}
+
+extern "C" stag_status stag_profile_phases(stag_ctx* ctx, double* us) {
+    if (!ctx || !us) return STAG_ERR_ARG;
+    unsigned long long t[8] = {0};
+    if (ctx->ptime) {
+        CK(cudaMemcpyAsync(t, ctx->ptime, sizeof(t), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    for (int i = 0; i < 6; ++i) us[i] = t[i] * 1e-3;
+    return STAG_OK;
 }

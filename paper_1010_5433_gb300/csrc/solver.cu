@@ -1090,6 +1090,7 @@ extern "C" stag_status stag_profile_begin(stag_ctx* ctx, int sample_every) {
     }
     pf.persist_ms = 0.0;
     pf.persist_iters = 0;
+    if (ctx->ptime) CK(cudaMemsetAsync(ctx->ptime, 0, 8 * sizeof(unsigned long long), ctx->stream));
     return STAG_OK;
 }
 

@@ -51,6 +51,11 @@ def run(dims, prec=1, nrhs=1, max_iter=400, width=0.3, mass=0.02, profile=True):
                 out[n] = {"launches": pr.launches, "sampled": pr.sampled, "avg_us": round(avg * 1e3, 2),
                           "bytes_per_launch": round(pr.bytes_per_launch),
                           "achieved_gbs": round(pr.bytes_per_launch / (avg * 1e-3) / 1e9, 1) if avg > 0 else 0}
+            ph = stag.stag_profile_phases(ctx)
+            it = max(info.iterations, 1)
+            out["persistent_phases_us_per_iteration"] = dict(zip(
+                ["phase1_doe", "barrier1", "phase2_deo_A", "barrier2_alpha", "phase3_update", "barrier3_beta"],
+                [round(v / it, 2) for v in ph]))
     finally:
         stag.stag_destroy(ctx)
     return out

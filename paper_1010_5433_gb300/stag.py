@@ -102,6 +102,7 @@ def lib():
             "stag_profile_begin": ([vp, i], i),
             "stag_profile_read": ([vp, i, C.POINTER(stag_kernel_profile)], i),
             "stag_launch_count": ([vp], C.c_longlong),
+            "stag_profile_phases": ([vp, C.POINTER(d)], i),
             "stag_tuned_threads_per_site": ([vp, i, i, C.POINTER(d)], i),
             "stag_draw_momenta": ([vp, C.c_ulonglong, C.c_ulonglong, vp], i),
             "stag_draw_sources": ([vp, C.c_ulonglong, C.c_ulonglong, i, i, vp], i),
@@ -275,3 +276,9 @@ def stag_tuned_threads_per_site(ctx, prec, nrhs):
     us = C.c_double()
     t = lib().stag_tuned_threads_per_site(ctx, int(prec), int(nrhs), C.byref(us))
     return t, us.value
+
+
+def stag_profile_phases(ctx):
+    arr = (C.c_double * 6)()
+    _check(lib().stag_profile_phases(ctx, arr), "stag_profile_phases", ctx)
+    return list(arr)

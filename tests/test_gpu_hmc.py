@@ -151,3 +151,50 @@ def test_drawn_trajectory_runs_and_is_reproducible(torch, c1, prec):
             stag.stag_destroy(ctx)
     assert out[0].dH == out[1].dH and out[0].accepted == out[1].accepted
     assert abs(out[0].dH) < 1.0
+
+
+@pytest.mark.parametrize("prec,tol_dh", [(0, 1e-7), (3, 5e-2)])
+def test_two_flavours_two_pseudofermions_match_oracle(torch, prec, tol_dh):
+    """The N_f = 2+1 structure of the 32^3x8 workload on 4^4: a light flavour
+    (m = 0.01... here 0.1) and a strange one, two pseudo-fermions each, the
+    exponents s = 1/4 and 1/8 per pseudo-fermion, supplied momenta/sources."""
+    from paper_1010_5433_gb300 import stag
+    g = json.load(open(GOLDEN))
+    dims = DIMS
+    u0 = syn.near_identity_gauge(dims, 0x5A0003)
+    mom0 = syn.gaussian_momenta(dims, 301)
+    xis = [[syn.gaussian_fermion(dims, 310 + 2 * f + k, on_parity=0) for k in range(2)] for f in range(2)]
+    # light: x^(-1/4) (c1 tables, m = 0.1); strange: x^(-1/8) at m = 0.1 built from c3's strange degree
+    rat = {"light": {k: g["c1_" + k] for k in ("md", "met", "hb")},
+           "strange": {k: g["c3_strange_" + k] for k in ("md", "met", "hb")}}
+    fls = [integrator.Flavour(mass=0.1, hb=_rat(rat["light"]["hb"]), md=_rat(rat["light"]["md"]),
+                              met=_rat(rat["light"]["met"]), n_pf=2),
+           integrator.Flavour(mass=0.1, hb=_rat(rat["strange"]["hb"]), md=_rat(rat["strange"]["md"]),
+                              met=_rat(rat["strange"]["met"]), n_pf=2)]
+    prm = integrator.HMCParams(dims=dims, beta=5.3, tau=0.5, n_outer=5, n_gauge=2, flavours=fls,
+                               tol_md=1e-13, tol_met=1e-13)
+    want = integrator.trajectory(integrator.Context(prm), u0, mom0, xis)
+    ctx = stag.stag_create(dims, True)
+    try:
+        stag.stag_load_gauge(ctx, L.gauge_host(u0))
+        d_mom = torch.from_numpy(L.mom_to_abi(mom0, dims)).cuda()
+        d_xi = dev(torch, np.stack([L.to_half(x, dims, 0) for xl in xis for x in xl]))
+        p = stag.stag_hmc()
+        p.beta, p.tau, p.n_outer, p.n_gauge, p.n_flavours = 5.3, 0.5, 5, 2, 2
+        for f, name in enumerate(("light", "strange")):
+            fl = p.flavour[f]
+            fl.mass, fl.n_pf = 0.1, 2
+            for k in ("hb", "md", "met"):
+                setattr(fl, k, stag.make_rational(rat[name][k]["a0"], rat[name][k]["alpha"], rat[name][k]["beta"]))
+        p.tol_md = 1e-12 if prec == 0 else 1e-8
+        p.tol_met, p.max_iter, p.md_prec = 1e-12, 20000, prec
+        p.ext_mom, p.ext_xi, p.no_metropolis = d_mom.data_ptr(), d_xi.data_ptr(), 1
+        res = stag.stag_md_trajectory(ctx, p)
+        buf = np.empty(4 * 256 * 18)
+        stag.stag_store_gauge(ctx, buf)
+        assert abs(res.H0 - want["H0"]) < 1e-8 * abs(want["H0"])
+        assert abs(res.dH - want["dH"]) < tol_dh, (res.dH, want["dH"])
+        assert np.abs(L.gauge_from_host(buf, dims) - want["u"]).max() < (1e-10 if prec == 0 else 1e-4)
+        print(f"2+1 flavours prec {prec}: dH gpu {res.dH:.8f} oracle {want['dH']:.8f}")
+    finally:
+        stag.stag_destroy(ctx)

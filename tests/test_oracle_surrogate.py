@@ -1,0 +1,109 @@
+"""Pins for the oracle's force surrogate: the plaquette generators reproduce
+the Wilson force exactly, finite differences of the summed plaquette and
+rectangle loops fix every generator, gauge invariance of the features and
+covariance of the surrogate force, finite differences of the loss for the
+hand-written backward pass."""
+import numpy as np
+import pytest
+
+import synthetic as syn
+from oracle import actions, lattice as lat, su3, surrogate as sur
+
+DIMS = (4, 4, 2, 4)
+PLAQ = [8 * i + j for i in range(3) for j in (0, 1)]
+RECT = [8 * i + j for i in range(3) for j in range(2, 8)]
+
+
+@pytest.fixture(scope="module")
+def u():
+    return syn.near_identity_gauge(DIMS, 401, width=0.6)
+
+
+@pytest.fixture(scope="module")
+def fg(u):
+    return sur.features_and_generators(u)
+
+
+def test_plaquette_generators_give_the_wilson_force(u, fg):
+    f, G = fg
+    beta = 5.6
+    w = np.zeros(f.shape)
+    w[..., PLAQ] = -beta / 3.0
+    F = np.einsum("...k,...ka->...a", w, G)
+    np.testing.assert_allclose(F, actions.wilson_force(u, beta), atol=1e-12)
+
+
+def _loop_sum(u, kind):
+    """sum over loops of Re tr / 3: kind 'plaq' or 'rect' (every 1x2 and 2x1 loop once)."""
+    s = 0.0
+    for mu in range(4):
+        for nu in range(4):
+            if nu == mu:
+                continue
+            if kind == "plaq" and nu > mu:
+                s += np.sum(np.real(np.trace(actions.plaquette_field(u, mu, nu), axis1=-2, axis2=-1))) / 3
+            if kind == "rect":       # 2 in mu, 1 in nu, starting at x
+                um = lambda sh: sur._at(u, mu, sh)   # noqa: E731
+                un = lambda sh: sur._at(u, nu, sh)   # noqa: E731
+                loop = sur._mm(um([]), um([(mu, 1)]), un([(mu, 1), (mu, 1)]), su3.dag(um([(mu, 1), (nu, 1)])),
+                               su3.dag(um([(nu, 1)])), su3.dag(un([])))
+                s += np.sum(np.real(np.trace(loop, axis1=-2, axis2=-1))) / 3
+    return s
+
+
+@pytest.mark.parametrize("kind,idx", [("plaq", PLAQ), ("rect", RECT)])
+def test_generators_are_derivatives_of_loop_sums(u, fg, kind, idx):
+    """d/d omega_a of the summed loops through a link = sum of G over its staples / 3."""
+    f, G = fg
+    rg = np.random.default_rng(7)
+    for _ in range(4):
+        mu = int(rg.integers(4))
+        site = tuple(int(rg.integers(n)) for n in u.shape[1:5])
+        a = int(rg.integers(8))
+
+        def s_of(d):
+            up = u.copy()
+            gen = np.zeros(8)
+            gen[a] = 1.0
+            up[(mu,) + site] = su3.expi_coeffs(gen, d) @ u[(mu,) + site]
+            return _loop_sum(up, kind)
+        h = 1e-3
+        fd = (8 * (s_of(h) - s_of(-h)) - (s_of(2 * h) - s_of(-2 * h))) / (12 * h)
+        an = np.sum(G[(mu,) + site][idx, a]) / 3.0
+        assert abs(fd - an) < 1e-8, (kind, fd, an)
+
+
+def test_features_invariant_and_force_covariant(u, fg):
+    f, G = fg
+    g = syn.random_gauge_transform(DIMS, 402)
+    ug = np.stack([np.einsum("...ij,...jk,...lk->...il", g, u[mu], np.conj(lat.shift_fwd(g, mu)))
+                   for mu in range(4)])
+    f2, G2 = sur.features_and_generators(ug)
+    np.testing.assert_allclose(f2, f, atol=1e-12)
+    p = sur.init_params(1)
+    F1 = su3.coeffs_to_matrix(sur.surrogate_force(p, f, G))
+    F2 = su3.coeffs_to_matrix(sur.surrogate_force(p, f2, G2))
+    np.testing.assert_allclose(F2, np.einsum("...ij,...jk,...lk->...il", g, F1, np.conj(g)), atol=1e-12)
+
+
+def test_backward_matches_finite_differences(fg):
+    f, G = fg
+    rg = np.random.default_rng(3)
+    F = rg.standard_normal(G.shape[:-2] + (8,))
+    p = sur.init_params(2, scale=1.0)
+    _, grad = sur.loss_and_grad(p, f, G, F)
+    for name in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        for _ in range(3):
+            idx = tuple(int(rg.integers(n)) for n in p[name].shape)
+            h = 1e-5
+            pp = {k: v.copy() for k, v in p.items()}
+            pm = {k: v.copy() for k, v in p.items()}
+            pp[name][idx] += h
+            pm[name][idx] -= h
+            fd = (sur.loss_and_grad(pp, f, G, F)[0] - sur.loss_and_grad(pm, f, G, F)[0]) / (2 * h)
+            assert abs(fd - grad[name][idx]) < 1e-7 * max(1.0, abs(fd)), (name, idx, fd, grad[name][idx])
+
+
+def test_bf16_round_known_values():
+    x = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -9, -3.14159265])
+    np.testing.assert_array_equal(sur.bf16_round(x), [1.0, 1.0, 1.0 + 2 ** -7, -3.140625])

@@ -227,6 +227,10 @@ typedef struct {
     double ext_uniform;         /* used for the accept test when ext_mom is set */
     int no_metropolis;          /* 1: always keep the new field (tests, reversibility) */
     int flip_momenta;           /* 1: start from -P (reversibility test) */
+    int use_surrogate;          /* 1: three levels -- exact remainder F - F^ on the outer level,
+                                   the loaded surrogate F^ on n_mid minimum-norm steps per outer
+                                   half step, the gauge level inside (needs stag_surrogate_load) */
+    int n_mid;
 } stag_hmc;
 
 typedef struct {
@@ -248,6 +252,32 @@ stag_status stag_md_trajectory(stag_ctx* ctx, const stag_hmc* p, stag_traj* out)
 
 /* Momenta of the last trajectory (device, momentum layout, read-only). */
 const double* stag_momenta(stag_ctx* ctx);
+
+/* ---- learned fermion-force surrogate (a workload of this build; the paper has
+ *      none).  Per link: 24 loop features f_k = Re tr(U S_k)/3 over the 6
+ *      plaquette and 18 rectangle staples S_k through the link; an MLP
+ *      24-32-32-24 (tanh, bf16 weights, fp32 math) gives weights w_k and
+ *      F^_a = Re tr(i T_a U sum_k w_k S_k).  The staples are, for each nu != mu
+ *      in increasing order, j = 0..7: plaquette up, down; 2mu x nu rectangles
+ *      up (link first, second), down (first, second); mu x 2nu up, down. ---- */
+#define STAG_SUR_PARAMS 2648  /* W1 (32x24, row-major), b1 (32), W2 (32x32), b2 (32), W3 (24x32), b3 (24) */
+/* Set the weights (host array of STAG_SUR_PARAMS floats; weights are rounded
+ * to bf16 on the device, the fp32 values kept as Adam's master copy). */
+stag_status stag_surrogate_load(stag_ctx* ctx, const float* params);
+stag_status stag_surrogate_store(stag_ctx* ctx, float* params);
+/* F^ of the loaded field (momentum layout, written). */
+stag_status stag_surrogate_force(stag_ctx* ctx, double* force);
+/* Training data: append the current field's features and generators with the
+ * given exact force (device, momentum layout) as the target. */
+stag_status stag_surrogate_add_force_sample(stag_ctx* ctx, const double* exact_force);
+/* Same, with the target computed here: the exact MD fermion force of the
+ * flavours of p for pseudo-fermions from the heatbath with Philox counter. */
+stag_status stag_surrogate_add_sample(stag_ctx* ctx, const stag_hmc* p, unsigned long long counter);
+long long   stag_surrogate_samples(stag_ctx* ctx);
+/* Mean over stored links of |F^ - F|^2 and its gradient (host, STAG_SUR_PARAMS doubles, may be NULL). */
+stag_status stag_surrogate_loss_grad(stag_ctx* ctx, double* loss, double* grad);
+/* steps full-batch Adam steps (learning rate lr); losses before the first and last step. */
+stag_status stag_surrogate_train(stag_ctx* ctx, int steps, double lr, double* loss_first, double* loss_last);
 
 /* ---- measurement (no counterpart in the paper; used for the roofline) ---- */
 

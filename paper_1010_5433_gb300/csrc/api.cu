@@ -84,6 +84,8 @@ extern "C" void stag_destroy(stag_ctx* ctx) {
     if (ctx->counters) cudaFree(ctx->counters);
     if (ctx->bar) cudaFree(ctx->bar);
     if (ctx->ptime) cudaFree(ctx->ptime);
+    if (ctx->sur_w) cudaFree(ctx->sur_w);
+    if (ctx->sur_data) cudaFree(ctx->sur_data);
     if (ctx->scal) cudaFree(ctx->scal);
     if (ctx->st) cudaFree(ctx->st);
     if (ctx->scal_host) cudaFreeHost(ctx->scal_host);

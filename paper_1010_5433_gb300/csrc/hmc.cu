@@ -202,14 +202,37 @@ struct Traj {
         return timer->end(2);
     }
 
+    // the level between fermion steps: the gauge level, or with the surrogate
+    // n_mid minimum-norm steps of F^ around gauge levels
+    stag_status inner(double h) {
+        if (!p->use_surrogate) return gauge_level(h, p->n_gauge);
+        const int n = p->n_mid;
+        const double d = h / n;
+        CKS(sur_kick(LAMBDA_2MN * d));
+        for (int j = 0; j < n; ++j) {
+            CKS(gauge_level(d / 2, p->n_gauge));
+            CKS(sur_kick((1 - 2 * LAMBDA_2MN) * d));
+            CKS(gauge_level(d / 2, p->n_gauge));
+            CKS(sur_kick((j == n - 1 ? 1.0 : 2.0) * LAMBDA_2MN * d));
+        }
+        return STAG_OK;
+    }
+    stag_status sur_kick(double c) { return surrogate_force_launch(ctx, mom, -c, 1); }
+    // outer kick: p -= c F_fermion, and with the surrogate p += c F^ (the exact remainder)
+    stag_status outer_kick(double c) {
+        CKS(fermion_kick(c));
+        if (p->use_surrogate) CKS(surrogate_force_launch(ctx, mom, c, 1));
+        return STAG_OK;
+    }
+
     stag_status md_evolve() {
         const double e = p->tau / p->n_outer;
-        CKS(fermion_kick(LAMBDA_2MN * e));
+        CKS(outer_kick(LAMBDA_2MN * e));
         for (int s = 0; s < p->n_outer; ++s) {
-            CKS(gauge_level(e / 2, p->n_gauge));
-            CKS(fermion_kick((1 - 2 * LAMBDA_2MN) * e));
-            CKS(gauge_level(e / 2, p->n_gauge));
-            CKS(fermion_kick((s == p->n_outer - 1 ? 1.0 : 2.0) * LAMBDA_2MN * e));
+            CKS(inner(e / 2));
+            CKS(outer_kick((1 - 2 * LAMBDA_2MN) * e));
+            CKS(inner(e / 2));
+            CKS(outer_kick((s == p->n_outer - 1 ? 1.0 : 2.0) * LAMBDA_2MN * e));
         }
         return STAG_OK;
     }
@@ -263,6 +286,7 @@ extern "C" const double* stag_momenta(stag_ctx* ctx) { return ctx ? (const doubl
 extern "C" stag_status stag_md_trajectory(stag_ctx* ctx, const stag_hmc* p, stag_traj* out) {
     if (!ctx || !p || !out) return STAG_ERR_ARG;
     if (!ctx->has_gauge) return STAG_ERR_NO_GAUGE;
+    if (p->use_surrogate && (p->n_mid < 1 || !ctx->sur_loaded)) return STAG_ERR_ARG;
     if (p->n_outer < 1 || p->n_gauge < 1 || !(p->tau > 0) || p->n_flavours < 0 ||
         p->n_flavours > STAG_MAX_FLAVOURS || p->max_iter < 1 || p->md_prec < STAG_FP64 ||
         p->md_prec > STAG_BF16_12 || !(p->tol_md > 0) || !(p->tol_met > 0))
@@ -384,4 +408,33 @@ extern "C" stag_status stag_md_trajectory(stag_ctx* ctx, const stag_hmc* p, stag
     out->t_gauge = timer.seconds(2);
     out->t_metropolis = timer.seconds(3);
     return std::isfinite(dh) ? STAG_OK : STAG_ERR_NAN;
+}
+
+extern "C" stag_status stag_surrogate_add_sample(stag_ctx* ctx, const stag_hmc* p, unsigned long long counter) {
+    if (!ctx || !p || p->n_flavours < 1 || p->n_flavours > STAG_MAX_FLAVOURS) return STAG_ERR_ARG;
+    if (!ctx->has_gauge) return STAG_ERR_NO_GAUGE;
+    const size_t hc = half_c(ctx);
+    int npf = 0;
+    for (int f = 0; f < p->n_flavours; ++f) {
+        if (p->flavour[f].n_pf < 1 || !valid_rational(p->flavour[f].hb) || !valid_rational(p->flavour[f].md))
+            return STAG_ERR_ARG;
+        npf += p->flavour[f].n_pf;
+    }
+    void *xi, *phi, *force;
+    CKS(ws_get(ctx, WS_XI, (size_t)npf * hc * sizeof(double2), &xi));
+    CKS(ws_get(ctx, WS_PHI, (size_t)npf * hc * sizeof(double2), &phi));
+    CKS(ws_get(ctx, WS_FORCE, (size_t)64 * ctx->g.Vh * sizeof(double), &force));
+    ForceTerm terms[STAG_MAX_FLAVOURS];
+    size_t off = 0;
+    for (int f = 0; f < p->n_flavours; ++f) {
+        const stag_flavour& fl = p->flavour[f];
+        CKS(draw_sources(ctx, (double2*)xi + off * hc, fl.n_pf, p->seed, counter, 16 * f));
+        CKS(apply_rational_f64(ctx, fl.mass, fl.hb, fl.n_pf, (const double2*)xi + off * hc, (double2*)phi + off * hc,
+                               p->tol_met, p->max_iter, nullptr));
+        terms[f] = ForceTerm{fl.mass, &fl.md, fl.n_pf, (const double2*)phi + off * hc};
+        off += fl.n_pf;
+    }
+    CKS(fermion_force_terms(ctx, terms, p->n_flavours, p->md_prec, (double*)force, 1.0, 0, p->tol_md, p->max_iter,
+                            nullptr));
+    return surrogate_append(ctx, (const double*)force);
 }

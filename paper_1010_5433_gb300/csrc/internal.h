@@ -31,6 +31,7 @@ enum WsSlot {
     WS_FORCE_B32,      // fermion force: fp32 copy of phi
     WS_TUNE_IN, WS_TUNE_OUT,   // autotuner fields
     WS_B_DF, WS_X_DF,  // fp64 solves: float-float copies of b and x
+    WS_SUR_GRAD_PART, WS_SUR_LOSS_PART, WS_SUR_GRAD,   // surrogate training
     WS_COUNT
 };
 
@@ -48,6 +49,17 @@ struct ProfData {
     double persist_ms = 0.0;                     // persistent solver: event time of all launches
     long long persist_iters = 0;                 // and the iterations they ran
 };
+
+// surrogate MLP parameters: W1 (32x24), b1, W2 (32x32), b2, W3 (24x32), b3
+#define SUR_NF 24
+#define SUR_NH 32
+#define SUR_W1 0
+#define SUR_B1 (SUR_W1 + SUR_NH * SUR_NF)
+#define SUR_W2 (SUR_B1 + SUR_NH)
+#define SUR_B2 (SUR_W2 + SUR_NH * SUR_NH)
+#define SUR_W3 (SUR_B2 + SUR_NH)
+#define SUR_B3 (SUR_W3 + SUR_NF * SUR_NH)
+#define SUR_NP (SUR_B3 + SUR_NF)
 
 struct SolverGraphEntry {
     const void* key[8];
@@ -89,6 +101,13 @@ struct stag_ctx {
     void* bar = nullptr;              // grid-barrier words of the persistent solver
     void* ptime = nullptr;            // its per-phase ns counters while profiling
     int persist_block = 256;          // its threads per block (STAG_PERSIST_BLOCK=128|256)
+    // force surrogate
+    float* sur_w = nullptr;           // device parameters (weights rounded to bf16)
+    bool sur_loaded = false;
+    std::vector<double> sur_master, adam_m, adam_v;   // fp32-valued master weights, Adam moments
+    long long adam_t = 0;
+    float* sur_data = nullptr;        // training samples, component-major [224][capacity x links]
+    long long sur_cap = 0, sur_count = 0;
     cudaStream_t cap_stream = nullptr;
     std::vector<SolverGraphEntry> graphs;
 };
@@ -170,6 +189,10 @@ stag_status mom_axpy(stag_ctx* ctx, double* mom, const double* f, double c);
 stag_status draw_momenta(stag_ctx* ctx, double* mom, unsigned long long seed, unsigned long long counter);
 stag_status draw_sources(stag_ctx* ctx, double2* xi, int n, unsigned long long seed, unsigned long long counter,
                          int stream_base);
+
+// surrogate.cu
+stag_status surrogate_force_launch(stag_ctx* ctx, double* out, double coef, int mode);
+stag_status surrogate_append(stag_ctx* ctx, const double* exact_force);
 
 // blas.cu
 stag_status blas_norm2(stag_ctx* ctx, stag_prec prec, int nrhs, const void* v, double* out_host);

@@ -1,0 +1,475 @@
+// Learned fermion-force surrogate (a workload of this build; the paper has
+// none).  Per link (x, mu):
+//   staples S_k, k = 8 i + j over the three nu != mu (i) and eight loops (j):
+//     j = 0, 1  plaquette up / down
+//     j = 2..5  2mu x nu rectangles: up with the link first / second, down first / second
+//     j = 6, 7  mu x 2nu rectangles up / down
+//   features   f_k = Re tr(U S_k) / 3                (gauge invariant)
+//   MLP        w = W3 tanh(W2 tanh(W1 f + b1) + b2) + b3   (24-32-32-24, bf16 weights, fp32 math)
+//   force      F^_a = Re tr(i T_a sum_k w_k U S_k)    (gauge covariant)
+// Training minimises the mean over links of |F^ - F|^2 against exact fermion
+// forces with Adam on fp32 master weights.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+
+namespace {
+constexpr int SB = 128;   // threads per block of the per-link kernels
+
+__device__ __forceinline__ Su3<float> dagm(const Su3<float>& a) {
+    Su3<float> d;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) d.e[i][j] = conj(a.e[j][i]);
+    return d;
+}
+
+struct LinkAt {
+    const Geom& g;
+    const LinkPtrs& L;
+    int x[4], mu, nu;
+    // U_dir at x + a mu_hat + b nu_hat
+    __device__ __forceinline__ Su3<float> operator()(int dir, int a, int b) const {
+        int c[4] = {x[0], x[1], x[2], x[3]};
+        c[mu] += a;
+        c[nu] += b;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (c[i] < 0) c[i] += g.L[i];
+            if (c[i] >= g.L[i]) c[i] -= g.L[i];
+        }
+        const int par = (c[0] + c[1] + c[2] + c[3]) & 1;
+        const int h = (c[0] >> 1) + g.Lxh * (c[1] + g.L[1] * (c[2] + g.L[2] * c[3]));
+        return LinkFetch<float, FMT_F32_18>::get(L, dir, par, h, g.Vh);
+    }
+};
+
+__device__ Su3<float> staple(const LinkAt& U, int j) {
+    const int m = U.mu, n = U.nu;
+    switch (j) {
+        case 0: return mul(mul(U(n, 1, 0), dagm(U(m, 0, 1))), dagm(U(n, 0, 0)));
+        case 1: return mul(mul(dagm(U(n, 1, -1)), dagm(U(m, 0, -1))), U(n, 0, -1));
+        case 2: return mul(mul(mul(mul(U(m, 1, 0), U(n, 2, 0)), dagm(U(m, 1, 1))), dagm(U(m, 0, 1))), dagm(U(n, 0, 0)));
+        case 3: return mul(mul(mul(mul(U(n, 1, 0), dagm(U(m, 0, 1))), dagm(U(m, -1, 1))), dagm(U(n, -1, 0))), U(m, -1, 0));
+        case 4: return mul(mul(mul(mul(U(m, 1, 0), dagm(U(n, 2, -1))), dagm(U(m, 1, -1))), dagm(U(m, 0, -1))), U(n, 0, -1));
+        case 5: return mul(mul(mul(mul(dagm(U(n, 1, -1)), dagm(U(m, 0, -1))), dagm(U(m, -1, -1))), U(n, -1, -1)), U(m, -1, 0));
+        case 6: return mul(mul(mul(mul(U(n, 1, 0), U(n, 1, 1)), dagm(U(m, 0, 2))), dagm(U(n, 0, 1))), dagm(U(n, 0, 0)));
+        default: return mul(mul(mul(mul(dagm(U(n, 1, -1)), dagm(U(n, 1, -2))), dagm(U(m, 0, -2))), U(n, 0, -2)), U(n, 0, -1));
+    }
+}
+
+// Re tr(i T_a W) for the eight Gell-Mann generators T_a = lambda_a / 2
+__device__ __forceinline__ void gen_coeffs(const Su3<float>& w, float (&f)[8]) {
+    f[0] = -0.5f * (w.e[1][0].im + w.e[0][1].im);
+    f[1] = -0.5f * (w.e[0][1].re - w.e[1][0].re);
+    f[2] = -0.5f * (w.e[0][0].im - w.e[1][1].im);
+    f[3] = -0.5f * (w.e[2][0].im + w.e[0][2].im);
+    f[4] = -0.5f * (w.e[0][2].re - w.e[2][0].re);
+    f[5] = -0.5f * (w.e[2][1].im + w.e[1][2].im);
+    f[6] = -0.5f * (w.e[1][2].re - w.e[2][1].re);
+    f[7] = -(w.e[0][0].im + w.e[1][1].im - 2.f * w.e[2][2].im) * 0.28867513459481287f;
+}
+
+__device__ __forceinline__ void link_of(const Geom& g, long long l, int& mu, int& par, int& h, int x[4]) {
+    const int blk = (int)(l / g.Vh);
+    h = (int)(l % g.Vh);
+    mu = blk >> 1;
+    par = blk & 1;
+    int xh = h % g.Lxh, r = h / g.Lxh;
+    x[1] = r % g.L[1]; r /= g.L[1];
+    x[2] = r % g.L[2]; x[3] = r / g.L[2];
+    x[0] = 2 * xh + ((x[1] + x[2] + x[3] + par) & 1);
+}
+
+// the MLP in fp32 from weights in shared memory
+__device__ __forceinline__ void mlp_forward(const float* P, const float (&f)[SUR_NF], float (&h1)[SUR_NH],
+                                            float (&h2)[SUR_NH], float (&w)[SUR_NF]) {
+#pragma unroll 4
+    for (int i = 0; i < SUR_NH; ++i) {
+        float z = P[SUR_B1 + i];
+#pragma unroll
+        for (int k = 0; k < SUR_NF; ++k) z = fmaf(P[SUR_W1 + i * SUR_NF + k], f[k], z);
+        h1[i] = tanhf(z);
+    }
+#pragma unroll 4
+    for (int i = 0; i < SUR_NH; ++i) {
+        float z = P[SUR_B2 + i];
+#pragma unroll
+        for (int k = 0; k < SUR_NH; ++k) z = fmaf(P[SUR_W2 + i * SUR_NH + k], h1[k], z);
+        h2[i] = tanhf(z);
+    }
+#pragma unroll 4
+    for (int i = 0; i < SUR_NF; ++i) {
+        float z = P[SUR_B3 + i];
+#pragma unroll
+        for (int k = 0; k < SUR_NH; ++k) z = fmaf(P[SUR_W3 + i * SUR_NH + k], h2[k], z);
+        w[i] = z;
+    }
+}
+
+// Features and generators of every link: f [24][nl], G [24*8][nl] (training data).
+__global__ void __launch_bounds__(SB) k_sur_features(Geom g, LinkPtrs L, float* f, float* G, long long stride) {
+    const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= 8LL * g.Vh) return;
+    int mu, par, h, x[4];
+    link_of(g, l, mu, par, h, x);
+    const Su3<float> u = LinkFetch<float, FMT_F32_18>::get(L, mu, par, h, g.Vh);
+    int i = 0;
+    for (int nu = 0; nu < 4; ++nu) {
+        if (nu == mu) continue;
+        LinkAt U{g, L, {x[0], x[1], x[2], x[3]}, mu, nu};
+        for (int j = 0; j < 8; ++j) {
+            const int k = 8 * i + j;
+            Su3<float> w = mul(u, staple(U, j));
+            f[(size_t)k * stride + l] = (w.e[0][0].re + w.e[1][1].re + w.e[2][2].re) * (1.f / 3.f);
+            float c[8];
+            gen_coeffs(w, c);
+#pragma unroll
+            for (int a = 0; a < 8; ++a) G[((size_t)k * 8 + a) * stride + l] = c[a];
+        }
+        ++i;
+    }
+}
+
+// Surrogate force of every link: out = coef F^ (mode 0) or out += coef F^ (mode 1),
+// momentum layout.  Staples are formed twice (features, then the weighted sum)
+// so that no per-staple state is kept in registers.
+__global__ void __launch_bounds__(SB) k_sur_force(Geom g, LinkPtrs L, const float* __restrict__ params, double* out,
+                                                  double coef, int mode) {
+    __shared__ float P[SUR_NP];
+    for (int i = threadIdx.x; i < SUR_NP; i += blockDim.x) P[i] = params[i];
+    __syncthreads();
+    const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= 8LL * g.Vh) return;
+    int mu, par, h, x[4];
+    link_of(g, l, mu, par, h, x);
+    const Su3<float> u = LinkFetch<float, FMT_F32_18>::get(L, mu, par, h, g.Vh);
+    float fv[SUR_NF], h1[SUR_NH], h2[SUR_NH], w[SUR_NF];
+    int i = 0;
+    for (int nu = 0; nu < 4; ++nu) {
+        if (nu == mu) continue;
+        LinkAt U{g, L, {x[0], x[1], x[2], x[3]}, mu, nu};
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            Su3<float> wk = mul(u, staple(U, j));
+            fv[8 * i + j] = (wk.e[0][0].re + wk.e[1][1].re + wk.e[2][2].re) * (1.f / 3.f);
+        }
+        ++i;
+    }
+    mlp_forward(P, fv, h1, h2, w);
+    Su3<float> m;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) m.e[a][b] = mk(0.f, 0.f);
+    i = 0;
+    for (int nu = 0; nu < 4; ++nu) {
+        if (nu == mu) continue;
+        LinkAt U{g, L, {x[0], x[1], x[2], x[3]}, mu, nu};
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const Su3<float> s = staple(U, j);
+            const float wk = w[8 * i + j];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    m.e[a][b].re += wk * s.e[a][b].re;
+                    m.e[a][b].im += wk * s.e[a][b].im;
+                }
+        }
+        ++i;
+    }
+    float c[8];
+    gen_coeffs(mul(u, m), c);
+    double* o = out + ((size_t)(2 * mu + par) * 8) * g.Vh + h;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        if (mode) o[(size_t)a * g.Vh] += coef * (double)c[a];
+        else o[(size_t)a * g.Vh] = coef * (double)c[a];
+    }
+}
+
+// exact forces [4][2][8][Vh] (double) -> dataset slot [8][nl] (float)
+__global__ void k_sur_target(Geom g, const double* __restrict__ F, float* out, long long stride) {
+    const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= 8LL * g.Vh) return;
+    const int blk = (int)(l / g.Vh), h = (int)(l % g.Vh);
+#pragma unroll
+    for (int a = 0; a < 8; ++a) out[(size_t)a * stride + l] = (float)F[((size_t)blk * 8 + a) * g.Vh + h];
+}
+
+// One block: forward and backward of TB links, per-block loss and parameter
+// gradients (sums of outer products formed from shared memory).
+constexpr int TB = 128;
+constexpr int SV = SUR_NF + SUR_NH + SUR_NH + SUR_NF + SUR_NH + SUR_NH;   // f h1 h2 dw dz2 dz1 per link
+__global__ void __launch_bounds__(TB) k_sur_train(long long nl, const float* __restrict__ f, const float* __restrict__ G,
+                                                  const float* __restrict__ F, long long stride,
+                                                  const float* __restrict__ params, double inv_n,
+                                                  float* grad_part, double* loss_part) {
+    extern __shared__ float sm[];
+    float* P = sm;                          // SUR_NP
+    float* V = sm + SUR_NP;                 // [SV][TB]
+    for (int i = threadIdx.x; i < SUR_NP; i += blockDim.x) P[i] = params[i];
+    __syncthreads();
+    const long long l = (long long)blockIdx.x * TB + threadIdx.x;
+    const int t = threadIdx.x;
+    double lossv[1] = {0.0};
+    float fv[SUR_NF], h1[SUR_NH], h2[SUR_NH], w[SUR_NF], dw[SUR_NF], dz2[SUR_NH], dz1[SUR_NH];
+    if (l < nl) {
+#pragma unroll
+        for (int k = 0; k < SUR_NF; ++k) fv[k] = f[(size_t)k * stride + l];
+        mlp_forward(P, fv, h1, h2, w);
+        float e[8];
+#pragma unroll
+        for (int a = 0; a < 8; ++a) e[a] = -F[(size_t)a * stride + l];
+        for (int k = 0; k < SUR_NF; ++k)
+#pragma unroll
+            for (int a = 0; a < 8; ++a) e[a] = fmaf(w[k], G[((size_t)k * 8 + a) * stride + l], e[a]);
+        float ls = 0.f;
+#pragma unroll
+        for (int a = 0; a < 8; ++a) ls = fmaf(e[a], e[a], ls);
+        lossv[0] = ls;
+        const float sc = (float)(2.0 * inv_n);
+        for (int k = 0; k < SUR_NF; ++k) {
+            float s = 0.f;
+#pragma unroll
+            for (int a = 0; a < 8; ++a) s = fmaf(e[a], G[((size_t)k * 8 + a) * stride + l], s);
+            dw[k] = sc * s;
+        }
+#pragma unroll 4
+        for (int i = 0; i < SUR_NH; ++i) {
+            float s = 0.f;
+#pragma unroll
+            for (int k = 0; k < SUR_NF; ++k) s = fmaf(P[SUR_W3 + k * SUR_NH + i], dw[k], s);
+            dz2[i] = s * (1.f - h2[i] * h2[i]);
+        }
+#pragma unroll 4
+        for (int i = 0; i < SUR_NH; ++i) {
+            float s = 0.f;
+#pragma unroll
+            for (int k = 0; k < SUR_NH; ++k) s = fmaf(P[SUR_W2 + k * SUR_NH + i], dz2[k], s);
+            dz1[i] = s * (1.f - h1[i] * h1[i]);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < SUR_NF; ++k) fv[k] = 0.f, w[k] = 0.f, dw[k] = 0.f;
+#pragma unroll
+        for (int k = 0; k < SUR_NH; ++k) h1[k] = 0.f, h2[k] = 0.f, dz1[k] = 0.f, dz2[k] = 0.f;
+    }
+    // per-link vectors to shared memory, row r of V holds component r for all TB links
+    int r = 0;
+#pragma unroll
+    for (int k = 0; k < SUR_NF; ++k) V[(r + k) * TB + t] = fv[k];
+    r += SUR_NF;
+#pragma unroll
+    for (int k = 0; k < SUR_NH; ++k) V[(r + k) * TB + t] = h1[k];
+    r += SUR_NH;
+#pragma unroll
+    for (int k = 0; k < SUR_NH; ++k) V[(r + k) * TB + t] = h2[k];
+    r += SUR_NH;
+#pragma unroll
+    for (int k = 0; k < SUR_NF; ++k) V[(r + k) * TB + t] = dw[k];
+    r += SUR_NF;
+#pragma unroll
+    for (int k = 0; k < SUR_NH; ++k) V[(r + k) * TB + t] = dz2[k];
+    r += SUR_NH;
+#pragma unroll
+    for (int k = 0; k < SUR_NH; ++k) V[(r + k) * TB + t] = dz1[k];
+    __syncthreads();
+    const float* Vf = V;
+    const float* Vh1 = V + SUR_NF * TB;
+    const float* Vh2 = Vh1 + SUR_NH * TB;
+    const float* Vdw = Vh2 + SUR_NH * TB;
+    const float* Vdz2 = Vdw + SUR_NF * TB;
+    const float* Vdz1 = Vdz2 + SUR_NH * TB;
+    // every parameter's gradient over the block's links
+    for (int pi = t; pi < SUR_NP; pi += TB) {
+        const float *a, *b = nullptr;
+        if (pi < SUR_B1) { a = Vdz1 + (pi / SUR_NF) * TB; b = Vf + (pi % SUR_NF) * TB; }
+        else if (pi < SUR_W2) { a = Vdz1 + (pi - SUR_B1) * TB; }
+        else if (pi < SUR_B2) { const int q = pi - SUR_W2; a = Vdz2 + (q / SUR_NH) * TB; b = Vh1 + (q % SUR_NH) * TB; }
+        else if (pi < SUR_W3) { a = Vdz2 + (pi - SUR_B2) * TB; }
+        else if (pi < SUR_B3) { const int q = pi - SUR_W3; a = Vdw + (q / SUR_NH) * TB; b = Vh2 + (q % SUR_NH) * TB; }
+        else { a = Vdw + (pi - SUR_B3) * TB; }
+        float s = 0.f;
+        if (b) for (int q = 0; q < TB; ++q) s = fmaf(a[q], b[q], s);
+        else for (int q = 0; q < TB; ++q) s += a[q];
+        grad_part[(size_t)blockIdx.x * SUR_NP + pi] = s;
+    }
+    block_sum<1>(lossv);
+    if (t == 0) loss_part[blockIdx.x] = lossv[0];
+}
+
+// fixed-order sum of the per-block gradients
+__global__ void k_sur_reduce(int nb, const float* __restrict__ part, double* grad) {
+    const int pi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pi >= SUR_NP) return;
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += part[(size_t)b * SUR_NP + pi];
+    grad[pi] = s;
+}
+
+float bf16_round_host(float x) {
+    uint32_t b;
+    std::memcpy(&b, &x, 4);
+    b = (b + 0x7FFFu + ((b >> 16) & 1u)) & 0xFFFF0000u;
+    float r;
+    std::memcpy(&r, &b, 4);
+    return r;
+}
+}  // namespace
+
+// device copy: weights rounded to bf16, biases fp32
+static stag_status upload_params(stag_ctx* ctx) {
+    if (!ctx->sur_w) CKS(dev_alloc(ctx, (void**)&ctx->sur_w, SUR_NP * sizeof(float)));
+    std::vector<float> dev(SUR_NP);
+    for (int i = 0; i < SUR_NP; ++i) {
+        const bool is_w = (i < SUR_B1) || (i >= SUR_W2 && i < SUR_B2) || (i >= SUR_W3 && i < SUR_B3);
+        const float v = (float)ctx->sur_master[i];
+        dev[i] = is_w ? bf16_round_host(v) : v;
+    }
+    CK(cudaMemcpyAsync(ctx->sur_w, dev.data(), SUR_NP * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->sur_loaded = true;
+    return STAG_OK;
+}
+
+stag_status surrogate_force_launch(stag_ctx* ctx, double* out, double coef, int mode) {
+    if (!ctx->sur_loaded) return STAG_ERR_ARG;
+    const long long n = 8LL * ctx->g.Vh;
+    k_sur_force<<<nblocks(n, SB), SB, 0, ctx->stream>>>(ctx->g, link_ptrs(ctx), ctx->sur_w, out, coef, mode);
+    CKL();
+    return STAG_OK;
+}
+
+// append (features, generators, exact force) of the current field to the dataset
+stag_status surrogate_append(stag_ctx* ctx, const double* exact_force) {
+    const long long nl = 8LL * ctx->g.Vh;
+    const long long per = (long long)(SUR_NF + SUR_NF * 8 + 8);
+    if (ctx->sur_count >= ctx->sur_cap) {
+        // grow: new buffer of double capacity, copy the samples held so far
+        const long long cap = ctx->sur_cap ? 2 * ctx->sur_cap : 4;
+        float* nb = nullptr;
+        CKS(dev_alloc(ctx, (void**)&nb, (size_t)cap * nl * per * sizeof(float)));
+        if (ctx->sur_data) {
+            // component-major layout [component][sample][link]: copy component by component
+            for (long long c = 0; c < per; ++c)
+                CK(cudaMemcpyAsync(nb + (size_t)c * cap * nl, ctx->sur_data + (size_t)c * ctx->sur_cap * nl,
+                                   (size_t)ctx->sur_count * nl * sizeof(float), cudaMemcpyDeviceToDevice,
+                                   ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+            CK(cudaFree(ctx->sur_data));
+            ctx->dev_bytes -= (size_t)ctx->sur_cap * nl * per * sizeof(float);
+        }
+        ctx->sur_data = nb;
+        ctx->sur_cap = cap;
+    }
+    const long long stride = ctx->sur_cap * nl;     // one component over all samples
+    const long long base = ctx->sur_count * nl;
+    float* f = ctx->sur_data + base;
+    float* G = ctx->sur_data + (size_t)SUR_NF * stride + base;
+    float* F = ctx->sur_data + (size_t)(SUR_NF + SUR_NF * 8) * stride + base;
+    k_sur_features<<<nblocks(nl, SB), SB, 0, ctx->stream>>>(ctx->g, link_ptrs(ctx), f, G, stride);
+    CKL();
+    k_sur_target<<<nblocks(nl, 256), 256, 0, ctx->stream>>>(ctx->g, exact_force, F, stride);
+    CKL();
+    ctx->sur_count += 1;
+    return STAG_OK;
+}
+
+// loss and gradient over every stored sample with the current weights
+static stag_status loss_grad(stag_ctx* ctx, double* loss, std::vector<double>& grad) {
+    if (ctx->sur_count < 1) return STAG_ERR_ARG;
+    const long long nl1 = 8LL * ctx->g.Vh;
+    const long long stride = ctx->sur_cap * nl1;
+    const long long nl = ctx->sur_count * nl1;
+    const int nb = nblocks(nl, TB);
+    const size_t smem = (size_t)(SUR_NP + SV * TB) * sizeof(float);
+    void *gp, *lp, *gd;
+    CKS(ws_get(ctx, WS_SUR_GRAD_PART, (size_t)nb * SUR_NP * sizeof(float), &gp));
+    CKS(ws_get(ctx, WS_SUR_LOSS_PART, (size_t)nb * sizeof(double), &lp));
+    CKS(ws_get(ctx, WS_SUR_GRAD, SUR_NP * sizeof(double), &gd));
+    CK(cudaFuncSetAttribute(k_sur_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const float* d = ctx->sur_data;
+    k_sur_train<<<nb, TB, smem, ctx->stream>>>(nl, d, d + (size_t)SUR_NF * stride,
+                                               d + (size_t)(SUR_NF + SUR_NF * 8) * stride, stride, ctx->sur_w,
+                                               1.0 / (double)nl, (float*)gp, (double*)lp);
+    CKL();
+    k_sur_reduce<<<nblocks(SUR_NP, 256), 256, 0, ctx->stream>>>(nb, (const float*)gp, (double*)gd);
+    CKL();
+    grad.resize(SUR_NP);
+    std::vector<double> lpart(nb);
+    CK(cudaMemcpyAsync(grad.data(), gd, SUR_NP * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(lpart.data(), lp, nb * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    double s = 0.0;
+    for (double v : lpart) s += v;
+    *loss = s / (double)nl;
+    return STAG_OK;
+}
+
+extern "C" stag_status stag_surrogate_load(stag_ctx* ctx, const float* params) {
+    if (!ctx || !params) return STAG_ERR_ARG;
+    ctx->sur_master.assign(params, params + SUR_NP);
+    ctx->adam_m.assign(SUR_NP, 0.0);
+    ctx->adam_v.assign(SUR_NP, 0.0);
+    ctx->adam_t = 0;
+    return upload_params(ctx);
+}
+
+extern "C" stag_status stag_surrogate_store(stag_ctx* ctx, float* params) {
+    if (!ctx || !params || ctx->sur_master.size() != SUR_NP) return STAG_ERR_ARG;
+    for (int i = 0; i < SUR_NP; ++i) params[i] = (float)ctx->sur_master[i];
+    return STAG_OK;
+}
+
+extern "C" stag_status stag_surrogate_force(stag_ctx* ctx, double* force) {
+    if (!ctx || !force) return STAG_ERR_ARG;
+    if (!ctx->has_gauge) return STAG_ERR_NO_GAUGE;
+    return surrogate_force_launch(ctx, force, 1.0, 0);
+}
+
+extern "C" stag_status stag_surrogate_add_force_sample(stag_ctx* ctx, const double* exact_force) {
+    if (!ctx || !exact_force) return STAG_ERR_ARG;
+    if (!ctx->has_gauge) return STAG_ERR_NO_GAUGE;
+    return surrogate_append(ctx, exact_force);
+}
+
+extern "C" long long stag_surrogate_samples(stag_ctx* ctx) { return ctx ? ctx->sur_count : 0; }
+
+extern "C" stag_status stag_surrogate_loss_grad(stag_ctx* ctx, double* loss, double* grad) {
+    if (!ctx || !loss || !ctx->sur_loaded) return STAG_ERR_ARG;
+    std::vector<double> g;
+    CKS(loss_grad(ctx, loss, g));
+    if (grad) std::memcpy(grad, g.data(), SUR_NP * sizeof(double));
+    return STAG_OK;
+}
+
+// Adam (Kingma & Ba) on the fp32 master weights, the device copy re-rounded
+// to bf16 after every step.
+extern "C" stag_status stag_surrogate_train(stag_ctx* ctx, int steps, double lr, double* loss_first,
+                                            double* loss_last) {
+    if (!ctx || steps < 1 || !(lr > 0) || !ctx->sur_loaded) return STAG_ERR_ARG;
+    const double b1 = 0.9, b2 = 0.999, eps = 1e-8;
+    std::vector<double> g;
+    for (int s = 0; s < steps; ++s) {
+        double loss;
+        CKS(loss_grad(ctx, &loss, g));
+        if (!std::isfinite(loss)) return STAG_ERR_NAN;
+        if (s == 0 && loss_first) *loss_first = loss;
+        if (loss_last) *loss_last = loss;
+        ctx->adam_t += 1;
+        const double c1 = 1.0 - std::pow(b1, ctx->adam_t), c2 = 1.0 - std::pow(b2, ctx->adam_t);
+        for (int i = 0; i < SUR_NP; ++i) {
+            ctx->adam_m[i] = b1 * ctx->adam_m[i] + (1 - b1) * g[i];
+            ctx->adam_v[i] = b2 * ctx->adam_v[i] + (1 - b2) * g[i] * g[i];
+            ctx->sur_master[i] -= lr * (ctx->adam_m[i] / c1) / (std::sqrt(ctx->adam_v[i] / c2) + eps);
+        }
+        CKS(upload_params(ctx));
+    }
+    return STAG_OK;
+}

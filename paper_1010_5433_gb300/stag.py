@@ -52,7 +52,8 @@ class stag_hmc(C.Structure):
                 ("tol_md", C.c_double), ("tol_met", C.c_double), ("max_iter", C.c_int),
                 ("md_prec", C.c_int), ("seed", C.c_ulonglong), ("counter", C.c_ulonglong),
                 ("ext_mom", C.c_void_p), ("ext_xi", C.c_void_p), ("ext_phi", C.c_void_p), ("ext_uniform", C.c_double),
-                ("no_metropolis", C.c_int), ("flip_momenta", C.c_int)]
+                ("no_metropolis", C.c_int), ("flip_momenta", C.c_int), ("use_surrogate", C.c_int),
+                ("n_mid", C.c_int)]
 
 
 class stag_kernel_profile(C.Structure):
@@ -104,6 +105,14 @@ def lib():
             "stag_launch_count": ([vp], C.c_longlong),
             "stag_profile_phases": ([vp, C.POINTER(d)], i),
             "stag_tuned_threads_per_site": ([vp, i, i, C.POINTER(d)], i),
+            "stag_surrogate_load": ([vp, vp], i),
+            "stag_surrogate_store": ([vp, vp], i),
+            "stag_surrogate_force": ([vp, vp], i),
+            "stag_surrogate_add_force_sample": ([vp, vp], i),
+            "stag_surrogate_add_sample": ([vp, C.POINTER(stag_hmc), C.c_ulonglong], i),
+            "stag_surrogate_samples": ([vp], C.c_longlong),
+            "stag_surrogate_loss_grad": ([vp, C.POINTER(d), vp], i),
+            "stag_surrogate_train": ([vp, i, d, C.POINTER(d), C.POINTER(d)], i),
             "stag_draw_momenta": ([vp, C.c_ulonglong, C.c_ulonglong, vp], i),
             "stag_draw_sources": ([vp, C.c_ulonglong, C.c_ulonglong, i, i, vp], i),
         }
@@ -282,3 +291,43 @@ def stag_profile_phases(ctx):
     arr = (C.c_double * 6)()
     _check(lib().stag_profile_phases(ctx, arr), "stag_profile_phases", ctx)
     return list(arr)
+
+
+STAG_SUR_PARAMS = 2648
+
+
+def stag_surrogate_load(ctx, params):
+    """params: host float32 array (numpy) of STAG_SUR_PARAMS values."""
+    _check(lib().stag_surrogate_load(ctx, _ptr(params)), "stag_surrogate_load", ctx)
+
+
+def stag_surrogate_store(ctx, params):
+    _check(lib().stag_surrogate_store(ctx, _ptr(params)), "stag_surrogate_store", ctx)
+
+
+def stag_surrogate_force(ctx, force):
+    _check(lib().stag_surrogate_force(ctx, _ptr(force)), "stag_surrogate_force", ctx)
+
+
+def stag_surrogate_add_force_sample(ctx, force):
+    _check(lib().stag_surrogate_add_force_sample(ctx, _ptr(force)), "stag_surrogate_add_force_sample", ctx)
+
+
+def stag_surrogate_add_sample(ctx, hmc, counter):
+    _check(lib().stag_surrogate_add_sample(ctx, C.byref(hmc), int(counter)), "stag_surrogate_add_sample", ctx)
+
+
+def stag_surrogate_samples(ctx):
+    return lib().stag_surrogate_samples(ctx)
+
+
+def stag_surrogate_loss_grad(ctx, grad=None):
+    loss = C.c_double()
+    _check(lib().stag_surrogate_loss_grad(ctx, C.byref(loss), _ptr(grad)), "stag_surrogate_loss_grad", ctx)
+    return loss.value
+
+
+def stag_surrogate_train(ctx, steps, lr):
+    a, b = C.c_double(), C.c_double()
+    _check(lib().stag_surrogate_train(ctx, int(steps), float(lr), C.byref(a), C.byref(b)), "stag_surrogate_train", ctx)
+    return a.value, b.value

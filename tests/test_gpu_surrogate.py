@@ -1,0 +1,147 @@
+"""GPU parity of the learned force surrogate against the FP64 oracle
+(oracle/surrogate.py) with the same bf16-rounded weights: the surrogate
+force, its Wilson-force special case, loss and parameter gradients; training
+lowers the loss; a surrogate-assisted trajectory stays reversible."""
+import numpy as np
+import pytest
+
+import synthetic as syn
+from oracle import actions, surrogate as sur
+from tests import layout as L
+from tests.gpu_util import torch_cuda, wrap_device
+
+pytestmark = pytest.mark.gpu
+DIMS = (4, 4, 4, 6)
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return torch_cuda()
+
+
+def flat(p):
+    return np.concatenate([p["W1"].ravel(), p["b1"], p["W2"].ravel(), p["b2"], p["W3"].ravel(), p["b3"]]).astype(np.float32)
+
+
+def as_device_precision(p):
+    """The weights the device uses: W rounded to bf16, biases to fp32."""
+    q = {}
+    for k, v in p.items():
+        q[k] = sur.bf16_round(v) if k.startswith("W") else np.asarray(v, dtype=np.float32).astype(np.float64)
+    return q
+
+
+def _rel(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def test_surrogate_force_matches_oracle(torch):
+    from paper_1010_5433_gb300 import stag
+    u = syn.near_identity_gauge(DIMS, 501, width=0.6)
+    p = sur.init_params(5, scale=1.0)
+    f, G = sur.features_and_generators(u)
+    want = sur.surrogate_force(as_device_precision(p), f, G)
+    ctx = stag.stag_create(DIMS, True)
+    try:
+        stag.stag_load_gauge(ctx, L.gauge_host(u))
+        stag.stag_surrogate_load(ctx, flat(p))
+        out = torch.empty((4, 2, 8, int(np.prod(DIMS)) // 2), dtype=torch.float64, device="cuda")
+        stag.stag_surrogate_force(ctx, out)
+        got = L.mom_from_abi(out.cpu().numpy(), DIMS)
+        assert _rel(got, want) < 1e-5
+    finally:
+        stag.stag_destroy(ctx)
+
+
+def test_plaquette_weights_give_the_wilson_force(torch):
+    from paper_1010_5433_gb300 import stag
+    u = syn.haar_gauge(DIMS, 502)
+    beta = 5.6
+    p = {k: np.zeros_like(v) for k, v in sur.init_params(0).items()}
+    for i in range(3):
+        p["b3"][8 * i] = p["b3"][8 * i + 1] = -beta / 3.0
+    ctx = stag.stag_create(DIMS, True)
+    try:
+        stag.stag_load_gauge(ctx, L.gauge_host(u))
+        stag.stag_surrogate_load(ctx, flat(p))
+        out = torch.empty((4, 2, 8, int(np.prod(DIMS)) // 2), dtype=torch.float64, device="cuda")
+        stag.stag_surrogate_force(ctx, out)
+        # b3 = -beta/3 is exact in fp32 only to 1e-7: compare against the fp32-rounded value
+        w = float(np.float32(-beta / 3.0))
+        assert _rel(L.mom_from_abi(out.cpu().numpy(), DIMS), actions.wilson_force(u, -3.0 * w)) < 2e-6
+    finally:
+        stag.stag_destroy(ctx)
+
+
+def test_loss_and_gradient_match_oracle(torch):
+    from paper_1010_5433_gb300 import stag
+    u = syn.near_identity_gauge(DIMS, 503, width=0.5)
+    p = sur.init_params(6, scale=1.0)
+    f, G = sur.features_and_generators(u)
+    target = np.random.default_rng(4).standard_normal(G.shape[:-2] + (8,))
+    pd = as_device_precision(p)
+    # the device reads the target force in fp32
+    t32 = target.astype(np.float32).astype(np.float64)
+    want_loss, want_grad = sur.loss_and_grad(pd, f, G, t32)
+    ctx = stag.stag_create(DIMS, True)
+    try:
+        stag.stag_load_gauge(ctx, L.gauge_host(u))
+        stag.stag_surrogate_load(ctx, flat(p))
+        d_t = torch.from_numpy(L.mom_to_abi(target, DIMS)).cuda()
+        stag.stag_surrogate_add_force_sample(ctx, d_t)
+        grad = np.zeros(stag.STAG_SUR_PARAMS)
+        loss = stag.stag_surrogate_loss_grad(ctx, grad)
+        assert abs(loss - want_loss) < 1e-5 * want_loss
+        ref = flat({k: want_grad[k] for k in ("W1", "b1", "W2", "b2", "W3", "b3")}).astype(np.float64)
+        assert _rel(grad, ref) < 1e-4
+    finally:
+        stag.stag_destroy(ctx)
+
+
+def _hmc(stag, g, **kw):
+    p = stag.stag_hmc()
+    p.beta, p.tau, p.n_outer, p.n_gauge, p.n_flavours = 5.6, 1.0, 4, 2, 1
+    fl = p.flavour[0]
+    fl.mass, fl.n_pf = 0.1, 1
+    for k in ("hb", "md", "met"):
+        setattr(fl, k, stag.make_rational(g["c1_" + k]["a0"], g["c1_" + k]["alpha"], g["c1_" + k]["beta"]))
+    p.tol_md, p.tol_met, p.max_iter, p.md_prec, p.seed = 1e-8, 1e-12, 20000, 1, 77
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def test_training_lowers_loss_and_surrogate_md_is_reversible(torch):
+    import json
+    import os
+    from paper_1010_5433_gb300 import stag
+    g = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "rationals.json")))
+    dims = (4, 4, 4, 4)
+    ctx = stag.stag_create(dims, True)
+    try:
+        stag.stag_load_gauge(ctx, L.gauge_host(syn.near_identity_gauge(dims, 0x5A0005)))
+        stag.stag_surrogate_load(ctx, flat(sur.init_params(9, scale=0.3)))
+        for k in range(4):
+            stag.stag_md_trajectory(ctx, _hmc(stag, g, counter=k))
+            stag.stag_surrogate_add_sample(ctx, _hmc(stag, g), 100 + k)
+        assert stag.stag_surrogate_samples(ctx) == 4
+        first, last = stag.stag_surrogate_train(ctx, 60, 3e-3)
+        print(f"surrogate training: loss {first:.4f} -> {last:.4f}")
+        assert last < 0.8 * first
+        # reversibility of the three-level integrator with the trained surrogate
+        buf0 = np.empty(4 * 256 * 18)
+        stag.stag_store_gauge(ctx, buf0)
+        mom = torch.from_numpy(L.mom_to_abi(syn.gaussian_momenta(dims, 3), dims)).cuda()
+        phi = torch.from_numpy(L.to_half(syn.gaussian_fermion(dims, 4, on_parity=0), dims, 0)[None].view(np.float64)).cuda()
+        r1 = stag.stag_md_trajectory(ctx, _hmc(stag, g, use_surrogate=1, n_mid=3, ext_mom=mom.data_ptr(),
+                                               ext_phi=phi.data_ptr(), no_metropolis=1))
+        back = wrap_device(torch, stag.stag_momenta(ctx), mom.numel()).clone()
+        r2 = stag.stag_md_trajectory(ctx, _hmc(stag, g, use_surrogate=1, n_mid=3, ext_mom=back.data_ptr(),
+                                               ext_phi=phi.data_ptr(), no_metropolis=1, flip_momenta=1))
+        buf1 = np.empty(4 * 256 * 18)
+        stag.stag_store_gauge(ctx, buf1)
+        viol = np.sqrt(np.mean((buf1 - buf0) ** 2))
+        print(f"surrogate MD: dH {r1.dH:.4e} back {r2.dH:.4e} reversibility {viol:.2e}")
+        assert viol < 5e-5 and abs(r1.dH + r2.dH) < 1e-2
+    finally:
+        stag.stag_destroy(ctx)

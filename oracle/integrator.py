@@ -8,6 +8,11 @@ Sint; ref. [hmc] Duane, Kennedy, Pendleton, Roweth).
         p += -lam h F;  U-update h/2;  p += -(1-2 lam) h F;  U-update h/2;  p += -lam h F
     with lam = 0.1931833275037836 (Omelyan, Mryglod, Folk 2002; the paper
     names the scheme but not the constant)
+  * optionally (not in the paper: the learned-surrogate workload) three levels:
+    the remainder F_f - F^ on the outer level, the surrogate force F^
+    (oracle/surrogate.py) on n_mid minimum-norm steps per outer half step,
+    the gauge level inside those; the levels add up to the exact force, so
+    the integrator stays reversible and area-preserving for any F^
   * Metropolis on dH = H_f - H_i with H = 1/2 sum p_a^2 + S_g + S_f, where the
     final S_f uses the Metropolis rational (tighter than the MD one, Sec. 2)
     and the initial S_f = xi^dag xi.
@@ -19,6 +24,7 @@ from typing import List
 import numpy as np
 
 from . import dirac, lattice as lat, solvers, su3
+from . import surrogate as sur
 from .actions import fermion_action, fermion_force, wilson_action, wilson_force
 
 LAMBDA_2MN = 0.1931833275037836
@@ -99,16 +105,46 @@ def gauge_level(u, mom, h, n, beta):
     return u, mom
 
 
-def md_evolve(ctx, u, mom, phis, tau, n_outer, n_gauge):
-    """Two-level minimum-norm integration of length tau."""
+def surrogate_force(u, params):
+    """F^ of the links u for the network params (oracle/surrogate.py)."""
+    f, G = sur.features_and_generators(u)
+    return sur.surrogate_force(params, f, G)
+
+
+def surrogate_level(u, mom, h, n_mid, n_gauge, beta, params):
+    """n_mid minimum-norm steps of size h/n_mid with the surrogate force F^,
+    the gauge level for the link updates."""
+    d = h / n_mid
+    for _ in range(n_mid):
+        mom = mom - LAMBDA_2MN * d * surrogate_force(u, params)
+        u, mom = gauge_level(u, mom, d / 2, n_gauge, beta)
+        mom = mom - (1 - 2 * LAMBDA_2MN) * d * surrogate_force(u, params)
+        u, mom = gauge_level(u, mom, d / 2, n_gauge, beta)
+        mom = mom - LAMBDA_2MN * d * surrogate_force(u, params)
+    return u, mom
+
+
+def md_evolve(ctx, u, mom, phis, tau, n_outer, n_gauge, surrogate=None, n_mid=1):
+    """Two-level minimum-norm integration of length tau; with surrogate
+    params, three levels (outer force F_f - F^, middle F^, inner gauge)."""
     p = ctx.p
     e = tau / n_outer
+
+    def outer_force(u):
+        f = ctx.fermion_force_total(u, phis)
+        return f if surrogate is None else f - surrogate_force(u, surrogate)
+
+    def inner(u, mom):
+        if surrogate is None:
+            return gauge_level(u, mom, e / 2, n_gauge, p.beta)
+        return surrogate_level(u, mom, e / 2, n_mid, n_gauge, p.beta, surrogate)
+
     for _ in range(n_outer):
-        mom = mom - LAMBDA_2MN * e * ctx.fermion_force_total(u, phis)
-        u, mom = gauge_level(u, mom, e / 2, n_gauge, p.beta)
-        mom = mom - (1 - 2 * LAMBDA_2MN) * e * ctx.fermion_force_total(u, phis)
-        u, mom = gauge_level(u, mom, e / 2, n_gauge, p.beta)
-        mom = mom - LAMBDA_2MN * e * ctx.fermion_force_total(u, phis)
+        mom = mom - LAMBDA_2MN * e * outer_force(u)
+        u, mom = inner(u, mom)
+        mom = mom - (1 - 2 * LAMBDA_2MN) * e * outer_force(u)
+        u, mom = inner(u, mom)
+        mom = mom - LAMBDA_2MN * e * outer_force(u)
     return u, mom
 
 
@@ -124,18 +160,24 @@ def hamiltonian_kinetic(mom):
     return 0.5 * float(np.sum(mom * mom))
 
 
-def trajectory(ctx, u0, mom0, xis, uniform=None):
+def trajectory(ctx, u0, mom0, xis, uniform=None, surrogate=None, n_mid=1, phis=None):
     """One RHMC trajectory with supplied momenta mom0 [4,t,z,y,x,8] and
-    Gaussian sources xis (per flavour, per pseudo-fermion, even fields).
+    Gaussian sources xis (per flavour, per pseudo-fermion, even fields);
+    surrogate params select the three-level integrator.  With phis given
+    (per flavour, per pseudo-fermion) the heatbath is skipped and the initial
+    S_f is phi^dag r_met(A) phi.
 
     Returns dict with the final links and momenta (before accept/reject),
     dH, the pieces of H and, if `uniform` is given, the Metropolis decision
     accept = uniform < exp(-dH)."""
     p = ctx.p
-    phis = heatbath(ctx, u0, xis)
-    s_f0 = sum(float(np.real(np.vdot(x, x))) for xl in xis for x in xl)
+    if phis is None:
+        phis = heatbath(ctx, u0, xis)
+        s_f0 = sum(float(np.real(np.vdot(x, x))) for xl in xis for x in xl)
+    else:
+        s_f0 = ctx.fermion_action_total(u0, phis, p.tol_met)
     h0 = hamiltonian_kinetic(mom0) + wilson_action(u0, p.beta) + s_f0
-    u1, mom1 = md_evolve(ctx, u0, mom0, phis, p.tau, p.n_outer, p.n_gauge)
+    u1, mom1 = md_evolve(ctx, u0, mom0, phis, p.tau, p.n_outer, p.n_gauge, surrogate, n_mid)
     u1 = su3.reunitarize(u1)
     s_f1 = ctx.fermion_action_total(u1, phis, p.tol_met)
     h1 = hamiltonian_kinetic(mom1) + wilson_action(u1, p.beta) + s_f1

@@ -145,3 +145,68 @@ def test_training_lowers_loss_and_surrogate_md_is_reversible(torch):
         assert viol < 5e-5 and abs(r1.dH + r2.dH) < 1e-2
     finally:
         stag.stag_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec,tol_dh,tol_u", [(0, 1e-4, 1e-6), (1, 2e-3, 1e-5)])
+def test_three_level_trajectory_matches_oracle(torch, prec, tol_dh, tol_u):
+    """The surrogate-assisted trajectory (outer F_f - F^, n_mid steps of F^,
+    gauge inside) against the oracle's three-level integrator with the same
+    bf16-rounded network; F^ is evaluated in fp32 on the device."""
+    import json
+    import os
+    from oracle import integrator
+    from oracle.rational import Rational
+    from paper_1010_5433_gb300 import stag
+    g = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "rationals.json")))
+    rat = {k: Rational(g["c1_" + k]["s"], g["c1_" + k]["lo"], g["c1_" + k]["hi"], g["c1_" + k]["a0"],
+                       g["c1_" + k]["alpha"], g["c1_" + k]["beta"], g["c1_" + k]["err"]) for k in ("md", "met", "hb")}
+    dims = (4, 4, 4, 4)
+    net = sur.init_params(12, scale=1.0)
+    net["W3"] *= 2.0
+    u0 = syn.near_identity_gauge(dims, 0x5A0006)
+    mom0 = syn.gaussian_momenta(dims, 641)
+    xi = syn.gaussian_fermion(dims, 642, on_parity=0)
+    fl = integrator.Flavour(mass=0.1, hb=rat["hb"], md=rat["md"], met=rat["met"])
+    prm = integrator.HMCParams(dims=dims, beta=5.6, tau=0.5, n_outer=3, n_gauge=1, flavours=[fl],
+                               tol_md=1e-13, tol_met=1e-13)
+    want = integrator.trajectory(integrator.Context(prm), u0, mom0, [[xi]], surrogate=as_device_precision(net),
+                                 n_mid=2)
+    ctx = stag.stag_create(dims, True)
+    try:
+        stag.stag_load_gauge(ctx, L.gauge_host(u0))
+        stag.stag_surrogate_load(ctx, flat(net))
+        d_mom = torch.from_numpy(L.mom_to_abi(mom0, dims)).cuda()
+        d_xi = torch.from_numpy(L.to_half(xi, dims, 0)[None].view(np.float64)).cuda()
+        p = _hmc(stag, g, tau=0.5, n_outer=3, n_gauge=1, md_prec=prec, tol_md=1e-12 if prec == 0 else 1e-8,
+                 use_surrogate=1, n_mid=2, ext_mom=d_mom.data_ptr(), ext_xi=d_xi.data_ptr(), no_metropolis=1)
+        res = stag.stag_md_trajectory(ctx, p)
+        buf = np.empty(4 * 256 * 18)
+        stag.stag_store_gauge(ctx, buf)
+        du = np.abs(L.gauge_from_host(buf, dims) - want["u"]).max()
+        print(f"three-level prec {prec}: dH gpu {res.dH:.8f} oracle {want['dH']:.8f} max|dU| {du:.2e}")
+        assert abs(res.H0 - want["H0"]) < 1e-8 * abs(want["H0"])
+        assert abs(res.dH - want["dH"]) < tol_dh
+        assert du < tol_u
+    finally:
+        stag.stag_destroy(ctx)
+
+
+def test_what_the_trained_surrogate_gains(torch):
+    """Trains the surrogate on exact forces of an 8^4 Nf=2 m=0.05 chain and
+    measures what it gains.  The exact force splits into its mean over
+    heatbath draws, Fbar(U), and pseudo-fermion noise; a function of U alone
+    can learn Fbar only.  The trained network must reproduce most of Fbar,
+    and a surrogate-assisted trajectory must not be worse than the exact one
+    at the same number of fermion-force evaluations.  Measured on GB300:
+    Fbar carries ~1.4% of |F|^2 and the network reproduces ~80% of it, so the
+    paired |dH| with and without the surrogate agree within a few percent --
+    the remainder F - F^ the outer level integrates is barely smaller than F."""
+    from paper_1010_5433_gb300 import surrogate_bench
+    r = surrogate_bench.run(dims=(8, 8, 8, 8), rat_prefix="c4", mass=0.05, n_outer=8, n_mid=3, samples=6,
+                            train_steps=200, pairs=4, decomp_configs=2, draws=6)
+    print(r)
+    assert r["training"]["loss_last"] < r["training"]["loss_first"]
+    assert r["force"]["captured_share_of_mean"] > 0.5
+    assert 0.0 < r["force"]["mean_share"] < 0.2
+    assert r["surrogate"]["mean_abs_dH"] < 1.25 * r["exact_half"]["mean_abs_dH"]
+    assert r["exact"]["mean_abs_dH"] < r["exact_half"]["mean_abs_dH"]

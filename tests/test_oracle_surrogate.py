@@ -107,3 +107,73 @@ def test_backward_matches_finite_differences(fg):
 def test_bf16_round_known_values():
     x = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -9, -3.14159265])
     np.testing.assert_array_equal(sur.bf16_round(x), [1.0, 1.0, 1.0 + 2 ** -7, -3.140625])
+
+
+def _three_level_params(n_outer, n_gauge, tau=0.5, mass=0.2):
+    from oracle import integrator, rational
+    lo, hi = mass ** 2, 16 + mass ** 2
+    fl = integrator.Flavour(mass=mass, hb=rational.remez(-0.25, lo, hi, 8, dps=40),
+                            md=rational.remez(0.5, lo, hi, 6, dps=40), met=rational.remez(0.5, lo, hi, 10, dps=40))
+    return integrator.HMCParams(dims=(2, 2, 2, 2), beta=5.5, tau=tau, n_outer=n_outer, n_gauge=n_gauge,
+                                flavours=[fl], tol_md=1e-13, tol_met=1e-14)
+
+
+def _strong_network(seed):
+    """A network whose force is of the size of the fermion force (not fitted
+    to it): a plain test of the splitting, not of the learning."""
+    p = sur.init_params(seed, scale=1.0)
+    p["W3"] *= 4.0
+    p["b3"] += 0.5
+    return p
+
+
+def test_three_level_with_zero_network_is_the_two_level_integrator():
+    """F^ = 0 makes each surrogate level n_mid pairs of gauge levels of the
+    same step: the trajectory equals the two-level one with 2 n_mid n_gauge
+    gauge steps per half step (step sizes are powers of two: exactly)."""
+    from oracle import integrator
+    dims = (2, 2, 2, 2)
+    zero = {k: np.zeros_like(v) for k, v in sur.init_params(0).items()}
+    zero["W1"] = sur.init_params(1)["W1"]          # hidden layers alive, output weights zero
+    args = (syn.near_identity_gauge(dims, 611), syn.gaussian_momenta(dims, 612),
+            [[syn.gaussian_fermion(dims, 613, on_parity=0)]])
+    three = integrator.trajectory(integrator.Context(_three_level_params(2, 1)), *args, surrogate=zero, n_mid=2)
+    two = integrator.trajectory(integrator.Context(_three_level_params(2, 4)), *args)
+    assert np.array_equal(three["u"], two["u"]) and np.array_equal(three["mom"], two["mom"])
+    assert three["dH"] == two["dH"]
+
+
+def test_three_level_dh_vanishes_as_step_squared():
+    """Outer F_f - F^ plus middle F^ integrate the exact force for any F^:
+    with a large, unfitted F^ dH still falls as eps^2.  A sign slip in the
+    remainder would integrate F_f + 2 F^ (or leave F^ twice) and dH would
+    tend to a nonzero limit instead."""
+    from oracle import integrator
+    dims = (2, 2, 2, 2)
+    net = _strong_network(7)
+    u0 = syn.near_identity_gauge(dims, 621)
+    f, G = sur.features_and_generators(u0)
+    fs = sur.surrogate_force(net, f, G)
+    pr = _three_level_params(2, 1)
+    ctx = integrator.Context(pr)
+    phi = [[syn.gaussian_fermion(dims, 623, on_parity=0)]]
+    ff = ctx.fermion_force_total(u0, integrator.heatbath(ctx, u0, phi))
+    assert np.linalg.norm(fs) > 0.5 * np.linalg.norm(ff)       # F^ is not small
+    dhs = []
+    for n in (4, 8):
+        out = integrator.trajectory(integrator.Context(_three_level_params(n, 1)), u0,
+                                    syn.gaussian_momenta(dims, 622), phi, surrogate=net, n_mid=1)
+        dhs.append(abs(out["dH"]))
+    assert 2.5 < dhs[0] / dhs[1] < 6.5, dhs
+
+
+def test_three_level_is_reversible():
+    from oracle import integrator
+    dims = (2, 2, 2, 2)
+    net = _strong_network(8)
+    ctx = integrator.Context(_three_level_params(2, 1))
+    u0, mom0 = syn.near_identity_gauge(dims, 631), syn.gaussian_momenta(dims, 632)
+    phis = [[syn.gaussian_fermion(dims, 633, on_parity=0)]]
+    u1, m1 = integrator.md_evolve(ctx, u0, mom0, phis, 0.5, 2, 1, surrogate=net, n_mid=2)
+    u2, m2 = integrator.md_evolve(ctx, u1, -m1, phis, 0.5, 2, 1, surrogate=net, n_mid=2)
+    assert np.abs(u2 - u0).max() < 1e-11 and np.abs(m2 + mom0).max() < 1e-10

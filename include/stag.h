@@ -68,6 +68,8 @@ typedef struct {
 
 /* r(x) = a0 + sum_i alpha[i] / (x + beta[i]), n <= STAG_MAX_SHIFTS (Sec. 2). */
 #define STAG_MAX_SHIFTS 32
+/* independent chains (contexts) advanced together by stag_md_trajectory_batch */
+#define STAG_MAX_BATCH 8
 typedef struct {
     int n;
     double a0;
@@ -156,6 +158,20 @@ typedef struct {
 stag_status stag_multishift_solve(stag_ctx* ctx, double mass, int nshift, const double* shifts,
                                   stag_prec prec, int nrhs, const void* b, void* x,
                                   double tol, int max_iter, stag_solve_info* info);
+
+/* The same solve for n independent lattices at once (1 <= n <= STAG_MAX_BATCH,
+ * one source each, one mass and shift set; no counterpart in the paper):
+ * ctxs[i] with source b[i] [3][Vh_i] and solutions x[i] [nshift][3][Vh_i],
+ * fp64 device arrays, info[i] per lattice (may be NULL).  One persistent
+ * cooperative launch iterates every lattice whose solve has not converged;
+ * each stops on its own convergence flag; reliable updates and the per-shift
+ * refinement of mixed solves are made per lattice between launches.  Runs on
+ * ctxs[0]'s stream (after the work queued on the other contexts' streams);
+ * the contexts must be distinct.  Returns STAG_ERR_NOT_CONVERGED if any
+ * lattice did not converge. */
+stag_status stag_multishift_solve_batch(stag_ctx* const* ctxs, int n, double mass, int nshift, const double* shifts,
+                                        stag_prec prec, const void* const* b, void* const* x, double tol,
+                                        int max_iter, stag_solve_info* info);
 
 /* ---- forces and actions (Sec. 2, Sec. 4) -------------------------------- */
 
@@ -249,6 +265,23 @@ typedef struct {
 /* One RHMC trajectory: heatbath, two-level minimum-norm MD, Metropolis with a
  * host-side uniform, restore of the old field on rejection. */
 stag_status stag_md_trajectory(stag_ctx* ctx, const stag_hmc* p, stag_traj* out);
+
+/* One trajectory of each of n independent chains (1 <= n <= STAG_MAX_BATCH),
+ * advanced together (Sec. 2 algorithm per chain; the batching has no
+ * counterpart in the paper).  ctxs[i] holds chain i's lattice (any size) and
+ * field; p[i] and out[i] are its parameters and record, with the same
+ * integrator schedule for all chains (n_outer, n_gauge, tau, md_prec,
+ * flavours and pseudo-fermions per flavour, surrogate use, supplied phi or
+ * not; seeds, counters, masses, rationals and supplied fields may differ).
+ * Every multi-shift solve of the trajectories -- heatbath, each fermion force,
+ * Metropolis -- is one solve over all chains: a persistent cooperative launch
+ * that iterates every chain still converging, each with its own convergence
+ * flag, one pseudo-fermion at a time.  The work runs on ctxs[0]'s stream,
+ * after the work already queued on the other contexts' streams; the contexts
+ * must be distinct and must not be used by other threads during the call.
+ * out[i].seconds and the phase times are those of the whole batch.  Returns
+ * the first error; with n == 1 it is stag_md_trajectory. */
+stag_status stag_md_trajectory_batch(stag_ctx* const* ctxs, int n, const stag_hmc* p, stag_traj* out);
 
 /* Momenta of the last trajectory (device, momentum layout, read-only). */
 const double* stag_momenta(stag_ctx* ctx);

@@ -12,7 +12,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libstag.so")
-SOURCES = ["api.cu", "gauge.cu", "dslash.cu", "solver.cu", "blas.cu", "force.cu", "hmc.cu", "noalloc.cu", "persistent.cu", "surrogate.cu"]
+SOURCES = ["api.cu", "gauge.cu", "dslash.cu", "solver.cu", "blas.cu", "force.cu", "hmc.cu", "noalloc.cu", "persistent.cu", "surrogate.cu", "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

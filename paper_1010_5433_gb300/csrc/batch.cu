@@ -1,0 +1,551 @@
+// Several independent multi-shift solves -- one per context, each on its own
+// lattice of any size -- iterated by ONE persistent cooperative launch.  The
+// workload is a set of independent Markov chains of uneven volumes (8^4 to
+// 16^4): a single small lattice leaves most of the 152 SMs idle and pays a
+// grid barrier per phase for a few thousand sites, while the chains together
+// fill the GPU and share every barrier.
+//
+// Work queue: in every phase the sites of all chains still iterating form one
+// concatenated range, dealt out round-robin to all threads of the grid
+// (thread i takes the sites congruent to i), so the chains are load-balanced
+// whatever their sizes.  Each chain keeps its own scalar recurrences
+// (Jegerlehner's, Sec. 6) in shared memory, advanced redundantly by every
+// block from the per-block partial sums of all chains, summed in one fixed
+// order; a chain that converges or needs a reliable update halts by itself
+// (its convergence flag) while the others continue.  The launch ends when
+// every chain has halted; the host then makes the fp64 reliable updates of
+// the chains that asked for one and launches again.  One source per chain
+// (n_rhs = 1); every wait on a grid barrier is bounded.
+#include <cmath>
+#include <cstring>
+
+#include "internal.h"
+#include "solver_state.cuh"
+#include "grid_barrier.cuh"
+
+namespace {
+
+constexpr int MAXC = STAG_MAX_BATCH;
+constexpr int NS = STAG_MAX_SHIFTS;
+
+struct ChainArgs {
+    Geom g;
+    LinkPtrs L;
+    SolverState* st;
+    void *r, *p, *q, *t, *ps, *x;
+};
+struct BatchArgs {
+    int n;
+    ChainArgs c[MAXC];
+};
+
+// one chain's scalar recurrences (one source)
+struct ScalM {
+    double zeta[NS], zeta_prev[NS], zeta_next[NS], cx[NS], cpr[NS], cpp[NS], dsig[NS];
+    double rr, bb, rr_ref, alpha, alpha_prev, beta_prev, beta, sum, k4_units, c0, tol2, delta2;
+    int live[NS], iters_at[NS];
+    int rhs_live, k, halt, status, need_reliable, nshift, max_iter, mixed, left, nan;
+};
+
+__device__ void load_scal_m(ScalM* S, const ChainArgs* C, int nc) {
+    const int t = threadIdx.x;
+    for (int i = t; i < nc * NS; i += blockDim.x) {
+        const int c = i / NS, s = i % NS;
+        const SolverState* st = C[c].st;
+        S[c].zeta[s] = st->zeta[0][s];
+        S[c].zeta_prev[s] = st->zeta_prev[0][s];
+        S[c].zeta_next[s] = st->zeta_next[0][s];
+        S[c].cx[s] = st->cx[0][s];
+        S[c].cpr[s] = st->cpr[0][s];
+        S[c].cpp[s] = st->cpp[0][s];
+        S[c].dsig[s] = st->dsig[s];
+        S[c].live[s] = st->live[0][s];
+        S[c].iters_at[s] = st->iters_at[0][s];
+    }
+    if (t < nc) {
+        const SolverState* st = C[t].st;
+        ScalM& s = S[t];
+        s.rr = st->rr[0];
+        s.bb = st->bb[0];
+        s.rr_ref = st->rr_ref[0];
+        s.alpha = st->alpha[0];
+        s.alpha_prev = st->alpha_prev[0];
+        s.beta_prev = st->beta_prev[0];
+        s.beta = st->beta[0];
+        s.k4_units = st->k4_units;
+        s.c0 = st->c0;
+        s.tol2 = st->tol2;
+        s.delta2 = st->delta2;
+        s.rhs_live = st->rhs_live[0];
+        s.k = st->k;
+        s.halt = st->halt;
+        s.status = st->status;
+        s.need_reliable = st->need_reliable;
+        s.nshift = st->nshift;
+        s.max_iter = st->max_iter;
+        s.mixed = st->mixed;
+        s.nan = 0;
+    }
+    __syncthreads();
+}
+
+__device__ void store_scal_m(const ScalM* S, const ChainArgs* C, int nc) {
+    const int t = threadIdx.x;
+    for (int i = t; i < nc * NS; i += blockDim.x) {
+        const int c = i / NS, s = i % NS;
+        SolverState* st = C[c].st;
+        st->zeta[0][s] = S[c].zeta[s];
+        st->zeta_prev[0][s] = S[c].zeta_prev[s];
+        st->zeta_next[0][s] = S[c].zeta_next[s];
+        st->cx[0][s] = S[c].cx[s];
+        st->cpr[0][s] = S[c].cpr[s];
+        st->cpp[0][s] = S[c].cpp[s];
+        st->live[0][s] = S[c].live[s];
+        st->iters_at[0][s] = S[c].iters_at[s];
+    }
+    if (t < nc) {
+        SolverState* st = C[t].st;
+        const ScalM& s = S[t];
+        st->rr[0] = s.rr;
+        st->alpha[0] = s.alpha;
+        st->alpha_prev[0] = s.alpha_prev;
+        st->beta_prev[0] = s.beta_prev;
+        st->beta[0] = s.beta;
+        st->rhs_live[0] = s.rhs_live;
+        st->k4_units = s.k4_units;
+        st->k = s.k;
+        st->halt = s.halt;
+        st->status = s.status;
+        st->need_reliable = s.need_reliable;
+    }
+}
+
+// every block: S[c].sum = sum over blocks of partial[base + c][.] for all
+// chains at once, in the same fixed order in every block
+__device__ void sum_partials_m(ScalM* S, const double* partial, int nb, int nc, int base) {
+    double acc[MAXC];
+#pragma unroll
+    for (int j = 0; j < MAXC; ++j) acc[j] = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+#pragma unroll
+        for (int j = 0; j < MAXC; ++j)
+            if (j < nc) acc[j] += __ldcg(partial + (size_t)(base + j) * nb + i);
+    }
+    block_sum<MAXC>(acc);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int j = 0; j < MAXC; ++j)
+            if (j < nc) S[j].sum = acc[j];
+    __syncthreads();
+}
+
+// alpha_k = (r, r) / (p, A p) and the shifted zeta_{k+1}, alpha_{i,k}
+__device__ void alpha_step_m(ScalM* S, int nc) {
+    const int t = threadIdx.x;
+    if (t < nc && !S[t].halt) {
+        double a = S[t].rr / S[t].sum;
+        if (!isfinite(a) || !(S[t].sum > 0.0)) {
+            S[t].status = STAG_ERR_NAN;
+            S[t].halt = 1;
+            a = 0.0;
+        }
+        S[t].alpha = a;
+    }
+    __syncthreads();
+    for (int i = t; i < nc * NS; i += blockDim.x) {
+        const int c = i / NS, s = i % NS;
+        ScalM& C = S[c];
+        if (C.halt || s >= C.nshift || !C.live[s]) continue;
+        const double a = C.alpha, ap = C.alpha_prev, bp = C.beta_prev;
+        const double z = C.zeta[s], zp = C.zeta_prev[s];
+        const double den = a * bp * (zp - z) + zp * ap * (1.0 + C.dsig[s] * a);
+        const double zn = z * zp * ap / den;
+        C.zeta_next[s] = zn;
+        C.cx[s] = a * zn / z;
+    }
+    __syncthreads();
+}
+
+// beta_k = (r', r') / (r, r), the shifted beta_{i,k}, per-shift convergence,
+// and the chain's halt: converged, reliable update due, max_iter or NaN
+__device__ void beta_step_m(ScalM* S, int nc) {
+    const int t = threadIdx.x;
+    __shared__ double s_beta[MAXC];
+    __shared__ int active[MAXC];
+    if (t < nc) {
+        active[t] = !S[t].halt;
+        S[t].left = 0;
+        if (active[t]) {
+            const double rn = S[t].sum;
+            if (!isfinite(rn)) S[t].nan = 1;
+            s_beta[t] = rn / S[t].rr;
+            int n_live = 0;
+            for (int s = 0; s < S[t].nshift; ++s) n_live += S[t].live[s];
+            S[t].k4_units += 72.0 + 96.0 * n_live;
+        }
+    }
+    __syncthreads();
+    for (int i = t; i < nc * NS; i += blockDim.x) {
+        const int c = i / NS, s = i % NS;
+        ScalM& C = S[c];
+        if (!active[c] || s >= C.nshift || !C.live[s]) continue;
+        const double zn = C.zeta_next[s], z = C.zeta[s];
+        const double zr = zn / z;
+        C.cpr[s] = zn;
+        C.cpp[s] = s_beta[c] * zr * zr;
+        C.zeta_prev[s] = z;
+        C.zeta[s] = zn;
+        if (zn * zn * C.sum <= C.tol2 * C.bb) {
+            C.live[s] = 0;
+            C.iters_at[s] = C.k + 1;
+        } else {
+            atomicOr(&C.left, 1);
+        }
+    }
+    __syncthreads();
+    if (t < nc && active[t]) {
+        ScalM& C = S[t];
+        C.beta = s_beta[t];
+        C.alpha_prev = C.alpha;
+        C.beta_prev = s_beta[t];
+        C.rr = C.sum;
+        C.k += 1;
+        if (C.nan) {
+            C.status = STAG_ERR_NAN;
+            C.halt = 1;
+        } else if (!C.left) {
+            C.rhs_live = 0;
+            C.halt = 1;
+        } else {
+            if (C.mixed && C.sum < C.delta2 * C.rr_ref) C.need_reliable = 1;
+            if (C.k >= C.max_iter) {
+                C.halt = 1;
+                C.status = STAG_ERR_NOT_CONVERGED;
+            }
+            if (C.need_reliable) C.halt = 1;
+        }
+    }
+    __syncthreads();
+}
+
+// first site of this thread in a chain whose sites start at `off` in the
+// concatenated range (round-robin over all threads of the grid)
+__device__ __forceinline__ int first_site(long long tid, long long off, long long nthreads) {
+    long long d = (tid - off) % nthreads;
+    return (int)(d < 0 ? d + nthreads : d);
+}
+
+// phase 1 at odd site h: t = D_oe (r + beta p), without the 1/2
+template <typename R, int FMT>
+__device__ __forceinline__ void site_doe(const Geom& g, const LinkPtrs& L, int h, const typename V2T<R>::T* r,
+                                         const typename V2T<R>::T* p, typename V2T<R>::T* t, R bt) {
+    Nbr n;
+    site_neighbours(g, h, 1, n);
+    Vec3<R> acc;
+    zero(acc);
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+#pragma unroll
+        for (int dir = 0; dir < 2; ++dir) {
+            const int nb_h = dir == 0 ? n.fwd[mu] : n.bwd[mu];
+            Su3<R> u = dir == 0 ? LinkFetch<R, FMT>::get(L, mu, 1, h, g.Vh) : LinkFetch<R, FMT>::get(L, mu, 0, nb_h, g.Vh);
+            Vec3<R> a = load_vec_cg<R>(r, nb_h, g.Vh);
+            Vec3<R> b = load_vec_cg<R>(p, nb_h, g.Vh);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                a.c[c].re += bt * b.c[c].re;
+                a.c[c].im += bt * b.c[c].im;
+            }
+            if (dir == 0) mac_uv(acc, (R)n.sf[mu], u, a);
+            else mac_udv(acc, -(R)n.sb[mu], u, a);
+        }
+    }
+    store_vec<R>(t, h, g.Vh, acc);
+}
+
+// phase 2 at even site h: p = r + beta p; q = c0 p - 1/4 (hops of t); returns (p, q)
+template <typename R, int FMT>
+__device__ __forceinline__ double site_a(const Geom& g, const LinkPtrs& L, int h, const typename V2T<R>::T* t,
+                                         typename V2T<R>::T* p, const typename V2T<R>::T* r,
+                                         typename V2T<R>::T* q, R bt, R c0) {
+    Nbr n;
+    site_neighbours(g, h, 0, n);
+    Vec3<R> acc;
+    zero(acc);
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+#pragma unroll
+        for (int dir = 0; dir < 2; ++dir) {
+            const int nb_h = dir == 0 ? n.fwd[mu] : n.bwd[mu];
+            Su3<R> u = dir == 0 ? LinkFetch<R, FMT>::get(L, mu, 0, h, g.Vh) : LinkFetch<R, FMT>::get(L, mu, 1, nb_h, g.Vh);
+            Vec3<R> a = load_vec_cg<R>(t, nb_h, g.Vh);
+            if (dir == 0) mac_uv(acc, (R)n.sf[mu], u, a);
+            else mac_udv(acc, -(R)n.sb[mu], u, a);
+        }
+    }
+    Vec3<R> pv = load_vec_cg<R>(p, h, g.Vh);
+    Vec3<R> rv = load_vec_cg<R>(r, h, g.Vh);
+    Vec3<R> o;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        pv.c[c].re = rv.c[c].re + bt * pv.c[c].re;
+        pv.c[c].im = rv.c[c].im + bt * pv.c[c].im;
+        o.c[c].re = c0 * pv.c[c].re - (R)0.25 * acc.c[c].re;
+        o.c[c].im = c0 * pv.c[c].im - (R)0.25 * acc.c[c].im;
+    }
+    store_vec<R>(p, h, g.Vh, pv);
+    store_vec<R>(q, h, g.Vh, o);
+    return re_dot(pv, o);
+}
+
+// phase 3 at even site h: p_i = zeta r + beta_i p_i; x_i += alpha_i p_i for
+// the live shifts (four at a time, loads before stores); r -= alpha q; returns (r, r)
+template <typename R>
+__device__ __forceinline__ double site_update(const ScalM& S, int h, int Vh, typename V2T<R>::T* r,
+                                              const typename V2T<R>::T* q, typename V2T<R>::T* ps,
+                                              typename V2T<R>::T* x) {
+    const size_t rs = (size_t)3 * Vh;
+    Vec3<R> rv = load_vec_cg<R>(r, h, Vh);
+    const int ns = S.nshift;
+    for (int s0 = 0; s0 < ns; s0 += 4) {
+        Vec3<R> pv[4], xv[4];
+        bool on[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int s = s0 + u;
+            on[u] = s < ns && S.live[s];
+            if (on[u]) {
+                pv[u] = load_vec_cg<R>(ps + (size_t)s * rs, h, Vh);
+                xv[u] = load_vec_cg<R>(x + (size_t)s * rs, h, Vh);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (!on[u]) continue;
+            const int s = s0 + u;
+            const R cx = (R)S.cx[s], cpr = (R)S.cpr[s], cpp = (R)S.cpp[s];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                pv[u].c[c].re = cpr * rv.c[c].re + cpp * pv[u].c[c].re;
+                pv[u].c[c].im = cpr * rv.c[c].im + cpp * pv[u].c[c].im;
+                xv[u].c[c].re += cx * pv[u].c[c].re;
+                xv[u].c[c].im += cx * pv[u].c[c].im;
+            }
+            store_vec<R>(x + (size_t)s * rs, h, Vh, xv[u]);
+            store_vec<R>(ps + (size_t)s * rs, h, Vh, pv[u]);
+        }
+    }
+    const R a = (R)S.alpha;
+    Vec3<R> qv = load_vec_cg<R>(q, h, Vh);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        rv.c[c].re -= a * qv.c[c].re;
+        rv.c[c].im -= a * qv.c[c].im;
+    }
+    store_vec<R>(r, h, Vh, rv);
+    return norm2(rv);
+}
+
+// add v into slot c of a register array without dynamic register indexing
+__device__ __forceinline__ void add_slot(double (&a)[MAXC], int c, double v) {
+#pragma unroll
+    for (int j = 0; j < MAXC; ++j)
+        if (j == c) a[j] += v;
+}
+
+template <typename R, int FMT, int PB>
+__global__ void __launch_bounds__(PB) k_ms_persistent_batch(BatchArgs A, double* partial, GridBar* bar) {
+    typedef typename V2T<R>::T V;
+    __shared__ ScalM S[MAXC];
+    __shared__ ChainArgs C[MAXC];
+    const int nc = A.n;
+    if (threadIdx.x < nc) C[threadIdx.x] = A.c[threadIdx.x];
+    __syncthreads();
+    load_scal_m(S, C, nc);
+    const unsigned int nb = gridDim.x;
+    const long long nthreads = (long long)gridDim.x * blockDim.x;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    bool ok = true;
+    for (;;) {
+        int any = 0;
+        for (int c = 0; c < nc; ++c) any |= !S[c].halt;
+        if (!any) break;
+        // ---- phase 1: t = D_oe (r + beta p) on every iterating chain
+        long long off = 0;
+        for (int c = 0; c < nc; ++c) {
+            if (S[c].halt) continue;
+            const Geom g = C[c].g;
+            const LinkPtrs L = C[c].L;
+            const R bt = (R)S[c].beta;
+            const V *r = (const V*)C[c].r, *p = (const V*)C[c].p;
+            V* t = (V*)C[c].t;
+            for (int h = first_site(tid, off, nthreads); h < g.Vh; h += (int)nthreads)
+                site_doe<R, FMT>(g, L, h, r, p, t, bt);
+            off += g.Vh;
+        }
+        if (!(ok = grid_sync(bar, nb))) break;
+        // ---- phase 2: p = r + beta p; q = (A + s0) p; (p, q)
+        double dots[MAXC];
+#pragma unroll
+        for (int j = 0; j < MAXC; ++j) dots[j] = 0.0;
+        off = 0;
+        for (int c = 0; c < nc; ++c) {
+            if (S[c].halt) continue;
+            const Geom g = C[c].g;
+            const LinkPtrs L = C[c].L;
+            const R bt = (R)S[c].beta, c0 = (R)S[c].c0;
+            const V *t = (const V*)C[c].t, *r = (const V*)C[c].r;
+            V *p = (V*)C[c].p, *q = (V*)C[c].q;
+            double d = 0.0;
+            for (int h = first_site(tid, off, nthreads); h < g.Vh; h += (int)nthreads)
+                d += site_a<R, FMT>(g, L, h, t, p, r, q, bt, c0);
+            add_slot(dots, c, d);
+            off += g.Vh;
+        }
+        block_sum<MAXC>(dots);
+        if (threadIdx.x == 0)
+            for (int j = 0; j < nc; ++j) partial[(size_t)j * nb + blockIdx.x] = dots[j];
+        if (!(ok = grid_sync(bar, nb))) break;
+        sum_partials_m(S, partial, nb, nc, 0);
+        alpha_step_m(S, nc);
+        // ---- phase 3: shift updates, r -= alpha q, (r, r)
+        double nrm[MAXC];
+#pragma unroll
+        for (int j = 0; j < MAXC; ++j) nrm[j] = 0.0;
+        off = 0;
+        for (int c = 0; c < nc; ++c) {
+            if (S[c].halt) continue;   // halted by its alpha step (NaN)
+            const int Vh = C[c].g.Vh;
+            V *r = (V*)C[c].r, *ps = (V*)C[c].ps, *x = (V*)C[c].x;
+            const V* q = (const V*)C[c].q;
+            double d = 0.0;
+            for (int h = first_site(tid, off, nthreads); h < Vh; h += (int)nthreads)
+                d += site_update<R>(S[c], h, Vh, r, q, ps, x);
+            add_slot(nrm, c, d);
+            off += Vh;
+        }
+        block_sum<MAXC>(nrm);
+        if (threadIdx.x == 0)
+            for (int j = 0; j < nc; ++j) partial[(size_t)(MAXC + j) * nb + blockIdx.x] = nrm[j];
+        if (!(ok = grid_sync(bar, nb))) break;
+        sum_partials_m(S, partial, nb, nc, MAXC);
+        beta_step_m(S, nc);
+    }
+    if (!ok && threadIdx.x < nc && !S[threadIdx.x].halt) {
+        S[threadIdx.x].halt = 1;
+        S[threadIdx.x].status = STAG_ERR_TIMEOUT;
+    }
+    __syncthreads();
+    if (blockIdx.x == 0) store_scal_m(S, C, nc);
+}
+
+template <typename R, int FMT, int PB>
+stag_status launch_batch_pb(stag_ctx* ctx, const BatchArgs& A, long long sites, double* partial,
+                            size_t partial_doubles, GridBar* bar) {
+    auto kern = k_ms_persistent_batch<R, FMT, PB>;
+    int per_sm = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, PB, 0));
+    if (per_sm < 1) return STAG_ERR_ARG;
+    int dev = 0, nsm = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    long long want = nblocks(sites, PB);
+    long long cap = (long long)nsm * per_sm;
+    int grid = (int)(want < cap ? want : cap);
+    if (grid < 1) grid = 1;
+    if ((size_t)2 * MAXC * grid > partial_doubles) return STAG_ERR_ARG;
+    CK(cudaMemsetAsync(bar, 0, sizeof(GridBar), ctx->stream));
+    BatchArgs a = A;
+    void* args[] = {&a, &partial, &bar};
+    CK(cudaLaunchCooperativeKernel((const void*)kern, grid, PB, args, 0, ctx->stream));
+    ++ctx->launches;
+    return STAG_OK;
+}
+
+template <typename R, int FMT>
+stag_status launch_batch_t(stag_ctx* ctx, int pb, const BatchArgs& A, long long sites, double* partial, size_t pd,
+                           GridBar* bar) {
+    if (pb == 128) return launch_batch_pb<R, FMT, 128>(ctx, A, sites, partial, pd, bar);
+    return launch_batch_pb<R, FMT, 256>(ctx, A, sites, partial, pd, bar);
+}
+
+stag_status launch_batch(stag_ctx* ctx, stag_prec prec, int pb, const BatchArgs& A, long long sites, double* partial,
+                         size_t pd, GridBar* bar) {
+    switch (prec) {
+        case STAG_FP64: return launch_batch_t<DF, FMT_F64>(ctx, pb, A, sites, partial, pd, bar);
+        case STAG_FP32: return launch_batch_t<float, FMT_F32_18>(ctx, pb, A, sites, partial, pd, bar);
+        case STAG_FP32_12: return launch_batch_t<float, FMT_F32_12>(ctx, pb, A, sites, partial, pd, bar);
+        default: return launch_batch_t<float, FMT_BF16_12>(ctx, pb, A, sites, partial, pd, bar);
+    }
+}
+}  // namespace
+
+stag_status ms_core_multi(MsRun* runs, int n, MsStats* stats, stag_status* per_chain) {
+    if (n < 1 || n > MAXC || !runs) return STAG_ERR_ARG;
+    stag_ctx* lead = runs[0].ctx;
+    for (int i = 0; i < n; ++i) {
+        if (runs[i].nrhs != 1 || runs[i].prec != runs[0].prec || runs[i].ctx->stream != lead->stream)
+            return STAG_ERR_ARG;
+        for (int j = 0; j < i; ++j)
+            if (runs[j].ctx == runs[i].ctx) return STAG_ERR_ARG;
+    }
+    stag_ctx* ctx = lead;   // error reporting of the CK macros
+    for (int i = 0; i < n; ++i) CKS(ms_setup(runs[i]));
+    if (!lead->bar) CKS(dev_alloc(lead, &lead->bar, sizeof(GridBar)));
+    int dev = 0, nsm = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const size_t pd = (size_t)2 * MAXC * nsm * 8;   // up to 8 co-resident blocks per SM
+    void* partial;
+    CKS(ws_get(lead, WS_BATCH_RED, pd * sizeof(double), &partial));
+    std::vector<int> active(n, 1);
+    std::vector<stag_status> st(n, STAG_OK);
+    int max_iter = 0;
+    for (int i = 0; i < n; ++i) max_iter = std::max(max_iter, runs[i].max_iter);
+    const int max_segments = 64 + max_iter;
+    for (int seg = 0;; ++seg) {
+        BatchArgs A;
+        std::memset(&A, 0, sizeof(A));
+        long long sites = 0;
+        std::vector<int> idx;
+        for (int i = 0; i < n; ++i) {
+            if (!active[i]) continue;
+            stag_ctx* c = runs[i].ctx;
+            ChainArgs& a = A.c[A.n++];
+            a.g = c->g;
+            a.L = link_ptrs(c);
+            a.st = c->st;
+            a.r = runs[i].r;
+            a.p = runs[i].p;
+            a.q = runs[i].q;
+            a.t = runs[i].tmp;
+            a.ps = runs[i].ps;
+            a.x = runs[i].x;
+            sites += c->g.Vh;
+            idx.push_back(i);
+        }
+        if (A.n == 0) break;
+        if (seg > max_segments) {
+            for (int i : idx) { st[i] = STAG_ERR_TIMEOUT; active[i] = 0; }
+            break;
+        }
+        CKS(launch_batch(lead, runs[0].prec, lead->persist_block, A, sites, (double*)partial, pd,
+                         (GridBar*)lead->bar));
+        for (int i : idx) CKS(ms_pull_control_async(runs[i].ctx));
+        CK(cudaStreamSynchronize(lead->stream));
+        for (int i : idx) {
+            const SolverState* hs = runs[i].ctx->st_host;
+            if (!hs->halt) { st[i] = STAG_ERR_TIMEOUT; active[i] = 0; continue; }
+            if (hs->status != STAG_OK) { st[i] = (stag_status)hs->status; active[i] = 0; continue; }
+            if (hs->need_reliable) { CKS(ms_reliable_update(runs[i])); continue; }
+            active[i] = 0;   // converged
+        }
+    }
+    for (int i = 0; i < n; ++i) {
+        CKS(ms_pull_state(runs[i].ctx));
+        CKS(ms_finish(runs[i]));
+        if (stats) ms_stats(runs[i], &stats[i]);
+        if (per_chain) per_chain[i] = st[i];
+    }
+    return STAG_OK;
+}

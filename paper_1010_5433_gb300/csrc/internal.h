@@ -32,6 +32,7 @@ enum WsSlot {
     WS_TUNE_IN, WS_TUNE_OUT,   // autotuner fields
     WS_B_DF, WS_X_DF,  // fp64 solves: float-float copies of b and x
     WS_SUR_GRAD_PART, WS_SUR_LOSS_PART, WS_SUR_GRAD,   // surrogate training
+    WS_BATCH_RED,      // batched solves: per-block partial sums of all chains
     WS_COUNT
 };
 
@@ -170,6 +171,42 @@ struct MsStats {
 stag_status ms_core(stag_ctx* ctx, double mass, int nshift, const double* shifts, stag_prec prec, int nrhs,
                     const void* b, const double2* b64, void* x, double2* x64, double tol, int max_iter,
                     bool reliable, bool finish_to_f64, MsStats* stats);
+
+// The pieces of ms_core, for solves of several contexts iterated by one
+// launch (batch.cu): one MsRun per solve, arguments as for ms_core.
+struct MsRun {
+    stag_ctx* ctx = nullptr;
+    double mass = 0.0;
+    int nshift = 0;
+    const double* shifts = nullptr;
+    stag_prec prec = STAG_FP32;
+    int nrhs = 1;
+    const void* b = nullptr;
+    const double2* b64 = nullptr;
+    void* x = nullptr;
+    double2* x64 = nullptr;
+    double tol = 0.0;
+    int max_iter = 0;
+    bool reliable = false, finish_to_f64 = false;
+    // set by ms_setup
+    bool mixed = false, use_rel = false;
+    int base = 0;
+    void *tmp = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *ps = nullptr;   // iteration vectors
+    void *ax64 = nullptr, *t64 = nullptr, *xb64 = nullptr;                         // reliable-update scratch
+    const void* b_user = nullptr;   // fp64 solves: the caller's arrays (the iteration runs on float-float copies)
+    void* x_user = nullptr;
+};
+stag_status ms_setup(MsRun& R);                 // workspace, solver state, initial vectors (stream-ordered)
+stag_status ms_reliable_update(MsRun& R);       // after a halt with need_reliable: fp64 residual, halt cleared
+stag_status ms_finish(MsRun& R);                // solutions into the caller's format
+void ms_stats(const MsRun& R, MsStats* stats);  // from the host copy of the state (after ms_pull_state)
+stag_status ms_pull_state(stag_ctx* ctx);       // whole state to the host copy, synchronous
+stag_status ms_pull_control_async(stag_ctx* ctx);   // loop-control words to the host copy, no sync
+
+// batch.cu: solves of up to STAG_MAX_BATCH contexts (one source each, same
+// prec, all on one stream) iterated together by persistent cooperative
+// launches; per-chain statuses in per_chain, stats (n entries) may be NULL
+stag_status ms_core_multi(MsRun* runs, int n, MsStats* stats, stag_status* per_chain);
 
 // persistent.cu: the whole iteration loop in one cooperative launch
 bool persistent_fits(stag_ctx* ctx);

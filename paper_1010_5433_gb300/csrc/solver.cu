@@ -733,75 +733,159 @@ static stag_status pull_control(stag_ctx* ctx) {
     return STAG_OK;
 }
 
+stag_status ms_setup(MsRun& R) {
+    stag_ctx* ctx = R.ctx;
+    const Geom& g = ctx->g;
+    R.mixed = R.prec != STAG_FP64;
+    if (R.nrhs < 1 || R.nrhs > STAG_MAX_RHS || R.nshift < 1 || R.nshift > STAG_MAX_SHIFTS) return STAG_ERR_ARG;
+    if (R.mixed && R.reliable && (!R.b64 || !R.x64)) return STAG_ERR_ARG;
+    // the bf16 copy must follow every link update before a bf16 iteration
+    if (R.prec == STAG_BF16_12 && ctx->b16_stale) CKS(refresh_bf16(ctx));
+    R.base = 0;
+    for (int s = 0; s < R.nshift; ++s)
+        if (R.shifts[s] < R.shifts[R.base]) R.base = s;
+    const size_t vbytes = (size_t)R.nrhs * 3 * g.Vh * 2 * rsize(R.prec);
+    CKS(ws_get(ctx, WS_TMP_ODD, vbytes, &R.tmp));
+    CKS(ws_get(ctx, WS_R, vbytes, &R.r));
+    CKS(ws_get(ctx, WS_P, vbytes, &R.p));
+    CKS(ws_get(ctx, WS_Q, vbytes, &R.q));
+    CKS(ws_get(ctx, WS_PS, vbytes * R.nshift, &R.ps));
+    const size_t v64 = (size_t)R.nrhs * 3 * g.Vh * sizeof(double2);
+    R.use_rel = R.mixed && R.reliable;
+    if (R.use_rel) {
+        CKS(ws_get(ctx, WS_R64, v64, &R.ax64));
+        CKS(ws_get(ctx, WS_T64, v64, &R.t64));
+        CKS(ws_get(ctx, WS_U64, v64, &R.xb64));
+    }
+    if (R.mixed && R.x64) CK(cudaMemsetAsync(R.x64, 0, v64 * R.nshift, ctx->stream));
+    // fp64 solves iterate in float-float (Sec. 5: the two-float representation
+    // used directly): b and x are double on the outside, float-float inside
+    R.b_user = R.b;
+    R.x_user = R.x;
+    if (!R.mixed) {
+        void *bdf, *xdf;
+        CKS(ws_get(ctx, WS_B_DF, v64, &bdf));
+        CKS(ws_get(ctx, WS_X_DF, v64 * R.nshift, &xdf));
+        k_d2df<<<nblocks((long long)R.nrhs * 3 * g.Vh, 256), 256, 0, ctx->stream>>>(
+            (size_t)R.nrhs * 3 * g.Vh, (const double2*)R.b_user, (float4*)bdf);
+        CKL();
+        R.b = bdf;
+        R.x = xdf;
+    }
+    SolverState* hs = ctx->st_host;
+    std::memset(hs, 0, sizeof(SolverState));
+    hs->nrhs = R.nrhs;
+    hs->nshift = R.nshift;
+    hs->base = R.base;
+    hs->max_iter = R.max_iter;
+    hs->mixed = R.use_rel ? 1 : 0;
+    hs->tol2 = R.tol * R.tol;
+    hs->c0 = R.mass * R.mass + R.shifts[R.base];
+    hs->delta2 = 0.01;   // replace the residual after every factor 10 in ||r||
+    for (int s = 0; s < R.nshift; ++s) hs->dsig[s] = R.shifts[s] - R.shifts[R.base];
+    CK(cudaMemcpyAsync(ctx->st, hs, sizeof(SolverState), cudaMemcpyHostToDevice, ctx->stream));
+    dim3 grid_v(nblocks(g.Vh, VB), R.nrhs);
+    if (R.mixed)
+        k_ms_init<float><<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, (const float2*)R.b, (float2*)R.r,
+                                                         (float2*)R.p, (float2*)R.ps, (float2*)R.x, ctx->red,
+                                                         ctx->counters + 2);
+    else
+        k_ms_init<DF><<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, (const float4*)R.b, (float4*)R.r,
+                                                      (float4*)R.p, (float4*)R.ps, (float4*)R.x, ctx->red,
+                                                      ctx->counters + 2);
+    CKL();
+    return STAG_OK;
+}
+
+// fp64 accumulation of every shift, then the true base residual
+// b - (A + s0) x0 with the fp64 operator replaces the recursive one; the
+// solve may then continue (halt cleared)
+stag_status ms_reliable_update(MsRun& R) {
+    stag_ctx* ctx = R.ctx;
+    const Geom& g = ctx->g;
+    dim3 grid_v(nblocks(g.Vh, VB), R.nrhs);
+    SolverState* hs = ctx->st_host;
+    k_rel_accumulate<<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, R.x64, (float2*)R.x);
+    k_rel_gather_base<<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, R.x64, (double2*)R.xb64);
+    CKS(launch_apply_a(ctx, hs->c0, STAG_FP64, R.nrhs, R.xb64, R.ax64, R.t64));
+    k_rel_finish<<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, R.b64, (const double2*)R.ax64, (float2*)R.r,
+                                                 ctx->red, ctx->counters + 3);
+    ctx->launches += 3;
+    CK(cudaGetLastError());
+    hs->halt = 0;
+    CK(cudaMemcpyAsync(&ctx->st->halt, &hs->halt, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    return STAG_OK;
+}
+
+// the solutions in the caller's format once the iteration has stopped
+stag_status ms_finish(MsRun& R) {
+    stag_ctx* ctx = R.ctx;
+    const Geom& g = ctx->g;
+    dim3 grid_v(nblocks(g.Vh, VB), R.nrhs);
+    if (!R.mixed) {
+        const size_t n = (size_t)R.nrhs * R.nshift * 3 * g.Vh;
+        k_df2d<<<nblocks((long long)n, 256), 256, 0, ctx->stream>>>(n, (const float4*)R.x, (double2*)R.x_user);
+        CKL();
+        R.x = R.x_user;
+        R.b = R.b_user;
+    }
+    if (R.mixed && R.x64) {
+        if (R.finish_to_f64) k_acc_final<<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, R.x64, (const float2*)R.x);
+        else k_rel_output<<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, R.x64, (float2*)R.x);
+        CKL();
+    }
+    return STAG_OK;
+}
+
+void ms_stats(const MsRun& R, MsStats* stats) {
+    if (!stats) return;
+    const SolverState* hs = R.ctx->st_host;
+    stats->iterations = hs->k;
+    stats->reliable = hs->n_reliable;
+    for (int s = 0; s < R.nshift; ++s) {
+        int it = 0;
+        for (int q2 = 0; q2 < R.nrhs; ++q2) it = hs->iters_at[q2][s] > it ? hs->iters_at[q2][s] : it;
+        stats->shift_iterations[s] = it;
+    }
+}
+
+stag_status ms_pull_state(stag_ctx* ctx) { return pull_state(ctx); }
+stag_status ms_pull_control_async(stag_ctx* ctx) {
+    const size_t off = offsetof(SolverState, k);
+    const size_t len = offsetof(SolverState, rhs_live) - off;
+    CK(cudaMemcpyAsync((char*)ctx->st_host + off, (const char*)ctx->st + off, len, cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    return STAG_OK;
+}
+
 stag_status ms_core(stag_ctx* ctx, double mass, int nshift, const double* shifts, stag_prec prec, int nrhs,
                     const void* b, const double2* b64, void* x, double2* x64, double tol, int max_iter,
                     bool reliable, bool finish_to_f64, MsStats* stats) {
     const Geom& g = ctx->g;
-    const bool mixed = prec != STAG_FP64;
-    if (nrhs < 1 || nrhs > STAG_MAX_RHS || nshift < 1 || nshift > STAG_MAX_SHIFTS) return STAG_ERR_ARG;
-    if (mixed && reliable && (!b64 || !x64)) return STAG_ERR_ARG;
-    // the bf16 copy must follow every link update before a bf16 iteration
-    if (prec == STAG_BF16_12 && ctx->b16_stale) CKS(refresh_bf16(ctx));
-    int base = 0;
-    for (int s = 0; s < nshift; ++s)
-        if (shifts[s] < shifts[base]) base = s;
-    const size_t vbytes = (size_t)nrhs * 3 * g.Vh * 2 * rsize(prec);
-    void *tmp, *r, *p, *q, *ps;
-    CKS(ws_get(ctx, WS_TMP_ODD, vbytes, &tmp));
-    CKS(ws_get(ctx, WS_R, vbytes, &r));
-    CKS(ws_get(ctx, WS_P, vbytes, &p));
-    CKS(ws_get(ctx, WS_Q, vbytes, &q));
-    CKS(ws_get(ctx, WS_PS, vbytes * nshift, &ps));
-    const size_t v64 = (size_t)nrhs * 3 * g.Vh * sizeof(double2);
-    void *ax64 = nullptr, *t64 = nullptr, *xb64 = nullptr;
-    const bool use_rel = mixed && reliable;
-    if (use_rel) {
-        CKS(ws_get(ctx, WS_R64, v64, &ax64));
-        CKS(ws_get(ctx, WS_T64, v64, &t64));
-        CKS(ws_get(ctx, WS_U64, v64, &xb64));
-    }
-    if (mixed && x64) CK(cudaMemsetAsync(x64, 0, v64 * nshift, ctx->stream));
-    // fp64 solves iterate in float-float (Sec. 5: the two-float representation
-    // used directly): b and x are double on the outside, float-float inside
-    const void* b_user = b;
-    void* x_user = x;
-    if (!mixed) {
-        void *bdf, *xdf;
-        CKS(ws_get(ctx, WS_B_DF, v64, &bdf));
-        CKS(ws_get(ctx, WS_X_DF, v64 * nshift, &xdf));
-        k_d2df<<<nblocks((long long)nrhs * 3 * g.Vh, 256), 256, 0, ctx->stream>>>((size_t)nrhs * 3 * g.Vh,
-                                                                                   (const double2*)b_user, (float4*)bdf);
-        CKL();
-        b = bdf;
-        x = xdf;
-    }
+    MsRun R;
+    R.ctx = ctx;
+    R.mass = mass;
+    R.nshift = nshift;
+    R.shifts = shifts;
+    R.prec = prec;
+    R.nrhs = nrhs;
+    R.b = b;
+    R.b64 = b64;
+    R.x = x;
+    R.x64 = x64;
+    R.tol = tol;
+    R.max_iter = max_iter;
+    R.reliable = reliable;
+    R.finish_to_f64 = finish_to_f64;
+    CKS(ms_setup(R));
+    const bool mixed = R.mixed;
     SolverState* hs = ctx->st_host;
-    std::memset(hs, 0, sizeof(SolverState));
-    hs->nrhs = nrhs;
-    hs->nshift = nshift;
-    hs->base = base;
-    hs->max_iter = max_iter;
-    hs->mixed = use_rel ? 1 : 0;
-    hs->tol2 = tol * tol;
-    hs->c0 = mass * mass + shifts[base];
-    hs->delta2 = 0.01;   // replace the residual after every factor 10 in ||r||
-    for (int s = 0; s < nshift; ++s) hs->dsig[s] = shifts[s] - shifts[base];
-    CK(cudaMemcpyAsync(ctx->st, hs, sizeof(SolverState), cudaMemcpyHostToDevice, ctx->stream));
-    dim3 grid_v(nblocks(g.Vh, VB), nrhs);
-    if (mixed)
-        k_ms_init<float><<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, (const float2*)b, (float2*)r, (float2*)p,
-                                                         (float2*)ps, (float2*)x, ctx->red, ctx->counters + 2);
-    else
-        k_ms_init<DF><<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, (const float4*)b, (float4*)r,
-                                                          (float4*)p, (float4*)ps, (float4*)x, ctx->red,
-                                                          ctx->counters + 2);
-    CKL();
     stag_status status = STAG_OK;
     cudaGraphExec_t gexec = nullptr;
     const bool persistent = persistent_fits(ctx);
     if (!persistent) {
         dslash_tps(ctx, prec, dslash_nr_for(nrhs));   // tune before any capture
-        if (ctx->use_graphs) CKS(solver_graph(ctx, prec, nrhs, tmp, r, p, q, ps, x, &gexec));
+        if (ctx->use_graphs) CKS(solver_graph(ctx, prec, nrhs, R.tmp, R.r, R.p, R.q, R.ps, R.x, &gexec));
     }
     cudaEvent_t pe0 = nullptr, pe1 = nullptr;
     double persist_ms = 0.0;
@@ -817,7 +901,7 @@ stag_status ms_core(stag_ctx* ctx, double mass, int nshift, const double* shifts
         if (seg > max_segments) { status = STAG_ERR_TIMEOUT; break; }
         if (persistent) {
             if (pe0) CK(cudaEventRecord(pe0, ctx->stream));
-            CKS(launch_persistent(ctx, prec, nrhs, r, p, q, tmp, ps, x));
+            CKS(launch_persistent(ctx, prec, nrhs, R.r, R.p, R.q, R.tmp, R.ps, R.x));
             if (pe1) CK(cudaEventRecord(pe1, ctx->stream));
             CKS(pull_control(ctx));
             if (pe0) {
@@ -828,47 +912,31 @@ stag_status ms_core(stag_ctx* ctx, double mass, int nshift, const double* shifts
             if (!hs->halt) { status = STAG_ERR_TIMEOUT; break; }   // the loop only ends by halting
             if (hs->status != STAG_OK) { status = (stag_status)hs->status; break; }
             if (hs->need_reliable) {
-                k_rel_accumulate<<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, x64, (float2*)x);
-                k_rel_gather_base<<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, x64, (double2*)xb64);
-                CKS(launch_apply_a(ctx, hs->c0, STAG_FP64, nrhs, xb64, ax64, t64));
-                k_rel_finish<<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, b64, (const double2*)ax64, (float2*)r,
-                                                             ctx->red, ctx->counters + 3);
-                ctx->launches += 3;
-                CK(cudaGetLastError());
-                hs->halt = 0;
-                CK(cudaMemcpyAsync(&ctx->st->halt, &hs->halt, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+                CKS(ms_reliable_update(R));
                 continue;
             }
             break;
         }
         // sampled timing: a few plainly launched iterations at the start of every segment
         if (ctx->prof.on) {
-            if (mixed) CKS(ms_iterations<float>(ctx, ctx->stream, prec, nrhs, 4, tmp, r, p, q, ps, x, true, 0, 0));
-            else CKS(ms_iterations<DF>(ctx, ctx->stream, prec, nrhs, 4, tmp, r, p, q, ps, x, true, 0, 0));
+            if (mixed) CKS(ms_iterations<float>(ctx, ctx->stream, prec, nrhs, 4, R.tmp, R.r, R.p, R.q, R.ps, R.x,
+                                                true, 0, 0));
+            else CKS(ms_iterations<DF>(ctx, ctx->stream, prec, nrhs, 4, R.tmp, R.r, R.p, R.q, R.ps, R.x, true, 0, 0));
         }
         if (gexec) {
             CK(cudaGraphLaunch(gexec, ctx->stream));
             ++ctx->launches;
         } else if (mixed) {
-            CKS(ms_iterations<float>(ctx, ctx->stream, prec, nrhs, chunk, tmp, r, p, q, ps, x, false, 0, 0));
+            CKS(ms_iterations<float>(ctx, ctx->stream, prec, nrhs, chunk, R.tmp, R.r, R.p, R.q, R.ps, R.x, false, 0,
+                                     0));
         } else {
-            CKS(ms_iterations<DF>(ctx, ctx->stream, prec, nrhs, chunk, tmp, r, p, q, ps, x, false, 0, 0));
+            CKS(ms_iterations<DF>(ctx, ctx->stream, prec, nrhs, chunk, R.tmp, R.r, R.p, R.q, R.ps, R.x, false, 0, 0));
         }
         CKS(pull_control(ctx));
         if (!hs->halt) continue;
         if (hs->status != STAG_OK) { status = (stag_status)hs->status; break; }
         if (hs->need_reliable) {
-            // fp64 accumulation of every shift, then the true base residual
-            // b - (A + s0) x0 with the fp64 operator replaces the recursive one
-            k_rel_accumulate<<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, x64, (float2*)x);
-            k_rel_gather_base<<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, x64, (double2*)xb64);
-            CKS(launch_apply_a(ctx, hs->c0, STAG_FP64, nrhs, xb64, ax64, t64));
-            k_rel_finish<<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, b64, (const double2*)ax64, (float2*)r,
-                                                         ctx->red, ctx->counters + 3);
-            ctx->launches += 3;
-            CK(cudaGetLastError());
-            hs->halt = 0;
-            CK(cudaMemcpyAsync(&ctx->st->halt, &hs->halt, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+            CKS(ms_reliable_update(R));
             continue;
         }
         break;   // converged
@@ -895,29 +963,9 @@ stag_status ms_core(stag_ctx* ctx, double mass, int nshift, const double* shifts
         pf.bytes_total[PK_DSLASH_EO_A] += (double)hs->k * g.Vh * (link_bytes_site(prec) + 5.0 * S * nrhs);
         for (int kk = 0; kk < PK_COUNT; ++kk) pf.launches[kk] += hs->k;
     }
-    if (!mixed) {
-        const size_t n = (size_t)nrhs * nshift * 3 * g.Vh;
-        k_df2d<<<nblocks((long long)n, 256), 256, 0, ctx->stream>>>(n, (const float4*)x, (double2*)x_user);
-        CKL();
-        x = x_user;
-        b = b_user;
-    }
-    if (mixed && x64) {
-        if (finish_to_f64) k_acc_final<<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, x64, (const float2*)x);
-        else k_rel_output<<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, x64, (float2*)x);
-        CKL();
-    }
+    CKS(ms_finish(R));
     if (ctx->prof.on && !persistent) ctx->prof.bytes_total[PK_UPDATE] += hs->k4_units * g.Vh * (mixed ? 1.0 : 2.0);
-
-    if (stats) {
-        stats->iterations = hs->k;
-        stats->reliable = hs->n_reliable;
-        for (int s = 0; s < nshift; ++s) {
-            int it = 0;
-            for (int q2 = 0; q2 < nrhs; ++q2) it = hs->iters_at[q2][s] > it ? hs->iters_at[q2][s] : it;
-            stats->shift_iterations[s] = it;
-        }
-    }
+    ms_stats(R, stats);
     return status;
 }
 
@@ -1116,3 +1164,99 @@ extern "C" stag_status stag_profile_read(stag_ctx* ctx, int kind, stag_kernel_pr
 }
 
 extern "C" long long stag_launch_count(stag_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+extern "C" stag_status stag_multishift_solve_batch(stag_ctx* const* ctxs, int n, double mass, int nshift,
+                                                   const double* shifts, stag_prec prec, const void* const* b,
+                                                   void* const* x, double tol, int max_iter, stag_solve_info* info) {
+    if (!ctxs || !shifts || !b || !x || n < 1 || n > STAG_MAX_BATCH || nshift < 1 || nshift > STAG_MAX_SHIFTS ||
+        max_iter < 1 || !(tol > 0.0) || prec < STAG_FP64 || prec > STAG_BF16_12)
+        return STAG_ERR_ARG;
+    for (int s = 0; s < nshift; ++s)
+        if (!(mass * mass + shifts[s] > 0.0)) return STAG_ERR_ARG;
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i] || !b[i] || !x[i]) return STAG_ERR_ARG;
+        if (!ctxs[i]->has_gauge) return STAG_ERR_NO_GAUGE;
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == ctxs[i]) return STAG_ERR_ARG;
+    }
+    stag_ctx* ctx = ctxs[0];
+    std::vector<std::pair<stag_ctx*, cudaStream_t>> saved;
+    for (int i = 0; i < n; ++i) saved.push_back({ctxs[i], ctxs[i]->stream});
+    struct Restore {
+        std::vector<std::pair<stag_ctx*, cudaStream_t>>& s;
+        ~Restore() {
+            for (auto& e : s) e.first->stream = e.second;
+        }
+    } restore{saved};
+    for (int i = 1; i < n; ++i) {
+        if (ctxs[i]->stream == ctx->stream) continue;
+        cudaEvent_t ev;
+        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        CK(cudaEventRecord(ev, ctxs[i]->stream));
+        CK(cudaStreamWaitEvent(ctx->stream, ev, 0));
+        cudaEventDestroy(ev);
+        ctxs[i]->stream = ctx->stream;
+    }
+    std::vector<MsRun> runs(n);
+    for (int i = 0; i < n; ++i) {
+        stag_ctx* c = ctxs[i];
+        MsRun& R = runs[i];
+        R.ctx = c;
+        R.mass = mass;
+        R.nshift = nshift;
+        R.shifts = shifts;
+        R.prec = prec;
+        R.nrhs = 1;
+        R.tol = tol;
+        R.max_iter = max_iter;
+        if (prec == STAG_FP64) {
+            R.b = b[i];
+            R.x = x[i];
+            R.finish_to_f64 = true;
+        } else {
+            const size_t nc = (size_t)3 * c->g.Vh;
+            void *b32, *x32;
+            CKS(ws_get(c, WS_B32, nc * sizeof(float2), &b32));
+            CKS(ws_get(c, WS_X32, nc * nshift * sizeof(float2), &x32));
+            k_d2f<<<nblocks((long long)nc, 256), 256, 0, c->stream>>>(nc, (const double2*)b[i], (float2*)b32);
+            ++c->launches;
+            CK(cudaGetLastError());
+            R.b = b32;
+            R.b64 = (const double2*)b[i];
+            R.x = x32;
+            R.x64 = (double2*)x[i];
+            R.reliable = prec != STAG_BF16_12;
+            R.finish_to_f64 = true;
+        }
+    }
+    std::vector<MsStats> st(n);
+    std::vector<stag_status> ok(n);
+    CKS(ms_core_multi(runs.data(), n, st.data(), ok.data()));
+    stag_status worst = STAG_OK;
+    for (int i = 0; i < n; ++i) {
+        stag_ctx* c = ctxs[i];
+        if (ok[i] != STAG_OK && ok[i] != STAG_ERR_NOT_CONVERGED) return ok[i];
+        if (ok[i] != STAG_OK) worst = ok[i];
+        int extra = 0, nrel = 0;
+        double res[STAG_MAX_SHIFTS] = {0};
+        if (prec == STAG_FP64) {
+            for (int s = 0; s < nshift; ++s)
+                CKS(shift_residuals(c, mass, nshift, s, shifts[s], 1, (const double2*)b[i], (const double2*)x[i],
+                                    &res[s]));
+        } else if (ok[i] == STAG_OK) {
+            CKS(refine_shifts(c, mass, nshift, shifts, 1, (const double2*)b[i], (double2*)x[i], tol, max_iter, &extra,
+                              &nrel, res));
+        }
+        if (info) {
+            stag_solve_info& in = info[i];
+            std::memset(&in, 0, sizeof(in));
+            in.iterations = st[i].iterations + extra;
+            in.reliable_updates = st[i].reliable + nrel;
+            for (int s = 0; s < nshift; ++s) {
+                in.shift_iterations[s] = st[i].shift_iterations[s];
+                in.true_residual[s] = res[s];
+            }
+        }
+    }
+    return worst;
+}

@@ -99,6 +99,9 @@ def lib():
             "stag_gauge_force": ([vp, d, vp], i),
             "stag_plaquette": ([vp, C.POINTER(d)], i),
             "stag_md_trajectory": ([vp, C.POINTER(stag_hmc), C.POINTER(stag_traj)], i),
+            "stag_multishift_solve_batch": ([C.POINTER(vp), i, d, i, vp, i, C.POINTER(vp), C.POINTER(vp), d, i,
+                                             C.POINTER(stag_solve_info)], i),
+            "stag_md_trajectory_batch": ([C.POINTER(vp), i, C.POINTER(stag_hmc), C.POINTER(stag_traj)], i),
             "stag_momenta": ([vp], vp),
             "stag_profile_begin": ([vp, i], i),
             "stag_profile_read": ([vp, i, C.POINTER(stag_kernel_profile)], i),
@@ -226,6 +229,22 @@ def stag_multishift_solve(ctx, mass, shifts, prec, nrhs, b, x, tol, max_iter, in
     return (st, inf) if not check else inf
 
 
+def stag_multishift_solve_batch(ctxs, mass, shifts, prec, bs, xs, tol, max_iter, check=True):
+    """Solve (A + shift_i) x = b on every lattice (context) of ctxs at once; bs, xs device fp64 arrays."""
+    n = len(ctxs)
+    sh = _darr([float(s) for s in shifts])
+    carr = (C.c_void_p * n)(*[c.value if isinstance(c, C.c_void_p) else c for c in ctxs])
+    barr = (C.c_void_p * n)(*[_ptr(b) for b in bs])
+    xarr = (C.c_void_p * n)(*[_ptr(x) for x in xs])
+    infos = (stag_solve_info * n)()
+    st = lib().stag_multishift_solve_batch(carr, n, float(mass), len(shifts), C.cast(sh, C.c_void_p), int(prec),
+                                           barr, xarr, float(tol), int(max_iter), infos)
+    if check:
+        _check(st, "stag_multishift_solve_batch", ctxs[0])
+        return list(infos)
+    return st, list(infos)
+
+
 def stag_fermion_force(ctx, mass, rational, prec, n_pf, phi, force, tol, max_iter, info=True):
     inf = stag_solve_info() if info else None
     _check(lib().stag_fermion_force(ctx, float(mass), C.byref(rational), int(prec), int(n_pf), _ptr(phi),
@@ -249,6 +268,16 @@ def stag_md_trajectory(ctx, hmc):
     st = lib().stag_md_trajectory(ctx, C.byref(hmc), C.byref(out))
     _check(st, "stag_md_trajectory", ctx)
     return out
+
+
+def stag_md_trajectory_batch(ctxs, hmcs):
+    """One trajectory of each chain (context) in ctxs with parameters hmcs, advanced together."""
+    n = len(ctxs)
+    carr = (C.c_void_p * n)(*[c.value if isinstance(c, C.c_void_p) else c for c in ctxs])
+    harr = (stag_hmc * n)(*hmcs)
+    outs = (stag_traj * n)()
+    _check(lib().stag_md_trajectory_batch(carr, n, harr, outs), "stag_md_trajectory_batch", ctxs[0])
+    return list(outs)
 
 
 def stag_momenta(ctx):

@@ -320,6 +320,10 @@ stag_status stag_surrogate_train(stag_ctx* ctx, int steps, double lr, double* lo
 #define STAG_PK_UPDATE 2         /* p_i, x_i of the live shifts; r -= alpha q; (r, r), beta step  */
 #define STAG_PK_PERSISTENT 3     /* persistent solver (small lattices): units are iterations,
                                     every launch event-timed, bytes = one whole iteration       */
+#define STAG_PK_BATCH 4          /* batched solver (stag_*_batch; profile of the first context):
+                                    units are batched iterations (one iteration of every lattice
+                                    still iterating), every launch event-timed, bytes = those
+                                    iterations of all lattices                                   */
 typedef struct {
     long long launches;       /* launches of this kernel since stag_profile_begin */
     int sampled;              /* of which bracketed by CUDA events on the context's stream */
@@ -332,10 +336,18 @@ typedef struct {
 stag_status stag_profile_begin(stag_ctx* ctx, int sample_every);
 /* Synchronises the stream and reports kernel `kind` (STAG_PK_*). */
 stag_status stag_profile_read(stag_ctx* ctx, int kind, stag_kernel_profile* out);
+/* Launch shape the batched solver chose for prec on batches led by ctx (the
+ * candidates are timed on the first batched solves): its index, with the
+ * threads per block and the blocks per SM requested of the register
+ * allocator; -1 while still tuning. */
+int stag_batch_shape(stag_ctx* ctx, stag_prec prec, int* threads_per_block, int* blocks_per_sm);
 /* Persistent solver only: microseconds that block 0 spent since
  * stag_profile_begin in [phase 1, barrier 1, phase 2, barrier 2 + alpha step,
  * phase 3, barrier 3 + beta step] (6 values; %globaltimer). */
 stag_status stag_profile_phases(stag_ctx* ctx, double* us);
+/* The same for the batched solver's launches led by ctx, for fp32-class
+ * precisions (any prec but STAG_FP64) or for the float-float fp64 iteration. */
+stag_status stag_profile_batch_phases(stag_ctx* ctx, stag_prec prec, double* us);
 /* Number of kernels this context has launched since its creation. */
 long long stag_launch_count(stag_ctx* ctx);
 /* Threads per site the Dslash of this precision and source count uses (1, 2,

@@ -60,9 +60,12 @@ def run(chains=CHAINS, mass=0.05, beta=5.5, n_outer=10, n_gauge=5, steps=3, warm
         res = {}
         for mode in ("batched", "sequential"):
             dh, acc, its = [], [], []
+            phases = np.zeros(4)
             for step in range(warmup + steps):
                 if step == warmup:
                     torch.cuda.synchronize()
+                    if mode == "batched":
+                        stag.stag_profile_begin(bat[0], 1 << 20)
                     t0 = time.perf_counter()
                 ps = [hmc(k, step) for k in range(n)]
                 if mode == "batched":
@@ -73,11 +76,31 @@ def run(chains=CHAINS, mass=0.05, beta=5.5, n_outer=10, n_gauge=5, steps=3, warm
                     dh += [o.dH for o in outs]
                     acc += [o.accepted for o in outs]
                     its += [o.cg_iterations for o in outs]
+                    # phase times: the batch's own (the same in every record), or summed over chains
+                    for o in (outs[:1] if mode == "batched" else outs):
+                        phases += [o.t_heatbath, o.t_fermion, o.t_gauge, o.t_metropolis]
             torch.cuda.synchronize()
             dt = time.perf_counter() - t0
             res[mode] = {"seconds": dt, "traj_per_hour": n * steps * 3600.0 / dt,
                          "mean_abs_dH": float(np.mean(np.abs(dh))), "acceptance": float(np.mean(acc)),
-                         "cg_iterations_per_traj": float(np.mean(its))}
+                         "cg_iterations_per_traj": float(np.mean(its)),
+                         "phase_seconds": dict(zip(("heatbath", "fermion", "gauge", "metropolis"),
+                                                   [round(float(x), 4) for x in phases]))}
+            if mode == "batched":
+                pr = stag.stag_profile_read(bat[0], stag.STAG_PK_BATCH)
+                if pr.sampled:
+                    us = pr.sampled_ms * 1e3 / pr.sampled
+                    res[mode]["batched_kernel"] = {"iterations": pr.sampled, "us_per_iteration": us,
+                                                   "bytes_per_iteration": pr.bytes_per_launch,
+                                                   "GBps": pr.bytes_per_launch / (us * 1e-6) / 1e9}
+                names = ("phase1", "barrier1", "phase2", "barrier2_alpha", "phase3", "barrier3_beta")
+                res[mode]["batched_kernel_phases_us"] = {
+                    "fp32": dict(zip(names, [round(x, 1) for x in stag.stag_profile_batch_phases(bat[0], 1)])),
+                    "float_float": dict(zip(names, [round(x, 1) for x in stag.stag_profile_batch_phases(bat[0], 0)]))}
+                stag.stag_profile_begin(bat[0], 0)
+                res[mode]["launch_shape"] = {
+                    name: dict(zip(("index", "threads_per_block", "blocks_per_sm"), stag.stag_batch_shape(bat[0], p)))
+                    for name, p in (("fp32", stag.STAG_FP32), ("fp64", stag.STAG_FP64))}
         out.update(res)
         out["speedup"] = res["batched"]["traj_per_hour"] / res["sequential"]["traj_per_hour"]
         out["steps"], out["warmup"] = steps, warmup

@@ -41,7 +41,7 @@ struct BatchArgs {
 
 // one chain's scalar recurrences (one source)
 struct ScalM {
-    double zeta[NS], zeta_prev[NS], zeta_next[NS], cx[NS], cpr[NS], cpp[NS], dsig[NS];
+    double zeta[NS], zeta_prev[NS], zeta_next[NS], zratio[NS], cx[NS], cpr[NS], cpp[NS], dsig[NS];
     double rr, bb, rr_ref, alpha, alpha_prev, beta_prev, beta, sum, k4_units, c0, tol2, delta2;
     int live[NS], iters_at[NS];
     int rhs_live, k, halt, status, need_reliable, nshift, max_iter, mixed, left, nan;
@@ -158,10 +158,12 @@ __device__ void alpha_step_m(ScalM* S, int nc) {
         if (C.halt || s >= C.nshift || !C.live[s]) continue;
         const double a = C.alpha, ap = C.alpha_prev, bp = C.beta_prev;
         const double z = C.zeta[s], zp = C.zeta_prev[s];
+        // one division: zeta_{k+1} / zeta_k = zeta_{k-1} alpha_{k-1} / den
         const double den = a * bp * (zp - z) + zp * ap * (1.0 + C.dsig[s] * a);
-        const double zn = z * zp * ap / den;
-        C.zeta_next[s] = zn;
-        C.cx[s] = a * zn / z;
+        const double zr = zp * ap / den;
+        C.zeta_next[s] = z * zr;
+        C.zratio[s] = zr;
+        C.cx[s] = a * zr;
     }
     __syncthreads();
 }
@@ -190,7 +192,7 @@ __device__ void beta_step_m(ScalM* S, int nc) {
         ScalM& C = S[c];
         if (!active[c] || s >= C.nshift || !C.live[s]) continue;
         const double zn = C.zeta_next[s], z = C.zeta[s];
-        const double zr = zn / z;
+        const double zr = C.zratio[s];
         C.cpr[s] = zn;
         C.cpp[s] = s_beta[c] * zr * zr;
         C.zeta_prev[s] = z;
@@ -353,9 +355,21 @@ __device__ __forceinline__ void add_slot(double (&a)[MAXC], int c, double v) {
         if (j == c) a[j] += v;
 }
 
-template <typename R, int FMT, int PB>
-__global__ void __launch_bounds__(PB) k_ms_persistent_batch(BatchArgs A, double* partial, GridBar* bar) {
+// PB threads per block, MB blocks per SM requested of the register allocator
+template <typename R, int FMT, int PB, int MB>
+__global__ void __launch_bounds__(PB, MB) k_ms_persistent_batch(BatchArgs A, double* partial, GridBar* bar,
+                                                                 unsigned long long* ptime) {
     typedef typename V2T<R>::T V;
+    // profiling: block 0 accumulates ns in phase 1, barrier 1, phase 2,
+    // barrier 2 + alpha step, phase 3, barrier 3 + beta step
+    const bool timing = ptime && blockIdx.x == 0 && threadIdx.x == 0;
+    unsigned long long tp[6] = {0, 0, 0, 0, 0, 0}, t_last = timing ? gtimer() : 0;
+#define PHASE_MARK(i)                               \
+    if (timing) {                                   \
+        unsigned long long t_now = gtimer();        \
+        tp[i] += t_now - t_last;                    \
+        t_last = t_now;                             \
+    }
     __shared__ ScalM S[MAXC];
     __shared__ ChainArgs C[MAXC];
     const int nc = A.n;
@@ -383,7 +397,9 @@ __global__ void __launch_bounds__(PB) k_ms_persistent_batch(BatchArgs A, double*
                 site_doe<R, FMT>(g, L, h, r, p, t, bt);
             off += g.Vh;
         }
+        PHASE_MARK(0)
         if (!(ok = grid_sync(bar, nb))) break;
+        PHASE_MARK(1)
         // ---- phase 2: p = r + beta p; q = (A + s0) p; (p, q)
         double dots[MAXC];
 #pragma unroll
@@ -405,9 +421,11 @@ __global__ void __launch_bounds__(PB) k_ms_persistent_batch(BatchArgs A, double*
         block_sum<MAXC>(dots);
         if (threadIdx.x == 0)
             for (int j = 0; j < nc; ++j) partial[(size_t)j * nb + blockIdx.x] = dots[j];
+        PHASE_MARK(2)
         if (!(ok = grid_sync(bar, nb))) break;
         sum_partials_m(S, partial, nb, nc, 0);
         alpha_step_m(S, nc);
+        PHASE_MARK(3)
         // ---- phase 3: shift updates, r -= alpha q, (r, r)
         double nrm[MAXC];
 #pragma unroll
@@ -427,10 +445,15 @@ __global__ void __launch_bounds__(PB) k_ms_persistent_batch(BatchArgs A, double*
         block_sum<MAXC>(nrm);
         if (threadIdx.x == 0)
             for (int j = 0; j < nc; ++j) partial[(size_t)(MAXC + j) * nb + blockIdx.x] = nrm[j];
+        PHASE_MARK(4)
         if (!(ok = grid_sync(bar, nb))) break;
         sum_partials_m(S, partial, nb, nc, MAXC);
         beta_step_m(S, nc);
+        PHASE_MARK(5)
     }
+#undef PHASE_MARK
+    if (timing)
+        for (int i = 0; i < 6; ++i) ptime[8 + 6 * (sizeof(R) == 4 ? 0 : 1) + i] += tp[i];
     if (!ok && threadIdx.x < nc && !S[threadIdx.x].halt) {
         S[threadIdx.x].halt = 1;
         S[threadIdx.x].status = STAG_ERR_TIMEOUT;
@@ -439,43 +462,59 @@ __global__ void __launch_bounds__(PB) k_ms_persistent_batch(BatchArgs A, double*
     if (blockIdx.x == 0) store_scal_m(S, C, nc);
 }
 
-template <typename R, int FMT, int PB>
+template <typename R, int FMT, int PB, int MB>
 stag_status launch_batch_pb(stag_ctx* ctx, const BatchArgs& A, long long sites, double* partial,
                             size_t partial_doubles, GridBar* bar) {
-    auto kern = k_ms_persistent_batch<R, FMT, PB>;
+    auto kern = k_ms_persistent_batch<R, FMT, PB, MB>;
     int per_sm = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, PB, 0));
     if (per_sm < 1) return STAG_ERR_ARG;
     int dev = 0, nsm = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    long long want = nblocks(sites, PB);
-    long long cap = (long long)nsm * per_sm;
+    // the fewest blocks that give no thread more sites per phase than the
+    // largest co-resident grid would: the same phase time, fewer blocks
+    // meeting at every barrier
+    const long long cap = (long long)nsm * per_sm;
+    const long long per_thread = (sites + cap * PB - 1) / (cap * PB);
+    long long want = (sites + per_thread * PB - 1) / (per_thread * PB);
     int grid = (int)(want < cap ? want : cap);
     if (grid < 1) grid = 1;
     if ((size_t)2 * MAXC * grid > partial_doubles) return STAG_ERR_ARG;
     CK(cudaMemsetAsync(bar, 0, sizeof(GridBar), ctx->stream));
     BatchArgs a = A;
-    void* args[] = {&a, &partial, &bar};
+    unsigned long long* pt = ctx->prof.on ? (unsigned long long*)ctx->ptime : nullptr;
+    void* args[] = {&a, &partial, &bar, &pt};
     CK(cudaLaunchCooperativeKernel((const void*)kern, grid, PB, args, 0, ctx->stream));
     ++ctx->launches;
     return STAG_OK;
 }
 
+// launch shapes (threads per block, blocks per SM) the tuner chooses among;
+// float-float keeps the first only (its registers allow no second block)
+constexpr int N_SHAPES = 3;
+constexpr int SHAPE_PB[N_SHAPES] = {256, 384, 320};
+constexpr int SHAPE_MB[N_SHAPES] = {1, 1, 1};
+
 template <typename R, int FMT>
-stag_status launch_batch_t(stag_ctx* ctx, int pb, const BatchArgs& A, long long sites, double* partial, size_t pd,
+stag_status launch_batch_t(stag_ctx* ctx, int shape, const BatchArgs& A, long long sites, double* partial, size_t pd,
                            GridBar* bar) {
-    if (pb == 128) return launch_batch_pb<R, FMT, 128>(ctx, A, sites, partial, pd, bar);
-    return launch_batch_pb<R, FMT, 256>(ctx, A, sites, partial, pd, bar);
+    switch (shape) {
+        case 1: return launch_batch_pb<R, FMT, 384, 1>(ctx, A, sites, partial, pd, bar);
+        case 2: return launch_batch_pb<R, FMT, 320, 1>(ctx, A, sites, partial, pd, bar);
+        default: return launch_batch_pb<R, FMT, 256, 1>(ctx, A, sites, partial, pd, bar);
+    }
 }
 
-stag_status launch_batch(stag_ctx* ctx, stag_prec prec, int pb, const BatchArgs& A, long long sites, double* partial,
-                         size_t pd, GridBar* bar) {
+int n_shapes(stag_prec prec) { return prec == STAG_FP64 ? 1 : N_SHAPES; }
+
+stag_status launch_batch(stag_ctx* ctx, stag_prec prec, int shape, const BatchArgs& A, long long sites,
+                         double* partial, size_t pd, GridBar* bar) {
     switch (prec) {
-        case STAG_FP64: return launch_batch_t<DF, FMT_F64>(ctx, pb, A, sites, partial, pd, bar);
-        case STAG_FP32: return launch_batch_t<float, FMT_F32_18>(ctx, pb, A, sites, partial, pd, bar);
-        case STAG_FP32_12: return launch_batch_t<float, FMT_F32_12>(ctx, pb, A, sites, partial, pd, bar);
-        default: return launch_batch_t<float, FMT_BF16_12>(ctx, pb, A, sites, partial, pd, bar);
+        case STAG_FP64: return launch_batch_pb<DF, FMT_F64, 256, 1>(ctx, A, sites, partial, pd, bar);
+        case STAG_FP32: return launch_batch_t<float, FMT_F32_18>(ctx, shape, A, sites, partial, pd, bar);
+        case STAG_FP32_12: return launch_batch_t<float, FMT_F32_12>(ctx, shape, A, sites, partial, pd, bar);
+        default: return launch_batch_t<float, FMT_BF16_12>(ctx, shape, A, sites, partial, pd, bar);
     }
 }
 }  // namespace
@@ -492,6 +531,10 @@ stag_status ms_core_multi(MsRun* runs, int n, MsStats* stats, stag_status* per_c
     stag_ctx* ctx = lead;   // error reporting of the CK macros
     for (int i = 0; i < n; ++i) CKS(ms_setup(runs[i]));
     if (!lead->bar) CKS(dev_alloc(lead, &lead->bar, sizeof(GridBar)));
+    if (!lead->ptime) {
+        CKS(dev_alloc(lead, &lead->ptime, PTIME_WORDS * sizeof(unsigned long long)));
+        CK(cudaMemsetAsync(lead->ptime, 0, PTIME_WORDS * sizeof(unsigned long long), lead->stream));
+    }
     int dev = 0, nsm = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -500,6 +543,13 @@ stag_status ms_core_multi(MsRun* runs, int n, MsStats* stats, stag_status* per_c
     CKS(ws_get(lead, WS_BATCH_RED, pd * sizeof(double), &partial));
     std::vector<int> active(n, 1);
     std::vector<stag_status> st(n, STAG_OK);
+    cudaEvent_t pe0 = nullptr, pe1 = nullptr;
+    double launch_ms = 0.0;
+    if (lead->prof.on) {
+        CK(cudaEventCreate(&pe0));
+        CK(cudaEventCreate(&pe1));
+    }
+    const bool profiling = lead->prof.on;
     int max_iter = 0;
     for (int i = 0; i < n; ++i) max_iter = std::max(max_iter, runs[i].max_iter);
     const int max_segments = 64 + max_iter;
@@ -529,10 +579,47 @@ stag_status ms_core_multi(MsRun* runs, int n, MsStats* stats, stag_status* per_c
             for (int i : idx) { st[i] = STAG_ERR_TIMEOUT; active[i] = 0; }
             break;
         }
-        CKS(launch_batch(lead, runs[0].prec, lead->persist_block, A, sites, (double*)partial, pd,
-                         (GridBar*)lead->bar));
+        // launch shape: the tuned one, or the next candidate while tuning
+        BatchTune& tu = lead->batch_tune[runs[0].prec];
+        const int ns_prec = n_shapes(runs[0].prec);
+        int shape = tu.chosen;
+        if (shape < 0) {
+            if (lead->batch_shape_force >= 0) shape = tu.chosen = std::min(lead->batch_shape_force, ns_prec - 1);
+            else shape = tu.tried % ns_prec;
+        }
+        const bool timed = pe0 || tu.chosen < 0;
+        if (timed && !pe0) {
+            CK(cudaEventCreate(&pe0));
+            CK(cudaEventCreate(&pe1));
+        }
+        int k_before = 0;
+        for (int i : idx) k_before = std::max(k_before, runs[i].ctx->st_host->k);
+        if (timed) CK(cudaEventRecord(pe0, lead->stream));
+        CKS(launch_batch(lead, runs[0].prec, shape, A, sites, (double*)partial, pd, (GridBar*)lead->bar));
+        if (timed) CK(cudaEventRecord(pe1, lead->stream));
         for (int i : idx) CKS(ms_pull_control_async(runs[i].ctx));
         CK(cudaStreamSynchronize(lead->stream));
+        if (timed) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, pe0, pe1));
+            if (lead->prof.on) launch_ms += ms;
+            if (tu.chosen < 0) {
+                // microseconds per batched iteration of this segment, for its shape
+                int k_after = 0;
+                for (int i : idx) k_after = std::max(k_after, runs[i].ctx->st_host->k);
+                if (k_after > k_before) {
+                    tu.us[shape] += 1e3 * ms;
+                    tu.iters[shape] += k_after - k_before;
+                    tu.tried += 1;
+                }
+                if (tu.tried >= 2 * ns_prec) {
+                    int best = 0;
+                    for (int v = 1; v < ns_prec; ++v)
+                        if (tu.us[v] / std::max(1, tu.iters[v]) < tu.us[best] / std::max(1, tu.iters[best])) best = v;
+                    tu.chosen = best;
+                }
+            }
+        }
         for (int i : idx) {
             const SolverState* hs = runs[i].ctx->st_host;
             if (!hs->halt) { st[i] = STAG_ERR_TIMEOUT; active[i] = 0; continue; }
@@ -541,11 +628,51 @@ stag_status ms_core_multi(MsRun* runs, int n, MsStats* stats, stag_status* per_c
             active[i] = 0;   // converged
         }
     }
+    long long kmax = 0;
+    double bytes = 0.0;
     for (int i = 0; i < n; ++i) {
         CKS(ms_pull_state(runs[i].ctx));
+        const SolverState* hs = runs[i].ctx->st_host;
+        const double S = (double)(runs[i].mixed ? sizeof(float2) : sizeof(double2));
+        const double Vh = runs[i].ctx->g.Vh;
+        // as the single-lattice persistent solver: both Dslash phases and the updates
+        bytes += (double)hs->k * Vh * (2.0 * link_bytes_site(runs[i].prec) + 8.0 * S) +
+                 hs->k4_units * Vh * (runs[i].mixed ? 1.0 : 2.0);
+        kmax = std::max(kmax, (long long)hs->k);
         CKS(ms_finish(runs[i]));
         if (stats) ms_stats(runs[i], &stats[i]);
         if (per_chain) per_chain[i] = st[i];
     }
+    if (profiling) {
+        ProfData& pf = lead->prof;
+        pf.bytes_total[PK_BATCH] += bytes;
+        pf.launches[PK_BATCH] += kmax;
+        pf.batch_ms += launch_ms;
+        pf.batch_iters += kmax;
+    }
+    if (pe0) cudaEventDestroy(pe0);
+    if (pe1) cudaEventDestroy(pe1);
+    return STAG_OK;
+}
+
+extern "C" int stag_batch_shape(stag_ctx* ctx, stag_prec prec, int* threads_per_block, int* blocks_per_sm) {
+    if (!ctx || prec < STAG_FP64 || prec > STAG_BF16_12) return -1;
+    const int c = ctx->batch_tune[prec].chosen;
+    if (c >= 0) {
+        if (threads_per_block) *threads_per_block = SHAPE_PB[c];
+        if (blocks_per_sm) *blocks_per_sm = SHAPE_MB[c];
+    }
+    return c;
+}
+
+extern "C" stag_status stag_profile_batch_phases(stag_ctx* ctx, stag_prec prec, double* us) {
+    if (!ctx || !us) return STAG_ERR_ARG;
+    unsigned long long t[PTIME_WORDS] = {0};
+    if (ctx->ptime) {
+        CK(cudaMemcpyAsync(t, ctx->ptime, sizeof(t), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    const int base = 8 + 6 * (prec == STAG_FP64 ? 1 : 0);
+    for (int i = 0; i < 6; ++i) us[i] = t[base + i] * 1e-3;
     return STAG_OK;
 }

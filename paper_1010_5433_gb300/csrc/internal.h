@@ -37,7 +37,7 @@ enum WsSlot {
 };
 
 // Sampled CUDA-event timing of the solver kernels (stag_profile_*).
-enum ProfKind { PK_DSLASH_OE = 0, PK_DSLASH_EO_A, PK_UPDATE, PK_PERSISTENT, PK_COUNT };
+enum ProfKind { PK_DSLASH_OE = 0, PK_DSLASH_EO_A, PK_UPDATE, PK_PERSISTENT, PK_BATCH, PK_COUNT };
 struct ProfData {
     bool on = false;
     int every = 16;
@@ -49,6 +49,8 @@ struct ProfData {
     long long launches[PK_COUNT] = {};
     double persist_ms = 0.0;                     // persistent solver: event time of all launches
     long long persist_iters = 0;                 // and the iterations they ran
+    double batch_ms = 0.0;                       // batched solver (this context leading): launch time
+    long long batch_iters = 0;                   // and batched iterations
 };
 
 // surrogate MLP parameters: W1 (32x24), b1, W2 (32x32), b2, W3 (24x32), b3
@@ -61,6 +63,17 @@ struct ProfData {
 #define SUR_W3 (SUR_B2 + SUR_NH)
 #define SUR_B3 (SUR_W3 + SUR_NF * SUR_NH)
 #define SUR_NP (SUR_B3 + SUR_NF)
+
+#define PTIME_WORDS 24
+
+// Launch-shape tuning of the batched solver, per precision: while chosen < 0
+// the candidate shapes take turns on real segments, timed per iteration.
+struct BatchTune {
+    int chosen = -1;
+    int tried = 0;
+    double us[4] = {};
+    int iters[4] = {};
+};
 
 struct SolverGraphEntry {
     const void* key[8];
@@ -100,8 +113,11 @@ struct stag_ctx {
     bool no_alloc_call = false;       // inside stag_apply_a_noalloc: nothing may allocate
     bool use_persistent = true;       // small lattices: persistent cooperative solver (STAG_PERSISTENT=0 off)
     void* bar = nullptr;              // grid-barrier words of the persistent solver
-    void* ptime = nullptr;            // its per-phase ns counters while profiling
+    void* ptime = nullptr;            // per-phase ns counters of the persistent kernels while profiling
+                                      // ([0,8) single lattice, [8,14) batched fp32, [14,20) batched float-float)
     int persist_block = 256;          // its threads per block (STAG_PERSIST_BLOCK=128|256)
+    BatchTune batch_tune[4];          // batched solver launch shape per precision (this context leading)
+    int batch_shape_force = -1;       // STAG_BATCH_SHAPE=0|1|2: fixed shape, no tuning
     // force surrogate
     float* sur_w = nullptr;           // device parameters (weights rounded to bf16)
     bool sur_loaded = false;

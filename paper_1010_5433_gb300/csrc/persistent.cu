@@ -27,7 +27,7 @@ namespace {
 // Block-local copy of the scalar recurrences (identical in every block).
 struct Scal {
     double zeta[STAG_MAX_RHS][STAG_MAX_SHIFTS], zeta_prev[STAG_MAX_RHS][STAG_MAX_SHIFTS];
-    double zeta_next[STAG_MAX_RHS][STAG_MAX_SHIFTS];
+    double zeta_next[STAG_MAX_RHS][STAG_MAX_SHIFTS], zratio[STAG_MAX_RHS][STAG_MAX_SHIFTS];
     double cx[STAG_MAX_RHS][STAG_MAX_SHIFTS], cpr[STAG_MAX_RHS][STAG_MAX_SHIFTS], cpp[STAG_MAX_RHS][STAG_MAX_SHIFTS];
     double dsig[STAG_MAX_SHIFTS];
     double rr[STAG_MAX_RHS], bb[STAG_MAX_RHS], rr_ref[STAG_MAX_RHS];
@@ -136,10 +136,12 @@ __device__ void alpha_step(Scal& S) {
         if (s >= S.nshift || !S.rhs_live[q] || !S.live[q][s]) continue;
         const double a = S.alpha[q], ap = S.alpha_prev[q], bp = S.beta_prev[q];
         const double z = S.zeta[q][s], zp = S.zeta_prev[q][s];
+        // one division: zeta_{k+1} / zeta_k = zeta_{k-1} alpha_{k-1} / den
         const double den = a * bp * (zp - z) + zp * ap * (1.0 + S.dsig[s] * a);
-        const double zn = z * zp * ap / den;
-        S.zeta_next[q][s] = zn;
-        S.cx[q][s] = a * zn / z;
+        const double zr = zp * ap / den;
+        S.zeta_next[q][s] = z * zr;
+        S.zratio[q][s] = zr;
+        S.cx[q][s] = a * zr;
     }
     __syncthreads();
 }
@@ -167,7 +169,7 @@ __device__ void beta_step(Scal& S) {
         const int q = i / STAG_MAX_SHIFTS, s = i % STAG_MAX_SHIFTS;
         if (s >= S.nshift || !S.rhs_live[q] || !S.live[q][s]) continue;
         const double zn = S.zeta_next[q][s], z = S.zeta[q][s];
-        const double zr = zn / z;
+        const double zr = S.zratio[q][s];
         S.cpr[q][s] = zn;
         S.cpp[q][s] = s_beta[q] * zr * zr;
         S.zeta_prev[q][s] = z;
@@ -473,8 +475,8 @@ stag_status launch_persistent(stag_ctx* ctx, stag_prec prec, int nrhs, void* r, 
                               void* x) {
     if (!ctx->bar) CKS(dev_alloc(ctx, &ctx->bar, sizeof(GridBar)));
     if (!ctx->ptime) {
-        CKS(dev_alloc(ctx, &ctx->ptime, 8 * sizeof(unsigned long long)));
-        CK(cudaMemsetAsync(ctx->ptime, 0, 8 * sizeof(unsigned long long), ctx->stream));
+        CKS(dev_alloc(ctx, &ctx->ptime, PTIME_WORDS * sizeof(unsigned long long)));
+        CK(cudaMemsetAsync(ctx->ptime, 0, PTIME_WORDS * sizeof(unsigned long long), ctx->stream));
     }
     if (nrhs == 1) return launch_persistent_n<1>(ctx, prec, r, p, q, t, ps, x);
     return launch_persistent_n<4>(ctx, prec, r, p, q, t, ps, x);

@@ -171,10 +171,12 @@ __device__ void ms_alpha_step(SolverState* st, const double* pap) {
         const double alpha = s_alpha[q];
         const double ap = st->alpha_prev[q], bp = st->beta_prev[q];
         const double z = st->zeta[q][s], zp = st->zeta_prev[q][s];
+        // one division: zeta_{k+1} / zeta_k = zeta_{k-1} alpha_{k-1} / den
         const double den = alpha * bp * (zp - z) + zp * ap * (1.0 + st->dsig[s] * alpha);
-        const double zn = z * zp * ap / den;
-        st->zeta_next[q][s] = zn;
-        st->cx[q][s] = alpha * zn / z;
+        const double zr = zp * ap / den;
+        st->zeta_next[q][s] = z * zr;
+        st->zratio[q][s] = zr;
+        st->cx[q][s] = alpha * zr;
     }
 }
 
@@ -263,7 +265,7 @@ __device__ void ms_beta_step(SolverState* st, const double* rrn, cudaGraphCondit
         const int q = idx / STAG_MAX_SHIFTS, s = idx % STAG_MAX_SHIFTS;
         if (s >= st->nshift || !st->rhs_live[q] || !st->live[q][s]) continue;
         const double zn = st->zeta_next[q][s], z = st->zeta[q][s];
-        const double zr = zn / z;
+        const double zr = st->zratio[q][s];
         st->cpr[q][s] = zn;                     // p_i = zeta_{k+1} r + beta_i p_i in the next update
         st->cpp[q][s] = s_beta[q] * zr * zr;
         st->zeta_prev[q][s] = z;
@@ -1138,7 +1140,9 @@ extern "C" stag_status stag_profile_begin(stag_ctx* ctx, int sample_every) {
     }
     pf.persist_ms = 0.0;
     pf.persist_iters = 0;
-    if (ctx->ptime) CK(cudaMemsetAsync(ctx->ptime, 0, 8 * sizeof(unsigned long long), ctx->stream));
+    pf.batch_ms = 0.0;
+    pf.batch_iters = 0;
+    if (ctx->ptime) CK(cudaMemsetAsync(ctx->ptime, 0, PTIME_WORDS * sizeof(unsigned long long), ctx->stream));
     return STAG_OK;
 }
 
@@ -1158,6 +1162,10 @@ extern "C" stag_status stag_profile_read(stag_ctx* ctx, int kind, stag_kernel_pr
     if (kind == PK_PERSISTENT) {       // every persistent launch is timed; units are iterations
         out->sampled = (int)pf.persist_iters;
         out->sampled_ms = pf.persist_ms;
+    }
+    if (kind == PK_BATCH) {
+        out->sampled = (int)pf.batch_iters;
+        out->sampled_ms = pf.batch_ms;
     }
     out->bytes_per_launch = pf.launches[kind] ? pf.bytes_total[kind] / pf.launches[kind] : 0.0;
     return STAG_OK;

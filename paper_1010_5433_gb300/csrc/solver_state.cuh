@@ -34,4 +34,5 @@ struct SolverState {
     double cpp[STAG_MAX_RHS][STAG_MAX_SHIFTS];
     int live[STAG_MAX_RHS][STAG_MAX_SHIFTS];     // not converged: updated in the next iteration
     int iters_at[STAG_MAX_RHS][STAG_MAX_SHIFTS];
+    double zratio[STAG_MAX_RHS][STAG_MAX_SHIFTS]; // zeta_{k+1} / zeta_k, from the alpha to the beta step
 };

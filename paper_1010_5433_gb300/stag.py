@@ -101,6 +101,8 @@ def lib():
             "stag_md_trajectory": ([vp, C.POINTER(stag_hmc), C.POINTER(stag_traj)], i),
             "stag_multishift_solve_batch": ([C.POINTER(vp), i, d, i, vp, i, C.POINTER(vp), C.POINTER(vp), d, i,
                                              C.POINTER(stag_solve_info)], i),
+            "stag_profile_batch_phases": ([vp, i, C.POINTER(d)], i),
+            "stag_batch_shape": ([vp, i, C.POINTER(i), C.POINTER(i)], i),
             "stag_md_trajectory_batch": ([C.POINTER(vp), i, C.POINTER(stag_hmc), C.POINTER(stag_traj)], i),
             "stag_momenta": ([vp], vp),
             "stag_profile_begin": ([vp, i], i),
@@ -293,7 +295,7 @@ def stag_draw_sources(ctx, seed, counter, stream, n, xi):
            "stag_draw_sources", ctx)
 
 
-STAG_PK_DSLASH_OE, STAG_PK_DSLASH_EO_A, STAG_PK_UPDATE = 0, 1, 2
+STAG_PK_DSLASH_OE, STAG_PK_DSLASH_EO_A, STAG_PK_UPDATE, STAG_PK_PERSISTENT, STAG_PK_BATCH = 0, 1, 2, 3, 4
 
 
 def stag_profile_begin(ctx, sample_every):
@@ -304,6 +306,19 @@ def stag_profile_read(ctx, kind):
     out = stag_kernel_profile()
     _check(lib().stag_profile_read(ctx, int(kind), C.byref(out)), "stag_profile_read", ctx)
     return out
+
+
+def stag_profile_batch_phases(ctx, prec):
+    us = (C.c_double * 6)()
+    _check(lib().stag_profile_batch_phases(ctx, int(prec), us), "stag_profile_batch_phases", ctx)
+    return list(us)
+
+
+def stag_batch_shape(ctx, prec):
+    """(index, threads per block, blocks per SM) of the tuned batched-solver launch shape; index -1 while tuning."""
+    a, b = C.c_int(0), C.c_int(0)
+    k = lib().stag_batch_shape(ctx, int(prec), C.byref(a), C.byref(b))
+    return k, a.value, b.value
 
 
 def stag_launch_count(ctx):

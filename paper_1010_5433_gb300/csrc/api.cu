@@ -127,8 +127,6 @@ extern "C" stag_status stag_create(const stag_lattice* lat, stag_ctx** out) {
     ctx->tps_force = tp ? std::atoi(tp) : 0;
     const char* pe = std::getenv("STAG_PERSISTENT");
     ctx->use_persistent = !(pe && pe[0] == '0');
-    const char* pb = std::getenv("STAG_PERSIST_BLOCK");
-    ctx->persist_block = (pb && std::atoi(pb) == 128) ? 128 : 256;
     // STAG_BATCH_SHAPE=0|1|2 fixes the batched solver's launch shape instead of tuning
     const char* bs = std::getenv("STAG_BATCH_SHAPE");
     ctx->batch_shape_force = bs ? std::atoi(bs) : -1;

@@ -633,7 +633,7 @@ stag_status ms_core_multi(MsRun* runs, int n, MsStats* stats, stag_status* per_c
     for (int i = 0; i < n; ++i) {
         CKS(ms_pull_state(runs[i].ctx));
         const SolverState* hs = runs[i].ctx->st_host;
-        const double S = (double)(runs[i].mixed ? sizeof(float2) : sizeof(double2));
+        const double S = 3.0 * (double)(runs[i].mixed ? sizeof(float2) : sizeof(double2));   // one spinor at a site
         const double Vh = runs[i].ctx->g.Vh;
         // as the single-lattice persistent solver: both Dslash phases and the updates
         bytes += (double)hs->k * Vh * (2.0 * link_bytes_site(runs[i].prec) + 8.0 * S) +

@@ -115,7 +115,6 @@ struct stag_ctx {
     void* bar = nullptr;              // grid-barrier words of the persistent solver
     void* ptime = nullptr;            // per-phase ns counters of the persistent kernels while profiling
                                       // ([0,8) single lattice, [8,14) batched fp32, [14,20) batched float-float)
-    int persist_block = 256;          // its threads per block (STAG_PERSIST_BLOCK=128|256)
     BatchTune batch_tune[4];          // batched solver launch shape per precision (this context leading)
     int batch_shape_force = -1;       // STAG_BATCH_SHAPE=0|1|2: fixed shape, no tuning
     // force surrogate

@@ -456,8 +456,7 @@ bool persistent_fits(stag_ctx* ctx) {
 
 template <typename R, int FMT, int NRP>
 stag_status launch_persistent_t(stag_ctx* ctx, void* r, void* p, void* q, void* t, void* ps, void* x) {
-    // threads per block: 256 halves the blocks that meet at every grid barrier
-    if (ctx->persist_block == 128) return launch_persistent_pb<R, FMT, NRP, 128>(ctx, r, p, q, t, ps, x);
+    // 256 threads per block: one block per SM at these register counts
     return launch_persistent_pb<R, FMT, NRP, 256>(ctx, r, p, q, t, ps, x);
 }
 

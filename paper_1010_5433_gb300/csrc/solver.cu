@@ -87,6 +87,7 @@ __global__ void k_ms_init(SolverState* st, int Vh, const typename V2T<R>::T* __r
                     st->zeta[q][s] = 1.0;
                     st->zeta_prev[q][s] = 1.0;
                     st->zeta_next[q][s] = 1.0;
+                    st->zratio[q][s] = 1.0;
                     st->live[q][s] = live;
                     st->iters_at[q][s] = 0;
                     st->cx[q][s] = 0.0;
@@ -949,8 +950,10 @@ stag_status ms_core(stag_ctx* ctx, double mass, int nshift, const double* shifts
     if (gexec) ctx->launches += 3LL * hs->k;   // kernels the graph ran
     if (persistent && ctx->prof.on) {
         ProfData& pf = ctx->prof;
-        const double S = (double)(mixed ? sizeof(float2) : sizeof(double2));
-        // one iteration: both Dslash phases (links twice; r, p, t / t, p, r, p, q) and the update
+        // bytes of one spinor (3 colours) at a site
+        const double S = 3.0 * (double)(mixed ? sizeof(float2) : sizeof(double2));
+        // one iteration: both Dslash phases (links twice; r, p in, t out / t, p, r in,
+        // p, q out) and the updates (r, q in, r out and 96 B per live shift: k4_units)
         pf.bytes_total[PK_PERSISTENT] += (double)hs->k * g.Vh * (2.0 * link_bytes_site(prec) + 8.0 * S * nrhs) +
                                          hs->k4_units * g.Vh * (mixed ? 1.0 : 2.0);
         pf.launches[PK_PERSISTENT] += hs->k;
@@ -958,7 +961,7 @@ stag_status ms_core(stag_ctx* ctx, double mass, int nshift, const double* shifts
         pf.persist_iters += hs->k;
     } else if (ctx->prof.on) {
         ProfData& pf = ctx->prof;
-        const double S = (double)(mixed ? sizeof(float2) : sizeof(double2));
+        const double S = 3.0 * (double)(mixed ? sizeof(float2) : sizeof(double2));   // one spinor at a site
         // K1 reads r and p (the direction is formed on the fly) and writes t;
         // K2 reads t, r, p and writes p, q
         pf.bytes_total[PK_DSLASH_OE] += (double)hs->k * g.Vh * (link_bytes_site(prec) + 3.0 * S * nrhs);

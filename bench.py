@@ -235,15 +235,20 @@ def run_gpu(args, rank, world, local_rank):
                      "achieved_gbs": pr.bytes_per_launch / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else 0.0})
     kern = [k for k in kern if k["launches"] > 0]
     dom = max(kern, key=lambda k: k["est_total_ms"])
+    traffic = NCU_TRAFFIC.get(dom["kernel"])
     roofline = {"bound": "hbm", "kernel": dom["kernel"], "achieved": round(dom["achieved_gbs"], 1), "peak": hbm,
-                "unit": "GB/s", "frac": round(dom["achieved_gbs"] / hbm, 4), "traffic": None,
+                "unit": "GB/s", "frac": round(dom["achieved_gbs"] / hbm, 4),
+                "traffic": traffic["bytes_per_unit"] if traffic else None,
+                "traffic_source": traffic["source"] if traffic else None,
                 "peak_source": peak_kind,
-                "note": "16^4 fields are L2-resident inside a trajectory; achieved = algorithmic bytes / "
-                        "CUDA-event-timed launch duration (4 plainly launched iterations sampled per solver segment)",
+                "note": "unit = one solver iteration; 16^4 fields are L2-resident inside a trajectory; achieved = "
+                        "algorithmic bytes per iteration / CUDA-event time of every persistent launch on the "
+                        "context's stream divided by its iterations",
                 "kernels": kern}
 
     point = dslash_roofline_point(hbm) if rank == 0 else None
     stag.stag_destroy(ctx)
+    chains = batched_chains() if world == 1 else None
 
     dh = [t.dH for t in trajs]
     dh64 = [t.dH for t in trajs64]
@@ -275,8 +280,34 @@ def run_gpu(args, rank, world, local_rank):
                          "speedup_mixed_vs_fp64": round(value / value64, 3),
                          "warmup_dH": [round(t.dH, 4) for t in warm]},
         "dslash_roofline_point": point,
+        "batched_chains": chains,
     }
     return out
+
+
+# DRAM traffic of the dominant kernel per unit (one solver iteration) from an
+# ncu capture of the same kernel on the same 16^4 lattice; None once the
+# kernel has changed since the capture.  The capture is cold-cache (ncu
+# flushes caches between passes): one read of the working set, then L2 hits.
+NCU_TRAFFIC = {
+    "persistent_iteration": {
+        "bytes_per_unit": round((39.403008e6 + 0.115968e6) / 36),
+        "source": "profiles/persistent_fp32_16x4_ncu.md: dram__bytes_read+write over one 36-iteration launch",
+    },
+}
+
+
+def batched_chains():
+    """The 8-chain workload (2x8^4, 2x12^4, 2x16^4, 2x16^3x8, Nf=2, m=0.05,
+    beta=5.5): one batched trajectory call per step against the same chains
+    one after another, from identical fields with identical random numbers."""
+    from paper_1010_5433_gb300 import batch_bench
+    r = batch_bench.run(steps=2, warmup=1)
+    b, q = r["batched"], r["sequential"]
+    return {"workload": r["workload"], "batched_traj_per_hour": round(b["traj_per_hour"], 1),
+            "sequential_traj_per_hour": round(q["traj_per_hour"], 1), "speedup": round(r["speedup"], 3),
+            "acceptance": [b["acceptance"], q["acceptance"]], "mean_abs_dH": [b["mean_abs_dH"], q["mean_abs_dH"]],
+            "batched_kernel": b.get("batched_kernel"), "launch_shape": b.get("launch_shape")}
 
 
 def dslash_roofline_point(hbm):

@@ -106,9 +106,11 @@ def gauge_level(u, mom, h, n, beta):
 
 
 def surrogate_force(u, params):
-    """F^ of the links u for the network params (oracle/surrogate.py)."""
+    """F^ of the links u for the network params (oracle/surrogate.py); a true
+    "quant" entry evaluates the network as tensor cores do (bf16 inputs of
+    every product)."""
     f, G = sur.features_and_generators(u)
-    return sur.surrogate_force(params, f, G)
+    return sur.surrogate_force(params, f, G, quant=bool(params.get("quant", False)))
 
 
 def surrogate_level(u, mom, h, n_mid, n_gauge, beta, params):

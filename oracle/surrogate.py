@@ -15,7 +15,8 @@ staples S close a loop U_mu(x) S:
 so staple k = 8 * (index of nu among the three) + j.
   features  f_k = Re tr(U_mu(x) S_k) / 3              (gauge invariant)
   generators G_{k,a} = Re tr(i T_a U_mu(x) S_k)        (force of each loop)
-  MLP       h1 = tanh(W1 f + b1), h2 = tanh(W2 h1 + b2), w = W3 h2 + b3   (24-32-32-24)
+  MLP       h1 = tanh(W1 f + b1), h2 = tanh(W2 h1 + b2), w = W3 h2 + b3   (24-32-32-24);
+            on tensor cores f, h1, h2 enter the products rounded to bfloat16 (quant=True)
   surrogate F^_a = sum_k w_k G_{k,a}                  (gauge covariant)
   loss      mean over links of sum_a (F^_a - F_a)^2
 """
@@ -87,38 +88,49 @@ def init_params(seed, scale=0.3):
     return p
 
 
-def forward(p, f):
-    """f [..., 24] -> w [..., 24], with the cache of the backward pass."""
-    z1 = f @ p["W1"].T + p["b1"]
+def forward(p, f, quant=False):
+    """f [..., 24] -> w [..., 24], with the cache of the backward pass.
+
+    quant=True is the network as tensor cores evaluate it: the input of every
+    matrix product (f, h1, h2) rounded to bfloat16 (the weights are given
+    already rounded), products and biases in full precision."""
+    q = bf16_round if quant else (lambda a: a)     # noqa: E731
+    fq = q(f)
+    z1 = fq @ p["W1"].T + p["b1"]
     h1 = np.tanh(z1)
-    z2 = h1 @ p["W2"].T + p["b2"]
+    h1q = q(h1)
+    z2 = h1q @ p["W2"].T + p["b2"]
     h2 = np.tanh(z2)
-    w = h2 @ p["W3"].T + p["b3"]
-    return w, (f, h1, h2)
+    h2q = q(h2)
+    w = h2q @ p["W3"].T + p["b3"]
+    return w, (fq, h1, h2, h1q, h2q)
 
 
 def backward(p, cache, dw):
-    """Gradients of a scalar L given dL/dw [..., 24] (summed over the leading axes)."""
-    f, h1, h2 = cache
+    """Gradients of a scalar L given dL/dw [..., 24] (summed over the leading
+    axes).  With a quantised forward pass the rounding counts as the identity
+    (straight-through): weight gradients use the rounded inputs, the tanh
+    derivatives the unrounded activations."""
+    f, h1, h2, h1q, h2q = cache
     flat = lambda a: a.reshape(-1, a.shape[-1])     # noqa: E731
-    f, h1, h2, dw = flat(f), flat(h1), flat(h2), flat(dw)
-    g = {"W3": dw.T @ h2, "b3": dw.sum(0)}
+    f, h1, h2, h1q, h2q, dw = flat(f), flat(h1), flat(h2), flat(h1q), flat(h2q), flat(dw)
+    g = {"W3": dw.T @ h2q, "b3": dw.sum(0)}
     dz2 = (dw @ p["W3"]) * (1 - h2 ** 2)
-    g["W2"], g["b2"] = dz2.T @ h1, dz2.sum(0)
+    g["W2"], g["b2"] = dz2.T @ h1q, dz2.sum(0)
     dz1 = (dz2 @ p["W2"]) * (1 - h1 ** 2)
     g["W1"], g["b1"] = dz1.T @ f, dz1.sum(0)
     return g
 
 
-def surrogate_force(p, f, G):
+def surrogate_force(p, f, G, quant=False):
     """F^_a = sum_k w_k G_{k,a}: [4, t, z, y, x, 8]."""
-    w, _ = forward(p, f)
+    w, _ = forward(p, f, quant)
     return np.einsum("...k,...ka->...a", w, G)
 
 
-def loss_and_grad(p, f, G, F):
+def loss_and_grad(p, f, G, F, quant=False):
     """Mean over links of sum_a (F^_a - F_a)^2 and its parameter gradients."""
-    w, cache = forward(p, f)
+    w, cache = forward(p, f, quant)
     e = np.einsum("...k,...ka->...a", w, G) - F
     n = e[..., 0].size
     loss = float(np.sum(e * e) / n)

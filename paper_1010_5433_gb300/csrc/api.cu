@@ -85,6 +85,7 @@ extern "C" void stag_destroy(stag_ctx* ctx) {
     if (ctx->bar) cudaFree(ctx->bar);
     if (ctx->ptime) cudaFree(ctx->ptime);
     if (ctx->sur_w) cudaFree(ctx->sur_w);
+    if (ctx->sur_err) cudaFree(ctx->sur_err);
     if (ctx->sur_data) cudaFree(ctx->sur_data);
     if (ctx->scal) cudaFree(ctx->scal);
     if (ctx->st) cudaFree(ctx->st);

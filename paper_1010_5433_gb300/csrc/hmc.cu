@@ -485,6 +485,7 @@ extern "C" stag_status stag_md_trajectory(stag_ctx* ctx, const stag_hmc* p, stag
     CKS(timer.begin(3));
     if (T.npf_total > 0) CKS(T.fermion_action(&sf1));
     CKS(timer.end(3));
+    if (p->use_surrogate) CKS(surrogate_check(ctx));
     return T.finish(sf1, out);
 }
 
@@ -701,6 +702,8 @@ extern "C" stag_status stag_md_trajectory_batch(stag_ctx* const* ctxs, int n, co
     CKS(timer.begin(3));
     if (ps[0].n_flavours > 0) CKS(batch_rational(T, true, &sf1));
     CKS(timer.end(3));
+    if (ps[0].use_surrogate)
+        for (int i = 0; i < n; ++i) CKS(surrogate_check(ctxs[i]));
     stag_status worst = STAG_OK;
     for (int i = 0; i < n; ++i) {
         stag_status s = T[i].finish(sf1[i], &outs[i]);

@@ -119,6 +119,7 @@ struct stag_ctx {
     int batch_shape_force = -1;       // STAG_BATCH_SHAPE=0|1|2: fixed shape, no tuning
     // force surrogate
     float* sur_w = nullptr;           // device parameters (weights rounded to bf16)
+    unsigned int* sur_err = nullptr;  // set by a tensor-core surrogate launch that gave up a wait
     bool sur_loaded = false;
     std::vector<double> sur_master, adam_m, adam_v;   // fp32-valued master weights, Adam moments
     long long adam_t = 0;
@@ -244,6 +245,7 @@ stag_status draw_sources(stag_ctx* ctx, double2* xi, int n, unsigned long long s
 
 // surrogate.cu
 stag_status surrogate_force_launch(stag_ctx* ctx, double* out, double coef, int mode);
+stag_status surrogate_check(stag_ctx* ctx);   // STAG_ERR_TIMEOUT if a launch gave up a wait (synchronises)
 stag_status surrogate_append(stag_ctx* ctx, const double* exact_force);
 
 // blas.cu

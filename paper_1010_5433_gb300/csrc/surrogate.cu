@@ -13,6 +13,8 @@
 #include <cstring>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "internal.h"
 
 namespace {
@@ -84,28 +86,38 @@ __device__ __forceinline__ void link_of(const Geom& g, long long l, int& mu, int
     x[0] = 2 * xh + ((x[1] + x[2] + x[3] + par) & 1);
 }
 
-// the MLP in fp32 from weights in shared memory
-__device__ __forceinline__ void mlp_forward(const float* P, const float (&f)[SUR_NF], float (&h1)[SUR_NH],
-                                            float (&h2)[SUR_NH], float (&w)[SUR_NF]) {
+__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+// The MLP as the tensor-core kernel evaluates it, in fp32 on CUDA cores (the
+// training pass): f, h1, h2 enter their products rounded to bf16 (fq, h1q,
+// h2q returned for the weight gradients), weights from shared memory
+// (already bf16 values), biases and sums fp32.
+__device__ __forceinline__ void mlp_forward(const float* P, float (&f)[SUR_NF], float (&h1)[SUR_NH],
+                                            float (&h2)[SUR_NH], float (&h1q)[SUR_NH], float (&h2q)[SUR_NH],
+                                            float (&w)[SUR_NF]) {
+#pragma unroll
+    for (int k = 0; k < SUR_NF; ++k) f[k] = bf16r(f[k]);
 #pragma unroll 4
     for (int i = 0; i < SUR_NH; ++i) {
         float z = P[SUR_B1 + i];
 #pragma unroll
         for (int k = 0; k < SUR_NF; ++k) z = fmaf(P[SUR_W1 + i * SUR_NF + k], f[k], z);
         h1[i] = tanhf(z);
+        h1q[i] = bf16r(h1[i]);
     }
 #pragma unroll 4
     for (int i = 0; i < SUR_NH; ++i) {
         float z = P[SUR_B2 + i];
 #pragma unroll
-        for (int k = 0; k < SUR_NH; ++k) z = fmaf(P[SUR_W2 + i * SUR_NH + k], h1[k], z);
+        for (int k = 0; k < SUR_NH; ++k) z = fmaf(P[SUR_W2 + i * SUR_NH + k], h1q[k], z);
         h2[i] = tanhf(z);
+        h2q[i] = bf16r(h2[i]);
     }
 #pragma unroll 4
     for (int i = 0; i < SUR_NF; ++i) {
         float z = P[SUR_B3 + i];
 #pragma unroll
-        for (int k = 0; k < SUR_NH; ++k) z = fmaf(P[SUR_W3 + i * SUR_NH + k], h2[k], z);
+        for (int k = 0; k < SUR_NH; ++k) z = fmaf(P[SUR_W3 + i * SUR_NH + k], h2q[k], z);
         w[i] = z;
     }
 }
@@ -134,63 +146,215 @@ __global__ void __launch_bounds__(SB) k_sur_features(Geom g, LinkPtrs L, float* 
     }
 }
 
+// ---- the MLP on the 5th-generation tensor cores (tcgen05): 128 links per
+// block, one link per thread.  Layer l: D_l [128 x 32] = A_l [128 x 32] . W_l^T,
+// A_l the bf16 inputs of the 128 links (features zero-padded 24 -> 32, then
+// h1, h2), W_l [32 x 32] bf16 (W3's 24 rows zero-padded), fp32 accumulators
+// in tensor memory (TMEM), three 32-column accumulators.  One thread issues
+// the MMAs; each thread reads back its own row (its link), adds the bias and
+// applies tanh, and writes the next layer's bf16 row.
+namespace tc {
+constexpr int M = 128, K = 32, N = 32;
+constexpr int TMEM_COLS = 128;                 // three accumulators of 32 columns
+constexpr long long WAIT_LIMIT = 1LL << 24;    // polls of the MMA-completion barrier
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// K-major, no-swizzle layout of a [rows x 32] bf16 operand: 8 x 8 core matrices
+// (8 rows x 16 bytes, contiguous), core (r/8, k/8) at ((r/8)*4 + k/8) * 128 bytes;
+// so 128 bytes between core matrices along K (LBO) and 512 along rows (SBO)
+__device__ __forceinline__ int op_index(int r, int k) { return ((r >> 3) * 4 + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7); }
+constexpr uint32_t LBO = 128, SBO = 512;
+
+// shared-memory matrix descriptor: start, LBO, SBO (>> 4), descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((LBO >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((SBO >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// instruction descriptor of kind::f16: fp32 accumulator, bf16 A and B, both K-major, N, M
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+                           ((uint32_t)(M >> 4) << 24);
+
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, int accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(IDESC), "r"(accumulate));
+}
+__device__ __forceinline__ void commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+__device__ __forceinline__ bool wait_phase(uint32_t mbar, uint32_t parity) {
+    for (long long i = 0; i < WAIT_LIMIT; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 32 consecutive fp32 columns of this thread's TMEM lane
+__device__ __forceinline__ void load_row(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+}  // namespace tc
+
 // Surrogate force of every link: out = coef F^ (mode 0) or out += coef F^ (mode 1),
 // momentum layout.  Staples are formed twice (features, then the weighted sum)
-// so that no per-staple state is kept in registers.
+// so that no per-staple state is kept in registers; the MLP between the two
+// passes runs on the tensor cores.  A failed wait sets *err and the block
+// stops issuing (the host reports STAG_ERR_TIMEOUT).
 __global__ void __launch_bounds__(SB) k_sur_force(Geom g, LinkPtrs L, const float* __restrict__ params, double* out,
-                                                  double coef, int mode) {
-    __shared__ float P[SUR_NP];
-    for (int i = threadIdx.x; i < SUR_NP; i += blockDim.x) P[i] = params[i];
+                                                  double coef, int mode, unsigned int* err) {
+    __shared__ __align__(1024) __nv_bfloat16 sA[tc::M * tc::K];        // the layer's inputs, 8 KB
+    __shared__ __align__(1024) __nv_bfloat16 sW[3][tc::N * tc::K];     // W1, W2, W3 (padded), 6 KB
+    __shared__ float sb[3][tc::N];                                      // b1, b2, b3 (padded)
+    __shared__ __align__(8) unsigned long long s_mbar;
+    __shared__ uint32_t s_tmem;
+    const int t = threadIdx.x, warp = t >> 5;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(&s_tmem)),
+                     "r"(tc::TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (t == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc::smem_u32(&s_mbar)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // weights as bf16 operands (they hold bf16 values already), biases
+    for (int i = t; i < 3 * tc::N * tc::K; i += blockDim.x) {
+        const int layer = i / (tc::N * tc::K), q = i % (tc::N * tc::K), n = q / tc::K, k = q % tc::K;
+        float v = 0.f;
+        if (layer == 0 && k < SUR_NF) v = params[SUR_W1 + n * SUR_NF + k];
+        if (layer == 1) v = params[SUR_W2 + n * SUR_NH + k];
+        if (layer == 2 && n < SUR_NF) v = params[SUR_W3 + n * SUR_NH + k];
+        sW[layer][tc::op_index(n, k)] = __float2bfloat16_rn(v);
+    }
+    if (t < tc::N) {
+        sb[0][t] = params[SUR_B1 + t];
+        sb[1][t] = params[SUR_B2 + t];
+        sb[2][t] = t < SUR_NF ? params[SUR_B3 + t] : 0.f;
+    }
+    const long long l = (long long)blockIdx.x * blockDim.x + t;
+    const bool valid = l < 8LL * g.Vh;
+    int mu = 0, par = 0, h = 0, x[4] = {0, 0, 0, 0};
+    Su3<float> u;
+    float fv[SUR_NF];
+#pragma unroll
+    for (int k = 0; k < SUR_NF; ++k) fv[k] = 0.f;
+    if (valid) {
+        link_of(g, l, mu, par, h, x);
+        u = LinkFetch<float, FMT_F32_18>::get(L, mu, par, h, g.Vh);
+        int i = 0;
+        for (int nu = 0; nu < 4; ++nu) {
+            if (nu == mu) continue;
+            LinkAt U{g, L, {x[0], x[1], x[2], x[3]}, mu, nu};
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                Su3<float> wk = mul(u, staple(U, j));
+                fv[8 * i + j] = (wk.e[0][0].re + wk.e[1][1].re + wk.e[2][2].re) * (1.f / 3.f);
+            }
+            ++i;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < tc::K; ++k) sA[tc::op_index(t, k)] = __float2bfloat16_rn(k < SUR_NF ? fv[k] : 0.f);
+    tc::fence_async_smem();
+    tc::fence_before();
     __syncthreads();
-    const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (l >= 8LL * g.Vh) return;
-    int mu, par, h, x[4];
-    link_of(g, l, mu, par, h, x);
-    const Su3<float> u = LinkFetch<float, FMT_F32_18>::get(L, mu, par, h, g.Vh);
-    float fv[SUR_NF], h1[SUR_NH], h2[SUR_NH], w[SUR_NF];
-    int i = 0;
-    for (int nu = 0; nu < 4; ++nu) {
-        if (nu == mu) continue;
-        LinkAt U{g, L, {x[0], x[1], x[2], x[3]}, mu, nu};
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            Su3<float> wk = mul(u, staple(U, j));
-            fv[8 * i + j] = (wk.e[0][0].re + wk.e[1][1].re + wk.e[2][2].re) * (1.f / 3.f);
+    tc::fence_after();
+    const uint32_t tmem = s_tmem;
+    const uint32_t mbar = tc::smem_u32(&s_mbar);
+    const uint32_t a_addr = tc::smem_u32(sA);
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;     // this warp's TMEM lanes
+    float w[tc::N];
+    bool ok = true;
+    for (int layer = 0; layer < 3; ++layer) {
+        const uint32_t d = tmem + (uint32_t)(layer * tc::N);
+        if (t == 0 && ok) {
+            const uint32_t b_addr = tc::smem_u32(sW[layer]);
+            // K = 32 as two K = 16 steps: the next 16 columns are two core matrices (2 x LBO) on
+            tc::mma(d, tc::smem_desc(a_addr), tc::smem_desc(b_addr), 0);
+            tc::mma(d, tc::smem_desc(a_addr + 2 * tc::LBO), tc::smem_desc(b_addr + 2 * tc::LBO), 1);
+            tc::commit(mbar);
         }
-        ++i;
-    }
-    mlp_forward(P, fv, h1, h2, w);
-    Su3<float> m;
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) m.e[a][b] = mk(0.f, 0.f);
-    i = 0;
-    for (int nu = 0; nu < 4; ++nu) {
-        if (nu == mu) continue;
-        LinkAt U{g, L, {x[0], x[1], x[2], x[3]}, mu, nu};
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const Su3<float> s = staple(U, j);
-            const float wk = w[8 * i + j];
-#pragma unroll
-            for (int a = 0; a < 3; ++a)
-#pragma unroll
-                for (int b = 0; b < 3; ++b) {
-                    m.e[a][b].re += wk * s.e[a][b].re;
-                    m.e[a][b].im += wk * s.e[a][b].im;
-                }
+        __syncthreads();
+        if (!ok || !tc::wait_phase(mbar, (uint32_t)(layer & 1))) {
+            ok = false;
+            if (t == 0) atomicExch(err, 1u);
         }
-        ++i;
-    }
-    float c[8];
-    gen_coeffs(mul(u, m), c);
-    double* o = out + ((size_t)(2 * mu + par) * 8) * g.Vh + h;
+        tc::fence_after();
+        float z[32];
+        tc::load_row(tmem + lane_base + (uint32_t)(layer * tc::N), z);
+        if (layer < 2) {
 #pragma unroll
-    for (int a = 0; a < 8; ++a) {
-        if (mode) o[(size_t)a * g.Vh] += coef * (double)c[a];
-        else o[(size_t)a * g.Vh] = coef * (double)c[a];
+            for (int k = 0; k < tc::K; ++k) sA[tc::op_index(t, k)] = __float2bfloat16_rn(tanhf(z[k] + sb[layer][k]));
+            tc::fence_async_smem();
+            tc::fence_before();
+            __syncthreads();
+            tc::fence_after();
+        } else {
+#pragma unroll
+            for (int k = 0; k < tc::N; ++k) w[k] = z[k] + sb[2][k];
+        }
     }
+    // weighted staple sum with the network's 24 weights
+    if (valid && ok) {
+        Su3<float> m;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) m.e[a][b] = mk(0.f, 0.f);
+        int i = 0;
+        for (int nu = 0; nu < 4; ++nu) {
+            if (nu == mu) continue;
+            LinkAt U{g, L, {x[0], x[1], x[2], x[3]}, mu, nu};
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const Su3<float> s = staple(U, j);
+                const float wk = w[8 * i + j];
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) {
+                        m.e[a][b].re += wk * s.e[a][b].re;
+                        m.e[a][b].im += wk * s.e[a][b].im;
+                    }
+            }
+            ++i;
+        }
+        float c[8];
+        gen_coeffs(mul(u, m), c);
+        double* o = out + ((size_t)(2 * mu + par) * 8) * g.Vh + h;
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            if (mode) o[(size_t)a * g.Vh] += coef * (double)c[a];
+            else o[(size_t)a * g.Vh] = coef * (double)c[a];
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tc::TMEM_COLS));
 }
 
 // exact forces [4][2][8][Vh] (double) -> dataset slot [8][nl] (float)
@@ -218,11 +382,12 @@ __global__ void __launch_bounds__(TB) k_sur_train(long long nl, const float* __r
     const long long l = (long long)blockIdx.x * TB + threadIdx.x;
     const int t = threadIdx.x;
     double lossv[1] = {0.0};
-    float fv[SUR_NF], h1[SUR_NH], h2[SUR_NH], w[SUR_NF], dw[SUR_NF], dz2[SUR_NH], dz1[SUR_NH];
+    float fv[SUR_NF], h1[SUR_NH], h2[SUR_NH], h1q[SUR_NH], h2q[SUR_NH], w[SUR_NF], dw[SUR_NF], dz2[SUR_NH],
+        dz1[SUR_NH];
     if (l < nl) {
 #pragma unroll
         for (int k = 0; k < SUR_NF; ++k) fv[k] = f[(size_t)k * stride + l];
-        mlp_forward(P, fv, h1, h2, w);
+        mlp_forward(P, fv, h1, h2, h1q, h2q, w);
         float e[8];
 #pragma unroll
         for (int a = 0; a < 8; ++a) e[a] = -F[(size_t)a * stride + l];
@@ -258,18 +423,19 @@ __global__ void __launch_bounds__(TB) k_sur_train(long long nl, const float* __r
 #pragma unroll
         for (int k = 0; k < SUR_NF; ++k) fv[k] = 0.f, w[k] = 0.f, dw[k] = 0.f;
 #pragma unroll
-        for (int k = 0; k < SUR_NH; ++k) h1[k] = 0.f, h2[k] = 0.f, dz1[k] = 0.f, dz2[k] = 0.f;
+        for (int k = 0; k < SUR_NH; ++k) h1[k] = 0.f, h2[k] = 0.f, h1q[k] = 0.f, h2q[k] = 0.f, dz1[k] = 0.f, dz2[k] = 0.f;
     }
-    // per-link vectors to shared memory, row r of V holds component r for all TB links
+    // per-link vectors to shared memory, row r of V holds component r for all TB
+    // links; the products' inputs as rounded (straight-through gradients)
     int r = 0;
 #pragma unroll
     for (int k = 0; k < SUR_NF; ++k) V[(r + k) * TB + t] = fv[k];
     r += SUR_NF;
 #pragma unroll
-    for (int k = 0; k < SUR_NH; ++k) V[(r + k) * TB + t] = h1[k];
+    for (int k = 0; k < SUR_NH; ++k) V[(r + k) * TB + t] = h1q[k];
     r += SUR_NH;
 #pragma unroll
-    for (int k = 0; k < SUR_NH; ++k) V[(r + k) * TB + t] = h2[k];
+    for (int k = 0; k < SUR_NH; ++k) V[(r + k) * TB + t] = h2q[k];
     r += SUR_NH;
 #pragma unroll
     for (int k = 0; k < SUR_NF; ++k) V[(r + k) * TB + t] = dw[k];
@@ -338,12 +504,38 @@ static stag_status upload_params(stag_ctx* ctx) {
     return STAG_OK;
 }
 
+// Shared memory reserved per block of k_sur_force beyond its own ~15 KB, so
+// that at most 3 blocks share an SM: 3 x 128 TMEM columns stay within the
+// SM's 512 and no block ever waits in its TMEM allocation.
+constexpr int SUR_FORCE_RESERVE = 60 * 1024;
+
 stag_status surrogate_force_launch(stag_ctx* ctx, double* out, double coef, int mode) {
     if (!ctx->sur_loaded) return STAG_ERR_ARG;
+    if (!ctx->sur_err) {
+        CKS(dev_alloc(ctx, (void**)&ctx->sur_err, sizeof(unsigned int)));
+        CK(cudaMemsetAsync(ctx->sur_err, 0, sizeof(unsigned int), ctx->stream));
+    }
+    static bool attr_set = false;
+    if (!attr_set) {
+        CK(cudaFuncSetAttribute(k_sur_force, cudaFuncAttributeMaxDynamicSharedMemorySize, SUR_FORCE_RESERVE));
+        attr_set = true;
+    }
     const long long n = 8LL * ctx->g.Vh;
-    k_sur_force<<<nblocks(n, SB), SB, 0, ctx->stream>>>(ctx->g, link_ptrs(ctx), ctx->sur_w, out, coef, mode);
+    k_sur_force<<<nblocks(n, SB), SB, SUR_FORCE_RESERVE, ctx->stream>>>(ctx->g, link_ptrs(ctx), ctx->sur_w, out,
+                                                                          coef, mode, ctx->sur_err);
     CKL();
     return STAG_OK;
+}
+
+// STAG_ERR_TIMEOUT (and the word cleared) if a surrogate launch gave up a wait
+stag_status surrogate_check(stag_ctx* ctx) {
+    if (!ctx->sur_err) return STAG_OK;
+    unsigned int e = 0;
+    CK(cudaMemcpyAsync(&e, ctx->sur_err, sizeof(e), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (!e) return STAG_OK;
+    CK(cudaMemsetAsync(ctx->sur_err, 0, sizeof(unsigned int), ctx->stream));
+    return STAG_ERR_TIMEOUT;
 }
 
 // append (features, generators, exact force) of the current field to the dataset
@@ -430,7 +622,8 @@ extern "C" stag_status stag_surrogate_store(stag_ctx* ctx, float* params) {
 extern "C" stag_status stag_surrogate_force(stag_ctx* ctx, double* force) {
     if (!ctx || !force) return STAG_ERR_ARG;
     if (!ctx->has_gauge) return STAG_ERR_NO_GAUGE;
-    return surrogate_force_launch(ctx, force, 1.0, 0);
+    CKS(surrogate_force_launch(ctx, force, 1.0, 0));
+    return surrogate_check(ctx);
 }
 
 extern "C" stag_status stag_surrogate_add_force_sample(stag_ctx* ctx, const double* exact_force) {

@@ -1,7 +1,14 @@
 """GPU parity of the learned force surrogate against the FP64 oracle
-(oracle/surrogate.py) with the same bf16-rounded weights: the surrogate
-force, its Wilson-force special case, loss and parameter gradients; training
-lowers the loss; a surrogate-assisted trajectory stays reversible."""
+(oracle/surrogate.py) with the same bf16-rounded weights, the oracle's network
+evaluated as the tensor cores do (bf16 inputs of every product): the
+surrogate force (tcgen05 MLP), its Wilson-force special case, loss and
+parameter gradients; training lowers the loss; a surrogate-assisted
+trajectory stays reversible and matches the oracle's three-level integrator.
+
+The device forms the features in fp32, the oracle in fp64: a feature or
+activation within ~1e-7 of a bf16 rounding boundary can round to the
+neighbouring bf16 value on one side only, so the tolerances below allow a few
+such single-ulp (2^-8 relative) differences."""
 import numpy as np
 import pytest
 
@@ -40,7 +47,8 @@ def test_surrogate_force_matches_oracle(torch):
     u = syn.near_identity_gauge(DIMS, 501, width=0.6)
     p = sur.init_params(5, scale=1.0)
     f, G = sur.features_and_generators(u)
-    want = sur.surrogate_force(as_device_precision(p), f, G)
+    want = sur.surrogate_force(as_device_precision(p), f, G, quant=True)
+    exact = sur.surrogate_force(as_device_precision(p), f, G)
     ctx = stag.stag_create(DIMS, True)
     try:
         stag.stag_load_gauge(ctx, L.gauge_host(u))
@@ -48,7 +56,12 @@ def test_surrogate_force_matches_oracle(torch):
         out = torch.empty((4, 2, 8, int(np.prod(DIMS)) // 2), dtype=torch.float64, device="cuda")
         stag.stag_surrogate_force(ctx, out)
         got = L.mom_from_abi(out.cpu().numpy(), DIMS)
-        assert _rel(got, want) < 1e-5
+        err = np.abs(got - want).reshape(-1, 8).max(1) / np.abs(want).max()
+        print(f"tensor-core surrogate force: rel L2 {_rel(got, want):.2e} vs bf16-activation oracle, "
+              f"{_rel(got, exact):.2e} vs fp32 activations; links off by > 1e-5: {(err > 1e-5).sum()} of {err.size}")
+        assert _rel(got, want) < 2e-4
+        assert (err > 1e-5).mean() < 0.01          # all but a few links agree to fp32 accumulation
+        assert _rel(got, exact) < 2e-2             # and bf16 activations stay close to fp32 ones
     finally:
         stag.stag_destroy(ctx)
 
@@ -82,7 +95,7 @@ def test_loss_and_gradient_match_oracle(torch):
     pd = as_device_precision(p)
     # the device reads the target force in fp32
     t32 = target.astype(np.float32).astype(np.float64)
-    want_loss, want_grad = sur.loss_and_grad(pd, f, G, t32)
+    want_loss, want_grad = sur.loss_and_grad(pd, f, G, t32, quant=True)
     ctx = stag.stag_create(DIMS, True)
     try:
         stag.stag_load_gauge(ctx, L.gauge_host(u))
@@ -91,9 +104,10 @@ def test_loss_and_gradient_match_oracle(torch):
         stag.stag_surrogate_add_force_sample(ctx, d_t)
         grad = np.zeros(stag.STAG_SUR_PARAMS)
         loss = stag.stag_surrogate_loss_grad(ctx, grad)
-        assert abs(loss - want_loss) < 1e-5 * want_loss
         ref = flat({k: want_grad[k] for k in ("W1", "b1", "W2", "b2", "W3", "b3")}).astype(np.float64)
-        assert _rel(grad, ref) < 1e-4
+        print(f"loss rel {abs(loss - want_loss) / want_loss:.2e}, gradient rel {_rel(grad, ref):.2e}")
+        assert abs(loss - want_loss) < 1e-4 * want_loss
+        assert _rel(grad, ref) < 1e-3
     finally:
         stag.stag_destroy(ctx)
 
@@ -147,11 +161,17 @@ def test_training_lowers_loss_and_surrogate_md_is_reversible(torch):
         stag.stag_destroy(ctx)
 
 
-@pytest.mark.parametrize("prec,tol_dh,tol_u", [(0, 1e-4, 1e-6), (1, 2e-3, 1e-5)])
+@pytest.mark.parametrize("prec,tol_dh,tol_u", [(0, 1e-2, 2e-4), (1, 1e-2, 2e-4)])
 def test_three_level_trajectory_matches_oracle(torch, prec, tol_dh, tol_u):
     """The surrogate-assisted trajectory (outer F_f - F^, n_mid steps of F^,
     gauge inside) against the oracle's three-level integrator with the same
-    bf16-rounded network; F^ is evaluated in fp32 on the device."""
+    bf16-rounded network evaluated as the tensor cores do.  Tolerance: each of
+    the ~40 evaluations of F^ in the trajectory can round an activation of
+    some link to the neighbouring bf16 value on one side only (fp32 vs fp64
+    features, see the module docstring), moving that link's F^ by ~2^-8 |W| of
+    its size, ~1e-3; a handful of such kicks moves the links by ~1e-4 and dH
+    (~4 here, an unfitted network with forces as large as the fermion force)
+    by ~1e-2.  Without quantisation the same comparison agrees to 1e-6 in dU."""
     import json
     import os
     from oracle import integrator
@@ -169,8 +189,8 @@ def test_three_level_trajectory_matches_oracle(torch, prec, tol_dh, tol_u):
     fl = integrator.Flavour(mass=0.1, hb=rat["hb"], md=rat["md"], met=rat["met"])
     prm = integrator.HMCParams(dims=dims, beta=5.6, tau=0.5, n_outer=3, n_gauge=1, flavours=[fl],
                                tol_md=1e-13, tol_met=1e-13)
-    want = integrator.trajectory(integrator.Context(prm), u0, mom0, [[xi]], surrogate=as_device_precision(net),
-                                 n_mid=2)
+    want = integrator.trajectory(integrator.Context(prm), u0, mom0, [[xi]],
+                                 surrogate=dict(as_device_precision(net), quant=True), n_mid=2)
     ctx = stag.stag_create(dims, True)
     try:
         stag.stag_load_gauge(ctx, L.gauge_host(u0))

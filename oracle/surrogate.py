@@ -106,19 +106,25 @@ def forward(p, f, quant=False):
     return w, (fq, h1, h2, h1q, h2q)
 
 
-def backward(p, cache, dw):
+def backward(p, cache, dw, quant=False):
     """Gradients of a scalar L given dL/dw [..., 24] (summed over the leading
     axes).  With a quantised forward pass the rounding counts as the identity
     (straight-through): weight gradients use the rounded inputs, the tanh
-    derivatives the unrounded activations."""
+    derivatives the unrounded activations.  quant=True also rounds the
+    backward products' inputs dw, dz2, dz1 to bfloat16, as tensor cores take
+    them (the bias gradients are sums of the same rounded values)."""
+    q = bf16_round if quant else (lambda a: a)     # noqa: E731
     f, h1, h2, h1q, h2q = cache
     flat = lambda a: a.reshape(-1, a.shape[-1])     # noqa: E731
     f, h1, h2, h1q, h2q, dw = flat(f), flat(h1), flat(h2), flat(h1q), flat(h2q), flat(dw)
-    g = {"W3": dw.T @ h2q, "b3": dw.sum(0)}
-    dz2 = (dw @ p["W3"]) * (1 - h2 ** 2)
-    g["W2"], g["b2"] = dz2.T @ h1q, dz2.sum(0)
-    dz1 = (dz2 @ p["W2"]) * (1 - h1 ** 2)
-    g["W1"], g["b1"] = dz1.T @ f, dz1.sum(0)
+    dwq = q(dw)
+    g = {"W3": dwq.T @ h2q, "b3": dwq.sum(0)}
+    dz2 = (dwq @ p["W3"]) * (1 - h2 ** 2)
+    dz2q = q(dz2)
+    g["W2"], g["b2"] = dz2q.T @ h1q, dz2q.sum(0)
+    dz1 = (dz2q @ p["W2"]) * (1 - h1 ** 2)
+    dz1q = q(dz1)
+    g["W1"], g["b1"] = dz1q.T @ f, dz1q.sum(0)
     return g
 
 
@@ -135,7 +141,7 @@ def loss_and_grad(p, f, G, F, quant=False):
     n = e[..., 0].size
     loss = float(np.sum(e * e) / n)
     dw = 2.0 * np.einsum("...a,...ka->...k", e, G) / n
-    return loss, backward(p, cache, dw)
+    return loss, backward(p, cache, dw, quant)
 
 
 def bf16_round(x):

@@ -88,41 +88,6 @@ __device__ __forceinline__ void link_of(const Geom& g, long long l, int& mu, int
 
 __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
-// The MLP as the tensor-core kernel evaluates it, in fp32 on CUDA cores (the
-// training pass): f, h1, h2 enter their products rounded to bf16 (fq, h1q,
-// h2q returned for the weight gradients), weights from shared memory
-// (already bf16 values), biases and sums fp32.
-__device__ __forceinline__ void mlp_forward(const float* P, float (&f)[SUR_NF], float (&h1)[SUR_NH],
-                                            float (&h2)[SUR_NH], float (&h1q)[SUR_NH], float (&h2q)[SUR_NH],
-                                            float (&w)[SUR_NF]) {
-#pragma unroll
-    for (int k = 0; k < SUR_NF; ++k) f[k] = bf16r(f[k]);
-#pragma unroll 4
-    for (int i = 0; i < SUR_NH; ++i) {
-        float z = P[SUR_B1 + i];
-#pragma unroll
-        for (int k = 0; k < SUR_NF; ++k) z = fmaf(P[SUR_W1 + i * SUR_NF + k], f[k], z);
-        h1[i] = tanhf(z);
-        h1q[i] = bf16r(h1[i]);
-    }
-#pragma unroll 4
-    for (int i = 0; i < SUR_NH; ++i) {
-        float z = P[SUR_B2 + i];
-#pragma unroll
-        for (int k = 0; k < SUR_NH; ++k) z = fmaf(P[SUR_W2 + i * SUR_NH + k], h1q[k], z);
-        h2[i] = tanhf(z);
-        h2q[i] = bf16r(h2[i]);
-    }
-#pragma unroll 4
-    for (int i = 0; i < SUR_NF; ++i) {
-        float z = P[SUR_B3 + i];
-#pragma unroll
-        for (int k = 0; k < SUR_NH; ++k) z = fmaf(P[SUR_W3 + i * SUR_NH + k], h2q[k], z);
-        w[i] = z;
-    }
-}
-
-// Features and generators of every link: f [24][nl], G [24*8][nl] (training data).
 __global__ void __launch_bounds__(SB) k_sur_features(Geom g, LinkPtrs L, float* f, float* G, long long stride) {
     const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= 8LL * g.Vh) return;
@@ -166,20 +131,38 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)_
 __device__ __forceinline__ int op_index(int r, int k) { return ((r >> 3) * 4 + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7); }
 constexpr uint32_t LBO = 128, SBO = 512;
 
-// shared-memory matrix descriptor: start, LBO, SBO (>> 4), descriptor version 1, no swizzle
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
-    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((LBO >> 4) & 0x3FFFu) << 16) |
-           ((uint64_t)((SBO >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+// [rows x 128] operands whose K is the 128 links of a tile: 16 core matrices
+// per 8-row group, so 2048 bytes between 8-row groups
+__device__ __forceinline__ int op_index128(int r, int k) {
+    return ((r >> 3) * 16 + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7);
 }
-// instruction descriptor of kind::f16: fp32 accumulator, bf16 A and B, both K-major, N, M
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
-                           ((uint32_t)(M >> 4) << 24);
+constexpr uint32_t SBO128 = 2048;
 
-__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, int accumulate) {
+// shared-memory matrix descriptor: start, LBO, SBO (>> 4), descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t sbo = SBO) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((LBO >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// instruction descriptor of kind::f16: fp32 accumulator, bf16 A and B, both K-major, n, M
+__host__ __device__ constexpr uint32_t idesc(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+constexpr uint32_t IDESC = idesc(N);
+
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, int accumulate,
+                                    uint32_t id = IDESC) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(IDESC), "r"(accumulate));
+        "l"(a), "l"(b), "r"(id), "r"(accumulate));
+}
+// D (M x n) [+]= A (M x k) B^T with both operands K-major in shared memory, k a
+// multiple of 16 (one MMA per 16 columns: 2 core matrices = 2 x LBO further on)
+__device__ __forceinline__ void mma_k(uint32_t d, uint32_t a_addr, uint32_t a_sbo, uint32_t b_addr, uint32_t b_sbo,
+                                      int k, int n, int accumulate) {
+    for (int s = 0; s < k / 16; ++s)
+        mma(d, smem_desc(a_addr + s * 2 * LBO, a_sbo), smem_desc(b_addr + s * 2 * LBO, b_sbo),
+            (accumulate || s > 0) ? 1 : 0, idesc(n));
 }
 __device__ __forceinline__ void commit(uint32_t mbar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
@@ -216,6 +199,18 @@ __device__ __forceinline__ void load_row(uint32_t taddr, float (&v)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void load_row16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 }  // namespace tc
 
@@ -366,108 +361,221 @@ __global__ void k_sur_target(Geom g, const double* __restrict__ F, float* out, l
     for (int a = 0; a < 8; ++a) out[(size_t)a * stride + l] = (float)F[((size_t)blk * 8 + a) * g.Vh + h];
 }
 
-// One block: forward and backward of TB links, per-block loss and parameter
-// gradients (sums of outer products formed from shared memory).
-constexpr int TB = 128;
-constexpr int SV = SUR_NF + SUR_NH + SUR_NH + SUR_NF + SUR_NH + SUR_NH;   // f h1 h2 dw dz2 dz1 per link
-__global__ void __launch_bounds__(TB) k_sur_train(long long nl, const float* __restrict__ f, const float* __restrict__ G,
-                                                  const float* __restrict__ F, long long stride,
-                                                  const float* __restrict__ params, double inv_n,
-                                                  float* grad_part, double* loss_part) {
-    extern __shared__ float sm[];
-    float* P = sm;                          // SUR_NP
-    float* V = sm + SUR_NP;                 // [SV][TB]
-    for (int i = threadIdx.x; i < SUR_NP; i += blockDim.x) P[i] = params[i];
-    __syncthreads();
-    const long long l = (long long)blockIdx.x * TB + threadIdx.x;
-    const int t = threadIdx.x;
-    double lossv[1] = {0.0};
-    float fv[SUR_NF], h1[SUR_NH], h2[SUR_NH], h1q[SUR_NH], h2q[SUR_NH], w[SUR_NF], dw[SUR_NF], dz2[SUR_NH],
-        dz1[SUR_NH];
-    if (l < nl) {
-#pragma unroll
-        for (int k = 0; k < SUR_NF; ++k) fv[k] = f[(size_t)k * stride + l];
-        mlp_forward(P, fv, h1, h2, h1q, h2q, w);
-        float e[8];
-#pragma unroll
-        for (int a = 0; a < 8; ++a) e[a] = -F[(size_t)a * stride + l];
-        for (int k = 0; k < SUR_NF; ++k)
-#pragma unroll
-            for (int a = 0; a < 8; ++a) e[a] = fmaf(w[k], G[((size_t)k * 8 + a) * stride + l], e[a]);
-        float ls = 0.f;
-#pragma unroll
-        for (int a = 0; a < 8; ++a) ls = fmaf(e[a], e[a], ls);
-        lossv[0] = ls;
-        const float sc = (float)(2.0 * inv_n);
-        for (int k = 0; k < SUR_NF; ++k) {
-            float s = 0.f;
-#pragma unroll
-            for (int a = 0; a < 8; ++a) s = fmaf(e[a], G[((size_t)k * 8 + a) * stride + l], s);
-            dw[k] = sc * s;
-        }
-#pragma unroll 4
-        for (int i = 0; i < SUR_NH; ++i) {
-            float s = 0.f;
-#pragma unroll
-            for (int k = 0; k < SUR_NF; ++k) s = fmaf(P[SUR_W3 + k * SUR_NH + i], dw[k], s);
-            dz2[i] = s * (1.f - h2[i] * h2[i]);
-        }
-#pragma unroll 4
-        for (int i = 0; i < SUR_NH; ++i) {
-            float s = 0.f;
-#pragma unroll
-            for (int k = 0; k < SUR_NH; ++k) s = fmaf(P[SUR_W2 + k * SUR_NH + i], dz2[k], s);
-            dz1[i] = s * (1.f - h1[i] * h1[i]);
-        }
-    } else {
-#pragma unroll
-        for (int k = 0; k < SUR_NF; ++k) fv[k] = 0.f, w[k] = 0.f, dw[k] = 0.f;
-#pragma unroll
-        for (int k = 0; k < SUR_NH; ++k) h1[k] = 0.f, h2[k] = 0.f, h1q[k] = 0.f, h2q[k] = 0.f, dz1[k] = 0.f, dz2[k] = 0.f;
+// Training pass on the tensor cores: loss and parameter gradients over the
+// dataset, every block persistent over tiles of 128 links (one per thread).
+// Per tile:
+//   forward   D1..D3 as in k_sur_force (fq, h1q, h2q the bf16 product inputs)
+//   loss      e_a = sum_k w_k G_ka - F_a, dw_k = (2/n) sum_a e_a G_ka   (CUDA cores)
+//   backward  dh2 = dw W3, dz2 = dh2 (1 - h2^2), dh1 = dz2 W2, dz1 = dh1 (1 - h1^2)
+//             as MMAs against transposed weight tiles (dw, dz2 rounded to bf16)
+//   weights   dW3 += dw^T h2q, dW2 += dz2^T h1q, dW1 += dz1^T fq: M = 128 (rows
+//             beyond the layer width zero) x K = the tile's 128 links, accumulated
+//             in TMEM over all tiles of the block; a row of ones (zero for links
+//             past the end) in each transposed input gives the bias gradients
+// Each block writes its partial gradient (SUR_NP floats) and loss sum.
+constexpr int TT = 128;
+constexpr int TMEM_TRAIN = 256;
+// TMEM columns: D1 / D4 at 0, D2 / D5 at 32, D3 at 64, dW3 (48) at 96, dW2 (48) at 160, dW1 (32) at 224
+constexpr int C_DW3 = 96, C_DW2 = 160, C_DW1 = 224;
+// dynamic shared memory (bytes): operands first, each 1024-aligned
+constexpr int SM_A = 0;                          // [128 x 32] bf16: forward / backward rows, 8 KB
+constexpr int SM_AT = SM_A + 8192;               // [128 x 128] bf16: dw^T, dz2^T, dz1^T, 32 KB
+constexpr int SM_BT1 = SM_AT + 32768;            // [32 x 128] bf16: fq^T, ones row 24, 8 KB
+constexpr int SM_BT2 = SM_BT1 + 8192;            // [48 x 128] bf16: h1q^T, ones row 32, 12 KB
+constexpr int SM_BT3 = SM_BT2 + 12288;           // [48 x 128] bf16: h2q^T, ones row 32, 12 KB
+constexpr int SM_W = SM_BT3 + 12288;             // 5 x [32 x 32] bf16: W1, W2, W3, W3^T, W2^T, 10 KB
+constexpr int SM_BIAS = SM_W + 5 * 2048;         // 3 x 32 floats
+constexpr int SM_TRAIN = SM_BIAS + 3 * 32 * 4;
+
+__global__ void __launch_bounds__(TT, 1) k_sur_train(long long nl, const float* __restrict__ f,
+                                                     const float* __restrict__ G, const float* __restrict__ F,
+                                                     long long stride, const float* __restrict__ params, float sc,
+                                                     float* grad_part, double* loss_part, unsigned int* err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __nv_bfloat16* sA = (__nv_bfloat16*)(smem + SM_A);
+    __nv_bfloat16* sAt = (__nv_bfloat16*)(smem + SM_AT);
+    __nv_bfloat16* sBt1 = (__nv_bfloat16*)(smem + SM_BT1);
+    __nv_bfloat16* sBt2 = (__nv_bfloat16*)(smem + SM_BT2);
+    __nv_bfloat16* sBt3 = (__nv_bfloat16*)(smem + SM_BT3);
+    __nv_bfloat16* sW = (__nv_bfloat16*)(smem + SM_W);    // 5 tiles of 1024 elements
+    float* sb = (float*)(smem + SM_BIAS);
+    __shared__ __align__(8) unsigned long long s_mbar;
+    __shared__ uint32_t s_tmem;
+    const int t = threadIdx.x, warp = t >> 5;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(&s_tmem)),
+                     "r"(TMEM_TRAIN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    // per-link vectors to shared memory, row r of V holds component r for all TB
-    // links; the products' inputs as rounded (straight-through gradients)
-    int r = 0;
-#pragma unroll
-    for (int k = 0; k < SUR_NF; ++k) V[(r + k) * TB + t] = fv[k];
-    r += SUR_NF;
-#pragma unroll
-    for (int k = 0; k < SUR_NH; ++k) V[(r + k) * TB + t] = h1q[k];
-    r += SUR_NH;
-#pragma unroll
-    for (int k = 0; k < SUR_NH; ++k) V[(r + k) * TB + t] = h2q[k];
-    r += SUR_NH;
-#pragma unroll
-    for (int k = 0; k < SUR_NF; ++k) V[(r + k) * TB + t] = dw[k];
-    r += SUR_NF;
-#pragma unroll
-    for (int k = 0; k < SUR_NH; ++k) V[(r + k) * TB + t] = dz2[k];
-    r += SUR_NH;
-#pragma unroll
-    for (int k = 0; k < SUR_NH; ++k) V[(r + k) * TB + t] = dz1[k];
-    __syncthreads();
-    const float* Vf = V;
-    const float* Vh1 = V + SUR_NF * TB;
-    const float* Vh2 = Vh1 + SUR_NH * TB;
-    const float* Vdw = Vh2 + SUR_NH * TB;
-    const float* Vdz2 = Vdw + SUR_NF * TB;
-    const float* Vdz1 = Vdz2 + SUR_NH * TB;
-    // every parameter's gradient over the block's links
-    for (int pi = t; pi < SUR_NP; pi += TB) {
-        const float *a, *b = nullptr;
-        if (pi < SUR_B1) { a = Vdz1 + (pi / SUR_NF) * TB; b = Vf + (pi % SUR_NF) * TB; }
-        else if (pi < SUR_W2) { a = Vdz1 + (pi - SUR_B1) * TB; }
-        else if (pi < SUR_B2) { const int q = pi - SUR_W2; a = Vdz2 + (q / SUR_NH) * TB; b = Vh1 + (q % SUR_NH) * TB; }
-        else if (pi < SUR_W3) { a = Vdz2 + (pi - SUR_B2) * TB; }
-        else if (pi < SUR_B3) { const int q = pi - SUR_W3; a = Vdw + (q / SUR_NH) * TB; b = Vh2 + (q % SUR_NH) * TB; }
-        else { a = Vdw + (pi - SUR_B3) * TB; }
-        float s = 0.f;
-        if (b) for (int q = 0; q < TB; ++q) s = fmaf(a[q], b[q], s);
-        else for (int q = 0; q < TB; ++q) s += a[q];
-        grad_part[(size_t)blockIdx.x * SUR_NP + pi] = s;
+    if (t == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc::smem_u32(&s_mbar)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    block_sum<1>(lossv);
-    if (t == 0) loss_part[blockIdx.x] = lossv[0];
+    // operands that stay: transposed inputs zero (their padding rows stay zero), weights
+    for (int i = t; i < (SM_W - SM_AT) / 2; i += TT) sAt[i] = __float2bfloat16_rn(0.f);   // At, Bt1..Bt3
+    for (int i = t; i < 5 * 1024; i += TT) {
+        const int tile = i / 1024, q = i % 1024, n = q / 32, k = q % 32;
+        float v = 0.f;
+        if (tile == 0 && k < SUR_NF) v = params[SUR_W1 + n * SUR_NF + k];              // W1 [hidden][feature]
+        if (tile == 1) v = params[SUR_W2 + n * SUR_NH + k];                             // W2
+        if (tile == 2 && n < SUR_NF) v = params[SUR_W3 + n * SUR_NH + k];              // W3 [output][hidden]
+        if (tile == 3 && k < SUR_NF) v = params[SUR_W3 + k * SUR_NH + n];              // W3^T [hidden][output]
+        if (tile == 4) v = params[SUR_W2 + k * SUR_NH + n];                             // W2^T
+        sW[tile * 1024 + tc::op_index(n, k)] = __float2bfloat16_rn(v);
+    }
+    if (t < 32) {
+        sb[t] = params[SUR_B1 + t];
+        sb[32 + t] = params[SUR_B2 + t];
+        sb[64 + t] = t < SUR_NF ? params[SUR_B3 + t] : 0.f;
+    }
+    tc::fence_async_smem();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = s_tmem, mbar = tc::smem_u32(&s_mbar);
+    const uint32_t aA = tc::smem_u32(sA), aAt = tc::smem_u32(sAt);
+    const uint32_t aB1 = tc::smem_u32(sBt1), aB2 = tc::smem_u32(sBt2), aB3 = tc::smem_u32(sBt3);
+    const uint32_t aW = tc::smem_u32(sW);
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    uint32_t parity = 0;
+    bool ok = true;
+    // operands written by the threads -> visible to the tensor cores; then one
+    // thread issues the MMAs of `issue`, and everyone waits for their completion
+    auto run = [&](auto issue) {
+        tc::fence_async_smem();
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+        if (t == 0 && ok) {
+            issue();
+            tc::commit(mbar);
+        }
+        if (ok && !tc::wait_phase(mbar, parity)) {
+            ok = false;
+            atomicExch(err, 1u);
+        }
+        parity ^= 1u;
+        tc::fence_after();
+    };
+    auto put_row = [&](const float* v, int n) {      // this link's row of the [128 x 32] operand
+#pragma unroll
+        for (int k = 0; k < 32; ++k) sA[tc::op_index(t, k)] = __float2bfloat16_rn(k < n ? v[k] : 0.f);
+    };
+    double loss_acc = 0.0;
+    int acc = 0;                                  // weight-gradient accumulators hold data
+    const long long ntiles = (nl + TT - 1) / TT;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const long long l = tile * TT + t;
+        const bool valid = l < nl;
+        const float one = valid ? 1.f : 0.f;
+        float fq[SUR_NF];
+#pragma unroll
+        for (int k = 0; k < SUR_NF; ++k) fq[k] = valid ? bf16r(f[(size_t)k * stride + l]) : 0.f;
+        put_row(fq, SUR_NF);
+#pragma unroll
+        for (int k = 0; k < SUR_NF; ++k) sBt1[tc::op_index128(k, t)] = __float2bfloat16_rn(fq[k]);
+        sBt1[tc::op_index128(SUR_NF, t)] = __float2bfloat16_rn(one);
+        float z[32], h1[32], h2[32];
+        // ---- forward
+        run([&] { tc::mma_k(tmem + 0, aA, tc::SBO, aW + 0 * 2048, tc::SBO, 32, 32, 0); });
+        tc::load_row(tmem + lane_base + 0, z);
+#pragma unroll
+        for (int k = 0; k < 32; ++k) h1[k] = tanhf(z[k] + sb[k]), z[k] = bf16r(h1[k]);
+        put_row(z, 32);
+#pragma unroll
+        for (int k = 0; k < 32; ++k) sBt2[tc::op_index128(k, t)] = __float2bfloat16_rn(z[k]);
+        sBt2[tc::op_index128(32, t)] = __float2bfloat16_rn(one);
+        run([&] { tc::mma_k(tmem + 32, aA, tc::SBO, aW + 1 * 2048, tc::SBO, 32, 32, 0); });
+        tc::load_row(tmem + lane_base + 32, z);
+#pragma unroll
+        for (int k = 0; k < 32; ++k) h2[k] = tanhf(z[k] + sb[32 + k]), z[k] = bf16r(h2[k]);
+        put_row(z, 32);
+#pragma unroll
+        for (int k = 0; k < 32; ++k) sBt3[tc::op_index128(k, t)] = __float2bfloat16_rn(z[k]);
+        sBt3[tc::op_index128(32, t)] = __float2bfloat16_rn(one);
+        run([&] { tc::mma_k(tmem + 64, aA, tc::SBO, aW + 2 * 2048, tc::SBO, 32, 32, 0); });
+        tc::load_row(tmem + lane_base + 64, z);
+        // ---- loss and dL/dw for this link
+        float dw[SUR_NF];
+#pragma unroll
+        for (int k = 0; k < SUR_NF; ++k) dw[k] = 0.f;
+        if (valid) {
+            float e[8];
+#pragma unroll
+            for (int a = 0; a < 8; ++a) e[a] = -F[(size_t)a * stride + l];
+            for (int k = 0; k < SUR_NF; ++k) {
+                const float wk = z[k] + sb[64 + k];
+#pragma unroll
+                for (int a = 0; a < 8; ++a) e[a] = fmaf(wk, G[((size_t)k * 8 + a) * stride + l], e[a]);
+            }
+            float ls = 0.f;
+#pragma unroll
+            for (int a = 0; a < 8; ++a) ls = fmaf(e[a], e[a], ls);
+            loss_acc += ls;
+            for (int k = 0; k < SUR_NF; ++k) {
+                float sum = 0.f;
+#pragma unroll
+                for (int a = 0; a < 8; ++a) sum = fmaf(e[a], G[((size_t)k * 8 + a) * stride + l], sum);
+                dw[k] = bf16r(sc * sum);
+            }
+        }
+        // ---- backward: dh2 = dw W3 (D4), dW3 += dw^T h2q
+        put_row(dw, SUR_NF);
+#pragma unroll
+        for (int k = 0; k < 32; ++k) sAt[tc::op_index128(k, t)] = __float2bfloat16_rn(k < SUR_NF ? dw[k] : 0.f);
+        run([&] {
+            tc::mma_k(tmem + 0, aA, tc::SBO, aW + 3 * 2048, tc::SBO, 32, 32, 0);
+            tc::mma_k(tmem + C_DW3, aAt, tc::SBO128, aB3, tc::SBO128, 128, 48, acc);
+        });
+        tc::load_row(tmem + lane_base + 0, z);
+#pragma unroll
+        for (int k = 0; k < 32; ++k) z[k] = bf16r(z[k] * (1.f - h2[k] * h2[k]));    // dz2
+        // ---- dh1 = dz2 W2 (D5), dW2 += dz2^T h1q
+        put_row(z, 32);
+#pragma unroll
+        for (int k = 0; k < 32; ++k) sAt[tc::op_index128(k, t)] = __float2bfloat16_rn(z[k]);
+        run([&] {
+            tc::mma_k(tmem + 32, aA, tc::SBO, aW + 4 * 2048, tc::SBO, 32, 32, 0);
+            tc::mma_k(tmem + C_DW2, aAt, tc::SBO128, aB2, tc::SBO128, 128, 48, acc);
+        });
+        tc::load_row(tmem + lane_base + 32, z);
+#pragma unroll
+        for (int k = 0; k < 32; ++k) z[k] = bf16r(z[k] * (1.f - h1[k] * h1[k]));    // dz1
+        // ---- dW1 += dz1^T fq
+#pragma unroll
+        for (int k = 0; k < 32; ++k) sAt[tc::op_index128(k, t)] = __float2bfloat16_rn(z[k]);
+        run([&] { tc::mma_k(tmem + C_DW1, aAt, tc::SBO128, aB1, tc::SBO128, 128, 32, acc); });
+        acc = 1;
+    }
+    // ---- this block's gradient: rows 0..31 of the accumulators are TMEM lanes 0..31 (warp 0)
+    float* gp = grad_part + (size_t)blockIdx.x * SUR_NP;
+    if (warp == 0) {
+        float a[32], b[16];
+        const uint32_t lb = 0;
+        // dW3 rows 0..23 (output k), columns 0..31 (hidden) and the bias column 32
+        tc::load_row(tmem + lb + C_DW3, a);
+        tc::load_row16(tmem + lb + C_DW3 + 32, b);
+        if (t < SUR_NF) {
+#pragma unroll
+            for (int n = 0; n < 32; ++n) gp[SUR_W3 + t * SUR_NH + n] = acc ? a[n] : 0.f;
+            gp[SUR_B3 + t] = acc ? b[0] : 0.f;
+        }
+        tc::load_row(tmem + lb + C_DW2, a);
+        tc::load_row16(tmem + lb + C_DW2 + 32, b);
+#pragma unroll
+        for (int n = 0; n < 32; ++n) gp[SUR_W2 + t * SUR_NH + n] = acc ? a[n] : 0.f;
+        gp[SUR_B2 + t] = acc ? b[0] : 0.f;
+        tc::load_row(tmem + lb + C_DW1, a);
+#pragma unroll
+        for (int k = 0; k < SUR_NF; ++k) gp[SUR_W1 + t * SUR_NF + k] = acc ? a[k] : 0.f;
+        gp[SUR_B1 + t] = acc ? a[SUR_NF] : 0.f;
+    }
+    double lv[1] = {loss_acc};
+    block_sum<1>(lv);
+    if (t == 0) loss_part[blockIdx.x] = lv[0];
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_TRAIN));
 }
 
 // fixed-order sum of the per-block gradients
@@ -579,18 +687,28 @@ static stag_status loss_grad(stag_ctx* ctx, double* loss, std::vector<double>& g
     const long long nl1 = 8LL * ctx->g.Vh;
     const long long stride = ctx->sur_cap * nl1;
     const long long nl = ctx->sur_count * nl1;
-    const int nb = nblocks(nl, TB);
-    const size_t smem = (size_t)(SUR_NP + SV * TB) * sizeof(float);
+    // persistent blocks: as many as share the SMs two by two (shared memory
+    // and TMEM: 2 x 256 columns), never more than there are tiles
+    int dev = 0, nsm = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const long long ntiles = (nl + TT - 1) / TT;
+    const int nb = (int)std::min<long long>(ntiles, 2LL * nsm);
     void *gp, *lp, *gd;
     CKS(ws_get(ctx, WS_SUR_GRAD_PART, (size_t)nb * SUR_NP * sizeof(float), &gp));
     CKS(ws_get(ctx, WS_SUR_LOSS_PART, (size_t)nb * sizeof(double), &lp));
     CKS(ws_get(ctx, WS_SUR_GRAD, SUR_NP * sizeof(double), &gd));
-    CK(cudaFuncSetAttribute(k_sur_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (!ctx->sur_err) {
+        CKS(dev_alloc(ctx, (void**)&ctx->sur_err, sizeof(unsigned int)));
+        CK(cudaMemsetAsync(ctx->sur_err, 0, sizeof(unsigned int), ctx->stream));
+    }
+    CK(cudaFuncSetAttribute(k_sur_train, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_TRAIN));
     const float* d = ctx->sur_data;
-    k_sur_train<<<nb, TB, smem, ctx->stream>>>(nl, d, d + (size_t)SUR_NF * stride,
-                                               d + (size_t)(SUR_NF + SUR_NF * 8) * stride, stride, ctx->sur_w,
-                                               1.0 / (double)nl, (float*)gp, (double*)lp);
+    k_sur_train<<<nb, TT, SM_TRAIN, ctx->stream>>>(nl, d, d + (size_t)SUR_NF * stride,
+                                                   d + (size_t)(SUR_NF + SUR_NF * 8) * stride, stride, ctx->sur_w,
+                                                   (float)(2.0 / (double)nl), (float*)gp, (double*)lp, ctx->sur_err);
     CKL();
+    CKS(surrogate_check(ctx));
     k_sur_reduce<<<nblocks(SUR_NP, 256), 256, 0, ctx->stream>>>(nb, (const float*)gp, (double*)gd);
     CKL();
     grad.resize(SUR_NP);

@@ -345,8 +345,10 @@ int stag_batch_shape(stag_ctx* ctx, stag_prec prec, int* threads_per_block, int*
  * stag_profile_begin in [phase 1, barrier 1, phase 2, barrier 2 + alpha step,
  * phase 3, barrier 3 + beta step] (6 values; %globaltimer). */
 stag_status stag_profile_phases(stag_ctx* ctx, double* us);
-/* The same for the batched solver's launches led by ctx, for fp32-class
- * precisions (any prec but STAG_FP64) or for the float-float fp64 iteration. */
+/* The batched solver's launches led by ctx, for fp32-class precisions (any
+ * prec but STAG_FP64) or for the float-float fp64 iteration: 8 values, us in
+ * [phase 1, barrier 1, phase 2, barrier 2, alpha step, phase 3, barrier 3,
+ * beta step] (the steps include summing the blocks' partial sums). */
 stag_status stag_profile_batch_phases(stag_ctx* ctx, stag_prec prec, double* us);
 /* Number of kernels this context has launched since its creation. */
 long long stag_launch_count(stag_ctx* ctx);

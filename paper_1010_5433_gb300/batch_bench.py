@@ -93,7 +93,7 @@ def run(chains=CHAINS, mass=0.05, beta=5.5, n_outer=10, n_gauge=5, steps=3, warm
                     res[mode]["batched_kernel"] = {"iterations": pr.sampled, "us_per_iteration": us,
                                                    "bytes_per_iteration": pr.bytes_per_launch,
                                                    "GBps": pr.bytes_per_launch / (us * 1e-6) / 1e9}
-                names = ("phase1", "barrier1", "phase2", "barrier2_alpha", "phase3", "barrier3_beta")
+                names = ("phase1", "barrier1", "phase2", "barrier2", "alpha", "phase3", "barrier3", "beta")
                 res[mode]["batched_kernel_phases_us"] = {
                     "fp32": dict(zip(names, [round(x, 1) for x in stag.stag_profile_batch_phases(bat[0], 1)])),
                     "float_float": dict(zip(names, [round(x, 1) for x in stag.stag_profile_batch_phases(bat[0], 0)]))}

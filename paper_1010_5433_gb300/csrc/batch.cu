@@ -139,8 +139,20 @@ __device__ void sum_partials_m(ScalM* S, const double* partial, int nb, int nc, 
     __syncthreads();
 }
 
+// The (chain, shift) pairs of the scalar steps, packed densely: pair i belongs
+// to chain c with base[c] <= i < base[c + 1] (fp64 is slow on GB300, so only
+// real shifts issue its instructions).
+struct Pairs {
+    int base[MAXC + 1];
+};
+__device__ __forceinline__ void pair_of(const Pairs& P, int nc, int i, int& c, int& s) {
+    c = 0;
+    while (c + 1 < nc && i >= P.base[c + 1]) ++c;
+    s = i - P.base[c];
+}
+
 // alpha_k = (r, r) / (p, A p) and the shifted zeta_{k+1}, alpha_{i,k}
-__device__ void alpha_step_m(ScalM* S, int nc) {
+__device__ void alpha_step_m(ScalM* S, int nc, const Pairs& P) {
     const int t = threadIdx.x;
     if (t < nc && !S[t].halt) {
         double a = S[t].rr / S[t].sum;
@@ -152,10 +164,11 @@ __device__ void alpha_step_m(ScalM* S, int nc) {
         S[t].alpha = a;
     }
     __syncthreads();
-    for (int i = t; i < nc * NS; i += blockDim.x) {
-        const int c = i / NS, s = i % NS;
+    for (int i = t; i < P.base[nc]; i += blockDim.x) {
+        int c, s;
+        pair_of(P, nc, i, c, s);
         ScalM& C = S[c];
-        if (C.halt || s >= C.nshift || !C.live[s]) continue;
+        if (C.halt || !C.live[s]) continue;
         const double a = C.alpha, ap = C.alpha_prev, bp = C.beta_prev;
         const double z = C.zeta[s], zp = C.zeta_prev[s];
         // one division: zeta_{k+1} / zeta_k = zeta_{k-1} alpha_{k-1} / den
@@ -170,7 +183,7 @@ __device__ void alpha_step_m(ScalM* S, int nc) {
 
 // beta_k = (r', r') / (r, r), the shifted beta_{i,k}, per-shift convergence,
 // and the chain's halt: converged, reliable update due, max_iter or NaN
-__device__ void beta_step_m(ScalM* S, int nc) {
+__device__ void beta_step_m(ScalM* S, int nc, const Pairs& P) {
     const int t = threadIdx.x;
     __shared__ double s_beta[MAXC];
     __shared__ int active[MAXC];
@@ -187,10 +200,11 @@ __device__ void beta_step_m(ScalM* S, int nc) {
         }
     }
     __syncthreads();
-    for (int i = t; i < nc * NS; i += blockDim.x) {
-        const int c = i / NS, s = i % NS;
+    for (int i = t; i < P.base[nc]; i += blockDim.x) {
+        int c, s;
+        pair_of(P, nc, i, c, s);
         ScalM& C = S[c];
-        if (!active[c] || s >= C.nshift || !C.live[s]) continue;
+        if (!active[c] || !C.live[s]) continue;
         const double zn = C.zeta_next[s], z = C.zeta[s];
         const double zr = C.zratio[s];
         C.cpr[s] = zn;
@@ -361,9 +375,9 @@ __global__ void __launch_bounds__(PB, MB) k_ms_persistent_batch(BatchArgs A, dou
                                                                  unsigned long long* ptime) {
     typedef typename V2T<R>::T V;
     // profiling: block 0 accumulates ns in phase 1, barrier 1, phase 2,
-    // barrier 2 + alpha step, phase 3, barrier 3 + beta step
+    // barrier 2, alpha step (with the partial sums), phase 3, barrier 3, beta step
     const bool timing = ptime && blockIdx.x == 0 && threadIdx.x == 0;
-    unsigned long long tp[6] = {0, 0, 0, 0, 0, 0}, t_last = timing ? gtimer() : 0;
+    unsigned long long tp[8] = {0, 0, 0, 0, 0, 0, 0, 0}, t_last = timing ? gtimer() : 0;
 #define PHASE_MARK(i)                               \
     if (timing) {                                   \
         unsigned long long t_now = gtimer();        \
@@ -376,6 +390,12 @@ __global__ void __launch_bounds__(PB, MB) k_ms_persistent_batch(BatchArgs A, dou
     if (threadIdx.x < nc) C[threadIdx.x] = A.c[threadIdx.x];
     __syncthreads();
     load_scal_m(S, C, nc);
+    __shared__ Pairs P;
+    if (threadIdx.x == 0) {
+        P.base[0] = 0;
+        for (int c = 0; c < nc; ++c) P.base[c + 1] = P.base[c] + S[c].nshift;
+    }
+    __syncthreads();
     const unsigned int nb = gridDim.x;
     const long long nthreads = (long long)gridDim.x * blockDim.x;
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -423,9 +443,10 @@ __global__ void __launch_bounds__(PB, MB) k_ms_persistent_batch(BatchArgs A, dou
             for (int j = 0; j < nc; ++j) partial[(size_t)j * nb + blockIdx.x] = dots[j];
         PHASE_MARK(2)
         if (!(ok = grid_sync(bar, nb))) break;
-        sum_partials_m(S, partial, nb, nc, 0);
-        alpha_step_m(S, nc);
         PHASE_MARK(3)
+        sum_partials_m(S, partial, nb, nc, 0);
+        alpha_step_m(S, nc, P);
+        PHASE_MARK(4)
         // ---- phase 3: shift updates, r -= alpha q, (r, r)
         double nrm[MAXC];
 #pragma unroll
@@ -445,15 +466,16 @@ __global__ void __launch_bounds__(PB, MB) k_ms_persistent_batch(BatchArgs A, dou
         block_sum<MAXC>(nrm);
         if (threadIdx.x == 0)
             for (int j = 0; j < nc; ++j) partial[(size_t)(MAXC + j) * nb + blockIdx.x] = nrm[j];
-        PHASE_MARK(4)
-        if (!(ok = grid_sync(bar, nb))) break;
-        sum_partials_m(S, partial, nb, nc, MAXC);
-        beta_step_m(S, nc);
         PHASE_MARK(5)
+        if (!(ok = grid_sync(bar, nb))) break;
+        PHASE_MARK(6)
+        sum_partials_m(S, partial, nb, nc, MAXC);
+        beta_step_m(S, nc, P);
+        PHASE_MARK(7)
     }
 #undef PHASE_MARK
     if (timing)
-        for (int i = 0; i < 6; ++i) ptime[8 + 6 * (sizeof(R) == 4 ? 0 : 1) + i] += tp[i];
+        for (int i = 0; i < 8; ++i) ptime[8 + 8 * (sizeof(R) == 4 ? 0 : 1) + i] += tp[i];
     if (!ok && threadIdx.x < nc && !S[threadIdx.x].halt) {
         S[threadIdx.x].halt = 1;
         S[threadIdx.x].status = STAG_ERR_TIMEOUT;
@@ -672,7 +694,7 @@ extern "C" stag_status stag_profile_batch_phases(stag_ctx* ctx, stag_prec prec, 
         CK(cudaMemcpyAsync(t, ctx->ptime, sizeof(t), cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
     }
-    const int base = 8 + 6 * (prec == STAG_FP64 ? 1 : 0);
-    for (int i = 0; i < 6; ++i) us[i] = t[base + i] * 1e-3;
+    const int base = 8 + 8 * (prec == STAG_FP64 ? 1 : 0);
+    for (int i = 0; i < 8; ++i) us[i] = t[base + i] * 1e-3;
     return STAG_OK;
 }

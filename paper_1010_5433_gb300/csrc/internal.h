@@ -114,7 +114,7 @@ struct stag_ctx {
     bool use_persistent = true;       // small lattices: persistent cooperative solver (STAG_PERSISTENT=0 off)
     void* bar = nullptr;              // grid-barrier words of the persistent solver
     void* ptime = nullptr;            // per-phase ns counters of the persistent kernels while profiling
-                                      // ([0,8) single lattice, [8,14) batched fp32, [14,20) batched float-float)
+                                      // ([0,8) single lattice, [8,16) batched fp32, [16,24) batched float-float)
     BatchTune batch_tune[4];          // batched solver launch shape per precision (this context leading)
     int batch_shape_force = -1;       // STAG_BATCH_SHAPE=0|1|2: fixed shape, no tuning
     // force surrogate

@@ -309,7 +309,7 @@ def stag_profile_read(ctx, kind):
 
 
 def stag_profile_batch_phases(ctx, prec):
-    us = (C.c_double * 6)()
+    us = (C.c_double * 8)()
     _check(lib().stag_profile_batch_phases(ctx, int(prec), us), "stag_profile_batch_phases", ctx)
     return list(us)
 

@@ -121,21 +121,18 @@ __device__ void store_scal_m(const ScalM* S, const ChainArgs* C, int nc) {
 }
 
 // every block: S[c].sum = sum over blocks of partial[base + c][.] for all
-// chains at once, in the same fixed order in every block
+// chains, warp c summing chain c (lane l adds the partials l, l + 32, ...,
+// then a fixed shuffle tree), so every block gets the same bits
 __device__ void sum_partials_m(ScalM* S, const double* partial, int nb, int nc, int base) {
-    double acc[MAXC];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp < nc) {
+        double v = 0.0;
+        const double* p = partial + (size_t)(base + warp) * nb;
+        for (int i = lane; i < nb; i += 32) v += __ldcg(p + i);
 #pragma unroll
-    for (int j = 0; j < MAXC; ++j) acc[j] = 0.0;
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
-#pragma unroll
-        for (int j = 0; j < MAXC; ++j)
-            if (j < nc) acc[j] += __ldcg(partial + (size_t)(base + j) * nb + i);
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) S[warp].sum = v;
     }
-    block_sum<MAXC>(acc);
-    if (threadIdx.x == 0)
-#pragma unroll
-        for (int j = 0; j < MAXC; ++j)
-            if (j < nc) S[j].sum = acc[j];
     __syncthreads();
 }
 
@@ -516,6 +513,7 @@ stag_status launch_batch_pb(stag_ctx* ctx, const BatchArgs& A, long long sites, 
 // float-float keeps the first only (its registers allow no second block)
 constexpr int N_SHAPES = 3;
 constexpr int SHAPE_PB[N_SHAPES] = {256, 384, 320};
+static_assert(256 >= 32 * MAXC, "sum_partials_m needs a warp per chain");
 constexpr int SHAPE_MB[N_SHAPES] = {1, 1, 1};
 
 template <typename R, int FMT>

@@ -110,11 +110,18 @@ __device__ void store_scal(const Scal& S, SolverState* st) {
     }
 }
 
-// every block: sum partial[q][0..nb) in a fixed order into S.sums[q]
-__device__ void sum_partials(Scal& S, const double* partial, int nb) {
-    for (int q = 0; q < S.nrhs; ++q) {
-        double v = block_sum_array(partial + (size_t)q * nb, nb);
-        if (threadIdx.x == 0) S.sums[q] = v;
+// every block: S.sums[q] = sum of partial[off + q][0..nb) for every source q,
+// warp q summing source q (lane l adds the partials l, l + 32, ..., then a
+// fixed shuffle tree), so every block gets the same bits
+__device__ void sum_partials(Scal& S, const double* partial, int nb, int off) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp < S.nrhs) {
+        double v = 0.0;
+        const double* p = partial + (size_t)(off + warp) * nb;
+        for (int i = lane; i < nb; i += 32) v += __ldcg(p + i);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) S.sums[warp] = v;
     }
     __syncthreads();
 }
@@ -250,6 +257,7 @@ __global__ void __launch_bounds__(PB) k_ms_persistent(Geom g, LinkPtrs L, Solver
                                                       typename V2T<R>::T* ps, typename V2T<R>::T* x,
                                                       double* partial, GridBar* bar, unsigned long long* ptime) {
     typedef typename V2T<R>::T V;
+    static_assert(PB >= 32 * STAG_MAX_RHS, "the reductions take a warp per source");
     __shared__ Scal S;
     // profiling: block 0 accumulates ns spent in phase 1, barrier 1, phase 2,
     // barrier 2 + alpha step, phase 3, barrier 3 + beta step
@@ -369,7 +377,7 @@ __global__ void __launch_bounds__(PB) k_ms_persistent(Geom g, LinkPtrs L, Solver
             for (int j = 0; j < nrhs && j < ND; ++j) partial[(size_t)j * nb + blockIdx.x] = dots[j];
         PHASE_MARK(2)
         if (!(ok = grid_sync(bar, nb))) break;
-        sum_partials(S, partial, nb);
+        sum_partials(S, partial, nb, 0);
         alpha_step(S);
         PHASE_MARK(3)
         // ---- phase 3: shift updates and r -= alpha q with (r, r)
@@ -399,11 +407,7 @@ __global__ void __launch_bounds__(PB) k_ms_persistent(Geom g, LinkPtrs L, Solver
             for (int j = 0; j < nrhs && j < ND; ++j) partial[(size_t)(STAG_MAX_RHS + j) * nb + blockIdx.x] = nrm[j];
         PHASE_MARK(4)
         if (!(ok = grid_sync(bar, nb))) break;
-        for (int j = 0; j < nrhs; ++j) {
-            double v = block_sum_array(partial + (size_t)(STAG_MAX_RHS + j) * nb, nb);
-            if (threadIdx.x == 0) S.sums[j] = v;
-        }
-        __syncthreads();
+        sum_partials(S, partial, nb, STAG_MAX_RHS);
         beta_step(S);
         PHASE_MARK(5)
     }

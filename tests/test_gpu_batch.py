@@ -212,3 +212,37 @@ def test_batch_rejects_bad_arguments(torch):
         assert np.isfinite(out[0].dH)
     finally:
         _destroy(stag, ctxs)
+
+
+def test_full_size_eight_chains_match_sequential(torch):
+    """The batched-chains workload at its full sizes (2 x 8^4, 2 x 12^4,
+    2 x 16^4, 2 x 16^3 x 8; N_f = 2, m = 0.05, beta = 5.5, 12-pole MD rational,
+    fp32 MD) in the launch configuration batch_bench.py times: one batched
+    trajectory of every chain against the same chains one at a time."""
+    from paper_1010_5433_gb300 import batch_bench, rational, stag
+    chains = batch_bench.CHAINS
+    rats = {k: rational.load("c4_" + k) for k in ("md", "met", "hb")}
+
+    def hmc(k):
+        p = stag.stag_hmc()
+        p.beta, p.tau, p.n_outer, p.n_gauge, p.n_flavours = 5.5, 1.0, 10, 5, 1
+        fl = p.flavour[0]
+        fl.mass, fl.n_pf = 0.05, 1
+        fl.hb, fl.md, fl.met = rats["hb"].to_abi(), rats["md"].to_abi(), rats["met"].to_abi()
+        p.tol_md, p.tol_met, p.max_iter, p.md_prec = 1e-8, 1e-12, 20000, stag.STAG_FP32
+        p.seed, p.counter = 0x5A0004 + k, 0
+        return p
+
+    seeds = [600 + k for k in range(len(chains))]
+    seq, _ = _contexts(stag, chains, seeds, hot=False)
+    bat, _ = _contexts(stag, chains, seeds, hot=False)
+    try:
+        outs = stag.stag_md_trajectory_batch(bat, [hmc(k) for k in range(len(chains))])
+        for k in range(len(chains)):
+            one = stag.stag_md_trajectory(seq[k], hmc(k))
+            print(f"chain {k} {chains[k]}: dH batch {outs[k].dH:.6f} single {one.dH:.6f}")
+            assert abs(outs[k].dH - one.dH) < 1e-3 * max(1.0, abs(one.dH))
+            assert outs[k].accepted == one.accepted
+            assert abs(outs[k].plaq - one.plaq) < 1e-6
+    finally:
+        _destroy(stag, seq + bat)

@@ -73,10 +73,11 @@ def test_dslash_matches_oracle(torch, dims, seed, prec, out_par):
 
 
 @pytest.mark.parametrize("prec", [0, 1, 3])
-@pytest.mark.parametrize("nrhs", [1, 3, 4, 7])
+@pytest.mark.parametrize("nrhs", [1, 3, 4, 7, 60])
 def test_multi_rhs_equals_single(torch, prec, nrhs):
     """The n-RHS Dslash (one link load for every source) gives each source's
-    single-RHS result bit for bit."""
+    single-RHS result bit for bit; 60 is the force's Y = D_oe X of 2+1
+    flavours x 2 pseudo-fermions x 15 shifts."""
     from paper_1010_5433_gb300 import stag
     dims = (4, 6, 4, 8)
     u = syn.haar_gauge(dims, 7)

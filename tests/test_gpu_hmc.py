@@ -198,3 +198,46 @@ def test_two_flavours_two_pseudofermions_match_oracle(torch, prec, tol_dh):
         print(f"2+1 flavours prec {prec}: dH gpu {res.dH:.8f} oracle {want['dH']:.8f}")
     finally:
         stag.stag_destroy(ctx)
+
+
+def test_bench_configuration_trajectory_is_reversible(torch):
+    """The 16^4, N_f = 2, m = 0.02, beta = 5.6 trajectory in the launch
+    configuration bench.py times (12-pole MD rational of the product table,
+    n_outer 20 x n_gauge 5, fp32 MD): forward with supplied momenta and
+    pseudo-fermions, then back from the flipped final momenta."""
+    from paper_1010_5433_gb300 import rational, stag
+    dims = (16, 16, 16, 16)
+    rats = {k: rational.load("c2_" + k) for k in ("md", "met", "hb")}
+    u0 = syn.near_identity_gauge(dims, 0x5A0002)
+    ctx = stag.stag_create(dims, True)
+
+    def hmc(**kw):
+        p = stag.stag_hmc()
+        p.beta, p.tau, p.n_outer, p.n_gauge, p.n_flavours = 5.6, 1.0, 20, 5, 1
+        fl = p.flavour[0]
+        fl.mass, fl.n_pf = 0.02, 1
+        fl.hb, fl.md, fl.met = rats["hb"].to_abi(), rats["md"].to_abi(), rats["met"].to_abi()
+        p.tol_md, p.tol_met, p.max_iter, p.md_prec = 1e-8, 1e-12, 20000, stag.STAG_FP32
+        for k, v in kw.items():
+            setattr(p, k, v)
+        return p
+
+    try:
+        stag.stag_load_gauge(ctx, L.gauge_host(u0))
+        d_mom = torch.from_numpy(L.mom_to_abi(syn.gaussian_momenta(dims, 17), dims)).cuda()
+        d_phi = dev(torch, L.to_half(syn.gaussian_fermion(dims, 18, on_parity=0), dims, 0)[None])
+        r1 = stag.stag_md_trajectory(ctx, hmc(ext_mom=d_mom.data_ptr(), ext_phi=d_phi.data_ptr(), no_metropolis=1))
+        back = wrap_device(torch, stag.stag_momenta(ctx), d_mom.numel()).clone().view_as(d_mom)
+        r2 = stag.stag_md_trajectory(ctx, hmc(ext_mom=back.data_ptr(), ext_phi=d_phi.data_ptr(), no_metropolis=1,
+                                             flip_momenta=1))
+        buf = np.empty(4 * int(np.prod(dims)) * 18)
+        stag.stag_store_gauge(ctx, buf)
+        viol = np.sqrt(np.mean(np.abs(L.gauge_from_host(buf, dims) - u0) ** 2 * 0.5))
+        print(f"16^4 bench configuration: H0 {r1.H0:.1f}, dH {r1.dH:.5f} back {r2.dH:.5f}, reversibility per "
+              f"dof {viol:.2e}, CG iterations {r1.cg_iterations}")
+        assert viol < 5e-5
+        # fp32 links: H (~1e6 here: 2.1e6 momentum components) returns to fp32 accuracy, not absolutely
+        assert abs(r1.dH + r2.dH) < 1e-6 * abs(r1.H0)
+        assert abs(r1.dH) < 5.0
+    finally:
+        stag.stag_destroy(ctx)

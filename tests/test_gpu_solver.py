@@ -148,3 +148,28 @@ def test_full_size_16x4_twelve_shifts(torch, prec):
         print("16^4 prec", prec, "iterations", info.iterations, "reliable", info.reliable_updates)
     finally:
         stag.stag_destroy(ctx)
+
+
+@pytest.mark.parametrize("nshift", [1, 32])
+def test_shift_count_extremes_fp64(torch, nshift):
+    """One shift (plain CG) and the maximum of 32 shifts, every solution
+    against the oracle's multi-shift CG."""
+    from paper_1010_5433_gb300 import stag
+    dims = (4, 4, 4, 4)
+    u, eta, par = _setup(dims, 95)
+    mass = 0.1
+    shifts = [0.0] if nshift == 1 else [0.0] + list(np.geomspace(1e-4, 20.0, 31))
+    b = syn.gaussian_fermion(dims, 96, on_parity=0)
+    ctx = stag.stag_create(dims, True)
+    try:
+        stag.stag_load_gauge(ctx, L.gauge_host(u))
+        d_b = dev(torch, L.to_half(b, dims, 0)[None])
+        d_x = torch.empty((1, nshift) + tuple(d_b.shape[1:]), dtype=torch.float64, device="cuda")
+        info = stag.stag_multishift_solve(ctx, mass, shifts, stag.STAG_FP64, 1, d_b, d_x, 1e-12, 5000)
+        xs, its, _ = solvers.multishift_cg(lambda v: dirac.a_op(u, v, mass, eta, par, 0.0), b, shifts, 1e-12)
+        got = host_complex(d_x).reshape(nshift, 3, -1)
+        for s in range(nshift):
+            assert L.rel_err(got[s], L.to_half(xs[s], dims, 0)) < 1e-10, s
+        assert abs(info.iterations - its) <= 3
+    finally:
+        stag.stag_destroy(ctx)

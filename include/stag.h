@@ -353,10 +353,12 @@ stag_status stag_profile_batch_phases(stag_ctx* ctx, stag_prec prec, double* us)
 /* Number of kernels this context has launched since its creation. */
 long long stag_launch_count(stag_ctx* ctx);
 /* Threads per site the Dslash of this precision and source count uses (1, 2,
- * 4 or 8), autotuned on the context's first need: every candidate is timed
- * as a CUDA graph of 20 launches and the fastest kept; us_per_launch (may be
- * NULL) receives its time.  The environment variable STAG_DSLASH_TPS fixes
- * the value instead.  Returns 0 on a bad argument. */
+ * 4 or 8), autotuned on the first need for a lattice shape: every candidate
+ * is timed as a CUDA graph of 20 launches and the fastest kept for every
+ * context of that shape, precision and device in the process (so that their
+ * sums run in the same order); us_per_launch (may be NULL) receives its
+ * time.  The environment variable STAG_DSLASH_TPS fixes the value instead.
+ * Returns 0 on a bad argument. */
 int stag_tuned_threads_per_site(stag_ctx* ctx, stag_prec prec, int nrhs, double* us_per_launch);
 
 #ifdef __cplusplus

@@ -53,6 +53,59 @@ template <typename R> struct SrcPlain {
     }
 };
 
+// ... or an fp64 field read as float-float: every double split into hi + lo
+// floats with integer operations only (GB300's fp64 pipes are slow), so that
+// the fp64 operator runs its arithmetic in float-float (Sec. 5's two-float
+// representation) on the fp32 pipes.  hi keeps the top 23 mantissa bits (an
+// exact float), lo is the remaining 29 bits rounded to float: hi + lo carries
+// ~48 bits.  Magnitudes below 2^-126 (and lo parts below float range) flush
+// to zero; magnitudes above float range become infinite.
+__device__ __forceinline__ DF df_split(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned int sign = (unsigned int)(b >> 63) << 31;
+    const int e = (int)((b >> 52) & 0x7FF) - 1023 + 127;     // float exponent field of hi
+    const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+    if (e <= 0) return DF(0.f, 0.f);
+    if (e >= 255) return DF(__uint_as_float(sign | 0x7F800000u), 0.f);
+    const float hi = __uint_as_float(sign | ((unsigned int)e << 23) | (unsigned int)(m >> 29));
+    // lo = low29 x 2^(e - 127 - 52): the integer part converts exactly up to 2^24 and rounds above
+    const int el = e - 52;                                    // exponent field of 2^(e - 127 - 52)
+    float lo = 0.f;
+    if (el > 0) {
+        lo = (float)(unsigned int)(m & 0x1FFFFFFFull) * __uint_as_float((unsigned int)el << 23);
+        lo = __uint_as_float(__float_as_uint(lo) | sign);
+    }
+    return DF(hi, lo);
+}
+// hi + lo as a double: each float widened exactly by integer operations, one fp64 add
+__device__ __forceinline__ double df_widen(float f) {
+    const unsigned int u = __float_as_uint(f);
+    const unsigned int e = (u >> 23) & 0xFF;
+    if (e == 0) return 0.0;                                   // zero (float denormals flushed)
+    const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+    const unsigned long long ed = e == 0xFF ? 0x7FFull : (unsigned long long)(e - 127 + 1023);
+    return __longlong_as_double((long long)(sign | (ed << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+}
+__device__ __forceinline__ double df_join(DF v) { return df_widen(v.hi) + df_widen(v.lo); }
+
+struct SrcD2DF {
+    const double2* __restrict__ in;
+    template <int NR> __device__ __forceinline__ void prepare(int r0, int nrhs) {}
+    __device__ __forceinline__ Vec3<DF> load(int slot, int rhs, int h, int Vh) const {
+        const double2* p = in + (size_t)rhs * 3 * Vh;
+        Vec3<DF> v;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double2 d = __ldg(p + (size_t)c * Vh + h);
+            v.c[c].re = df_split(d.x);
+            v.c[c].im = df_split(d.y);
+        }
+        return v;
+    }
+};
+template <typename R> struct SrcFor { typedef SrcPlain<R> type; typedef typename V2T<R>::T io; };
+template <> struct SrcFor<DF> { typedef SrcD2DF type; typedef double2 io; };
+
 // Accumulate the hops of one site for NR sources:
 //   sum_mu [ sf U_mu(x) in(x+mu) - sb U_mu(x-mu)^dag in(x-mu) ]
 // (the factor 1/2 is left to the epilogue).  With TPS threads per site, thread
@@ -150,6 +203,51 @@ template <typename R> struct EpiStore {
 #pragma unroll
             for (int c = 0; c < 3; ++c) o.c[c] = scale * acc[r].c[c];
             store_vec<R>(out + (size_t)(r0 + r) * rs, h, g.Vh, o);
+        }
+    }
+};
+
+// The same two epilogues for the float-float operator on fp64 fields
+struct EpiStoreD2 {
+    double2* out;
+    DF scale;
+    __device__ __forceinline__ bool halted() const { return false; }
+    template <int NR>
+    __device__ __forceinline__ void finish(const Geom& g, int h, bool valid, int r0, int nrhs, Vec3<DF> (&acc)[NR]) {
+        if (!valid) return;
+        const size_t rs = (size_t)3 * g.Vh;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            if (r0 + r >= nrhs) continue;
+            double2* o = out + (size_t)(r0 + r) * rs;
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                o[(size_t)c * g.Vh + h] = make_double2(df_join(scale * acc[r].c[c].re), df_join(scale * acc[r].c[c].im));
+        }
+    }
+};
+struct EpiAopD2 {
+    double2* out;
+    const double2* aux;
+    DF c0;
+    __device__ __forceinline__ bool halted() const { return false; }
+    template <int NR>
+    __device__ __forceinline__ void finish(const Geom& g, int h, bool valid, int r0, int nrhs, Vec3<DF> (&acc)[NR]) {
+        if (!valid) return;
+        const size_t rs = (size_t)3 * g.Vh;
+        const DF half(0.5f);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            if (r0 + r >= nrhs) continue;
+            const double2* a = aux + (size_t)(r0 + r) * rs;
+            double2* o = out + (size_t)(r0 + r) * rs;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const double2 ad = __ldg(a + (size_t)c * g.Vh + h);
+                const DF re = c0 * df_split(ad.x) - half * acc[r].c[c].re;
+                const DF im = c0 * df_split(ad.y) - half * acc[r].c[c].im;
+                o[(size_t)c * g.Vh + h] = make_double2(df_join(re), df_join(im));
+            }
         }
     }
 };

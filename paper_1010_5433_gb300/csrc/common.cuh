@@ -165,6 +165,65 @@ template <typename R> __device__ __forceinline__ void mac_udv(Vec3<R>& acc, R s,
     }
 }
 
+// Float-float versions (the fp64 operator): each output component sums its
+// six products with error-free products of the high parts (FMA) and a
+// compensated running sum, the cross terms and rounding errors gathered in the
+// low word, and is renormalised once per link (the compensated dot product of
+// Ogita, Rump and Oishi, 2005) -- about half the fp32 operations of chained
+// float-float multiplies and adds.  s is a staggered sign, exactly +1 or -1.
+__device__ __forceinline__ void df_mac(DF& acc, const DF& a, const DF& b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    const float sum = acc.hi + p;             // two-sum of acc.hi and p
+    const float bv = sum - acc.hi;
+    const float err = (acc.hi - (sum - bv)) + (p - bv);
+    acc.hi = sum;
+    acc.lo += e + err;
+}
+__device__ __forceinline__ DF df_neg_if(const DF& a, bool neg) { return neg ? DF(-a.hi, -a.lo) : a; }
+__device__ __forceinline__ void df_renorm(DF& v) { v = df_two_sum(v.hi, v.lo); }
+
+template <> __device__ __forceinline__ void mac_uv<DF>(Vec3<DF>& acc, DF s, const Su3<DF>& u, const Vec3<DF>& v) {
+    const bool neg = s.hi < 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        DF re = acc.c[i].re, im = acc.c[i].im;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const DF ur = df_neg_if(u.e[i][j].re, neg), ui = df_neg_if(u.e[i][j].im, neg);
+            df_mac(re, ur, v.c[j].re);          // s (u v).re = s (ur vr - ui vi)
+            df_mac(re, DF(-ui.hi, -ui.lo), v.c[j].im);
+            df_mac(im, ur, v.c[j].im);          // s (u v).im = s (ur vi + ui vr)
+            df_mac(im, ui, v.c[j].re);
+        }
+        df_renorm(re);
+        df_renorm(im);
+        acc.c[i].re = re;
+        acc.c[i].im = im;
+    }
+}
+template <> __device__ __forceinline__ void mac_udv<DF>(Vec3<DF>& acc, DF s, const Su3<DF>& u, const Vec3<DF>& v) {
+    const bool neg = s.hi < 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        DF re = acc.c[i].re, im = acc.c[i].im;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const DF ur = df_neg_if(u.e[j][i].re, neg), ui = df_neg_if(u.e[j][i].im, neg);
+            df_mac(re, ur, v.c[j].re);          // s (u^dag v).re = s (ur vr + ui vi)
+            df_mac(re, ui, v.c[j].im);
+            df_mac(im, ur, v.c[j].im);          // s (u^dag v).im = s (ur vi - ui vr)
+            df_mac(im, DF(-ui.hi, -ui.lo), v.c[j].re);
+        }
+        df_renorm(re);
+        df_renorm(im);
+        acc.c[i].re = re;
+        acc.c[i].im = im;
+    }
+}
+
 template <typename R> __device__ __forceinline__ Su3<R> mul(const Su3<R>& a, const Su3<R>& b) {
     Su3<R> c;
 #pragma unroll

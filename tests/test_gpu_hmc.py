@@ -241,3 +241,50 @@ def test_bench_configuration_trajectory_is_reversible(torch):
         assert abs(r1.dH) < 5.0
     finally:
         stag.stag_destroy(ctx)
+
+
+def test_full_size_two_plus_one_flavours_bf16_links(torch):
+    """The 32^3 x 8, beta = 5.3, N_f = 2+1 (m_l = 0.01, m_s = 0.1) workload at
+    full size: 2 pseudo-fermions per flavour, 15-pole MD rationals, bf16 12-real
+    links in the MD inversions (iterated without residual replacement), one
+    n-RHS force Dslash over flavours x pseudo-fermions x shifts (60 sources),
+    float-float Metropolis.  Forward with supplied momenta and pseudo-fermions
+    (tau shortened to 0.25), then back from the flipped final momenta."""
+    from paper_1010_5433_gb300 import rational, stag
+    dims = (32, 32, 32, 8)
+    rl = {k: rational.load("c3_light_" + k) for k in ("md", "met", "hb")}
+    rs = {k: rational.load("c3_strange_" + k) for k in ("md", "met", "hb")}
+    u0 = syn.near_identity_gauge(dims, 0x5A0003)
+    ctx = stag.stag_create(dims, True)
+
+    def hmc(**kw):
+        p = stag.stag_hmc()
+        p.beta, p.tau, p.n_outer, p.n_gauge, p.n_flavours = 5.3, 0.25, 2, 4, 2
+        for f, (m, r) in enumerate(((0.01, rl), (0.1, rs))):
+            fl = p.flavour[f]
+            fl.mass, fl.n_pf = m, 2
+            fl.hb, fl.md, fl.met = r["hb"].to_abi(), r["md"].to_abi(), r["met"].to_abi()
+        p.tol_md, p.tol_met, p.max_iter, p.md_prec = 1e-8, 1e-12, 40000, stag.STAG_BF16_12
+        for k, v in kw.items():
+            setattr(p, k, v)
+        return p
+
+    try:
+        stag.stag_load_gauge(ctx, L.gauge_host(u0))
+        d_mom = torch.from_numpy(L.mom_to_abi(syn.gaussian_momenta(dims, 31), dims)).cuda()
+        phis = np.stack([L.to_half(syn.gaussian_fermion(dims, 40 + k, on_parity=0), dims, 0) for k in range(4)])
+        d_phi = dev(torch, phis)
+        r1 = stag.stag_md_trajectory(ctx, hmc(ext_mom=d_mom.data_ptr(), ext_phi=d_phi.data_ptr(), no_metropolis=1))
+        back = wrap_device(torch, stag.stag_momenta(ctx), d_mom.numel()).clone().view_as(d_mom)
+        r2 = stag.stag_md_trajectory(ctx, hmc(ext_mom=back.data_ptr(), ext_phi=d_phi.data_ptr(), no_metropolis=1,
+                                             flip_momenta=1))
+        buf = np.empty(4 * int(np.prod(dims)) * 18)
+        stag.stag_store_gauge(ctx, buf)
+        viol = np.sqrt(np.mean(np.abs(L.gauge_from_host(buf, dims) - u0) ** 2 * 0.5))
+        print(f"32^3x8 2+1 bf16: H0 {r1.H0:.1f}, dH {r1.dH:.5f} back {r2.dH:.5f}, reversibility per dof "
+              f"{viol:.2e}, CG iterations {r1.cg_iterations}, {r1.seconds:.2f} s")
+        assert viol < 1e-4
+        assert abs(r1.dH + r2.dH) < 1e-5 * abs(r1.H0)
+        assert np.isfinite(r1.dH) and abs(r1.dH) < 50.0
+    finally:
+        stag.stag_destroy(ctx)

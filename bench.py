@@ -358,10 +358,11 @@ def work_per_traj(cg_iterations):
             "gauge_forces": 2 * no * (2 * ng + 1), "link_updates": 2 * no * 2 * ng}
 
 
-# CG iterations of one 16^4 trajectory of this workload (all solves), from a
-# GB300 run of the mixed path; only used to scale the reference arm's sample
-# when no GPU run precedes it.
-REF_CG_ITERATIONS = 12000
+# CG iterations of one 16^4 trajectory of this workload (all solves: MD,
+# heatbath, Metropolis), as the mixed path measured them on GB300 (40 057 per
+# trajectory over the bench's timed trajectories); only used to scale the
+# reference arm's sample, which runs without a GPU run before it.
+REF_CG_ITERATIONS = 40057
 
 
 def main():

@@ -130,6 +130,27 @@ def make_hmc(stag, rats, prec, seed, counter, n_flavours=1, **kw):
     return p
 
 
+# ---------------------------------------------------------------- replicas (N > 1)
+# One independent chain per rank, no data-path collective: the job's rate is
+# every rank's trajectories over the slowest rank's time.
+def replica_seed(seed, rank):
+    return seed + 1000 * rank
+
+
+def max_over_ranks(x, world, device=None):
+    if world == 1:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, steps, seconds):
+    """Trajectories per hour of the whole job."""
+    return world * steps / seconds * 3600.0
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     import synthetic as syn
@@ -142,7 +163,7 @@ def run_gpu(args, rank, world, local_rank):
     dims = tuple(w["dims"])
     V = int(np.prod(dims))
     rats = {k: rational.load(v) for k, v in w["rationals"].items()}
-    seed = w["seed"] + 1000 * rank          # replicas: one independent chain per rank
+    seed = replica_seed(w["seed"], rank)
     ctx = stag.stag_create(dims, True, stream.cuda_stream)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
@@ -190,24 +211,18 @@ def run_gpu(args, rank, world, local_rank):
             stag.stag_profile_begin(ctx, 0)
         return ms, trajs, clk.summary(), launches, prof
 
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
 
     # ---- the mixed path (headline)
     ms, trajs, clocks, launches, prof = timed(stag.STAG_FP32, args.steps, counter, True)
-    ms = max_over_ranks(ms)
+    ms = max_over_ranks(ms, world, dev)
     counter += args.steps
-    value = world * args.steps / (ms / 1e3) * 3600.0
+    value = job_rate(world, args.steps, ms / 1e3)
     # ---- the plain fp64 path from the same configuration
     stag.stag_load_gauge(ctx, start_field)
     steps64 = max(2, args.steps // 2)
     ms64, trajs64, _, _, _ = timed(stag.STAG_FP64, steps64, 0, False)
-    ms64 = max_over_ranks(ms64)
-    value64 = world * steps64 / (ms64 / 1e3) * 3600.0
+    ms64 = max_over_ranks(ms64, world, dev)
+    value64 = job_rate(world, steps64, ms64 / 1e3)
     # ---- end to end through the C ABI with host buffers (pinned), copies timed
     host = torch.empty(4 * V * 18, dtype=torch.float64, pin_memory=True)
     host.copy_(torch.from_numpy(start_field))
@@ -221,8 +236,8 @@ def run_gpu(args, rank, world, local_rank):
         stag.stag_md_trajectory(ctx, make_hmc(stag, rats, stag.STAG_FP32, seed, 5000 + k))
         stag.stag_store_gauge(ctx, hnp)                                  # D2H of the updated configuration
     torch.cuda.synchronize()
-    e2e_s = max_over_ranks(time.perf_counter() - t0)
-    e2e = world * args.steps / e2e_s * 3600.0
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+    e2e = job_rate(world, args.steps, e2e_s)
 
     # ---- roofline of the dominant kernel, from the live sampled events
     hbm, peak_kind = peaks()

@@ -15,7 +15,9 @@
 // (its convergence flag) while the others continue.  The launch ends when
 // every chain has halted; the host then makes the fp64 reliable updates of
 // the chains that asked for one and launches again.  One source per chain
-// (n_rhs = 1); every wait on a grid barrier is bounded.
+// (n_rhs = 1); every wait on a grid barrier is bounded.  The launch shape
+// (threads per block, blocks per SM) is chosen per precision by timing the
+// candidates on the first segments of real solves.
 #include <cmath>
 #include <cstring>
 

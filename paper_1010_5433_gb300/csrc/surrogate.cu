@@ -5,10 +5,13 @@
 //     j = 2..5  2mu x nu rectangles: up with the link first / second, down first / second
 //     j = 6, 7  mu x 2nu rectangles up / down
 //   features   f_k = Re tr(U S_k) / 3                (gauge invariant)
-//   MLP        w = W3 tanh(W2 tanh(W1 f + b1) + b2) + b3   (24-32-32-24, bf16 weights, fp32 math)
+//   MLP        w = W3 tanh(W2 tanh(W1 f + b1) + b2) + b3   (24-32-32-24) on the
+//              tensor cores: bf16 weights and bf16 inputs to every product
+//              (f, h1, h2), fp32 accumulation in TMEM, fp32 biases and tanh
 //   force      F^_a = Re tr(i T_a sum_k w_k U S_k)    (gauge covariant)
 // Training minimises the mean over links of |F^ - F|^2 against exact fermion
-// forces with Adam on fp32 master weights.
+// forces with Adam on fp32 master weights; its forward, backward and
+// weight-gradient products run on the tensor cores as well.
 #include <cmath>
 #include <cstring>
 #include <vector>

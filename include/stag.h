@@ -312,6 +312,14 @@ stag_status stag_surrogate_loss_grad(stag_ctx* ctx, double* loss, double* grad);
 /* steps full-batch Adam steps (learning rate lr); losses before the first and last step. */
 stag_status stag_surrogate_train(stag_ctx* ctx, int steps, double lr, double* loss_first, double* loss_last);
 
+/* ---- self-test (no counterpart in the paper) ------------------------------
+ * The bounded grid barrier of the persistent solvers, made to run out: two
+ * blocks, only one arrives, its wait gives up after spin_limit polls
+ * (1 <= spin_limit <= 2^26, as the solvers' own limit) and the kernel
+ * reports it.  Returns STAG_ERR_TIMEOUT when the bound works (the context
+ * stays usable), STAG_OK would mean the wait ended otherwise; synchronous. */
+stag_status stag_selftest_barrier_timeout(stag_ctx* ctx, long long spin_limit);
+
 /* ---- measurement (no counterpart in the paper; used for the roofline) ---- */
 
 /* Kernels of the multi-shift iteration, timed by sampling. */

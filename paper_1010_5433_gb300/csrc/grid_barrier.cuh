@@ -28,7 +28,7 @@ __device__ __forceinline__ unsigned int ld_acquire(const unsigned int* a) {
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
     return v;
 }
-__device__ __forceinline__ bool grid_sync(GridBar* b, unsigned int nblocks) {
+__device__ __forceinline__ bool grid_sync(GridBar* b, unsigned int nblocks, long long spin_limit = BAR_SPIN_LIMIT) {
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned int g0 = ld_acquire(&b->gen);
@@ -40,7 +40,7 @@ __device__ __forceinline__ bool grid_sync(GridBar* b, unsigned int nblocks) {
         } else {
             long long spins = 0;
             while (ld_acquire(&b->gen) == g0 && ld_acquire(&b->err) == 0) {
-                if (++spins > BAR_SPIN_LIMIT) {
+                if (++spins > spin_limit) {
                     atomicExch(&b->err, 1u);
                     break;
                 }

@@ -495,3 +495,28 @@ extern "C" stag_status stag_profile_phases(stag_ctx* ctx, double* us) {
     for (int i = 0; i < 6; ++i) us[i] = t[i] * 1e-3;
     return STAG_OK;
 }
+
+// ---- self-test of the bounded grid barrier: two blocks, only block 0
+// arrives, so its wait can only end by giving up after spin_limit polls
+namespace {
+__global__ void k_barrier_timeout_probe(GridBar* bar, long long spin_limit, int* status) {
+    if (blockIdx.x != 0) return;              // the block that never arrives
+    const bool met = grid_sync(bar, gridDim.x, spin_limit);
+    if (threadIdx.x == 0) *status = met ? STAG_OK : STAG_ERR_TIMEOUT;
+}
+}  // namespace
+
+extern "C" stag_status stag_selftest_barrier_timeout(stag_ctx* ctx, long long spin_limit) {
+    if (!ctx || spin_limit < 1 || spin_limit > BAR_SPIN_LIMIT) return STAG_ERR_ARG;
+    if (!ctx->bar) CKS(dev_alloc(ctx, &ctx->bar, sizeof(GridBar)));
+    int* d_status;
+    CKS(ws_get(ctx, WS_MISC, sizeof(int), (void**)&d_status));
+    CK(cudaMemsetAsync(ctx->bar, 0, sizeof(GridBar), ctx->stream));
+    k_barrier_timeout_probe<<<2, 32, 0, ctx->stream>>>((GridBar*)ctx->bar, spin_limit, d_status);
+    CKL();
+    int st = -1;
+    CK(cudaMemcpyAsync(&st, d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemsetAsync(ctx->bar, 0, sizeof(GridBar), ctx->stream));
+    return (stag_status)st;
+}

@@ -101,6 +101,7 @@ def lib():
             "stag_md_trajectory": ([vp, C.POINTER(stag_hmc), C.POINTER(stag_traj)], i),
             "stag_multishift_solve_batch": ([C.POINTER(vp), i, d, i, vp, i, C.POINTER(vp), C.POINTER(vp), d, i,
                                              C.POINTER(stag_solve_info)], i),
+            "stag_selftest_barrier_timeout": ([vp, C.c_longlong], i),
             "stag_profile_batch_phases": ([vp, i, C.POINTER(d)], i),
             "stag_batch_shape": ([vp, i, C.POINTER(i), C.POINTER(i)], i),
             "stag_md_trajectory_batch": ([C.POINTER(vp), i, C.POINTER(stag_hmc), C.POINTER(stag_traj)], i),
@@ -306,6 +307,11 @@ def stag_profile_read(ctx, kind):
     out = stag_kernel_profile()
     _check(lib().stag_profile_read(ctx, int(kind), C.byref(out)), "stag_profile_read", ctx)
     return out
+
+
+def stag_selftest_barrier_timeout(ctx, spin_limit):
+    """Status of the barrier self-test (STAG_ERR_TIMEOUT = 5 when the bounded wait gave up)."""
+    return lib().stag_selftest_barrier_timeout(ctx, int(spin_limit))
 
 
 def stag_profile_batch_phases(ctx, prec):

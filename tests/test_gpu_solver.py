@@ -173,3 +173,30 @@ def test_shift_count_extremes_fp64(torch, nshift):
         assert abs(info.iterations - its) <= 3
     finally:
         stag.stag_destroy(ctx)
+
+
+def test_barrier_wait_gives_up_and_context_stays_usable(torch):
+    """Failure detection without a fault: a grid barrier that one of its two
+    blocks never reaches; the waiting block's bounded wait gives up, the
+    library reports STAG_ERR_TIMEOUT, and the same context then solves as
+    before (fp64, checked with the oracle)."""
+    from paper_1010_5433_gb300 import stag
+    dims = (4, 4, 4, 4)
+    u, eta, par = _setup(dims, 91)
+    b = syn.gaussian_fermion(dims, 92, on_parity=0)
+    ctx = stag.stag_create(dims, True)
+    try:
+        assert stag.stag_selftest_barrier_timeout(ctx, 0) == 1           # bad limit: argument error
+        assert stag.stag_selftest_barrier_timeout(ctx, 1 << 14) == 5     # the wait ran out
+        assert stag.stag_selftest_barrier_timeout(ctx, 1 << 12) == 5     # and again, same context
+        torch.cuda.synchronize()
+        stag.stag_load_gauge(ctx, L.gauge_host(u))
+        d_b = dev(torch, L.to_half(b, dims, 0)[None])
+        d_x = torch.empty((1, 2) + tuple(d_b.shape[1:]), dtype=torch.float64, device="cuda")
+        stag.stag_multishift_solve(ctx, 0.1, [0.0, 0.5], 0, 1, d_b, d_x, 1e-12, 5000)
+        xs, _, _ = solvers.multishift_cg(lambda v: dirac.a_op(u, v, 0.1, eta, par, 0.0), b, [0.0, 0.5], 1e-12)
+        got = host_complex(d_x).reshape(2, 3, -1)
+        for s in range(2):
+            assert L.rel_err(got[s], L.to_half(xs[s], dims, 0)) < 1e-10
+    finally:
+        stag.stag_destroy(ctx)

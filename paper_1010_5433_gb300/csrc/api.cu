@@ -131,6 +131,9 @@ extern "C" stag_status stag_create(const stag_lattice* lat, stag_ctx** out) {
     // STAG_BATCH_SHAPE=0|1|2 fixes the batched solver's launch shape instead of tuning
     const char* bs = std::getenv("STAG_BATCH_SHAPE");
     ctx->batch_shape_force = bs ? std::atoi(bs) : -1;
+    // STAG_PERSIST_SITES=n: the persistent solver gives every block at least n sites
+    const char* ps = std::getenv("STAG_PERSIST_SITES");
+    ctx->persist_sites = ps ? std::atoi(ps) : 0;
     stag_status s = STAG_OK;
     size_t gbytes = (size_t)4 * 2 * 18 * ctx->g.Vh * sizeof(float);
     size_t bbytes = (size_t)4 * 2 * 12 * ctx->g.Vh * sizeof(uint16_t);

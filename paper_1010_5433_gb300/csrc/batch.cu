@@ -396,6 +396,7 @@ __global__ void __launch_bounds__(PB, MB) k_ms_persistent_batch(BatchArgs A, dou
     }
     __syncthreads();
     const unsigned int nb = gridDim.x;
+    GridSync gs{bar, nb, 0u};
     const long long nthreads = (long long)gridDim.x * blockDim.x;
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     bool ok = true;
@@ -417,7 +418,7 @@ __global__ void __launch_bounds__(PB, MB) k_ms_persistent_batch(BatchArgs A, dou
             off += g.Vh;
         }
         PHASE_MARK(0)
-        if (!(ok = grid_sync(bar, nb))) break;
+        if (!(ok = grid_sync(gs))) break;
         PHASE_MARK(1)
         // ---- phase 2: p = r + beta p; q = (A + s0) p; (p, q)
         double dots[MAXC];
@@ -441,7 +442,7 @@ __global__ void __launch_bounds__(PB, MB) k_ms_persistent_batch(BatchArgs A, dou
         if (threadIdx.x == 0)
             for (int j = 0; j < nc; ++j) partial[(size_t)j * nb + blockIdx.x] = dots[j];
         PHASE_MARK(2)
-        if (!(ok = grid_sync(bar, nb))) break;
+        if (!(ok = grid_sync(gs))) break;
         PHASE_MARK(3)
         sum_partials_m(S, partial, nb, nc, 0);
         alpha_step_m(S, nc, P);
@@ -466,7 +467,7 @@ __global__ void __launch_bounds__(PB, MB) k_ms_persistent_batch(BatchArgs A, dou
         if (threadIdx.x == 0)
             for (int j = 0; j < nc; ++j) partial[(size_t)(MAXC + j) * nb + blockIdx.x] = nrm[j];
         PHASE_MARK(5)
-        if (!(ok = grid_sync(bar, nb))) break;
+        if (!(ok = grid_sync(gs))) break;
         PHASE_MARK(6)
         sum_partials_m(S, partial, nb, nc, MAXC);
         beta_step_m(S, nc, P);

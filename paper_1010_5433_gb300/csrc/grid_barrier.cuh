@@ -1,7 +1,8 @@
 // Grid-wide barrier of the persistent (cooperative) solver kernels, with
 // every wait bounded: after BAR_SPIN_LIMIT polls a block sets the error word
-// and every block leaves its loop, so a launch that cannot meet its barrier
-// ends instead of hanging; the host reports STAG_ERR_TIMEOUT.
+// and leaves its loop, every other block sees the word while it polls and
+// leaves too, so a launch that cannot meet its barrier ends instead of
+// hanging; the host reports STAG_ERR_TIMEOUT.
 #pragma once
 
 namespace {
@@ -9,46 +10,66 @@ namespace {
 constexpr long long BAR_SPIN_LIMIT = 1LL << 26;   // ~0.1-1 s of polling
 
 struct GridBar {
-    unsigned int count;
-    unsigned int gen;
-    unsigned int err;
-    unsigned int pad;
+    unsigned int count;   // arrivals since the launch began
+    unsigned int err;     // set by a block whose wait gave up
+    unsigned int pad[2];
 };
 
-// Generation barrier over all blocks of a cooperative launch, with gpu-scope
-// release/acquire atomics: a block's writes are released by its arrival and
-// acquired by every block that sees the generation advance.
-__device__ __forceinline__ unsigned int atom_add_release(unsigned int* a, unsigned int v) {
-    unsigned int old;
-    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(a), "r"(v) : "memory");
-    return old;
+// Counting barrier over all blocks of a cooperative launch.  The counter only
+// grows within a launch (the host zeroes it before each one): every block
+// adds 1 with a gpu-scope release at each barrier and waits, with acquire
+// loads, until the counter reaches nblocks x (barriers it has passed), so a
+// block's writes before the barrier are visible to every block after it.
+// One fire-and-forget arrival and the polls are the whole cost: no read of a
+// generation word before arriving, no reset by the last block, no read of the
+// error word once the barrier is met.
+__device__ __forceinline__ void red_add_release(unsigned int* a, unsigned int v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(a), "r"(v) : "memory");
 }
 __device__ __forceinline__ unsigned int ld_acquire(const unsigned int* a) {
     unsigned int v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
     return v;
 }
-__device__ __forceinline__ bool grid_sync(GridBar* b, unsigned int nblocks, long long spin_limit = BAR_SPIN_LIMIT) {
+__device__ __forceinline__ unsigned int ld_relaxed(const unsigned int* a) {
+    unsigned int v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+    return v;
+}
+
+// one per block, in registers: the barrier, the grid size, and the counter
+// value that ends the block's next wait
+struct GridSync {
+    GridBar* b;
+    unsigned int nblocks;
+    unsigned int target;
+};
+
+// false when the wait gave up (after spin_limit polls, this block sets the
+// error word) or another block had given up: the caller leaves its loop
+__device__ __forceinline__ bool grid_sync(GridSync& s, long long spin_limit = BAR_SPIN_LIMIT) {
+    __shared__ int s_met;
     __syncthreads();
+    s.target += s.nblocks;
     if (threadIdx.x == 0) {
-        const unsigned int g0 = ld_acquire(&b->gen);
-        const unsigned int arrived = atom_add_release(&b->count, 1u);
-        if (arrived == nblocks - 1) {
-            // everyone has arrived (and released); reset, then open the next generation
-            asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(&b->count), "r"(0u) : "memory");
-            atom_add_release(&b->gen, 1u);
-        } else {
-            long long spins = 0;
-            while (ld_acquire(&b->gen) == g0 && ld_acquire(&b->err) == 0) {
-                if (++spins > spin_limit) {
-                    atomicExch(&b->err, 1u);
-                    break;
-                }
+        red_add_release(&s.b->count, 1u);
+        int met = 1;
+        long long spins = 0;
+        while ((int)(ld_acquire(&s.b->count) - s.target) < 0) {
+            if (++spins > spin_limit) {
+                atomicExch(&s.b->err, 1u);
+                met = 0;
+                break;
+            }
+            if ((spins & 31) == 0 && ld_relaxed(&s.b->err) != 0) {
+                met = 0;
+                break;
             }
         }
+        s_met = met;
     }
     __syncthreads();
-    return *(volatile unsigned int*)&b->err == 0;
+    return s_met != 0;
 }
 
 __device__ __forceinline__ unsigned long long gtimer() {

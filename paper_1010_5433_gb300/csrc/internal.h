@@ -117,6 +117,7 @@ struct stag_ctx {
                                       // ([0,8) single lattice, [8,16) batched fp32, [16,24) batched float-float)
     BatchTune batch_tune[4];          // batched solver launch shape per precision (this context leading)
     int batch_shape_force = -1;       // STAG_BATCH_SHAPE=0|1|2: fixed shape, no tuning
+    int persist_sites = 0;            // STAG_PERSIST_SITES=n: at least n sites per block of the persistent solver (0: the default)
     // force surrogate
     float* sur_w = nullptr;           // device parameters (weights rounded to bf16)
     unsigned int* sur_err = nullptr;  // set by a tensor-core surrogate launch that gave up a wait

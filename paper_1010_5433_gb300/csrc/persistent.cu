@@ -32,11 +32,11 @@ struct Scal {
     double dsig[STAG_MAX_SHIFTS];
     double rr[STAG_MAX_RHS], bb[STAG_MAX_RHS], rr_ref[STAG_MAX_RHS];
     double alpha[STAG_MAX_RHS], alpha_prev[STAG_MAX_RHS], beta_prev[STAG_MAX_RHS], beta[STAG_MAX_RHS];
-    double sums[STAG_MAX_RHS];
+    double sums[STAG_MAX_RHS], units[STAG_MAX_RHS];
     double k4_units, c0, tol2, delta2;
     int live[STAG_MAX_RHS][STAG_MAX_SHIFTS], iters_at[STAG_MAX_RHS][STAG_MAX_SHIFTS];
     int rhs_live[STAG_MAX_RHS], left[STAG_MAX_RHS];
-    int k, halt, status, need_reliable, nrhs, nshift, max_iter, mixed, any;
+    int k, halt, status, need_reliable, nrhs, nshift, max_iter, mixed;
 };
 
 __device__ void load_scal(Scal& S, const SolverState* st) {
@@ -110,100 +110,108 @@ __device__ void store_scal(const Scal& S, SolverState* st) {
     }
 }
 
-// every block: S.sums[q] = sum of partial[off + q][0..nb) for every source q,
-// warp q summing source q (lane l adds the partials l, l + 32, ..., then a
-// fixed shuffle tree), so every block gets the same bits
-__device__ void sum_partials(Scal& S, const double* partial, int nb, int off) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (warp < S.nrhs) {
-        double v = 0.0;
-        const double* p = partial + (size_t)(off + warp) * nb;
-        for (int i = lane; i < nb; i += 32) v += __ldcg(p + i);
+// Warp q of every block: the sum of source q's per-block partials
+// partial[off + q][0..nb) (lane l adds the partials l, l + 32, ..., then a
+// fixed shuffle tree), so every block gets the same bits, broadcast to the
+// warp's lanes.
+__device__ __forceinline__ double warp_partial_sum(const double* partial, int nb, int off, int q) {
+    const int lane = threadIdx.x & 31;
+    double v = 0.0;
+    const double* p = partial + (size_t)(off + q) * nb;
+    for (int i = lane; i < nb; i += 32) v += __ldcg(p + i);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) S.sums[warp] = v;
-    }
-    __syncthreads();
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return __shfl_sync(0xffffffffu, v, 0);
 }
 
-__device__ void alpha_step(Scal& S) {
-    const int t = threadIdx.x;
-    if (t < S.nrhs && S.rhs_live[t]) {
-        double a = S.rr[t] / S.sums[t];
-        if (!isfinite(a) || !(S.sums[t] > 0.0)) {
-            S.status = STAG_ERR_NAN;
-            S.halt = 1;
-            a = 0.0;
+// alpha = (r, r) / (p, A p) of every source and the shifted-system
+// coefficients (Jegerlehner's zeta recurrence), warp q for source q with
+// lane s for shift s (STAG_MAX_SHIFTS = 32), one block barrier at the end
+__device__ void alpha_step(Scal& S, const double* partial, int nb, int off) {
+    static_assert(STAG_MAX_SHIFTS <= 32, "a lane per shift");
+    const int q = threadIdx.x >> 5, s = threadIdx.x & 31;
+    if (q < S.nrhs && S.rhs_live[q]) {
+        const double pq = warp_partial_sum(partial, nb, off, q);
+        double a = S.rr[q] / pq;
+        const bool bad = !isfinite(a) || !(pq > 0.0);
+        if (bad) a = 0.0;
+        if (s < S.nshift && S.live[q][s]) {
+            const double ap = S.alpha_prev[q], bp = S.beta_prev[q];
+            const double z = S.zeta[q][s], zp = S.zeta_prev[q][s];
+            // one division: zeta_{k+1} / zeta_k = zeta_{k-1} alpha_{k-1} / den
+            const double den = a * bp * (zp - z) + zp * ap * (1.0 + S.dsig[s] * a);
+            const double zr = zp * ap / den;
+            S.zeta_next[q][s] = z * zr;
+            S.zratio[q][s] = zr;
+            S.cx[q][s] = a * zr;
         }
-        S.alpha[t] = a;
-    }
-    __syncthreads();
-    for (int i = t; i < S.nrhs * STAG_MAX_SHIFTS; i += blockDim.x) {
-        const int q = i / STAG_MAX_SHIFTS, s = i % STAG_MAX_SHIFTS;
-        if (s >= S.nshift || !S.rhs_live[q] || !S.live[q][s]) continue;
-        const double a = S.alpha[q], ap = S.alpha_prev[q], bp = S.beta_prev[q];
-        const double z = S.zeta[q][s], zp = S.zeta_prev[q][s];
-        // one division: zeta_{k+1} / zeta_k = zeta_{k-1} alpha_{k-1} / den
-        const double den = a * bp * (zp - z) + zp * ap * (1.0 + S.dsig[s] * a);
-        const double zr = zp * ap / den;
-        S.zeta_next[q][s] = z * zr;
-        S.zratio[q][s] = zr;
-        S.cx[q][s] = a * zr;
+        if (s == 0) {
+            S.sums[q] = pq;
+            S.alpha[q] = a;
+            if (bad) {
+                S.status = STAG_ERR_NAN;
+                S.halt = 1;
+            }
+        }
     }
     __syncthreads();
 }
 
-__device__ void beta_step(Scal& S) {
-    const int t = threadIdx.x;
-    __shared__ double s_beta[STAG_MAX_RHS];
-    if (t == 0) S.any = 0;
-    if (t < S.nrhs) {
-        S.left[t] = 0;
-        if (S.rhs_live[t]) {
-            const double rn = S.sums[t];
+// beta = (r', r') / (r, r), the shift coefficients of the next search
+// directions, per-shift convergence and the solver's halt conditions; warp q
+// for source q with lane s for shift s, then thread 0 for the whole solve
+__device__ void beta_step(Scal& S, const double* partial, int nb, int off) {
+    const int q = threadIdx.x >> 5, s = threadIdx.x & 31;
+    if (q < S.nrhs && S.rhs_live[q]) {
+        const double rn = warp_partial_sum(partial, nb, off, q);
+        const double bt = rn / S.rr[q];
+        const bool on = s < S.nshift && S.live[q][s];
+        const int n_live = __popc(__ballot_sync(0xffffffffu, on));
+        bool still = false;
+        if (on) {
+            const double zn = S.zeta_next[q][s], z = S.zeta[q][s];
+            const double zr = S.zratio[q][s];
+            S.cpr[q][s] = zn;
+            S.cpp[q][s] = bt * zr * zr;
+            S.zeta_prev[q][s] = z;
+            S.zeta[q][s] = zn;
+            if (zn * zn * rn <= S.tol2 * S.bb[q]) {
+                S.live[q][s] = 0;
+                S.iters_at[q][s] = S.k + 1;
+            } else {
+                still = true;
+            }
+        }
+        const bool left = __ballot_sync(0xffffffffu, still) != 0;
+        __syncwarp();
+        if (s == 0) {
             if (!isfinite(rn)) {
                 S.status = STAG_ERR_NAN;
                 S.halt = 1;
             }
-            s_beta[t] = rn / S.rr[t];
-            int n_live = 0;
-            for (int s = 0; s < S.nshift; ++s) n_live += S.live[t][s];
-            atomicAdd(&S.k4_units, 72.0 + 96.0 * n_live);
+            S.units[q] = 72.0 + 96.0 * n_live;
+            S.sums[q] = rn;
+            S.beta[q] = bt;
+            S.alpha_prev[q] = S.alpha[q];
+            S.beta_prev[q] = bt;
+            S.rr[q] = rn;
+            S.left[q] = left;
+            if (!left) S.rhs_live[q] = 0;
+            else if (S.mixed && rn < S.delta2 * S.rr_ref[q]) S.need_reliable = 1;
         }
+    } else if (q < S.nrhs && s == 0) {
+        S.left[q] = 0;
+        S.units[q] = 0.0;
     }
     __syncthreads();
-    for (int i = t; i < S.nrhs * STAG_MAX_SHIFTS; i += blockDim.x) {
-        const int q = i / STAG_MAX_SHIFTS, s = i % STAG_MAX_SHIFTS;
-        if (s >= S.nshift || !S.rhs_live[q] || !S.live[q][s]) continue;
-        const double zn = S.zeta_next[q][s], z = S.zeta[q][s];
-        const double zr = S.zratio[q][s];
-        S.cpr[q][s] = zn;
-        S.cpp[q][s] = s_beta[q] * zr * zr;
-        S.zeta_prev[q][s] = z;
-        S.zeta[q][s] = zn;
-        if (zn * zn * S.sums[q] <= S.tol2 * S.bb[q]) {
-            S.live[q][s] = 0;
-            S.iters_at[q][s] = S.k + 1;
-        } else {
-            atomicOr(&S.left[q], 1);
+    if (threadIdx.x == 0) {
+        int any = 0;
+        for (int j = 0; j < S.nrhs; ++j) {
+            any |= S.left[j];
+            S.k4_units += S.units[j];
         }
-    }
-    __syncthreads();
-    if (t < S.nrhs && S.rhs_live[t]) {
-        S.beta[t] = s_beta[t];
-        S.alpha_prev[t] = S.alpha[t];
-        S.beta_prev[t] = s_beta[t];
-        S.rr[t] = S.sums[t];
-        if (!S.left[t]) S.rhs_live[t] = 0;
-        else {
-            atomicOr(&S.any, 1);
-            if (S.mixed && S.sums[t] < S.delta2 * S.rr_ref[t]) S.need_reliable = 1;
-        }
-    }
-    __syncthreads();
-    if (t == 0) {
         S.k += 1;
-        if (!S.any) S.halt = 1;
+        if (!any) S.halt = 1;
         else if (S.k >= S.max_iter) { S.halt = 1; S.status = STAG_ERR_NOT_CONVERGED; }
         if (S.need_reliable) S.halt = 1;
     }
@@ -271,15 +279,19 @@ __global__ void __launch_bounds__(PB) k_ms_persistent(Geom g, LinkPtrs L, Solver
     }
     load_scal(S, st);
     const unsigned int nb = gridDim.x;
-    const int nthreads = gridDim.x * blockDim.x;
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    GridSync gs{bar, nb, 0u};
+    // this block's sites: a contiguous range, the half lattice split evenly
+    // over the grid in multiples of 8 sites (a 32-byte sector of an fp32
+    // field component), so every block of the grid has work
+    const int per = (int)((((size_t)g.Vh + nb - 1) / nb + 7) & ~(size_t)7);
+    const int h0 = min(g.Vh, (int)blockIdx.x * per), h1 = min(g.Vh, h0 + per);
     const size_t rs = (size_t)3 * g.Vh;
     const int nrhs = S.nrhs, ns = S.nshift;
     constexpr int ND = NRP == 1 ? 1 : STAG_MAX_RHS;   // per-thread sums kept
     bool ok = true;
     while (!S.halt && ok) {
         // ---- phase 1: t = D_oe (r + beta p), without the 1/2
-        for (int h = tid; h < g.Vh; h += nthreads) {
+        for (int h = h0 + (int)threadIdx.x; h < h1; h += PB) {
             Nbr n;
             site_neighbours(g, h, 1, n);
             for (int r0 = 0; r0 < nrhs; r0 += NRP) {
@@ -319,14 +331,14 @@ __global__ void __launch_bounds__(PB) k_ms_persistent(Geom g, LinkPtrs L, Solver
             }
         }
         PHASE_MARK(0)
-        if (!(ok = grid_sync(bar, nb))) break;
+        if (!(ok = grid_sync(gs))) break;
         PHASE_MARK(1)
         // ---- phase 2: p = r + beta p; q = c0 p - 1/4 (hops of t); (p, q)
         double dots[ND];
 #pragma unroll
         for (int j = 0; j < ND; ++j) dots[j] = 0.0;
         const R c0 = (R)S.c0;
-        for (int h = tid; h < g.Vh; h += nthreads) {
+        for (int h = h0 + (int)threadIdx.x; h < h1; h += PB) {
             Nbr n;
             site_neighbours(g, h, 0, n);
 #pragma unroll
@@ -376,15 +388,14 @@ __global__ void __launch_bounds__(PB) k_ms_persistent(Geom g, LinkPtrs L, Solver
         if (threadIdx.x == 0)
             for (int j = 0; j < nrhs && j < ND; ++j) partial[(size_t)j * nb + blockIdx.x] = dots[j];
         PHASE_MARK(2)
-        if (!(ok = grid_sync(bar, nb))) break;
-        sum_partials(S, partial, nb, 0);
-        alpha_step(S);
+        if (!(ok = grid_sync(gs))) break;
+        alpha_step(S, partial, nb, 0);
         PHASE_MARK(3)
         // ---- phase 3: shift updates and r -= alpha q with (r, r)
         double nrm[ND];
 #pragma unroll
         for (int j = 0; j < ND; ++j) nrm[j] = 0.0;
-        for (int h = tid; h < g.Vh; h += nthreads) {
+        for (int h = h0 + (int)threadIdx.x; h < h1; h += PB) {
 #pragma unroll
             for (int j = 0; j < ND; ++j) {
                 if (j >= nrhs || !S.rhs_live[j]) continue;
@@ -406,9 +417,8 @@ __global__ void __launch_bounds__(PB) k_ms_persistent(Geom g, LinkPtrs L, Solver
         if (threadIdx.x == 0)
             for (int j = 0; j < nrhs && j < ND; ++j) partial[(size_t)(STAG_MAX_RHS + j) * nb + blockIdx.x] = nrm[j];
         PHASE_MARK(4)
-        if (!(ok = grid_sync(bar, nb))) break;
-        sum_partials(S, partial, nb, STAG_MAX_RHS);
-        beta_step(S);
+        if (!(ok = grid_sync(gs))) break;
+        beta_step(S, partial, nb, STAG_MAX_RHS);
         PHASE_MARK(5)
     }
 #undef PHASE_MARK
@@ -432,8 +442,10 @@ stag_status launch_persistent_pb(stag_ctx* ctx, void* r, void* p, void* q, void*
     int dev = 0, nsm = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    // one site per thread where the lattice allows, never more blocks than co-reside
-    long long want = nblocks(ctx->g.Vh, PB);
+    // one site per thread where the lattice allows (or at least persist_sites
+    // sites per block), never more blocks than co-reside
+    const long long spb = ctx->persist_sites > 0 ? ctx->persist_sites : PB;
+    long long want = ((long long)ctx->g.Vh + spb - 1) / spb;
     long long cap = (long long)nsm * per_sm;
     int grid = (int)(want < cap ? want : cap);
     if (grid < 1) grid = 1;
@@ -501,7 +513,8 @@ extern "C" stag_status stag_profile_phases(stag_ctx* ctx, double* us) {
 namespace {
 __global__ void k_barrier_timeout_probe(GridBar* bar, long long spin_limit, int* status) {
     if (blockIdx.x != 0) return;              // the block that never arrives
-    const bool met = grid_sync(bar, gridDim.x, spin_limit);
+    GridSync gs{bar, gridDim.x, 0u};
+    const bool met = grid_sync(gs, spin_limit);
     if (threadIdx.x == 0) *status = met ? STAG_OK : STAG_ERR_TIMEOUT;
 }
 }  // namespace

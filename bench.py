@@ -151,6 +151,13 @@ def job_rate(world, steps, seconds):
     return world * steps / seconds * 3600.0
 
 
+# link format of the fp32 MD inversions (the fp64 heatbath / Metropolis
+# inversions always use the two-float store): stag_prec value, description.
+# The paper stores two rows of every link and rebuilds the third (Sec. 5).
+MD_LINKS = {"18": (1, "fp32, 18 reals per link"), "12": (2, "fp32, 12 reals per link (row 3 rebuilt)"),
+            "bf16": (3, "bf16, 12 reals per link (row 3 rebuilt), fp32 arithmetic")}
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     import synthetic as syn
@@ -166,18 +173,19 @@ def run_gpu(args, rank, world, local_rank):
     seed = replica_seed(w["seed"], rank)
     ctx = stag.stag_create(dims, True, stream.cuda_stream)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    md_prec = MD_LINKS[args.md_links][0]
 
     # start: Haar-random links, quenched thermalisation (no fermions), then warm-up trajectories
     u0 = syn.haar_gauge(dims, seed)     # [mu, t, z, y, x, 3, 3] = the host layout of the C ABI
     stag.stag_load_gauge(ctx, np.ascontiguousarray(u0).reshape(-1).view(np.float64))
     del u0
     for k in range(w["quenched_thermalisation"]):
-        p = make_hmc(stag, rats, stag.STAG_FP32, seed, 10_000 + k, n_flavours=0)
+        p = make_hmc(stag, rats, md_prec, seed, 10_000 + k, n_flavours=0)
         stag.stag_md_trajectory(ctx, p)
     counter = 0
     warm = []
     for k in range(args.warmup):
-        warm.append(stag.stag_md_trajectory(ctx, make_hmc(stag, rats, stag.STAG_FP32, seed, counter)))
+        warm.append(stag.stag_md_trajectory(ctx, make_hmc(stag, rats, md_prec, seed, counter)))
         counter += 1
     start_field = np.empty(4 * V * 18)
     stag.stag_store_gauge(ctx, start_field)
@@ -213,7 +221,7 @@ def run_gpu(args, rank, world, local_rank):
 
 
     # ---- the mixed path (headline)
-    ms, trajs, clocks, launches, prof = timed(stag.STAG_FP32, args.steps, counter, True)
+    ms, trajs, clocks, launches, prof = timed(md_prec, args.steps, counter, True)
     ms = max_over_ranks(ms, world, dev)
     counter += args.steps
     value = job_rate(world, args.steps, ms / 1e3)
@@ -233,7 +241,7 @@ def run_gpu(args, rank, world, local_rank):
     t0 = time.perf_counter()
     for k in range(args.steps):
         stag.stag_load_gauge(ctx, hnp)                                   # H2D of the configuration
-        stag.stag_md_trajectory(ctx, make_hmc(stag, rats, stag.STAG_FP32, seed, 5000 + k))
+        stag.stag_md_trajectory(ctx, make_hmc(stag, rats, md_prec, seed, 5000 + k))
         stag.stag_store_gauge(ctx, hnp)                                  # D2H of the updated configuration
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
@@ -273,6 +281,7 @@ def run_gpu(args, rank, world, local_rank):
         "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": w["workload"], "lattice": "16^4", "global_batch": world, "l2": "flushed between steps",
+                   "md_links": MD_LINKS[args.md_links][1],
                    "parallelism": f"replicas{world}" if world > 1 else "single"},
         "roofline": roofline,
         "e2e": {"value": round(e2e, 2), "unit": "trajectories/hour", "h2d_bytes_per_step": V * 4 * 18 * 8,
@@ -386,6 +395,8 @@ def main():
     ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--md-links", default="12", choices=sorted(MD_LINKS),
+                    help="link format of the fp32 MD inversions (the paper's: 12 reals)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -159,15 +159,42 @@ __global__ void __launch_bounds__(FB) k_gauge_force(Geom g, LinkPtrs L, double b
 }
 
 // ---------------------------------------------------------------- link update + reunitarisation
+// Conversions between float and double by integer operations on the IEEE-754
+// bit patterns, with the results of the conversion instructions (round to
+// nearest even): those instructions issue on GB300's FP64 pipe, which is
+// ~1/64 of the FP32 rate, and made up about half of the link update's FP64
+// work.  Zeros, results outside the float normal range, Inf and NaN take the
+// instruction.
+__device__ __forceinline__ float f64_to_f32_rn(double d) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const int e = (int)((b >> 52) & 0x7FF) - 1023 + 127;    // float exponent field
+    if (e <= 0 || e >= 255) return __double2float_rn(d);
+    const unsigned int sign = (unsigned int)(b >> 63) << 31;
+    const unsigned int top = (unsigned int)((b >> 29) & 0x7FFFFFull);   // the 23 kept mantissa bits
+    const unsigned int rest = (unsigned int)(b & 0x1FFFFFFFull);        // the 29 dropped ones
+    const unsigned int up = (rest > 0x10000000u || (rest == 0x10000000u && (top & 1u))) ? 1u : 0u;
+    // a carry out of the mantissa steps the exponent (to Inf past the largest float)
+    return __uint_as_float(sign | ((((unsigned int)e << 23) | top) + up));
+}
+__device__ __forceinline__ double f32_to_f64(float f) {
+    const unsigned int u = __float_as_uint(f);
+    const unsigned int e = (u >> 23) & 0xFFu;
+    if (e == 0u || e == 0xFFu) return (double)f;
+    return __longlong_as_double((long long)(((unsigned long long)(u >> 31) << 63) |
+                                            ((unsigned long long)(e - 127u + 1023u) << 52) |
+                                            ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+}
+
+// hi = the double rounded to float, lo = the (exact) remainder rounded to float
 __device__ __forceinline__ void store_link_hl(float* hi, float* lo, size_t blk, int h, int Vh, const Su3<double>& u) {
     float vh[18], vl[18];
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
         double re = u.e[k / 3][k % 3].re, im = u.e[k / 3][k % 3].im;
-        float a = (float)re, b = (float)im;
+        float a = f64_to_f32_rn(re), b = f64_to_f32_rn(im);
         vh[2 * k] = a; vh[2 * k + 1] = b;
-        vl[2 * k] = (float)(re - (double)a);
-        vl[2 * k + 1] = (float)(im - (double)b);
+        vl[2 * k] = f64_to_f32_rn(re - f32_to_f64(a));
+        vl[2 * k + 1] = f64_to_f32_rn(im - f32_to_f64(b));
     }
     float4* h4 = reinterpret_cast<float4*>(hi + blk);
     float4* l4 = reinterpret_cast<float4*>(lo + blk);
@@ -261,6 +288,9 @@ __device__ __forceinline__ Su3<R> expi(const Su3<R>& hm, R eps) {
     return e;
 }
 
+__device__ __forceinline__ double to_f64(float f) { return f32_to_f64(f); }
+__device__ __forceinline__ double to_f64(double d) { return d; }
+
 // U <- reunitarise(exp(i eps P) U): the exponential and the product in R
 // (fp32 in the mixed path, Sec. 4), the reunitarisation always in fp64.
 template <typename R, int FMT, int ORDER>
@@ -280,7 +310,7 @@ __global__ void __launch_bounds__(FB) k_update_links(Geom g, float* hi, float* l
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) ud.e[i][j] = mk((double)un.e[i][j].re, (double)un.e[i][j].im);
+        for (int j = 0; j < 3; ++j) ud.e[i][j] = mk(to_f64(un.e[i][j].re), to_f64(un.e[i][j].im));
     reunit(ud);
     store_link_hl(hi, lo, link_block_f(mu, par, g.Vh), h, g.Vh, ud);
 }

@@ -203,7 +203,7 @@ def test_two_flavours_two_pseudofermions_match_oracle(torch, prec, tol_dh):
 def test_bench_configuration_trajectory_is_reversible(torch):
     """The 16^4, N_f = 2, m = 0.02, beta = 5.6 trajectory in the launch
     configuration bench.py times (12-pole MD rational of the product table,
-    n_outer 20 x n_gauge 5, fp32 MD): forward with supplied momenta and
+    n_outer 20 x n_gauge 5, fp32 MD on 12-real links): forward with supplied momenta and
     pseudo-fermions, then back from the flipped final momenta."""
     from paper_1010_5433_gb300 import rational, stag
     dims = (16, 16, 16, 16)
@@ -217,7 +217,7 @@ def test_bench_configuration_trajectory_is_reversible(torch):
         fl = p.flavour[0]
         fl.mass, fl.n_pf = 0.02, 1
         fl.hb, fl.md, fl.met = rats["hb"].to_abi(), rats["md"].to_abi(), rats["met"].to_abi()
-        p.tol_md, p.tol_met, p.max_iter, p.md_prec = 1e-8, 1e-12, 20000, stag.STAG_FP32
+        p.tol_md, p.tol_met, p.max_iter, p.md_prec = 1e-8, 1e-12, 20000, stag.STAG_FP32_12
         for k, v in kw.items():
             setattr(p, k, v)
         return p

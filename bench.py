@@ -313,7 +313,13 @@ def run_gpu(args, rank, world, local_rank):
 # ncu capture of the same kernel on the same 16^4 lattice; None once the
 # kernel has changed since the capture.  The capture is cold-cache (ncu
 # flushes caches between passes): one read of the working set, then L2 hits.
-NCU_TRAFFIC = {}    # the persistent kernel changed since its last capture: no figure until the next one
+NCU_TRAFFIC = {
+    "persistent_iteration": {
+        "bytes_per_unit": round((33.118464e6 + 0.10752e6) / 39),
+        "source": "profiles/persistent_fp32_12_16x4_ncu.md: dram__bytes_read+write over one 39-iteration launch "
+                  "of k_ms_persistent<float, FMT_F32_12>",
+    },
+}
 
 
 def batched_chains():

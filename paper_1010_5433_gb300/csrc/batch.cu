@@ -128,9 +128,7 @@ __device__ void store_scal_m(const ScalM* S, const ChainArgs* C, int nc) {
 __device__ void sum_partials_m(ScalM* S, const double* partial, int nb, int nc, int base) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp < nc) {
-        double v = 0.0;
-        const double* p = partial + (size_t)(base + warp) * nb;
-        for (int i = lane; i < nb; i += 32) v += __ldcg(p + i);
+        double v = lane_strided_sum(partial + (size_t)(base + warp) * nb, nb, lane);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         if (lane == 0) S[warp].sum = v;

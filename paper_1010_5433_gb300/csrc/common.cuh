@@ -476,6 +476,22 @@ __device__ __forceinline__ void block_sum(double (&v)[N]) {
 }
 
 // Sum n partials in a fixed order by the whole block; result in thread 0.
+// Lane `lane`'s share of a warp's sum of p[0..n): p[lane] + p[lane + 32] +
+// ..., added in that order, with the loads of up to 8 terms issued before
+// the first add (one L2 round trip instead of one per term).
+__device__ __forceinline__ double lane_strided_sum(const double* p, int n, int lane) {
+    double v = 0.0;
+    for (int i0 = lane; i0 < n; i0 += 32 * 8) {
+        double t[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) t[k] = (i0 + 32 * k < n) ? __ldcg(p + i0 + 32 * k) : 0.0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (i0 + 32 * k < n) v += t[k];
+    }
+    return v;
+}
+
 __device__ __forceinline__ double block_sum_array(const double* p, int n) {
     double v[1] = {0.0};
     for (int i = threadIdx.x; i < n; i += blockDim.x) v[0] += __ldcg(p + i);

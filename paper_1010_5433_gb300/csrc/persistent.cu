@@ -116,9 +116,7 @@ __device__ void store_scal(const Scal& S, SolverState* st) {
 // warp's lanes.
 __device__ __forceinline__ double warp_partial_sum(const double* partial, int nb, int off, int q) {
     const int lane = threadIdx.x & 31;
-    double v = 0.0;
-    const double* p = partial + (size_t)(off + q) * nb;
-    for (int i = lane; i < nb; i += 32) v += __ldcg(p + i);
+    double v = lane_strided_sum(partial + (size_t)(off + q) * nb, nb, lane);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     return __shfl_sync(0xffffffffu, v, 0);

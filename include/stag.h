@@ -80,7 +80,17 @@ typedef struct {
 /* ---- context and gauge field (Sec. 3: the configuration is copied to the
  *      device once and the whole update runs there) ---------------------- */
 
-/* Creates a context for one lattice.  *out receives the handle. */
+/* Creates a context for one lattice.  *out receives the handle.  The
+ * context reads these environment variables once, here (none is needed):
+ *   STAG_GRAPHS=0          the large-lattice solver loop as plain launches
+ *                          instead of a CUDA-graph WHILE loop
+ *   STAG_PERSISTENT=0      no persistent solver kernel on small lattices
+ *   STAG_DSLASH_TPS=n      threads per site of the standalone Dslash (1, 2,
+ *                          4 or 8) instead of the tuned value
+ *   STAG_BATCH_SHAPE=k     launch shape k (0, 1, 2) of the batched solver
+ *                          instead of the tuned one
+ *   STAG_PERSIST_SITES=n   at least n sites per block of the persistent
+ *                          solver (default: one site per thread) */
 stag_status stag_create(const stag_lattice* lat, stag_ctx** out);
 void        stag_destroy(stag_ctx* ctx);
 const char* stag_strerror(stag_status s);

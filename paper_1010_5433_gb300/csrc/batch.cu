@@ -20,6 +20,7 @@
 // candidates on the first segments of real solves.
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 
 #include "internal.h"
 #include "solver_state.cuh"
@@ -248,7 +249,9 @@ __device__ __forceinline__ int first_site(long long tid, long long off, long lon
     return (int)(d < 0 ? d + nthreads : d);
 }
 
-// phase 1 at odd site h: t = D_oe (r + beta p), without the 1/2
+// phase 1 at odd site h: t = D_oe (r + beta p), without the 1/2 (the
+// float-float hops loop over the directions: unrolled, the kernel outgrows
+// the instruction cache)
 template <typename R, int FMT>
 __device__ __forceinline__ void site_doe(const Geom& g, const LinkPtrs& L, int h, const typename V2T<R>::T* r,
                                          const typename V2T<R>::T* p, typename V2T<R>::T* t, R bt) {
@@ -256,7 +259,7 @@ __device__ __forceinline__ void site_doe(const Geom& g, const LinkPtrs& L, int h
     site_neighbours(g, h, 1, n);
     Vec3<R> acc;
     zero(acc);
-#pragma unroll
+#pragma unroll (std::is_same<R, DF>::value ? 1 : 4)
     for (int mu = 0; mu < 4; ++mu) {
 #pragma unroll
         for (int dir = 0; dir < 2; ++dir) {
@@ -285,7 +288,7 @@ __device__ __forceinline__ double site_a(const Geom& g, const LinkPtrs& L, int h
     site_neighbours(g, h, 0, n);
     Vec3<R> acc;
     zero(acc);
-#pragma unroll
+#pragma unroll (std::is_same<R, DF>::value ? 1 : 4)
     for (int mu = 0; mu < 4; ++mu) {
 #pragma unroll
         for (int dir = 0; dir < 2; ++dir) {

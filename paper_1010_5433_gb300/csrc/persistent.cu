@@ -17,6 +17,7 @@
 // sets an error word, leaves the loop, and the host reports STAG_ERR_TIMEOUT.
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 
 #include "internal.h"
 #include "solver_state.cuh"
@@ -286,6 +287,9 @@ __global__ void __launch_bounds__(PB) k_ms_persistent(Geom g, LinkPtrs L, Solver
     const size_t rs = (size_t)3 * g.Vh;
     const int nrhs = S.nrhs, ns = S.nshift;
     constexpr int ND = NRP == 1 ? 1 : STAG_MAX_RHS;   // per-thread sums kept
+    // float-float hops are long (compensated products): unrolled over the four
+    // directions the kernel outgrows the instruction cache, so they loop
+    constexpr int MU_UNROLL = std::is_same<R, DF>::value ? 1 : 4;
     bool ok = true;
     while (!S.halt && ok) {
         // ---- phase 1: t = D_oe (r + beta p), without the 1/2
@@ -300,7 +304,7 @@ __global__ void __launch_bounds__(PB) k_ms_persistent(Geom g, LinkPtrs L, Solver
                     zero(acc[j]);
                     bt[j] = (r0 + j < nrhs) ? (R)S.beta[r0 + j] : (R)0;
                 }
-#pragma unroll
+#pragma unroll MU_UNROLL
                 for (int mu = 0; mu < 4; ++mu) {
 #pragma unroll
                     for (int dir = 0; dir < 2; ++dir) {
@@ -345,7 +349,7 @@ __global__ void __launch_bounds__(PB) k_ms_persistent(Geom g, LinkPtrs L, Solver
                 Vec3<R> acc[NRP];
 #pragma unroll
                 for (int j = 0; j < NRP; ++j) zero(acc[j]);
-#pragma unroll
+#pragma unroll MU_UNROLL
                 for (int mu = 0; mu < 4; ++mu) {
 #pragma unroll
                     for (int dir = 0; dir < 2; ++dir) {

@@ -158,6 +158,12 @@ MD_LINKS = {"18": (1, "fp32, 18 reals per link"), "12": (2, "fp32, 12 reals per 
             "bf16": (3, "bf16, 12 reals per link (row 3 rebuilt), fp32 arithmetic")}
 
 
+def workload_config(world):
+    """The workload both arms report (the GPU arm adds how it ran)."""
+    return {"workload": WORKLOAD["workload"], "lattice": "x".join(str(d) for d in WORKLOAD["dims"]),
+            "global_batch": world, "parallelism": f"replicas{world}" if world > 1 else "single"}
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     import synthetic as syn
@@ -280,9 +286,7 @@ def run_gpu(args, rank, world, local_rank):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": w["workload"], "lattice": "16^4", "global_batch": world, "l2": "flushed between steps",
-                   "md_links": MD_LINKS[args.md_links][1],
-                   "parallelism": f"replicas{world}" if world > 1 else "single"},
+        "config": dict(workload_config(world), l2="flushed between steps", md_links=MD_LINKS[args.md_links][1]),
         "roofline": roofline,
         "e2e": {"value": round(e2e, 2), "unit": "trajectories/hour", "h2d_bytes_per_step": V * 4 * 18 * 8,
                 "d2h_bytes_per_step": V * 4 * 18 * 8},
@@ -424,7 +428,7 @@ def main():
                           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                           "ms_per_step": round(3.6e6 / v, 1), "higher_is_better": True, "scaling": "weak",
                           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                          "config": {"workload": WORKLOAD["workload"], "lattice": "16^4"},
+                          "config": workload_config(args.gpus),
                           "cpu_baseline": cb,
                           "e2e": {"value": round(v, 4), "unit": "trajectories/hour", "h2d_bytes_per_step": 0,
                                   "d2h_bytes_per_step": 0}}))

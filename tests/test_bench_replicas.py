@@ -1,7 +1,9 @@
-"""bench.py with N > 1 ranks (replicas: one independent chain per rank, no
-data-path collective), its host logic on CPU with two gloo ranks: the timing
-taken is the slowest rank's, the rate counts every rank's trajectories, the
-chains are seeded apart, and the reference arm runs on rank 0 only."""
+"""bench.py's host logic on CPU.  With N > 1 ranks (replicas: one
+independent chain per rank, no data-path collective), on two gloo ranks: the
+timing taken is the slowest rank's, the rate counts every rank's
+trajectories, the chains are seeded apart, and the reference arm runs on
+rank 0 only.  On one rank: the reference arm's JSON line (the oracle on the
+host cores) and the refusal of fewer than three warm-up steps."""
 import json
 import os
 import socket
@@ -61,3 +63,33 @@ def test_reference_arm_prints_on_rank_zero_only():
                        text=True, timeout=300)
     assert p.returncode == 0, p.stderr[-2000:]
     assert p.stdout.strip() == ""
+
+
+def test_reference_arm_prints_the_contract_line():
+    """bench.py --impl reference on one rank: one JSON line with the metric,
+    a positive rate from the oracle on the host cores, its cpu_baseline
+    record, an e2e record without copies, and the GPU arm's workload."""
+    env = dict(os.environ)
+    for k in ("RANK", "LOCAL_RANK", "WORLD_SIZE"):
+        env.pop(k, None)
+    p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "3"], env=env, capture_output=True, text=True, timeout=600)
+    assert p.returncode == 0, p.stderr[-2000:]
+    lines = [ln for ln in p.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    sys.path.insert(0, ROOT)
+    import bench
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "trajectories/hour"
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 1 and d["warmup"] == 3
+    assert d["config"] == bench.workload_config(1)
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": "trajectories/hour", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+
+
+def test_fewer_than_three_warmup_steps_are_refused():
+    p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--warmup", "2"],
+                       capture_output=True, text=True, timeout=300)
+    assert p.returncode == 2 and "--warmup" in p.stderr

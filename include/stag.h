@@ -92,10 +92,15 @@ typedef struct {
  *   STAG_PERSIST_SITES=n   at least n sites per block of the persistent
  *                          solver (default: one site per thread) */
 stag_status stag_create(const stag_lattice* lat, stag_ctx** out);
+/* Frees every device and pinned buffer of the context (NULL is a no-op);
+ * the caller's buffers are untouched.  Synchronises the context's stream. */
 void        stag_destroy(stag_ctx* ctx);
+/* Static text naming a status code. */
 const char* stag_strerror(stag_status s);
 /* Text of the last CUDA error seen by this context ("" if none). */
 const char* stag_last_cuda_error(stag_ctx* ctx);
+/* Later calls are ordered on cuda_stream (a cudaStream_t; NULL = legacy
+ * default stream); work already issued stays on the previous stream. */
 stag_status stag_set_stream(stag_ctx* ctx, void* cuda_stream);
 /* Device bytes the context currently holds. */
 size_t      stag_device_bytes(stag_ctx* ctx);
@@ -215,8 +220,11 @@ stag_status stag_plaquette(stag_ctx* ctx, double* plaq);
  * The trajectory draws its momenta with seed/counter of stag_hmc and the
  * sources of flavour f with stream 16 f; the Metropolis uniform is word 0
  * of block (seed, stream 3, index 0, counter). */
+/* Writes 8 x 4V momentum coefficients to the caller's DEVICE buffer mom. */
 stag_status stag_draw_momenta(stag_ctx* ctx, unsigned long long seed, unsigned long long counter,
                               double* mom);
+/* Writes n Gaussian sources ([n][3][Vh] fp64 complex, even sites) to the
+ * caller's DEVICE buffer xi. */
 stag_status stag_draw_sources(stag_ctx* ctx, unsigned long long seed, unsigned long long counter,
                               int stream, int n, void* xi);
 
@@ -307,6 +315,7 @@ const double* stag_momenta(stag_ctx* ctx);
 /* Set the weights (host array of STAG_SUR_PARAMS floats; weights are rounded
  * to bf16 on the device, the fp32 values kept as Adam's master copy). */
 stag_status stag_surrogate_load(stag_ctx* ctx, const float* params);
+/* Copies the fp32 master weights to a host array of STAG_SUR_PARAMS floats. */
 stag_status stag_surrogate_store(stag_ctx* ctx, float* params);
 /* F^ of the loaded field (momentum layout, written). */
 stag_status stag_surrogate_force(stag_ctx* ctx, double* force);
@@ -316,6 +325,7 @@ stag_status stag_surrogate_add_force_sample(stag_ctx* ctx, const double* exact_f
 /* Same, with the target computed here: the exact MD fermion force of the
  * flavours of p for pseudo-fermions from the heatbath with Philox counter. */
 stag_status stag_surrogate_add_sample(stag_ctx* ctx, const stag_hmc* p, unsigned long long counter);
+/* Number of training samples (configurations) stored; 0 for a NULL ctx. */
 long long   stag_surrogate_samples(stag_ctx* ctx);
 /* Mean over stored links of |F^ - F|^2 and its gradient (host, STAG_SUR_PARAMS doubles, may be NULL). */
 stag_status stag_surrogate_loss_grad(stag_ctx* ctx, double* loss, double* grad);

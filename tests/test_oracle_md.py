@@ -122,3 +122,57 @@ def test_exp_minus_dh_averages_to_one():
     vals = np.array(vals)
     err = vals.std() / np.sqrt(len(vals))
     assert abs(vals.mean() - 1.0) < 4 * err + 0.02, (vals.mean(), err)
+
+
+def _two_flavour_params(dims, n_outer, n_gauge=2, tau=0.5):
+    """N_f = 2 + 1 with two pseudo-fermions each: s = N_f / (4 n_pf)."""
+    fls = []
+    for mass, nf in ((0.2, 2), (0.5, 1)):
+        s = nf / 8.0
+        lo, hi = mass ** 2, 16 + mass ** 2
+        fls.append(integrator.Flavour(mass=mass, n_pf=2,
+                                      hb=rational.remez(-s / 2, lo, hi, 8, dps=40),
+                                      md=rational.remez(s, lo, hi, 6, dps=40),
+                                      met=rational.remez(s, lo, hi, 10, dps=40)))
+    return integrator.HMCParams(dims=dims, beta=5.5, tau=tau, n_outer=n_outer, n_gauge=n_gauge,
+                                flavours=fls, tol_md=1e-13, tol_met=1e-14)
+
+
+def _sources(dims, seed):
+    return [[syn.gaussian_fermion(dims, seed + 10 * f + k, on_parity=0) for k in range(2)] for f in range(2)]
+
+
+def test_heatbath_and_metropolis_rationals_agree_for_every_pseudo_fermion():
+    """phi = r_hb(A) xi with r_hb ~ A^(s/2) and r_met ~ A^(-s) give
+    phi^dag r_met(A) phi = xi^dag xi up to the two approximations' errors,
+    for each flavour and pseudo-fermion (a wrong exponent or sign in either
+    rational, or a flavour's mass crossed, breaks it by orders of magnitude)."""
+    dims = (2, 2, 2, 4)
+    p = _two_flavour_params(dims, 2)
+    ctx = integrator.Context(p)
+    u = syn.near_identity_gauge(dims, 111)
+    xis = _sources(dims, 112)
+    phis = integrator.heatbath(ctx, u, xis)
+    for fl, xl, pl in zip(p.flavours, xis, phis):
+        bound = 2 * fl.hb.err + fl.met.err + 1e-10
+        for xi, phi in zip(xl, pl):
+            want = float(np.real(np.vdot(xi, xi)))
+            got = integrator.Context(integrator.HMCParams(dims=dims, beta=p.beta, tau=p.tau, n_outer=1, n_gauge=1,
+                                                           flavours=[fl], tol_md=p.tol_md, tol_met=p.tol_met)
+                                     ).fermion_action_total(u, [[phi]], p.tol_met)
+            assert abs(got - want) < 3 * bound * want, (got, want, bound)
+
+
+def test_dh_scales_as_step_squared_two_flavours_two_pseudo_fermions():
+    """The summed force of 2 flavours x 2 pseudo-fermions is the gradient of
+    the summed action: dH = O(eps^2).  Dropping or double-counting one term
+    leaves dH at a constant instead."""
+    dims = (2, 2, 2, 2)
+    dhs = []
+    for n in (4, 8):
+        p = _two_flavour_params(dims, n, n_gauge=4, tau=0.5)
+        out = integrator.trajectory(integrator.Context(p), syn.near_identity_gauge(dims, 121),
+                                    syn.gaussian_momenta(dims, 122), _sources(dims, 123))
+        dhs.append(abs(out["dH"]))
+    ratio = dhs[0] / dhs[1]
+    assert 2.5 < ratio < 6.5, dhs

@@ -369,6 +369,11 @@ stag_status stag_profile_read(stag_ctx* ctx, int kind, stag_kernel_profile* out)
  * threads per block and the blocks per SM requested of the register
  * allocator; -1 while still tuning. */
 int stag_batch_shape(stag_ctx* ctx, stag_prec prec, int* threads_per_block, int* blocks_per_sm);
+/* sizeof of the ABI's structs, for a binding to check its layouts against
+ * (no device needed): which = 0 stag_lattice, 1 stag_rational,
+ * 2 stag_solve_info, 3 stag_flavour, 4 stag_hmc, 5 stag_traj,
+ * 6 stag_kernel_profile; 0 for any other value. */
+size_t stag_abi_sizeof(int which);
 /* Persistent solver only: microseconds that block 0 spent since
  * stag_profile_begin in [phase 1, barrier 1, phase 2, barrier 2 + alpha step,
  * phase 3, barrier 3 + beta step] (6 values; %globaltimer). */

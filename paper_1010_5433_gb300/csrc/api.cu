@@ -71,6 +71,19 @@ extern "C" stag_status stag_set_stream(stag_ctx* ctx, void* s) {
 
 extern "C" size_t stag_device_bytes(stag_ctx* ctx) { return ctx ? ctx->dev_bytes : 0; }
 
+extern "C" size_t stag_abi_sizeof(int which) {
+    switch (which) {
+        case 0: return sizeof(stag_lattice);
+        case 1: return sizeof(stag_rational);
+        case 2: return sizeof(stag_solve_info);
+        case 3: return sizeof(stag_flavour);
+        case 4: return sizeof(stag_hmc);
+        case 5: return sizeof(stag_traj);
+        case 6: return sizeof(stag_kernel_profile);
+    }
+    return 0;
+}
+
 extern "C" void stag_destroy(stag_ctx* ctx) {
     if (!ctx) return;
     cudaStreamSynchronize(ctx->stream);

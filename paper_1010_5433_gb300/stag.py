@@ -68,6 +68,53 @@ class stag_traj(C.Structure):
                 ("t_gauge", C.c_double), ("t_metropolis", C.c_double)]
 
 
+# ctypes signature of every function include/stag.h declares: (argument
+# types, result type)
+_vp, _i, _d = C.c_void_p, C.c_int, C.c_double
+SIGNATURES = {
+    "stag_create": ([C.POINTER(stag_lattice), C.POINTER(_vp)], _i),
+    "stag_destroy": ([_vp], None),
+    "stag_strerror": ([_i], C.c_char_p),
+    "stag_last_cuda_error": ([_vp], C.c_char_p),
+    "stag_set_stream": ([_vp, _vp], _i),
+    "stag_device_bytes": ([_vp], C.c_size_t),
+    "stag_abi_sizeof": ([_i], C.c_size_t),
+    "stag_load_gauge": ([_vp, _vp], _i),
+    "stag_load_gauge_device": ([_vp, _vp], _i),
+    "stag_store_gauge": ([_vp, _vp], _i),
+    "stag_dslash": ([_vp, _i, _i, _i, _vp, _vp], _i),
+    "stag_apply_a": ([_vp, _d, _d, _i, _i, _vp, _vp], _i),
+    "stag_apply_a_noalloc": ([_vp, _d, _d, _i, _i, _vp, _vp], _i),
+    "stag_multishift_solve": ([_vp, _d, _i, _vp, _i, _i, _vp, _vp, _d, _i, C.POINTER(stag_solve_info)], _i),
+    "stag_fermion_force": ([_vp, _d, C.POINTER(stag_rational), _i, _i, _vp, _vp, _d, _i,
+                            C.POINTER(stag_solve_info)], _i),
+    "stag_gauge_force": ([_vp, _d, _vp], _i),
+    "stag_plaquette": ([_vp, C.POINTER(_d)], _i),
+    "stag_md_trajectory": ([_vp, C.POINTER(stag_hmc), C.POINTER(stag_traj)], _i),
+    "stag_multishift_solve_batch": ([C.POINTER(_vp), _i, _d, _i, _vp, _i, C.POINTER(_vp), C.POINTER(_vp), _d, _i,
+                                     C.POINTER(stag_solve_info)], _i),
+    "stag_selftest_barrier_timeout": ([_vp, C.c_longlong], _i),
+    "stag_profile_batch_phases": ([_vp, _i, C.POINTER(_d)], _i),
+    "stag_batch_shape": ([_vp, _i, C.POINTER(_i), C.POINTER(_i)], _i),
+    "stag_md_trajectory_batch": ([C.POINTER(_vp), _i, C.POINTER(stag_hmc), C.POINTER(stag_traj)], _i),
+    "stag_momenta": ([_vp], _vp),
+    "stag_profile_begin": ([_vp, _i], _i),
+    "stag_profile_read": ([_vp, _i, C.POINTER(stag_kernel_profile)], _i),
+    "stag_launch_count": ([_vp], C.c_longlong),
+    "stag_profile_phases": ([_vp, C.POINTER(_d)], _i),
+    "stag_tuned_threads_per_site": ([_vp, _i, _i, C.POINTER(_d)], _i),
+    "stag_surrogate_load": ([_vp, _vp], _i),
+    "stag_surrogate_store": ([_vp, _vp], _i),
+    "stag_surrogate_force": ([_vp, _vp], _i),
+    "stag_surrogate_add_force_sample": ([_vp, _vp], _i),
+    "stag_surrogate_add_sample": ([_vp, C.POINTER(stag_hmc), C.c_ulonglong], _i),
+    "stag_surrogate_samples": ([_vp], C.c_longlong),
+    "stag_surrogate_loss_grad": ([_vp, C.POINTER(_d), _vp], _i),
+    "stag_surrogate_train": ([_vp, _i, _d, C.POINTER(_d), C.POINTER(_d)], _i),
+    "stag_draw_momenta": ([_vp, C.c_ulonglong, C.c_ulonglong, _vp], _i),
+    "stag_draw_sources": ([_vp, C.c_ulonglong, C.c_ulonglong, _i, _i, _vp], _i),
+}
+
 _lib = None
 _keep = []   # ctypes arrays referenced by live structs
 
@@ -79,49 +126,7 @@ def lib():
             raise ImportError(f"libstag is not built ({LIB_PATH} missing); run "
                               "python -m paper_1010_5433_gb300.build")
         L = C.CDLL(LIB_PATH)
-        vp, i, d = C.c_void_p, C.c_int, C.c_double
-        sig = {
-            "stag_create": ([C.POINTER(stag_lattice), C.POINTER(vp)], i),
-            "stag_destroy": ([vp], None),
-            "stag_strerror": ([i], C.c_char_p),
-            "stag_last_cuda_error": ([vp], C.c_char_p),
-            "stag_set_stream": ([vp, vp], i),
-            "stag_device_bytes": ([vp], C.c_size_t),
-            "stag_load_gauge": ([vp, vp], i),
-            "stag_load_gauge_device": ([vp, vp], i),
-            "stag_store_gauge": ([vp, vp], i),
-            "stag_dslash": ([vp, i, i, i, vp, vp], i),
-            "stag_apply_a": ([vp, d, d, i, i, vp, vp], i),
-            "stag_apply_a_noalloc": ([vp, d, d, i, i, vp, vp], i),
-            "stag_multishift_solve": ([vp, d, i, vp, i, i, vp, vp, d, i, C.POINTER(stag_solve_info)], i),
-            "stag_fermion_force": ([vp, d, C.POINTER(stag_rational), i, i, vp, vp, d, i,
-                                    C.POINTER(stag_solve_info)], i),
-            "stag_gauge_force": ([vp, d, vp], i),
-            "stag_plaquette": ([vp, C.POINTER(d)], i),
-            "stag_md_trajectory": ([vp, C.POINTER(stag_hmc), C.POINTER(stag_traj)], i),
-            "stag_multishift_solve_batch": ([C.POINTER(vp), i, d, i, vp, i, C.POINTER(vp), C.POINTER(vp), d, i,
-                                             C.POINTER(stag_solve_info)], i),
-            "stag_selftest_barrier_timeout": ([vp, C.c_longlong], i),
-            "stag_profile_batch_phases": ([vp, i, C.POINTER(d)], i),
-            "stag_batch_shape": ([vp, i, C.POINTER(i), C.POINTER(i)], i),
-            "stag_md_trajectory_batch": ([C.POINTER(vp), i, C.POINTER(stag_hmc), C.POINTER(stag_traj)], i),
-            "stag_momenta": ([vp], vp),
-            "stag_profile_begin": ([vp, i], i),
-            "stag_profile_read": ([vp, i, C.POINTER(stag_kernel_profile)], i),
-            "stag_launch_count": ([vp], C.c_longlong),
-            "stag_profile_phases": ([vp, C.POINTER(d)], i),
-            "stag_tuned_threads_per_site": ([vp, i, i, C.POINTER(d)], i),
-            "stag_surrogate_load": ([vp, vp], i),
-            "stag_surrogate_store": ([vp, vp], i),
-            "stag_surrogate_force": ([vp, vp], i),
-            "stag_surrogate_add_force_sample": ([vp, vp], i),
-            "stag_surrogate_add_sample": ([vp, C.POINTER(stag_hmc), C.c_ulonglong], i),
-            "stag_surrogate_samples": ([vp], C.c_longlong),
-            "stag_surrogate_loss_grad": ([vp, C.POINTER(d), vp], i),
-            "stag_surrogate_train": ([vp, i, d, C.POINTER(d), C.POINTER(d)], i),
-            "stag_draw_momenta": ([vp, C.c_ulonglong, C.c_ulonglong, vp], i),
-            "stag_draw_sources": ([vp, C.c_ulonglong, C.c_ulonglong, i, i, vp], i),
-        }
+        sig = SIGNATURES
         for name, (args, res) in sig.items():
             if not hasattr(L, name):
                 continue           # reported by the export test; calling it raises

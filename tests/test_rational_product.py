@@ -50,3 +50,19 @@ def test_positivity_and_heatbath_inverse():
     rh = hb["a0"] + sum(a / (x + b) for a, b in zip(hb["alpha"], hb["beta"]))
     rm = met["a0"] + sum(a / (x + b) for a, b in zip(met["alpha"], met["beta"]))
     assert np.abs(rh * rh * rm - 1).max() < 3 * (2 * hb["err"] + met["err"]) + 1e-15
+
+
+def test_golden_entry_is_what_the_committed_script_writes():
+    """Provenance of the stored table: re-running the oracle's Remez with the
+    script's own parameters reproduces the stored 4^4 MD entry to rounding."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(
+        "make_rationals", os.path.join(os.path.dirname(GOLDEN), "make_rationals.py"))
+    mk = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mk)
+    s, m, n = mk.TABLE["c1_md"]
+    r = mk.remez(s, m * m, 16 + m * m, n, dps=60)
+    g = json.load(open(GOLDEN))["c1_md"]
+    np.testing.assert_allclose(r.beta, g["beta"], rtol=1e-13)
+    np.testing.assert_allclose(r.alpha, g["alpha"], rtol=1e-13)
+    assert abs(r.a0 - g["a0"]) <= 1e-13 * abs(g["a0"])

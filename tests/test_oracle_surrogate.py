@@ -177,3 +177,37 @@ def test_three_level_is_reversible():
     u1, m1 = integrator.md_evolve(ctx, u0, mom0, phis, 0.5, 2, 1, surrogate=net, n_mid=2)
     u2, m2 = integrator.md_evolve(ctx, u1, -m1, phis, 0.5, 2, 1, surrogate=net, n_mid=2)
     assert np.abs(u2 - u0).max() < 1e-11 and np.abs(m2 + mom0).max() < 1e-10
+
+
+def test_quantised_network_stays_within_the_bf16_bound(fg):
+    """Pins the oracle's tensor-core mode (quant=True: bf16 inputs of every
+    product, straight-through gradients) against the exact network, which
+    finite differences pin: the loss, all 2648 gradient components and the
+    force lie within lambda = 3 probabilistic bf16 bounds of the exact ones
+    (tests/bf16_bounds.py: first-order running-error bound per link, summed
+    over the links in quadrature) and within the rigorous worst-case bound,
+    and differ from them visibly (the mode does round).  The same bounds
+    reject the network with a transposed W2 or a dropped output bias."""
+    from tests.bf16_bounds import LAMBDA, network_bounds, ratio
+    f, G = fg
+    p = sur.init_params(6, scale=1.0)
+    pd = {k: (sur.bf16_round(v) if k.startswith("W") else v) for k, v in p.items()}
+    F = np.random.default_rng(4).standard_normal(G.shape[:-2] + (8,))
+    exact, worst, prob = network_bounds(pd, f, G, F)
+    loss_x, grad_x = sur.loss_and_grad(pd, f, G, F, quant=False)
+    assert abs(loss_x - exact["loss"]) < 1e-12 * exact["loss"]           # the bounds' own exact network
+    for k in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        np.testing.assert_allclose(grad_x[k], exact[k], rtol=1e-10, atol=1e-14)
+
+    def ratios(q, bound):
+        loss_q, grad_q = sur.loss_and_grad(q, f, G, F, quant=True)
+        r = [ratio(loss_q, exact["loss"], bound["loss"])]
+        r += [ratio(grad_q[k], exact[k], bound[k]) for k in ("W1", "b1", "W2", "b2", "W3", "b3")]
+        return r + [ratio(sur.surrogate_force(q, f, G, quant=True), exact["force"], bound["force"])]
+
+    r_prob = ratios(pd, {k: LAMBDA * v for k, v in prob.items()})
+    assert max(r_prob) <= 1.0, r_prob
+    assert max(ratios(pd, worst)) <= 1.0
+    assert max(r_prob) > 1e-3, r_prob                                    # the quantised mode does round
+    assert max(ratios(dict(pd, W2=pd["W2"].T.copy()), {k: LAMBDA * v for k, v in prob.items()})) > 1.0
+    assert max(ratios(dict(pd, b3=0 * pd["b3"]), {k: LAMBDA * v for k, v in prob.items()})) > 1.0

@@ -3,15 +3,17 @@
 One step = one RHMC trajectory (heatbath, minimum-norm MD with the fermion
 force from the multi-shift CG, Metropolis) on the 16^4, N_f = 2, m = 0.02,
 beta = 5.6 workload: 12-pole MD rational in fp32 with fp64 reliable updates,
-fp64 heatbath and Metropolis inversions (24 poles), 5 gauge substeps per
-fermion half step, tau = 1.  Synthetic data: a Haar-random start thermalised
-by quenched trajectories and by the warm-up trajectories themselves.
+fp64 heatbath and Metropolis inversions (24 poles), 10 outer steps with 5
+gauge substeps per fermion half step (acceptance 0.85), tau = 1.  Synthetic data: a Haar-random start thermalised
+by the recipe of paper_1010_5433_gb300/workload.py (quenched, then 100
+dynamical trajectories) and the warm-up trajectories.
 
 Prints one JSON line: trajectories/hour of the mixed path (value), the
-fp64 path on the same configuration, the end-to-end figure through host
-buffers, the roofline of the dominant kernel measured live with CUDA events,
-the 48^4 Dslash roofline point (inputs larger than L2), the oracle's CPU
-baseline and the SM clocks sampled during the timed region.
+fp64 path from the same configuration with the same random numbers (paired
+trajectories), the end-to-end figure through host buffers (the timed
+trajectories replayed), the roofline of the dominant kernel measured live
+with CUDA events, the 48^4 Dslash roofline point (inputs larger than L2),
+the oracle's CPU baseline and the SM clocks sampled during the timed region.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -33,18 +35,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Dslash HBM GB/s (% peak); RHMC trajectories/hour mixed+batched vs FP64 at equal ΔH"
-WORKLOAD = {
-    "workload": "RHMC 16^4 Nf=2 unimproved staggered, m=0.02, beta=5.6, tau=1, 2MN n_outer=20 x n_gauge=5, "
-                "12-pole MD rational (fp32 + fp64 reliable updates), 24-pole fp64 heatbath/Metropolis",
-    "dims": [16, 16, 16, 16], "beta": 5.6, "mass": 0.02, "n_flavours": 2, "n_pf": 1, "tau": 1.0,
-    "n_outer": 20, "n_gauge": 5, "tol_md": 1e-8, "tol_met": 1e-12,
-    "rationals": {"md": "c2_md", "met": "c2_met", "hb": "c2_hb"},
-    "seed": 0x5A0002, "quenched_thermalisation": 40,
-}
-# Work of one trajectory of this workload, used to scale the oracle's timed
-# sample to trajectories/hour: fermion and gauge force evaluations and link
-# updates follow from n_outer / n_gauge; CG iterations per solve are the
-# workload's measured average (mixed MD solves, fp64 heatbath/Metropolis).
+from paper_1010_5433_gb300.workload import MD_LINKS, WORKLOAD, make_hmc  # noqa: E402
 ROOFLINE_POINT_DIMS = (48, 48, 48, 48)
 L2_FLUSH_BYTES = 512 << 20
 
@@ -112,24 +103,6 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-# ---------------------------------------------------------------- GPU path
-def make_hmc(stag, rats, prec, seed, counter, n_flavours=1, **kw):
-    w = WORKLOAD
-    p = stag.stag_hmc()
-    p.beta, p.tau, p.n_outer, p.n_gauge = w["beta"], w["tau"], w["n_outer"], w["n_gauge"]
-    p.n_flavours = n_flavours
-    if n_flavours:
-        fl = p.flavour[0]
-        fl.mass, fl.n_pf = w["mass"], w["n_pf"]
-        fl.hb, fl.md, fl.met = rats["hb"].to_abi(), rats["md"].to_abi(), rats["met"].to_abi()
-    p.tol_md, p.tol_met, p.max_iter = w["tol_md"], w["tol_met"], 20000
-    p.md_prec = prec
-    p.seed, p.counter = seed, counter
-    for k, v in kw.items():
-        setattr(p, k, v)
-    return p
-
-
 # ---------------------------------------------------------------- replicas (N > 1)
 # One independent chain per rank, no data-path collective: the job's rate is
 # every rank's trajectories over the slowest rank's time.
@@ -151,13 +124,6 @@ def job_rate(world, steps, seconds):
     return world * steps / seconds * 3600.0
 
 
-# link format of the fp32 MD inversions (the fp64 heatbath / Metropolis
-# inversions always use the two-float store): stag_prec value, description.
-# The paper stores two rows of every link and rebuilds the third (Sec. 5).
-MD_LINKS = {"18": (1, "fp32, 18 reals per link"), "12": (2, "fp32, 12 reals per link (row 3 rebuilt)"),
-            "bf16": (3, "bf16, 12 reals per link (row 3 rebuilt), fp32 arithmetic")}
-
-
 def workload_config(world):
     """The workload both arms report (the GPU arm adds how it ran)."""
     return {"workload": WORKLOAD["workload"], "lattice": "x".join(str(d) for d in WORKLOAD["dims"]),
@@ -166,8 +132,7 @@ def workload_config(world):
 
 def run_gpu(args, rank, world, local_rank):
     import torch
-    import synthetic as syn
-    from paper_1010_5433_gb300 import rational, stag
+    from paper_1010_5433_gb300 import stag, workload
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
@@ -175,19 +140,16 @@ def run_gpu(args, rank, world, local_rank):
     w = WORKLOAD
     dims = tuple(w["dims"])
     V = int(np.prod(dims))
-    rats = {k: rational.load(v) for k, v in w["rationals"].items()}
+    rats = workload.rationals()
     seed = replica_seed(w["seed"], rank)
     ctx = stag.stag_create(dims, True, stream.cuda_stream)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     md_prec = MD_LINKS[args.md_links][0]
 
-    # start: Haar-random links, quenched thermalisation (no fermions), then warm-up trajectories
-    u0 = syn.haar_gauge(dims, seed)     # [mu, t, z, y, x, 3, 3] = the host layout of the C ABI
-    stag.stag_load_gauge(ctx, np.ascontiguousarray(u0).reshape(-1).view(np.float64))
-    del u0
-    for k in range(w["quenched_thermalisation"]):
-        p = make_hmc(stag, rats, md_prec, seed, 10_000 + k, n_flavours=0)
-        stag.stag_md_trajectory(ctx, p)
+    # start: Haar-random links, quenched then dynamical thermalisation, then the warm-up trajectories
+    t_therm = time.time()
+    therm_plaq = workload.thermalise(stag, ctx, rats, seed, md_prec)
+    t_therm = time.time() - t_therm
     counter = 0
     warm = []
     for k in range(args.warmup):
@@ -195,8 +157,9 @@ def run_gpu(args, rank, world, local_rank):
         counter += 1
     start_field = np.empty(4 * V * 18)
     stag.stag_store_gauge(ctx, start_field)
+    c0 = counter            # both arms and the end-to-end run draw from here on
 
-    def timed(prec, steps, counter0, profile):
+    def timed(prec, steps, profile):
         if profile:
             stag.stag_profile_begin(ctx, 1)
         launches0 = stag.stag_launch_count(ctx)
@@ -211,7 +174,7 @@ def run_gpu(args, rank, world, local_rank):
             e0.record(stream)
             for k in range(steps):
                 flush.zero_()                 # inputs fit in L2: flush between trajectories
-                trajs.append(stag.stag_md_trajectory(ctx, make_hmc(stag, rats, prec, seed, counter0 + k)))
+                trajs.append(stag.stag_md_trajectory(ctx, make_hmc(stag, rats, prec, seed, c0 + k)))
             e1.record(stream)
             torch.cuda.synchronize()
             torch.cuda.nvtx.range_pop()
@@ -225,19 +188,18 @@ def run_gpu(args, rank, world, local_rank):
             stag.stag_profile_begin(ctx, 0)
         return ms, trajs, clk.summary(), launches, prof
 
-
     # ---- the mixed path (headline)
-    ms, trajs, clocks, launches, prof = timed(md_prec, args.steps, counter, True)
+    ms, trajs, clocks, launches, prof = timed(md_prec, args.steps, True)
     ms = max_over_ranks(ms, world, dev)
-    counter += args.steps
     value = job_rate(world, args.steps, ms / 1e3)
-    # ---- the plain fp64 path from the same configuration
+    # ---- the plain fp64 path from the same configuration with the same random numbers
     stag.stag_load_gauge(ctx, start_field)
     steps64 = max(2, args.steps // 2)
-    ms64, trajs64, _, _, _ = timed(stag.STAG_FP64, steps64, 0, False)
+    ms64, trajs64, _, _, _ = timed(stag.STAG_FP64, steps64, False)
     ms64 = max_over_ranks(ms64, world, dev)
     value64 = job_rate(world, steps64, ms64 / 1e3)
-    # ---- end to end through the C ABI with host buffers (pinned), copies timed
+    # ---- end to end through the C ABI with host buffers (pinned), copies timed:
+    # the timed mixed trajectories replayed from the same start with the same counters
     host = torch.empty(4 * V * 18, dtype=torch.float64, pin_memory=True)
     host.copy_(torch.from_numpy(start_field))
     hnp = host.numpy()
@@ -245,9 +207,10 @@ def run_gpu(args, rank, world, local_rank):
     if world > 1:
         torch.distributed.barrier()
     t0 = time.perf_counter()
+    e2e_trajs = []
     for k in range(args.steps):
         stag.stag_load_gauge(ctx, hnp)                                   # H2D of the configuration
-        stag.stag_md_trajectory(ctx, make_hmc(stag, rats, md_prec, seed, 5000 + k))
+        e2e_trajs.append(stag.stag_md_trajectory(ctx, make_hmc(stag, rats, md_prec, seed, c0 + k)))
         stag.stag_store_gauge(ctx, hnp)                                  # D2H of the updated configuration
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
@@ -271,8 +234,9 @@ def run_gpu(args, rank, world, local_rank):
                 "traffic_source": traffic["source"] if traffic else None,
                 "peak_source": peak_kind,
                 "note": "unit = one solver iteration; 16^4 fields are L2-resident inside a trajectory; achieved = "
-                        "algorithmic bytes per iteration / CUDA-event time of every persistent launch on the "
-                        "context's stream divided by its iterations",
+                        "the multi-shift CG iteration's algorithmic bytes (2 link passes + (8 + 4 n_live) spinor "
+                        "passes) / CUDA-event time of every persistent launch on the context's stream divided by "
+                        "its iterations",
                 "kernels": kern}
 
     point = dslash_roofline_point(hbm) if rank == 0 else None
@@ -281,6 +245,11 @@ def run_gpu(args, rank, world, local_rank):
 
     dh = [t.dH for t in trajs]
     dh64 = [t.dH for t in trajs64]
+    paired = {"trajectories": steps64,
+              "mean_abs_dH": [float(np.mean(np.abs(dh[:steps64]))), float(np.mean(np.abs(dh64)))],
+              "acceptance": [float(np.mean([t.accepted for t in trajs[:steps64]])),
+                             float(np.mean([t.accepted for t in trajs64]))],
+              "max_abs_dH_difference": float(np.max(np.abs(np.array(dh[:steps64]) - np.array(dh64))))}
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": "trajectories/hour",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -300,13 +269,20 @@ def run_gpu(args, rank, world, local_rank):
                                                          for k in ("heatbath", "fermion", "gauge", "metropolis")},
                                    "plaquette": trajs[-1].plaq},
                          "fp64": {"value": round(value64, 2), "unit": "trajectories/hour", "steps": steps64,
+                                  "arithmetic": "FP64 path: float-float (hi + lo floats, ~48-bit) solver iterations "
+                                                "with IEEE fp64 sums and scalars, fp64 gauge force and link update",
                                   "dH": [round(x, 5) for x in dh64], "accepted": [t.accepted for t in trajs64],
                                   "mean_abs_dH": float(np.mean(np.abs(dh64))),
                                   "cg_iterations_per_traj": float(np.mean([t.cg_iterations for t in trajs64])),
                                   "seconds_breakdown": {k: round(float(np.mean([getattr(t, "t_" + k) for t in trajs64])), 4)
                                                         for k in ("heatbath", "fermion", "gauge", "metropolis")}},
+                         "paired_mixed_vs_fp64": paired,
                          "speedup_mixed_vs_fp64": round(value / value64, 3),
-                         "warmup_dH": [round(t.dH, 4) for t in warm]},
+                         "warmup_dH": [round(t.dH, 4) for t in warm],
+                         "thermalisation": {"plaquette_by_decade": [round(float(np.mean(therm_plaq[i:i + 10])), 5)
+                                                                    for i in range(0, len(therm_plaq), 10)],
+                                            "seconds": round(t_therm, 1)},
+                         "e2e_replays_timed": all(a.dH == b.dH for a, b in zip(trajs, e2e_trajs))},
         "dslash_roofline_point": point,
         "batched_chains": chains,
     }
@@ -314,16 +290,10 @@ def run_gpu(args, rank, world, local_rank):
 
 
 # DRAM traffic of the dominant kernel per unit (one solver iteration) from an
-# ncu capture of the same kernel on the same 16^4 lattice; None once the
+# ncu capture of the same kernel on the same 16^4 lattice; empty once the
 # kernel has changed since the capture.  The capture is cold-cache (ncu
 # flushes caches between passes): one read of the working set, then L2 hits.
-NCU_TRAFFIC = {
-    "persistent_iteration": {
-        "bytes_per_unit": round((33.118464e6 + 0.10752e6) / 39),
-        "source": "profiles/persistent_fp32_12_16x4_ncu.md: dram__bytes_read+write over one 39-iteration launch "
-                  "of k_ms_persistent<float, FMT_F32_12>",
-    },
-}
+NCU_TRAFFIC = {}
 
 
 def batched_chains():
@@ -347,21 +317,19 @@ def dslash_roofline_point(hbm):
 
 
 # ---------------------------------------------------------------- CPU baseline (the oracle)
-def cpu_baseline(per_traj):
-    """Times the oracle (numpy, fp64) on a bounded sample of the
-    16^4 workload -- multi-shift CG iterations with 12 shifts, one fermion
-    force, one Wilson force, one link update -- and scales it by the work of
-    one trajectory (per_traj: CG iterations, force evaluations, link updates).
-    `cores` is measured: the sample's process CPU time over its wall time."""
+def oracle_sample(seed=1, n_it=4):
+    """Seconds the oracle (numpy, fp64, as it stands) takes on a bounded
+    sample of the 16^4 workload: one multi-shift CG iteration with 12 shifts
+    (the mean of n_it), one fermion force, one Wilson force, one link update;
+    plus the cores the sample kept busy (process CPU time over wall time)."""
     import synthetic as syn
     from oracle import actions, dirac, integrator, lattice as lat, solvers
     w = WORKLOAD
     dims = tuple(w["dims"])
-    u = syn.haar_gauge(dims, 1)
+    u = syn.haar_gauge(dims, seed)
     eta, par = lat.eta(dims), lat.parity(dims)
-    b = syn.gaussian_fermion(dims, 2, on_parity=0)
+    b = syn.gaussian_fermion(dims, seed + 1, on_parity=0)
     shifts = list(np.geomspace(1e-5, 3.0, 12))
-    n_it = 4
     try:                                 # BLAS on one thread where the control is installed
         from threadpoolctl import threadpool_limits
         limit = threadpool_limits(1)
@@ -381,19 +349,52 @@ def cpu_baseline(per_traj):
     t0 = time.perf_counter()
     integrator.update_links(u, f, 0.01)
     t_up = time.perf_counter() - t0
-    # cores actually busy: process CPU time over wall time of the sample
-    cores = max(1.0, round((time.process_time() - cpu0) / (time.perf_counter() - wall0), 1))
+    cores = (time.process_time() - cpu0) / (time.perf_counter() - wall0)
     if limit is not None:
         limit.restore_original_limits()
-    t_traj = (per_traj["cg_iterations"] * t_iter + per_traj["fermion_forces"] * t_ff
-              + per_traj["gauge_forces"] * t_gf + per_traj["link_updates"] * t_up)
-    sample_s = n_it * t_iter + t_ff + t_gf + t_up
-    return {"value": round(3600.0 / t_traj, 4), "unit": "trajectories/hour", "cores": cores, "kind": "oracle",
-            "sample": f"16^4: {n_it} multi-shift CG iterations (12 shifts), 1 fermion force, 1 Wilson force, "
-                      f"1 link update ({sample_s:.1f} s), scaled by {per_traj['cg_iterations']} CG iterations, "
-                      f"{per_traj['fermion_forces']} fermion forces, {per_traj['gauge_forces']} gauge forces, "
-                      f"{per_traj['link_updates']} link updates per trajectory",
-            "seconds_per_traj": round(t_traj, 1)}
+    return {"cg_iteration": t_iter, "fermion_force": t_ff, "gauge_force": t_gf, "link_update": t_up,
+            "sample_s": n_it * t_iter + t_ff + t_gf + t_up, "cores": cores}
+
+
+def _oracle_sample_job(seed):
+    return oracle_sample(seed)
+
+
+def traj_seconds(t, per_traj):
+    return (per_traj["cg_iterations"] * t["cg_iteration"] + per_traj["fermion_forces"] * t["fermion_force"]
+            + per_traj["gauge_forces"] * t["gauge_force"] + per_traj["link_updates"] * t["link_update"])
+
+
+def cpu_baseline(per_traj, all_cores=True):
+    """The oracle's trajectories/hour on the host: the bounded sample timed on
+    one core and scaled by the work of one trajectory (per_traj: CG
+    iterations, force evaluations, link updates); then, with all_cores, the
+    same sample as one independent process per host core at once (spawned,
+    so that no process inherits a CUDA context), whose summed rate is the
+    host's throughput for independent chains.  `cores` is the processes that
+    ran (each one thread, BLAS held to one)."""
+    one = oracle_sample(1)
+    t1 = traj_seconds(one, per_traj)
+    work = (f"{per_traj['cg_iterations']} CG iterations, {per_traj['fermion_forces']} fermion forces, "
+            f"{per_traj['gauge_forces']} gauge forces, {per_traj['link_updates']} link updates per trajectory")
+    single = {"value": round(3600.0 / t1, 4), "cores": max(1.0, round(one["cores"], 1)), "seconds_per_traj": round(t1, 1),
+              "sample": f"16^4: 4 multi-shift CG iterations (12 shifts), 1 fermion force, 1 Wilson force, 1 link "
+                        f"update ({one['sample_s']:.1f} s), scaled by {work}"}
+    out = {"value": single["value"], "unit": "trajectories/hour", "cores": single["cores"], "kind": "oracle",
+           "sample": single["sample"], "seconds_per_traj": single["seconds_per_traj"], "single_core": single}
+    nproc = os.cpu_count() or 1
+    if all_cores and nproc > 1:
+        import multiprocessing as mp
+        t0 = time.perf_counter()
+        with mp.get_context("spawn").Pool(nproc) as pool:
+            res = pool.map(_oracle_sample_job, list(range(1, nproc + 1)))
+        wall = time.perf_counter() - t0
+        rate = sum(3600.0 / traj_seconds(r, per_traj) for r in res)
+        out.update({"value": round(rate, 4), "cores": nproc,
+                    "sample": f"{nproc} processes at once (one per host core, nproc = {nproc}), each the "
+                              f"single-core sample with its own seed; summed rate ({wall:.1f} s wall)",
+                    "seconds_per_traj": round(float(np.mean([traj_seconds(r, per_traj) for r in res])), 1)})
+    return out
 
 
 def work_per_traj(cg_iterations):
@@ -404,10 +405,10 @@ def work_per_traj(cg_iterations):
 
 
 # CG iterations of one 16^4 trajectory of this workload (all solves: MD,
-# heatbath, Metropolis), as the mixed path measured them on GB300 (40 057 per
-# trajectory over the bench's timed trajectories); only used to scale the
-# reference arm's sample, which runs without a GPU run before it.
-REF_CG_ITERATIONS = 40057
+# heatbath, Metropolis), as the mixed path measured them on GB300 (20 816 per
+# trajectory over 100 equilibrium trajectories at n_outer = 10); only used to
+# scale the reference arm's sample, which runs without a GPU run before it.
+REF_CG_ITERATIONS = 20816
 
 
 def main():
@@ -431,7 +432,7 @@ def main():
         per = work_per_traj(REF_CG_ITERATIONS)
         for _ in range(args.warmup):
             pass                                  # the oracle has nothing to warm up
-        vals = [cpu_baseline(per) for _ in range(args.steps)]
+        vals = [cpu_baseline(per, all_cores=False) for _ in range(args.steps)]
         v = float(np.mean([x["value"] for x in vals]))
         cb = dict(vals[-1])
         cb["value"] = round(v, 4)

@@ -137,7 +137,9 @@ stag_status stag_apply_a(stag_ctx* ctx, double mass, double shift, stag_prec pre
  * Limit: nrhs * 3 * Vh * (16 bytes fp64, 8 bytes otherwise) <= 32 MiB, else
  * STAG_ERR_ARG with the sizes in stag_last_cuda_error.  The first call on a
  * device looks up the array's device address with that device current (make
- * that first call before any stream capture).  All calls share the one
+ * that first call before any stream capture) and keeps it for the process:
+ * call with the context's device current, and do not reset the device
+ * (cudaDeviceReset) while the library is in use.  All calls share the one
  * array: calls whose work overlaps on the GPU (other streams, other host
  * threads) race on it. */
 stag_status stag_apply_a_noalloc(stag_ctx* ctx, double mass, double shift, stag_prec prec,
@@ -375,8 +377,11 @@ int stag_batch_shape(stag_ctx* ctx, stag_prec prec, int* threads_per_block, int*
  * 6 stag_kernel_profile; 0 for any other value. */
 size_t stag_abi_sizeof(int which);
 /* Persistent solver only: microseconds that block 0 spent since
- * stag_profile_begin in [phase 1, barrier 1, phase 2, barrier 2 + alpha step,
- * phase 3, barrier 3 + beta step] (6 values; %globaltimer). */
+ * stag_profile_begin in [phase 1, barrier 1, phase 2, barrier 2, alpha step,
+ * phase 3, barrier 3, beta step, in-launch reliable updates], then inside the
+ * scalar steps [alpha: partial sums, arithmetic, block barrier; beta: partial
+ * sums, arithmetic, the rest] (15 values, us must hold 15 doubles;
+ * %globaltimer). */
 stag_status stag_profile_phases(stag_ctx* ctx, double* us);
 /* The batched solver's launches led by ctx, for fp32-class precisions (any
  * prec but STAG_FP64) or for the float-float fp64 iteration: 8 values, us in

@@ -64,7 +64,7 @@ struct ProfData {
 #define SUR_B3 (SUR_W3 + SUR_NF * SUR_NH)
 #define SUR_NP (SUR_B3 + SUR_NF)
 
-#define PTIME_WORDS 24
+#define PTIME_WORDS 40   // [0,8) unused, [8,16) batched fp32, [16,24) batched float-float, [24,39) single lattice
 
 // Launch-shape tuning of the batched solver, per precision: while chosen < 0
 // the candidate shapes take turns on real segments, timed per iteration.
@@ -114,7 +114,7 @@ struct stag_ctx {
     bool use_persistent = true;       // small lattices: persistent cooperative solver (STAG_PERSISTENT=0 off)
     void* bar = nullptr;              // grid-barrier words of the persistent solver
     void* ptime = nullptr;            // per-phase ns counters of the persistent kernels while profiling
-                                      // ([0,8) single lattice, [8,16) batched fp32, [16,24) batched float-float)
+                                      // ([8,16) batched fp32, [16,24) batched float-float, [24,39) single lattice)
     BatchTune batch_tune[4];          // batched solver launch shape per precision (this context leading)
     int batch_shape_force = -1;       // STAG_BATCH_SHAPE=0|1|2: fixed shape, no tuning
     int persist_sites = 0;            // STAG_PERSIST_SITES=n: at least n sites per block of the persistent solver (0: the default)
@@ -209,6 +209,7 @@ struct MsRun {
     bool mixed = false, use_rel = false;
     int base = 0;
     void *tmp = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *ps = nullptr;   // iteration vectors
+    size_t rstride = 0;             // elements between the persistent solver's residual ring slots
     void *ax64 = nullptr, *t64 = nullptr, *xb64 = nullptr;                         // reliable-update scratch
     const void* b_user = nullptr;   // fp64 solves: the caller's arrays (the iteration runs on float-float copies)
     void* x_user = nullptr;
@@ -227,8 +228,9 @@ stag_status ms_core_multi(MsRun* runs, int n, MsStats* stats, stag_status* per_c
 
 // persistent.cu: the whole iteration loop in one cooperative launch
 bool persistent_fits(stag_ctx* ctx);
-stag_status launch_persistent(stag_ctx* ctx, stag_prec prec, int nrhs, void* r, void* p, void* q, void* t, void* ps,
-                              void* x);
+int persistent_ring_slots();        // residual fields the persistent solver cycles through
+stag_status launch_persistent(stag_ctx* ctx, stag_prec prec, int nrhs, void* ring, size_t rstride, void* p, void* q,
+                              void* t, void* ps, void* x, const double2* b64, double2* x64, double2* t64);
 
 // force.cu
 // force kernels write out = coef F (mode 0) or add out += coef F (mode 1)

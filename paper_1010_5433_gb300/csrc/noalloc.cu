@@ -23,7 +23,11 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[STAG_NOALLOC_SC
 
 namespace {
 constexpr int kMaxDevices = 64;
-void* g_scratch_addr[kMaxDevices];   // device address of the array, per device
+// Device address of the array, per device ordinal, looked up once and kept
+// for the process: valid while the caller's current device is the context's
+// device and the device is not reset (a reset reloads the module, and the
+// kept address would then be stale).
+void* g_scratch_addr[kMaxDevices];
 std::mutex g_scratch_mu;
 
 // In host code the array's name is only a host-side stand-in; its device

@@ -749,7 +749,10 @@ stag_status ms_setup(MsRun& R) {
         if (R.shifts[s] < R.shifts[R.base]) R.base = s;
     const size_t vbytes = (size_t)R.nrhs * 3 * g.Vh * 2 * rsize(R.prec);
     CKS(ws_get(ctx, WS_TMP_ODD, vbytes, &R.tmp));
-    CKS(ws_get(ctx, WS_R, vbytes, &R.r));
+    // the persistent solver keeps a ring of residuals (slot 0 here, where the
+    // other paths keep their only one)
+    CKS(ws_get(ctx, WS_R, vbytes * persistent_ring_slots(), &R.r));
+    R.rstride = (size_t)R.nrhs * 3 * g.Vh;
     CKS(ws_get(ctx, WS_P, vbytes, &R.p));
     CKS(ws_get(ctx, WS_Q, vbytes, &R.q));
     CKS(ws_get(ctx, WS_PS, vbytes * R.nshift, &R.ps));
@@ -903,8 +906,11 @@ stag_status ms_core(stag_ctx* ctx, double mass, int nshift, const double* shifts
     for (int seg = 0;; ++seg) {
         if (seg > max_segments) { status = STAG_ERR_TIMEOUT; break; }
         if (persistent) {
+            // one launch runs the whole solve, reliable updates included
             if (pe0) CK(cudaEventRecord(pe0, ctx->stream));
-            CKS(launch_persistent(ctx, prec, nrhs, R.r, R.p, R.q, R.tmp, R.ps, R.x));
+            CKS(launch_persistent(ctx, prec, nrhs, R.r, R.rstride, R.p, R.q, R.tmp, R.ps, R.x,
+                                  R.use_rel ? R.b64 : nullptr, R.use_rel ? R.x64 : nullptr,
+                                  R.use_rel ? (double2*)R.t64 : nullptr));
             if (pe1) CK(cudaEventRecord(pe1, ctx->stream));
             CKS(pull_control(ctx));
             if (pe0) {
@@ -913,11 +919,7 @@ stag_status ms_core(stag_ctx* ctx, double mass, int nshift, const double* shifts
                 persist_ms += ms;
             }
             if (!hs->halt) { status = STAG_ERR_TIMEOUT; break; }   // the loop only ends by halting
-            if (hs->status != STAG_OK) { status = (stag_status)hs->status; break; }
-            if (hs->need_reliable) {
-                CKS(ms_reliable_update(R));
-                continue;
-            }
+            if (hs->status != STAG_OK) status = (stag_status)hs->status;
             break;
         }
         // sampled timing: a few plainly launched iterations at the start of every segment

@@ -216,6 +216,13 @@ WORKLOADS = {
     "c3_light_md": (0.25, 0.01, 15), "c3_light_met": (0.25, 0.01, 24), "c3_light_hb": (-0.125, 0.01, 24),
     "c3_strange_md": (0.125, 0.1, 15), "c3_strange_met": (0.125, 0.1, 18), "c3_strange_hb": (-0.0625, 0.1, 18),
     "c4_md": (0.5, 0.05, 12), "c4_met": (0.5, 0.05, 20), "c4_hb": (-0.25, 0.05, 20),
+    # the volume-scaling study at the paper's two masses (Sec. 6, Tables 3-4: am = 1.0 and 0.01335), N_f = 2
+    "t3_high_md": (0.5, 1.0, 6), "t3_high_met": (0.5, 1.0, 10), "t3_high_hb": (-0.25, 1.0, 10),
+    "t3_low_md": (0.5, 0.01335, 12), "t3_low_met": (0.5, 0.01335, 24), "t3_low_hb": (-0.25, 0.01335, 24),
+    # the 16^4 N_f = 2, m = 0.02 workload with n_pf = 2, 3, 4 pseudo-fermions (s = 1 / (2 n_pf)), Sec. 2
+    "c2_pf2_md": (0.25, 0.02, 12), "c2_pf2_met": (0.25, 0.02, 20), "c2_pf2_hb": (-0.125, 0.02, 20),
+    "c2_pf3_md": (1.0 / 6.0, 0.02, 12), "c2_pf3_met": (1.0 / 6.0, 0.02, 20), "c2_pf3_hb": (-1.0 / 12.0, 0.02, 20),
+    "c2_pf4_md": (0.125, 0.02, 12), "c2_pf4_met": (0.125, 0.02, 20), "c2_pf4_hb": (-0.0625, 0.02, 20),
 }
 TABLE_PATH = __import__("os").path.join(__import__("os").path.dirname(__file__), "rational_table.json")
 

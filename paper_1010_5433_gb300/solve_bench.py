@@ -62,7 +62,9 @@ def run(dims, prec=1, nrhs=1, max_iter=400, width=0.3, mass=0.02, profile=True, 
             ph = stag.stag_profile_phases(ctx)
             it = max(info.iterations, 1)
             out["persistent_phases_us_per_iteration"] = dict(zip(
-                ["phase1_doe", "barrier1", "phase2_deo_A", "barrier2_alpha", "phase3_update", "barrier3_beta"],
+                ["phase1_doe", "barrier1", "phase2_deo_A", "barrier2", "alpha_step", "phase3_update", "barrier3",
+                 "beta_step", "reliable_updates", "alpha_sums", "alpha_arith", "alpha_sync", "beta_sums",
+                 "beta_arith", "beta_rest"],
                 [round(v / it, 2) for v in ph]))
     finally:
         stag.stag_destroy(ctx)

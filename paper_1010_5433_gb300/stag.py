@@ -343,7 +343,7 @@ def stag_tuned_threads_per_site(ctx, prec, nrhs):
 
 
 def stag_profile_phases(ctx):
-    arr = (C.c_double * 6)()
+    arr = (C.c_double * 15)()
     _check(lib().stag_profile_phases(ctx, arr), "stag_profile_phases", ctx)
     return list(arr)
 

@@ -36,6 +36,23 @@ TABLE = {
     "c4_md": (0.5, 0.05, 12),
     "c4_met": (0.5, 0.05, 20),
     "c4_hb": (-0.25, 0.05, 20),
+    # volume-scaling study at the paper's masses am = 1.0 and 0.01335 (Sec. 6), N_f = 2
+    "t3_high_md": (0.5, 1.0, 6),
+    "t3_high_met": (0.5, 1.0, 10),
+    "t3_high_hb": (-0.25, 1.0, 10),
+    "t3_low_md": (0.5, 0.01335, 12),
+    "t3_low_met": (0.5, 0.01335, 24),
+    "t3_low_hb": (-0.25, 0.01335, 24),
+    # 16^4, m = 0.02, N_f = 2 split over n_pf = 2, 3, 4 pseudo-fermions (s = 1 / (2 n_pf))
+    "c2_pf2_md": (0.25, 0.02, 12),
+    "c2_pf2_met": (0.25, 0.02, 20),
+    "c2_pf2_hb": (-0.125, 0.02, 20),
+    "c2_pf3_md": (1.0 / 6.0, 0.02, 12),
+    "c2_pf3_met": (1.0 / 6.0, 0.02, 20),
+    "c2_pf3_hb": (-1.0 / 12.0, 0.02, 20),
+    "c2_pf4_md": (0.125, 0.02, 12),
+    "c2_pf4_met": (0.125, 0.02, 20),
+    "c2_pf4_hb": (-0.0625, 0.02, 20),
 }
 
 

@@ -203,42 +203,59 @@ def test_two_flavours_two_pseudofermions_match_oracle(torch, prec, tol_dh):
 def test_bench_configuration_trajectory_is_reversible(torch):
     """The 16^4, N_f = 2, m = 0.02, beta = 5.6 trajectory in the launch
     configuration bench.py times (12-pole MD rational of the product table,
-    n_outer 20 x n_gauge 5, fp32 MD on 12-real links): forward with supplied momenta and
-    pseudo-fermions, then back from the flipped final momenta."""
+    n_outer 20 x n_gauge 5, fp32 MD on 12-real links), from a thermalised
+    start (hot start, quenched and dynamical trajectories, as the bench's
+    recipe but shorter): forward with supplied momenta and pseudo-fermions,
+    then back from the flipped final momenta.  The fp64 path returns dH to
+    1e-8; the fp32 link updates and forces leave ~5e-7 per degree of freedom
+    in the links (the paper quotes ~5e-6 for its fp32 update, Sec. 4) and,
+    measured on GB300, 2e-3 .. 4e-3 in dH_forward + dH_backward at H ~ 2e6;
+    the bound is 1e-2, below the equilibrium <|dH|> of ~0.06 at these
+    settings.  (From an ordered near-identity start the same fp32 sum reaches
+    0.13 with 5 gauge substeps, 5e-4 with one: that start is far from where
+    the workload runs.)"""
     from paper_1010_5433_gb300 import rational, stag
     dims = (16, 16, 16, 16)
+    V = int(np.prod(dims))
     rats = {k: rational.load("c2_" + k) for k in ("md", "met", "hb")}
-    u0 = syn.near_identity_gauge(dims, 0x5A0002)
     ctx = stag.stag_create(dims, True)
 
-    def hmc(**kw):
+    def hmc(prec, **kw):
         p = stag.stag_hmc()
         p.beta, p.tau, p.n_outer, p.n_gauge, p.n_flavours = 5.6, 1.0, 20, 5, 1
         fl = p.flavour[0]
         fl.mass, fl.n_pf = 0.02, 1
         fl.hb, fl.md, fl.met = rats["hb"].to_abi(), rats["md"].to_abi(), rats["met"].to_abi()
-        p.tol_md, p.tol_met, p.max_iter, p.md_prec = 1e-8, 1e-12, 20000, stag.STAG_FP32_12
+        p.tol_md, p.tol_met, p.max_iter, p.md_prec = (1e-12 if prec == 0 else 1e-8), 1e-12, 20000, prec
+        p.seed = 91
         for k, v in kw.items():
             setattr(p, k, v)
         return p
 
     try:
-        stag.stag_load_gauge(ctx, L.gauge_host(u0))
+        stag.stag_load_gauge(ctx, L.gauge_host(syn.haar_gauge(dims, 0x5A0013)))
+        for k in range(20):
+            stag.stag_md_trajectory(ctx, hmc(2, n_flavours=0, counter=100 + k))
+        for k in range(10):
+            stag.stag_md_trajectory(ctx, hmc(2, n_outer=10, counter=200 + k))
+        u0 = np.empty(4 * V * 18)
+        stag.stag_store_gauge(ctx, u0)
         d_mom = torch.from_numpy(L.mom_to_abi(syn.gaussian_momenta(dims, 17), dims)).cuda()
         d_phi = dev(torch, L.to_half(syn.gaussian_fermion(dims, 18, on_parity=0), dims, 0)[None])
-        r1 = stag.stag_md_trajectory(ctx, hmc(ext_mom=d_mom.data_ptr(), ext_phi=d_phi.data_ptr(), no_metropolis=1))
-        back = wrap_device(torch, stag.stag_momenta(ctx), d_mom.numel()).clone().view_as(d_mom)
-        r2 = stag.stag_md_trajectory(ctx, hmc(ext_mom=back.data_ptr(), ext_phi=d_phi.data_ptr(), no_metropolis=1,
-                                             flip_momenta=1))
-        buf = np.empty(4 * int(np.prod(dims)) * 18)
-        stag.stag_store_gauge(ctx, buf)
-        viol = np.sqrt(np.mean(np.abs(L.gauge_from_host(buf, dims) - u0) ** 2 * 0.5))
-        print(f"16^4 bench configuration: H0 {r1.H0:.1f}, dH {r1.dH:.5f} back {r2.dH:.5f}, reversibility per "
-              f"dof {viol:.2e}, CG iterations {r1.cg_iterations}")
-        assert viol < 5e-5
-        # fp32 links: H (~1e6 here: 2.1e6 momentum components) returns to fp32 accuracy, not absolutely
-        assert abs(r1.dH + r2.dH) < 1e-6 * abs(r1.H0)
-        assert abs(r1.dH) < 5.0
+        for prec, bound_h, bound_u in ((stag.STAG_FP32_12, 1e-2, 5e-6), (stag.STAG_FP64, 1e-8, 1e-13)):
+            stag.stag_load_gauge(ctx, u0)
+            r1 = stag.stag_md_trajectory(ctx, hmc(prec, ext_mom=d_mom.data_ptr(), ext_phi=d_phi.data_ptr(),
+                                                  no_metropolis=1))
+            back = wrap_device(torch, stag.stag_momenta(ctx), d_mom.numel()).clone().view_as(d_mom)
+            r2 = stag.stag_md_trajectory(ctx, hmc(prec, ext_mom=back.data_ptr(), ext_phi=d_phi.data_ptr(),
+                                                  no_metropolis=1, flip_momenta=1))
+            buf = np.empty(4 * V * 18)
+            stag.stag_store_gauge(ctx, buf)
+            viol = np.sqrt(np.mean((buf - u0) ** 2))
+            print(f"16^4 bench configuration, prec {prec}: H0 {r1.H0:.1f}, dH {r1.dH:.5f} back {r2.dH:.5f}, sum "
+                  f"{r1.dH + r2.dH:.2e}, reversibility per dof {viol:.2e}, CG iterations {r1.cg_iterations}")
+            assert viol < bound_u
+            assert abs(r1.dH + r2.dH) < bound_h
     finally:
         stag.stag_destroy(ctx)
 
@@ -284,7 +301,114 @@ def test_full_size_two_plus_one_flavours_bf16_links(torch):
         print(f"32^3x8 2+1 bf16: H0 {r1.H0:.1f}, dH {r1.dH:.5f} back {r2.dH:.5f}, reversibility per dof "
               f"{viol:.2e}, CG iterations {r1.cg_iterations}, {r1.seconds:.2f} s")
         assert viol < 1e-4
-        assert abs(r1.dH + r2.dH) < 1e-5 * abs(r1.H0)
+        assert abs(r1.dH + r2.dH) < 1e-2
         assert np.isfinite(r1.dH) and abs(r1.dH) < 50.0
+    finally:
+        stag.stag_destroy(ctx)
+
+
+def _c2_hmc(stag, rats, prec, **kw):
+    """The integrator and rationals of the 16^4 N_f = 2 workload: m = 0.02,
+    beta = 5.6, tau = 1, 20 outer x 5 gauge minimum-norm steps, 12-pole MD and
+    24-pole heatbath / Metropolis rationals, MD tolerance 1e-8 (1e-12 on the
+    FP64 path, which the oracle comparison holds to 1e-7 in dH)."""
+    p = stag.stag_hmc()
+    p.beta, p.tau, p.n_outer, p.n_gauge, p.n_flavours = 5.6, 1.0, 20, 5, 1
+    fl = p.flavour[0]
+    fl.mass, fl.n_pf = 0.02, 1
+    for k in ("hb", "md", "met"):
+        setattr(fl, k, stag.make_rational(rats[k]["a0"], rats[k]["alpha"], rats[k]["beta"]))
+    p.tol_md = 1e-12 if prec == 0 else 1e-8
+    p.tol_met, p.max_iter, p.md_prec = 1e-12, 20000, prec
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def _golden_8x4():
+    import importlib.util
+    here = os.path.dirname(GOLDEN)
+    spec = importlib.util.spec_from_file_location("make_traj_8x4_c2", os.path.join(here, "make_traj_8x4_c2.py"))
+    mk = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mk)
+    return mk, json.load(open(os.path.join(here, "traj_8x4_c2.json")))
+
+
+@pytest.mark.parametrize("prec,tol_dh,tol_u", [(0, 1e-7, 1e-10), (2, 5e-3, 1e-5), (1, 5e-3, 1e-5)])
+def test_trajectory_at_the_16x4_settings_matches_oracle_on_8x4(torch, prec, tol_dh, tol_u):
+    """One trajectory on 8^4 with the 16^4 workload's rationals, mass and
+    integrator (20 x 5 steps, tau = 1) against the oracle's, stored by
+    tests/golden/make_traj_8x4_c2.py from the same seeded links, momenta and
+    heatbath source.  FP64: dH to 1e-7, links to 1e-10.  Mixed (fp32 MD
+    inversions with fp64 reliable updates, fp32 link updates): the fp32
+    rounding of ~400 link updates and of the MD force (relative ~4e-6, the
+    solver's fp32 operator) moves the links by a few 1e-6 and dH by ~1e-3 on
+    this lattice; the bounds are 5e-3 and 1e-5."""
+    from paper_1010_5433_gb300 import stag
+    mk, gold = _golden_8x4()
+    dims, u0, mom0, xi = mk.inputs(gold["setup"])
+    rats = {k: json.load(open(GOLDEN))["c2_" + k] for k in ("md", "met", "hb")}
+    ctx = stag.stag_create(dims, True)
+    try:
+        stag.stag_load_gauge(ctx, L.gauge_host(u0))
+        d_mom = torch.from_numpy(L.mom_to_abi(mom0, dims)).cuda()
+        d_xi = dev(torch, L.to_half(xi, dims, 0)[None])
+        res = stag.stag_md_trajectory(ctx, _c2_hmc(stag, rats, prec, ext_mom=d_mom.data_ptr(),
+                                                   ext_xi=d_xi.data_ptr(), no_metropolis=1))
+        buf = np.empty(4 * int(np.prod(dims)) * 18)
+        stag.stag_store_gauge(ctx, buf)
+        u1 = L.gauge_from_host(buf, dims)
+        got = np.array([u1[tuple(q)].reshape(-1) for q in gold["u_sample_pos"]])
+        want = np.array([[complex(*v) for v in row] for row in gold["u_sample"]])
+        du = np.abs(got - want).max()
+        print(f"8^4 c2 settings prec {prec}: dH gpu {res.dH:.9f} oracle {gold['dH']:.9f}, max|dU| {du:.2e}, "
+              f"CG iterations {res.cg_iterations}")
+        assert abs(res.H0 - gold["H0"]) < 1e-10 * abs(gold["H0"])
+        assert abs(res.dH - gold["dH"]) < tol_dh
+        assert du < tol_u
+    finally:
+        stag.stag_destroy(ctx)
+
+
+def test_fp64_and_mixed_paths_integrate_alike_at_16x4(torch):
+    """The two arms of the trajectories/hour comparison from identical links,
+    momenta and heatbath source at the 16^4 workload's settings: the FP64 path
+    and the mixed path (fp32 MD inversions on 12-real links with fp64
+    reliable updates) end at the same links to 1e-4 and the same dH to 1e-2
+    (measured on GB300: 4.5e-6 and 3.6e-3 at |dH| ~ 0.2, H ~ 2e6), so a
+    difference in their |dH| statistics can only come from the random
+    numbers or the start, not from the integration."""
+    from paper_1010_5433_gb300 import rational, stag
+    dims = (16, 16, 16, 16)
+    V = int(np.prod(dims))
+    rats = {k: rational.load("c2_" + k) for k in ("md", "met", "hb")}
+    rj = {k: {"a0": r.a0, "alpha": list(r.alpha), "beta": list(r.beta)} for k, r in rats.items()}
+    ctx = stag.stag_create(dims, True)
+    try:
+        stag.stag_load_gauge(ctx, L.gauge_host(syn.haar_gauge(dims, 0x5A0012)))
+        for k in range(20):                       # quenched trajectories away from the hot start
+            q = stag.stag_hmc()
+            q.beta, q.tau, q.n_outer, q.n_gauge, q.n_flavours = 5.6, 1.0, 20, 5, 0
+            q.tol_md, q.tol_met, q.max_iter, q.md_prec, q.seed, q.counter = 1e-8, 1e-12, 100, 2, 5, k
+            stag.stag_md_trajectory(ctx, q)
+        start = np.empty(4 * V * 18)
+        stag.stag_store_gauge(ctx, start)
+        d_mom = torch.from_numpy(L.mom_to_abi(syn.gaussian_momenta(dims, 1201), dims)).cuda()
+        d_xi = dev(torch, L.to_half(syn.gaussian_fermion(dims, 1202, on_parity=0), dims, 0)[None])
+        out = {}
+        for prec in (0, 2):
+            stag.stag_load_gauge(ctx, start)
+            r = stag.stag_md_trajectory(ctx, _c2_hmc(stag, rj, prec, ext_mom=d_mom.data_ptr(),
+                                                     ext_xi=d_xi.data_ptr(), no_metropolis=1, tol_md=1e-8))
+            buf = np.empty(4 * V * 18)
+            stag.stag_store_gauge(ctx, buf)
+            out[prec] = (r, buf)
+        (r64, u64), (r32, u32) = out[0], out[2]
+        du = np.abs(u64 - u32).max()
+        print(f"16^4 paired arms: H0 {r64.H0:.3f} / {r32.H0:.3f}, dH fp64 {r64.dH:.6f} mixed {r32.dH:.6f}, "
+              f"max|dU| {du:.2e}")
+        assert abs(r64.H0 - r32.H0) < 1e-9 * abs(r64.H0)
+        assert abs(r64.dH - r32.dH) < 1e-2
+        assert du < 1e-4
     finally:
         stag.stag_destroy(ctx)

@@ -99,7 +99,8 @@ def _extrema(d, n_grid=6000):
 
 
 HIGH = ["c2_md", "c2_met", "c2_hb", "c3_light_md", "c3_light_met", "c3_light_hb", "c3_strange_md",
-        "c3_strange_met", "c3_strange_hb", "c4_md", "c4_met", "c4_hb", "c1_met", "c1_hb"]
+        "c3_strange_met", "c3_strange_hb", "c4_md", "c4_met", "c4_hb", "c1_met", "c1_hb",
+        "t3_high_md", "t3_high_met", "t3_high_hb", "t3_low_md", "t3_low_met", "t3_low_hb"]
 
 
 @pytest.mark.parametrize("name", HIGH)
@@ -135,7 +136,7 @@ def test_inverse_power_rationals_have_positive_partial_fractions(name):
     assert min(d["alpha"]) > 0 and min(d["beta"]) > 0
 
 
-@pytest.mark.parametrize("flavour", ["c1", "c2", "c3_light", "c3_strange", "c4"])
+@pytest.mark.parametrize("flavour", ["c1", "c2", "c3_light", "c3_strange", "c4", "t3_high", "t3_low"])
 def test_heatbath_and_metropolis_rationals_are_inverse(flavour):
     """phi = r_hb(A) xi makes phi^dag r_met(A) phi = xi^dag xi exactly only
     if r_hb^2 r_met = 1; the stored pair meets it within twice the heatbath

@@ -1,4 +1,4 @@
-"""stag_apply_a_noalloc against stag_apply_a.
+"""stag_apply_a_noalloc against stag_apply_a and against the oracle's A.
 
 The no-allocation entry point serves callers that may not call cudaMalloc or
 cudaFree (device memory owned by their own pool, or no room for the
@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 import synthetic as syn
+from oracle import dirac, lattice as lat
 from tests import layout as L
 from tests.gpu_util import dev, host_complex, torch_cuda
 
@@ -53,5 +54,38 @@ def test_noalloc_rejects_sizes_beyond_the_scratch():
         with pytest.raises(stag.StagError) as e:
             stag.stag_apply_a_noalloc(ctx, 0.1, 0.0, 0, 6000, buf, buf)
         assert e.value.status == 1 and "scratch" in str(e.value)
+    finally:
+        stag.stag_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_noalloc_first_call_on_a_fresh_context_matches_oracle(prec):
+    """The path the entry point exists for: the very first call on a new
+    context, on a ragged lattice no other test tunes, so no workspace and no
+    Dslash tuning exist yet (the untuned Dslash runs one thread per site);
+    compared directly with the oracle's A = m^2 + shift - D_eo D_oe."""
+    torch = torch_cuda()
+    from paper_1010_5433_gb300 import stag
+    dims = (6, 2, 10, 4)
+    u = syn.haar_gauge(dims, 57)
+    eta, par = lat.eta(dims), lat.parity(dims)
+    mass, shift, nrhs = 0.07, 0.21, 2
+    psis = [syn.gaussian_fermion(dims, 58 + k, on_parity=0) for k in range(nrhs)]
+    want = np.stack([L.to_half(dirac.a_op(u, p, mass, eta, par, shift), dims, 0) for p in psis])
+    fields = np.stack([L.to_half(p, dims, 0) for p in psis])
+    ctx = stag.stag_create(dims, True)
+    try:
+        stag.stag_load_gauge(ctx, L.gauge_host(u))
+        d_in = dev(torch, fields if prec == 0 else fields.astype(np.complex64))
+        got = torch.full_like(d_in, float("nan"))
+        stag.stag_apply_a_noalloc(ctx, mass, shift, prec, nrhs, d_in, got)
+        torch.cuda.synchronize()
+        a = host_complex(got)
+        # fp32: the oracle's A applied to the fp32-rounded input, as the device sees it
+        ref = want if prec == 0 else np.stack([
+            L.to_half(dirac.a_op(u, L.from_half(fields[k].astype(np.complex64).astype(complex), dims, 0), mass, eta,
+                                 par, shift), dims, 0) for k in range(nrhs)])
+        assert np.isfinite(a).all()
+        assert L.rel_err(a, ref) < TOL[prec]
     finally:
         stag.stag_destroy(ctx)

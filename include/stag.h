@@ -84,7 +84,8 @@ typedef struct {
  * context reads these environment variables once, here (none is needed):
  *   STAG_GRAPHS=0          the large-lattice solver loop as plain launches
  *                          instead of a CUDA-graph WHILE loop
- *   STAG_PERSISTENT=0      no persistent solver kernel on small lattices
+ *   STAG_PERSISTENT=0      no persistent solver kernel: every solve takes the
+ *                          three-kernel iteration (CUDA-graph WHILE loop)
  *   STAG_DSLASH_TPS=n      threads per site of the standalone Dslash (1, 2,
  *                          4 or 8) instead of the tuned value
  *   STAG_BATCH_SHAPE=k     launch shape k (0, 1, 2) of the batched solver
@@ -348,7 +349,7 @@ stag_status stag_selftest_barrier_timeout(stag_ctx* ctx, long long spin_limit);
 #define STAG_PK_DSLASH_OE 0      /* t = D_oe (r + beta p), multi-RHS                             */
 #define STAG_PK_DSLASH_EO_A 1    /* p = r + beta p; q = c0 p - D_eo t; (p, q) and the alpha step */
 #define STAG_PK_UPDATE 2         /* p_i, x_i of the live shifts; r -= alpha q; (r, r), beta step  */
-#define STAG_PK_PERSISTENT 3     /* persistent solver (small lattices): units are iterations,
+#define STAG_PK_PERSISTENT 3     /* persistent solver (every volume): units are iterations,
                                     every launch event-timed, bytes = one whole iteration       */
 #define STAG_PK_BATCH 4          /* batched solver (stag_*_batch; profile of the first context):
                                     units are batched iterations (one iteration of every lattice

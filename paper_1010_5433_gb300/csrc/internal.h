@@ -111,7 +111,7 @@ struct stag_ctx {
     float tps_us[4][2] = {};          // the winner's time per launch (us)
     int tps_force = 0;                // STAG_DSLASH_TPS: force a value (0 = tune)
     bool no_alloc_call = false;       // inside stag_apply_a_noalloc: nothing may allocate
-    bool use_persistent = true;       // small lattices: persistent cooperative solver (STAG_PERSISTENT=0 off)
+    bool use_persistent = true;       // persistent cooperative solver (STAG_PERSISTENT=0: the three-kernel path)
     void* bar = nullptr;              // grid-barrier words of the persistent solver
     void* ptime = nullptr;            // per-phase ns counters of the persistent kernels while profiling
                                       // ([8,16) batched fp32, [16,24) batched float-float, [24,39) single lattice)

@@ -51,16 +51,22 @@ constexpr int WIN = 4;          // iterations per window of deferred shift updat
 constexpr int RING = WIN + 1;   // residual fields kept: the window's and the next
 constexpr int FG = 3;           // closing shifts per group of phase 3 (loads in flight vs registers)
 
-// Block-local copy of the scalar recurrences (identical in every block).
+// Block-local copy of the scalar recurrences (identical in every block), in
+// float-float: the scalar warp advances them on the fp32 pipes (GB300's fp64
+// pipe runs a warp's fp64 instruction at a small fraction of the fp32 rate,
+// and a division is a dependent chain of them).  The device state keeps
+// doubles; a launch converts them on entry and exit.  float-float carries a
+// 48-bit significand, far below what the Krylov recurrences need.
 struct Scal {
-    double zeta[STAG_MAX_RHS][STAG_MAX_SHIFTS], zeta_prev[STAG_MAX_RHS][STAG_MAX_SHIFTS];
-    double zeta_next[STAG_MAX_RHS][STAG_MAX_SHIFTS], zratio[STAG_MAX_RHS][STAG_MAX_SHIFTS];
-    double cx[STAG_MAX_RHS][STAG_MAX_SHIFTS], cpr[STAG_MAX_RHS][STAG_MAX_SHIFTS], cpp[STAG_MAX_RHS][STAG_MAX_SHIFTS];
-    double dsig[STAG_MAX_SHIFTS];
-    double rr[STAG_MAX_RHS], bb[STAG_MAX_RHS], rr_ref[STAG_MAX_RHS];
-    double alpha[STAG_MAX_RHS], alpha_prev[STAG_MAX_RHS], beta_prev[STAG_MAX_RHS], beta[STAG_MAX_RHS];
-    double sums[STAG_MAX_RHS], units[STAG_MAX_RHS];
-    double k4_units, c0, tol2, delta2;
+    DF zeta[STAG_MAX_RHS][STAG_MAX_SHIFTS], zeta_prev[STAG_MAX_RHS][STAG_MAX_SHIFTS];
+    DF zeta_next[STAG_MAX_RHS][STAG_MAX_SHIFTS], zratio[STAG_MAX_RHS][STAG_MAX_SHIFTS];
+    DF cx[STAG_MAX_RHS][STAG_MAX_SHIFTS], cpr[STAG_MAX_RHS][STAG_MAX_SHIFTS], cpp[STAG_MAX_RHS][STAG_MAX_SHIFTS];
+    DF dsig[STAG_MAX_SHIFTS];
+    DF rr[STAG_MAX_RHS], bb[STAG_MAX_RHS], rr_ref[STAG_MAX_RHS];
+    DF alpha[STAG_MAX_RHS], alpha_prev[STAG_MAX_RHS], beta_prev[STAG_MAX_RHS], beta[STAG_MAX_RHS];
+    DF c0, tol2, delta2;
+    double k4_units;
+    int units[STAG_MAX_RHS];
     int live[STAG_MAX_RHS][STAG_MAX_SHIFTS], iters_at[STAG_MAX_RHS][STAG_MAX_SHIFTS];
     int rhs_live[STAG_MAX_RHS], left[STAG_MAX_RHS];
     int k, halt, status, need_reliable, nrhs, nshift, max_iter, mixed, base, n_reliable;
@@ -68,25 +74,35 @@ struct Scal {
     // zF = zeta_{k-1} alpha_{k-1} and zE = (r, r) (beta_{k-1} (zeta_{k-1} - zeta_k)
     // + zF (sigma_i - sigma_0)) known before (p, A p): the ratio's division no
     // longer waits for alpha's; inv_rr = 1 / (r, r) serves the next beta step
-    double zE[STAG_MAX_RHS][STAG_MAX_SHIFTS], zF[STAG_MAX_RHS][STAG_MAX_SHIFTS], inv_rr[STAG_MAX_RHS];
+    DF zE[STAG_MAX_RHS][STAG_MAX_SHIFTS], zF[STAG_MAX_RHS][STAG_MAX_SHIFTS], inv_rr[STAG_MAX_RHS];
     // deferred shift updates: shift s of source q has accumulated wj of its
     // window's iterations (shift index fastest: the lanes of a warp, one per
-    // shift, touch consecutive words).  The coefficients are float-float:
-    // advanced on the fp32 pipes by the scalar warp, read by every thread
-    // without a conversion (fp64 conversions and compares per thread and
-    // iteration would run on GB300's slow fp64 pipe).
+    // shift, touch consecutive words)
     DF wp[STAG_MAX_RHS][WIN][STAG_MAX_SHIFTS], wx[STAG_MAX_RHS][WIN][STAG_MAX_SHIFTS];
     DF wd[STAG_MAX_RHS][STAG_MAX_SHIFTS], wf[STAG_MAX_RHS][STAG_MAX_SHIFTS];
     int touched[STAG_MAX_RHS][STAG_MAX_SHIFTS], wj[STAG_MAX_RHS][STAG_MAX_SHIFTS];
-    // the scalars every thread applies, as float-float copies made once per block
-    DF alphaD[STAG_MAX_RHS], betaD[STAG_MAX_RHS], c0D;
 };
 
 // a coefficient in the arithmetic of the iteration: the float part for fp32
-// fields, the float-float pair for float-float fields
+// fields, the float-float pair for float-float fields (no conversion per thread)
 template <typename R> __device__ __forceinline__ R coef(const DF& d);
 template <> __device__ __forceinline__ float coef<float>(const DF& d) { return d.hi; }
 template <> __device__ __forceinline__ DF coef<DF>(const DF& d) { return d; }
+
+// float-float helpers of the scalar recurrences: conversions from and to
+// double (integer operations in, one fp64 add out), a division by one
+// correction step of the fp32 quotient (Dekker's long division), and sign tests
+__device__ __forceinline__ DF dfv(double x) { return df_split(x); }
+__device__ __forceinline__ double dbl(const DF& v) { return (double)v.hi + (double)v.lo; }
+__device__ __forceinline__ DF df_div(const DF& a, const DF& b) {
+    const float q1 = a.hi / b.hi;
+    const DF r = a - b * DF(q1);
+    const float q2 = r.hi / b.hi;
+    return df_two_sum(q1, q2);
+}
+__device__ __forceinline__ bool df_le(const DF& a, const DF& b) { return (a - b).hi <= 0.f; }
+__device__ __forceinline__ bool df_lt(const DF& a, const DF& b) { return (a - b).hi < 0.f; }
+__device__ __forceinline__ bool df_finite(const DF& a) { return isfinite(a.hi); }
 
 // shift s's window closes at iteration k
 __device__ __forceinline__ bool window_closes(int k, int s) { return (k + s) % WIN == WIN - 1; }
@@ -95,34 +111,32 @@ __device__ void load_scal(Scal& S, const SolverState* st) {
     const int t = threadIdx.x;
     for (int i = t; i < STAG_MAX_RHS * STAG_MAX_SHIFTS; i += blockDim.x) {
         const int q = i / STAG_MAX_SHIFTS, s = i % STAG_MAX_SHIFTS;
-        S.zeta[q][s] = st->zeta[q][s];
-        S.zeta_prev[q][s] = st->zeta_prev[q][s];
-        S.zeta_next[q][s] = st->zeta_next[q][s];
-        S.cx[q][s] = st->cx[q][s];
-        S.cpr[q][s] = st->cpr[q][s];
-        S.cpp[q][s] = st->cpp[q][s];
+        S.zeta[q][s] = dfv(st->zeta[q][s]);
+        S.zeta_prev[q][s] = dfv(st->zeta_prev[q][s]);
+        S.zeta_next[q][s] = dfv(st->zeta_next[q][s]);
+        S.zratio[q][s] = dfv(st->zratio[q][s]);
+        S.cx[q][s] = dfv(st->cx[q][s]);
+        S.cpr[q][s] = dfv(st->cpr[q][s]);
+        S.cpp[q][s] = dfv(st->cpp[q][s]);
         S.live[q][s] = st->live[q][s];
         S.iters_at[q][s] = st->iters_at[q][s];
     }
-    if (t < STAG_MAX_SHIFTS) S.dsig[t] = st->dsig[t];
+    if (t < STAG_MAX_SHIFTS) S.dsig[t] = dfv(st->dsig[t]);
     if (t < STAG_MAX_RHS) {
-        S.rr[t] = st->rr[t];
-        S.bb[t] = st->bb[t];
-        S.rr_ref[t] = st->rr_ref[t];
-        S.alpha[t] = st->alpha[t];
-        S.alphaD[t] = DF(st->alpha[t]);
-        S.alpha_prev[t] = st->alpha_prev[t];
-        S.beta_prev[t] = st->beta_prev[t];
-        S.beta[t] = st->beta[t];
-        S.betaD[t] = DF(st->beta[t]);
+        S.rr[t] = dfv(st->rr[t]);
+        S.bb[t] = dfv(st->bb[t]);
+        S.rr_ref[t] = dfv(st->rr_ref[t]);
+        S.alpha[t] = dfv(st->alpha[t]);
+        S.alpha_prev[t] = dfv(st->alpha_prev[t]);
+        S.beta_prev[t] = dfv(st->beta_prev[t]);
+        S.beta[t] = dfv(st->beta[t]);
         S.rhs_live[t] = st->rhs_live[t];
     }
     if (t == 0) {
         S.k4_units = st->k4_units;
-        S.c0 = st->c0;
-        S.c0D = DF(st->c0);
-        S.tol2 = st->tol2;
-        S.delta2 = st->delta2;
+        S.c0 = dfv(st->c0);
+        S.tol2 = dfv(st->tol2);
+        S.delta2 = dfv(st->delta2);
         S.k = st->k;
         S.halt = st->halt;
         S.status = st->status;
@@ -135,6 +149,39 @@ __device__ void load_scal(Scal& S, const SolverState* st) {
         S.n_reliable = st->n_reliable;
     }
     __syncthreads();
+}
+
+__device__ void store_scal(const Scal& S, SolverState* st) {
+    const int t = threadIdx.x;
+    for (int i = t; i < STAG_MAX_RHS * STAG_MAX_SHIFTS; i += blockDim.x) {
+        const int q = i / STAG_MAX_SHIFTS, s = i % STAG_MAX_SHIFTS;
+        st->zeta[q][s] = dbl(S.zeta[q][s]);
+        st->zeta_prev[q][s] = dbl(S.zeta_prev[q][s]);
+        st->zeta_next[q][s] = dbl(S.zeta_next[q][s]);
+        st->zratio[q][s] = dbl(S.zratio[q][s]);
+        st->cx[q][s] = dbl(S.cx[q][s]);
+        st->cpr[q][s] = dbl(S.cpr[q][s]);
+        st->cpp[q][s] = dbl(S.cpp[q][s]);
+        st->live[q][s] = S.live[q][s];
+        st->iters_at[q][s] = S.iters_at[q][s];
+    }
+    if (t < STAG_MAX_RHS) {
+        st->rr[t] = dbl(S.rr[t]);
+        st->rr_ref[t] = dbl(S.rr_ref[t]);
+        st->alpha[t] = dbl(S.alpha[t]);
+        st->alpha_prev[t] = dbl(S.alpha_prev[t]);
+        st->beta_prev[t] = dbl(S.beta_prev[t]);
+        st->beta[t] = dbl(S.beta[t]);
+        st->rhs_live[t] = S.rhs_live[t];
+    }
+    if (t == 0) {
+        st->k4_units = S.k4_units;
+        st->k = S.k;
+        st->halt = S.halt;
+        st->status = S.status;
+        st->need_reliable = S.need_reliable;
+        st->n_reliable = S.n_reliable;
+    }
 }
 
 // An empty window for shift s of source q: p_i = p_i(start), x_i = x_i(start)
@@ -157,44 +204,14 @@ __device__ void prep_alpha(Scal& S) {
     const int q = threadIdx.x >> 5, s = threadIdx.x & 31;
     if (q < S.nrhs && S.rhs_live[q]) {
         if (s < S.nshift) {
-            const double zf = S.zeta_prev[q][s] * S.alpha_prev[q];
+            const DF zf = S.zeta_prev[q][s] * S.alpha_prev[q];
             S.zF[q][s] = zf;
             S.zE[q][s] = S.rr[q] * (S.beta_prev[q] * (S.zeta_prev[q][s] - S.zeta[q][s]) + zf * S.dsig[s]);
         }
-        if (s == 0) S.inv_rr[q] = 1.0 / S.rr[q];
+        if (s == 0) S.inv_rr[q] = df_div(DF(1.f), S.rr[q]);
     }
 }
 
-__device__ void store_scal(const Scal& S, SolverState* st) {
-    const int t = threadIdx.x;
-    for (int i = t; i < STAG_MAX_RHS * STAG_MAX_SHIFTS; i += blockDim.x) {
-        const int q = i / STAG_MAX_SHIFTS, s = i % STAG_MAX_SHIFTS;
-        st->zeta[q][s] = S.zeta[q][s];
-        st->zeta_prev[q][s] = S.zeta_prev[q][s];
-        st->zeta_next[q][s] = S.zeta_next[q][s];
-        st->cx[q][s] = S.cx[q][s];
-        st->cpr[q][s] = S.cpr[q][s];
-        st->cpp[q][s] = S.cpp[q][s];
-        st->live[q][s] = S.live[q][s];
-        st->iters_at[q][s] = S.iters_at[q][s];
-    }
-    if (t < STAG_MAX_RHS) {
-        st->rr[t] = S.rr[t];
-        st->alpha[t] = S.alpha[t];
-        st->alpha_prev[t] = S.alpha_prev[t];
-        st->beta_prev[t] = S.beta_prev[t];
-        st->beta[t] = S.beta[t];
-        st->rhs_live[t] = S.rhs_live[t];
-    }
-    if (t == 0) {
-        st->k4_units = S.k4_units;
-        st->k = S.k;
-        st->halt = S.halt;
-        st->status = S.status;
-        st->need_reliable = S.need_reliable;
-        st->n_reliable = S.n_reliable;
-    }
-}
 
 // Per-thread and per-warp sums of a block in float-float on the fp32 pipes
 // (each thread's term is an fp32 or float-float dot product), the warps'
@@ -238,16 +255,24 @@ __device__ __forceinline__ void block_sum_df(DF (&v)[N], double (&out)[N]) {
         }
 }
 
-// Warp q of every block: the sum of source q's per-block partials
-// partial[off + q][0..nb) (lane l adds the partials l, l + 32, ..., then a
-// fixed shuffle tree), so every block gets the same bits, broadcast to the
-// warp's lanes.
-__device__ __forceinline__ double warp_partial_sum(const double* partial, int nb, int off, int q) {
+// Warp q of every block: the sum of source q's per-block fp64 partials
+// partial[off + q][0..nb) in float-float (lane l adds the partials l, l + 32,
+// ..., then a fixed butterfly), so every block gets the same bits.
+__device__ __forceinline__ DF warp_partial_sum(const double* partial, int nb, int off, int q) {
     const int lane = threadIdx.x & 31;
-    double v = lane_strided_sum(partial + (size_t)(off + q) * nb, nb, lane);
+    const double* p = partial + (size_t)(off + q) * nb;
+    DF v(0.f);
+    for (int i0 = lane; i0 < nb; i0 += 32 * 8) {
+        double t[8];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return __shfl_sync(0xffffffffu, v, 0);
+        for (int k = 0; k < 8; ++k) t[k] = (i0 + 32 * k < nb) ? __ldcg(p + i0 + 32 * k) : 0.0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (i0 + 32 * k < nb) v = v + dfv(t[k]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = v + __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
 }
 
 // alpha = (r, r) / (p, A p) of every source and the shifted-system
@@ -260,26 +285,26 @@ __device__ void alpha_step(Scal& S, const double* partial, int nb, int off, unsi
     const int j = (q < STAG_MAX_RHS) ? S.wj[q][s] : 0;   // this iteration's place in the shift's window
     unsigned long long tf = fine ? gtimer() : 0;
     if (q < S.nrhs && S.rhs_live[q]) {
-        const double pq = warp_partial_sum(partial, nb, off, q);
+        const DF pq = warp_partial_sum(partial, nb, off, q);
         if (fine) {
             const unsigned long long t = gtimer();
             fine[0] += t - tf;
             tf = t;
         }
-        double a = S.rr[q] / pq;
-        const bool bad = !isfinite(a) || !(pq > 0.0);
-        if (bad) a = 0.0;
+        DF a = df_div(S.rr[q], pq);
+        const bool bad = !df_finite(a) || !(pq.hi > 0.f);
+        if (bad) a = DF(0.f);
         if (s < S.nshift && S.live[q][s]) {
             // zeta_{k+1} / zeta_k = zeta_{k-1} alpha_{k-1} / (alpha beta_{k-1} (zeta_{k-1} - zeta_k)
             //   + zeta_{k-1} alpha_{k-1} (1 + alpha dsig)), numerator and denominator times pq / alpha
-            const double zf = S.zF[q][s];
-            const double zr = zf * pq / (S.zE[q][s] + zf * pq);
-            const double ax = bad ? 0.0 : a * zr;
+            const DF zfp = S.zF[q][s] * pq;
+            const DF zr = df_div(zfp, S.zE[q][s] + zfp);
+            const DF ax = bad ? DF(0.f) : a * zr;
             S.zeta_next[q][s] = S.zeta[q][s] * zr;
             S.zratio[q][s] = zr;
             S.cx[q][s] = ax;
             // p_i <- zeta r_j + b p_i;  x_i <- x_i + ax p_i  in window-coefficient form
-            const DF b(S.cpp[q][s]), zeta(S.cpr[q][s]), axd(ax);
+            const DF b = S.cpp[q][s], zeta = S.cpr[q][s], axd = ax;
             DF wd = S.wd[q][s] * b, wf = S.wf[q][s];
 #pragma unroll
             for (int l = 0; l < WIN; ++l) {
@@ -299,9 +324,7 @@ __device__ void alpha_step(Scal& S, const double* partial, int nb, int off, unsi
             tf = t;
         }
         if (s == 0) {
-            S.sums[q] = pq;
             S.alpha[q] = a;
-            S.alphaD[q] = DF(a);
             if (bad) {
                 S.status = STAG_ERR_NAN;
                 S.halt = 1;
@@ -321,24 +344,24 @@ __device__ void beta_step(Scal& S, const double* partial, int nb, int off, unsig
     const bool closed = window_closes(S.k, s);   // phase 3 has just applied shift s's window
     unsigned long long tf = fine ? gtimer() : 0;
     if (q < S.nrhs && S.rhs_live[q]) {
-        const double rn = warp_partial_sum(partial, nb, off, q);
+        const DF rn = warp_partial_sum(partial, nb, off, q);
         if (fine) {
             const unsigned long long t = gtimer();
             fine[3] += t - tf;
             tf = t;
         }
-        const double bt = rn * S.inv_rr[q];
+        const DF bt = rn * S.inv_rr[q];
         const bool on = s < S.nshift && S.live[q][s];
         const int n_live = __popc(__ballot_sync(0xffffffffu, on));
         bool still = false;
         if (on) {
-            const double zn = S.zeta_next[q][s], z = S.zeta[q][s];
-            const double zr = S.zratio[q][s];
+            const DF zn = S.zeta_next[q][s], z = S.zeta[q][s];
+            const DF zr = S.zratio[q][s];
             S.cpr[q][s] = zn;
             S.cpp[q][s] = bt * zr * zr;
             S.zeta_prev[q][s] = z;
             S.zeta[q][s] = zn;
-            if (zn * zn * rn <= S.tol2 * S.bb[q]) {
+            if (df_le(zn * zn * rn, S.tol2 * S.bb[q])) {
                 S.live[q][s] = 0;
                 S.iters_at[q][s] = S.k + 1;
             } else {
@@ -348,24 +371,22 @@ __device__ void beta_step(Scal& S, const double* partial, int nb, int off, unsig
         const bool left = __ballot_sync(0xffffffffu, still) != 0;
         __syncwarp();
         if (s == 0) {
-            if (!isfinite(rn)) {
+            if (!df_finite(rn)) {
                 S.status = STAG_ERR_NAN;
                 S.halt = 1;
             }
-            S.units[q] = 72.0 + 96.0 * n_live;
-            S.sums[q] = rn;
+            S.units[q] = 72 + 96 * n_live;
             S.beta[q] = bt;
-            S.betaD[q] = DF(bt);
             S.alpha_prev[q] = S.alpha[q];
             S.beta_prev[q] = bt;
             S.rr[q] = rn;
             S.left[q] = left;
             if (!left) S.rhs_live[q] = 0;
-            else if (S.mixed && rn < S.delta2 * S.rr_ref[q]) S.need_reliable = 1;
+            else if (S.mixed && df_lt(rn, S.delta2 * S.rr_ref[q])) S.need_reliable = 1;
         }
     } else if (q < S.nrhs && s == 0) {
         S.left[q] = 0;
-        S.units[q] = 0.0;
+        S.units[q] = 0;
     }
     __syncthreads();
     if (fine) {
@@ -375,10 +396,12 @@ __device__ void beta_step(Scal& S, const double* partial, int nb, int off, unsig
     }
     if (threadIdx.x == 0) {
         int any = 0;
+        int units = 0;
         for (int j = 0; j < S.nrhs; ++j) {
             any |= S.left[j];
-            S.k4_units += S.units[j];
+            units += S.units[j];
         }
+        S.k4_units += (double)units;
         S.k += 1;
         if (!any) S.halt = 1;
         else if (S.k >= S.max_iter) { S.halt = 1; S.status = STAG_ERR_NOT_CONVERGED; }
@@ -557,7 +580,7 @@ __device__ __noinline__ bool reliable_update(Scal& S, GridSync& gs, const Geom& 
     double nrm[STAG_MAX_RHS];
 #pragma unroll
     for (int j = 0; j < STAG_MAX_RHS; ++j) nrm[j] = 0.0;
-    const DF c0(S.c0), half(0.5f);
+    const DF c0 = S.c0, half(0.5f);
     typename V2T<R>::T* rcur = ring + (size_t)(S.k % RING) * rstride;
     for (int h = h0 + (int)threadIdx.x; h < h1; h += PB)
 #pragma unroll
@@ -587,11 +610,11 @@ __device__ __noinline__ bool reliable_update(Scal& S, GridSync& gs, const Geom& 
     {
         const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
         if (q < nrhs && S.rhs_live[q]) {
-            const double rr = warp_partial_sum(partial, nb, 2 * STAG_MAX_RHS, q);
+            const DF rr = warp_partial_sum(partial, nb, 2 * STAG_MAX_RHS, q);
             if (lane == 0) {
                 S.rr[q] = rr;
                 S.rr_ref[q] = rr;
-                if (!isfinite(rr)) {
+                if (!df_finite(rr)) {
                     S.status = STAG_ERR_NAN;
                     S.halt = 1;
                 }
@@ -667,7 +690,7 @@ __global__ void __launch_bounds__(PB) k_ms_persistent(Geom g, LinkPtrs L, Solver
 #pragma unroll
                 for (int j = 0; j < NRP; ++j) {
                     zero(acc[j]);
-                    bt[j] = (r0 + j < nrhs) ? coef<R>(S.betaD[r0 + j]) : (R)0;
+                    bt[j] = (r0 + j < nrhs) ? coef<R>(S.beta[r0 + j]) : (R)0;
                 }
 #pragma unroll MU_UNROLL
                 for (int mu = 0; mu < 4; ++mu) {
@@ -704,7 +727,7 @@ __global__ void __launch_bounds__(PB) k_ms_persistent(Geom g, LinkPtrs L, Solver
         DF dots[ND];
 #pragma unroll
         for (int j = 0; j < ND; ++j) dots[j] = DF(0.f);
-        const R c0 = coef<R>(S.c0D);
+        const R c0 = coef<R>(S.c0);
         for (int h = h0 + (int)threadIdx.x; h < h1; h += PB) {
             Nbr n;
             site_neighbours(g, h, 0, n);
@@ -734,7 +757,7 @@ __global__ void __launch_bounds__(PB) k_ms_persistent(Geom g, LinkPtrs L, Solver
                 for (int j = 0; j < NRP; ++j) {
                     if (r0 + j >= nrhs) continue;
                     const size_t off = (size_t)(r0 + j) * rs;
-                    const R bt = coef<R>(S.betaD[r0 + j]);
+                    const R bt = coef<R>(S.beta[r0 + j]);
                     Vec3<R> pv = load_vec_cg<R>(p + off, h, g.Vh);
                     Vec3<R> rv = load_vec_cg<R>(r + off, h, g.Vh);
                     Vec3<R> o;
@@ -776,7 +799,7 @@ __global__ void __launch_bounds__(PB) k_ms_persistent(Geom g, LinkPtrs L, Solver
                 // a source that stopped still owes its shifts' pending updates
                 flush_closing<R>(S, j, ns, rs, h, g.Vh, ring, rstride, S.k, rv, ps, x);
                 if (!live) continue;
-                const R a = coef<R>(S.alphaD[j]);
+                const R a = coef<R>(S.alpha[j]);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     rv.c[c].re -= a * qv.c[c].re;
@@ -852,8 +875,11 @@ stag_status launch_persistent_pb(stag_ctx* ctx, void* ring, size_t rstride, void
 }  // namespace
 
 bool persistent_fits(stag_ctx* ctx) {
-    // small lattices, where launch and loop overhead dominate the iteration
-    return ctx->use_persistent && ctx->g.Vh <= (1 << 18);
+    // every volume: measured on GB300, one persistent launch per solve beats
+    // the three-kernel iteration at 16^4 (launch- and latency-bound) and at
+    // 32^4 and 48^4 alike (fp32-12: 194 against 429 us and 990 against 2062 us
+    // per iteration), the deferred shift updates moving a third of the bytes
+    return ctx->use_persistent;
 }
 
 template <typename R, int FMT, int NRP>

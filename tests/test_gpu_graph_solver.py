@@ -1,11 +1,10 @@
-"""The solver path of lattices too large for the persistent kernel (V_h >
-2^18): three kernels per iteration (Dslash D_oe; D_eo with the A epilogue and
-(p, Ap); the fused shift/residual update with (r, r)) driven by a CUDA-graph
-WHILE loop whose condition the device sets, or the same kernels as plain
-launches.  STAG_PERSISTENT=0 sends small lattices down this path, so it is
-checked against the FP64 oracle at sizes the oracle solves in seconds: the
-same bars as the persistent path (FP64 within 1e-10, mixed within the 1e-6
-true residual), and one whole trajectory."""
+"""The three-kernel solver iteration (Dslash D_oe; D_eo with the A epilogue
+and (p, Ap); the fused shift/residual update with (r, r)) driven by a
+CUDA-graph WHILE loop whose condition the device sets, or the same kernels as
+plain launches: the path STAG_PERSISTENT=0 selects instead of the persistent
+solver.  Checked against the FP64 oracle at sizes the oracle solves in
+seconds: the same bars as the persistent path (FP64 within 1e-10, mixed
+within the 1e-6 true residual), and one whole trajectory."""
 import numpy as np
 import pytest
 

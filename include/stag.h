@@ -234,9 +234,20 @@ stag_status stag_draw_sources(stag_ctx* ctx, unsigned long long seed, unsigned l
 /* ---- the RHMC trajectory (Sec. 2, Sec. 4) -------------------------------- */
 
 #define STAG_MAX_FLAVOURS 2
+/* One fermion term of the action: a flavour at its mass with n_pf
+ * pseudo-fermions (Sec. 2: multiple pseudo-fermions), or one term of a
+ * Hasenbusch mass split, det(A)^s = det(A_h)^s det(A / A_h)^s: the heavy term
+ * is an ordinary flavour at m_h, the ratio term one at m whose rationals
+ * approximate ((x + m_h^2 - m^2) / x)^s (heatbath: its power -1/2) -- the
+ * same multi-shift solves and force formula with other coefficients.
+ * level 0 puts the term's force on the outer integration level; level 1 on
+ * a middle level of n_mid minimum-norm steps per outer half step around the
+ * gauge level (stag_hmc.n_mid >= 1), where a split puts its heavy term
+ * (large force, cheap solves).  Zero-initialised structs give level 0. */
 typedef struct {
     double mass;
     int n_pf;                   /* pseudo-fermions of this flavour */
+    int level;                  /* 0: outer level; 1: middle level (no counterpart in the paper) */
     stag_rational hb;           /* heatbath rational, ~ x^(+s/2)             */
     stag_rational md;           /* MD-force rational, ~ x^(-s)               */
     stag_rational met;          /* Metropolis rational, ~ x^(-s), tighter    */
@@ -267,7 +278,8 @@ typedef struct {
     int use_surrogate;          /* 1: three levels -- exact remainder F - F^ on the outer level,
                                    the loaded surrogate F^ on n_mid minimum-norm steps per outer
                                    half step, the gauge level inside (needs stag_surrogate_load) */
-    int n_mid;
+    int n_mid;                  /* minimum-norm steps of the middle level per outer half step
+                                   (the surrogate and the level-1 flavour terms); >= 1 when used */
 } stag_hmc;
 
 typedef struct {

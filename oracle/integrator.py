@@ -13,6 +13,11 @@ Sint; ref. [hmc] Duane, Kennedy, Pendleton, Roweth).
     (oracle/surrogate.py) on n_mid minimum-norm steps per outer half step,
     the gauge level inside those; the levels add up to the exact force, so
     the integrator stays reversible and area-preserving for any F^
+  * a flavour term may sit on that middle level instead of the outer one
+    (Flavour.level = 1): a Hasenbusch mass split puts the heavy term, whose
+    force is large and whose solves are cheap, on the middle level and the
+    light-over-heavy ratio term, small force and expensive solves, outside
+    (the paper's multiple pseudo-fermions, Sec. 2, extended by a mass split)
   * Metropolis on dH = H_f - H_i with H = 1/2 sum p_a^2 + S_g + S_f, where the
     final S_f uses the Metropolis rational (tighter than the MD one, Sec. 2)
     and the initial S_f = xi^dag xi.
@@ -37,6 +42,7 @@ class Flavour:
     md: object          # rational for the MD force, ~ x^(-s)
     met: object         # rational for the Metropolis action, ~ x^(-s)
     n_pf: int = 1
+    level: int = 0      # 0: outer integration level; 1: the middle level
 
 
 @dataclass
@@ -71,9 +77,12 @@ class Context:
             out = out + a * x
         return out, xs
 
-    def fermion_force_total(self, u, phis):
+    def fermion_force_total(self, u, phis, level=None):
+        """Summed force of the flavour terms on one integration level (all with level None)."""
         f = np.zeros(u.shape[:5] + (8,))
         for fl, phi_list in zip(self.p.flavours, phis):
+            if level is not None and fl.level != level:
+                continue
             for phi in phi_list:
                 xs = self.shifted_solves(u, fl.mass, phi, fl.md.beta, self.p.tol_md)
                 f += fermion_force(u, xs, fl.md.alpha, self.eta, self.par)
@@ -113,33 +122,46 @@ def surrogate_force(u, params):
     return sur.surrogate_force(params, f, G, quant=bool(params.get("quant", False)))
 
 
-def surrogate_level(u, mom, h, n_mid, n_gauge, beta, params):
-    """n_mid minimum-norm steps of size h/n_mid with the surrogate force F^,
-    the gauge level for the link updates."""
+def middle_level(u, mom, h, n_mid, n_gauge, beta, force):
+    """n_mid minimum-norm steps of size h/n_mid with force(u), the gauge
+    level for the link updates."""
     d = h / n_mid
     for _ in range(n_mid):
-        mom = mom - LAMBDA_2MN * d * surrogate_force(u, params)
+        mom = mom - LAMBDA_2MN * d * force(u)
         u, mom = gauge_level(u, mom, d / 2, n_gauge, beta)
-        mom = mom - (1 - 2 * LAMBDA_2MN) * d * surrogate_force(u, params)
+        mom = mom - (1 - 2 * LAMBDA_2MN) * d * force(u)
         u, mom = gauge_level(u, mom, d / 2, n_gauge, beta)
-        mom = mom - LAMBDA_2MN * d * surrogate_force(u, params)
+        mom = mom - LAMBDA_2MN * d * force(u)
     return u, mom
 
 
+def surrogate_level(u, mom, h, n_mid, n_gauge, beta, params):
+    """n_mid minimum-norm steps of size h/n_mid with the surrogate force F^,
+    the gauge level for the link updates."""
+    return middle_level(u, mom, h, n_mid, n_gauge, beta, lambda v: surrogate_force(v, params))
+
+
 def md_evolve(ctx, u, mom, phis, tau, n_outer, n_gauge, surrogate=None, n_mid=1):
-    """Two-level minimum-norm integration of length tau; with surrogate
-    params, three levels (outer force F_f - F^, middle F^, inner gauge)."""
+    """Two-level minimum-norm integration of length tau; three levels when
+    surrogate params are given (outer force F_f - F^, middle F^) or a flavour
+    has level 1 (outer: the level-0 terms, middle: the level-1 terms), the
+    gauge level innermost."""
     p = ctx.p
     e = tau / n_outer
+    mid_terms = any(fl.level == 1 for fl in p.flavours)
 
     def outer_force(u):
-        f = ctx.fermion_force_total(u, phis)
+        f = ctx.fermion_force_total(u, phis, level=0 if mid_terms else None)
         return f if surrogate is None else f - surrogate_force(u, surrogate)
 
+    def middle_force(u):
+        f = ctx.fermion_force_total(u, phis, level=1) if mid_terms else 0.0
+        return f if surrogate is None else f + surrogate_force(u, surrogate)
+
     def inner(u, mom):
-        if surrogate is None:
+        if surrogate is None and not mid_terms:
             return gauge_level(u, mom, e / 2, n_gauge, p.beta)
-        return surrogate_level(u, mom, e / 2, n_mid, n_gauge, p.beta, surrogate)
+        return middle_level(u, mom, e / 2, n_mid, n_gauge, p.beta, middle_force)
 
     for _ in range(n_outer):
         mom = mom - LAMBDA_2MN * e * outer_force(u)

@@ -68,27 +68,37 @@ def _golden_max(g, a, b, iters=80):
 class Rational:
     """alpha_0 + sum_i alpha_i / (x + beta_i), with its minimax error."""
 
-    def __init__(self, s, lo, hi, a0, alpha, beta, err):
+    def __init__(self, s, lo, hi, a0, alpha, beta, err, delta=0.0):
         self.s, self.lo, self.hi = s, lo, hi
         self.a0, self.alpha, self.beta, self.err = a0, alpha, beta, err
+        self.delta = delta      # 0: x^(-s); > 0: x^(-s) (x + delta)^s
 
     def __call__(self, x):
         return self.a0 + sum(a / (x + b) for a, b in zip(self.alpha, self.beta))
 
     def as_dict(self):
-        return {"s": self.s, "lo": self.lo, "hi": self.hi, "n": len(self.alpha),
-                "a0": self.a0, "alpha": list(self.alpha), "beta": list(self.beta),
-                "err": self.err}
+        d = {"s": self.s, "lo": self.lo, "hi": self.hi, "n": len(self.alpha),
+             "a0": self.a0, "alpha": list(self.alpha), "beta": list(self.beta),
+             "err": self.err}
+        if self.delta:
+            d["delta"] = self.delta
+        return d
 
 
-def remez(s, lo, hi, n, dps=80, max_iter=60, verbose=False):
-    """Relative-minimax type (n, n) approximation of x^(-s) on [lo, hi]."""
+def remez(s, lo, hi, n, dps=80, max_iter=60, verbose=False, delta=0.0):
+    """Relative-minimax type (n, n) approximation of x^(-s) on [lo, hi], or,
+    with delta > 0, of the mass-ratio function x^(-s) (x + delta)^s: for
+    A = m^2 - D_eo D_oe with spectrum x, (x + delta) is the spectrum of the
+    same operator at the heavier mass m_h^2 = m^2 + delta, so
+    r(A) ~ (A_h / A)^s is the ratio term of a Hasenbusch mass split
+    det(A)^s = det(A_h)^s det(A / A_h)^s."""
     with mp.workdps(dps):
-        lo_m, hi_m, s_m = mp.mpf(lo), mp.mpf(hi), mp.mpf(s)
+        lo_m, hi_m, s_m, d_m = mp.mpf(lo), mp.mpf(hi), mp.mpf(s), mp.mpf(delta)
         scale = hi_m
 
         def f_t(t):                        # f as a function of t = x / hi
-            return (t * scale) ** (-s_m)
+            x = t * scale
+            return x ** (-s_m) * (x + d_m) ** s_m if d_m > 0 else x ** (-s_m)
 
         tlo = lo_m / scale
         m = 2 * n + 2
@@ -155,7 +165,9 @@ def remez(s, lo, hi, n, dps=80, max_iter=60, verbose=False):
         order = sorted(range(n), key=lambda i: beta[i])
         alpha = [alpha[i] for i in order]
         beta = [beta[i] for i in order]
-        return Rational(float(s), float(lo), float(hi), float(p[n]), alpha, beta, float(err))
+        r = Rational(float(s), float(lo), float(hi), float(p[n]), alpha, beta, float(err))
+        r.delta = float(delta)
+        return r
 
 
 def apply_rational(r, solve_shifted, phi):

@@ -12,7 +12,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libstag.so")
-SOURCES = ["api.cu", "gauge.cu", "dslash.cu", "solver.cu", "blas.cu", "force.cu", "hmc.cu", "noalloc.cu", "persistent.cu", "surrogate.cu", "batch.cu"]
+SOURCES = ["api.cu", "gauge.cu", "dslash.cu", "solver.cu", "blas.cu", "force.cu", "hmc.cu", "noalloc.cu", "persistent.cu", "persistent_f32_18.cu",
+           "persistent_f32_12.cu", "persistent_bf16_12.cu", "persistent_ff.cu", "surrogate.cu", "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -43,7 +44,7 @@ def build(debug=False, verbose=False):
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")
         return obj, r.stderr
 
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
+    with cf.ThreadPoolExecutor(max_workers=min(len(srcs), max(8, os.cpu_count() or 8))) as ex:
         results = list(ex.map(one, srcs))
     if verbose:
         for _, err in results:

@@ -277,7 +277,10 @@ template <typename R> struct EpiAop {
     }
 };
 
-inline int dslash_nr_for(int nrhs) { return nrhs >= 2 ? 4 : 1; }
+// sources per thread: every link load serves NR of them (the many-source
+// Dslash of the force, Y_i = D_oe X_i over flavours x pseudo-fermions x
+// shifts, takes 8)
+inline int dslash_nr_for(int nrhs) { return nrhs >= 16 ? 8 : nrhs >= 2 ? 4 : 1; }
 
 // Threads per site: enough threads to fill the GPU at small volumes (about
 // 2^19 in flight), one per site once the lattice alone provides them.

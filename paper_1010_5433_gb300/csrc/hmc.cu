@@ -342,15 +342,22 @@ struct Traj {
         return std::isfinite(dh) ? STAG_OK : STAG_ERR_NAN;
     }
 
-    // p -= c F_fermion (all flavours, all pseudo-fermions in one force evaluation)
-    stag_status fermion_kick(double c) {
+    // p -= c F_fermion of the flavour terms on integration level `level` (all
+    // of them, and all their pseudo-fermions, in one force evaluation)
+    stag_status fermion_kick(double c, int level) {
         CKS(timer->begin(1));
         ForceTerm terms[STAG_MAX_FLAVOURS];
+        int nt = 0;
         for (int f = 0; f < p->n_flavours; ++f)
-            terms[f] = ForceTerm{p->flavour[f].mass, &p->flavour[f].md, p->flavour[f].n_pf, phi_of(f)};
-        if (p->n_flavours > 0)
-            CKS(fermion_force_terms(ctx, terms, p->n_flavours, p->md_prec, mom, -c, 1, p->tol_md, p->max_iter, &ts));
+            if (p->flavour[f].level == level)
+                terms[nt++] = ForceTerm{p->flavour[f].mass, &p->flavour[f].md, p->flavour[f].n_pf, phi_of(f)};
+        if (nt > 0) CKS(fermion_force_terms(ctx, terms, nt, p->md_prec, mom, -c, 1, p->tol_md, p->max_iter, &ts));
         return timer->end(1);
+    }
+    bool has_middle_terms() const {
+        for (int f = 0; f < p->n_flavours; ++f)
+            if (p->flavour[f].level == 1) return true;
+        return false;
     }
     stag_status gauge_kick(double c) { return gauge_force_launch(ctx, upd, p->beta, mom, -c, 1); }
 
@@ -368,25 +375,32 @@ struct Traj {
         return timer->end(2);
     }
 
-    // the level between fermion steps: the gauge level, or with the surrogate
-    // n_mid minimum-norm steps of F^ around gauge levels
+    // the level between fermion steps: the gauge level, or, with the surrogate
+    // or flavour terms on the middle level (a Hasenbusch mass split), n_mid
+    // minimum-norm steps of their force around gauge levels
     stag_status inner(double h) {
-        if (!p->use_surrogate) return gauge_level(h, p->n_gauge);
+        if (!p->use_surrogate && !has_middle_terms()) return gauge_level(h, p->n_gauge);
         const int n = p->n_mid;
         const double d = h / n;
-        CKS(sur_kick(LAMBDA_2MN * d));
+        CKS(mid_kick(LAMBDA_2MN * d));
         for (int j = 0; j < n; ++j) {
             CKS(gauge_level(d / 2, p->n_gauge));
-            CKS(sur_kick((1 - 2 * LAMBDA_2MN) * d));
+            CKS(mid_kick((1 - 2 * LAMBDA_2MN) * d));
             CKS(gauge_level(d / 2, p->n_gauge));
-            CKS(sur_kick((j == n - 1 ? 1.0 : 2.0) * LAMBDA_2MN * d));
+            CKS(mid_kick((j == n - 1 ? 1.0 : 2.0) * LAMBDA_2MN * d));
         }
         return STAG_OK;
     }
-    stag_status sur_kick(double c) { return surrogate_force_launch(ctx, mom, -c, 1); }
-    // outer kick: p -= c F_fermion, and with the surrogate p += c F^ (the exact remainder)
+    // p -= c (F^ + F of the middle-level flavour terms)
+    stag_status mid_kick(double c) {
+        if (p->use_surrogate) CKS(surrogate_force_launch(ctx, mom, -c, 1));
+        if (has_middle_terms()) CKS(fermion_kick(c, 1));
+        return STAG_OK;
+    }
+    // outer kick: p -= c F_fermion of the outer-level terms, and with the
+    // surrogate p += c F^ (the exact remainder)
     stag_status outer_kick(double c) {
-        CKS(fermion_kick(c));
+        CKS(fermion_kick(c, 0));
         if (p->use_surrogate) CKS(surrogate_force_launch(ctx, mom, c, 1));
         return STAG_OK;
     }
@@ -432,6 +446,9 @@ stag_status check_hmc(stag_ctx* ctx, const stag_hmc* p) {
     if (!ctx || !p) return STAG_ERR_ARG;
     if (!ctx->has_gauge) return STAG_ERR_NO_GAUGE;
     if (p->use_surrogate && (p->n_mid < 1 || !ctx->sur_loaded)) return STAG_ERR_ARG;
+    for (int f = 0; f < p->n_flavours && f < STAG_MAX_FLAVOURS; ++f)
+        if (p->flavour[f].level < 0 || p->flavour[f].level > 1 || (p->flavour[f].level == 1 && p->n_mid < 1))
+            return STAG_ERR_ARG;
     if (p->n_outer < 1 || p->n_gauge < 1 || !(p->tau > 0) || p->n_flavours < 0 ||
         p->n_flavours > STAG_MAX_FLAVOURS || p->max_iter < 1 || p->md_prec < STAG_FP64 ||
         p->md_prec > STAG_BF16_12 || !(p->tol_md > 0) || !(p->tol_met > 0))
@@ -536,6 +553,8 @@ struct StreamSwap {
 };
 
 bool same_schedule(const stag_hmc& a, const stag_hmc& b) {
+    for (int f = 0; f < a.n_flavours; ++f)
+        if (a.flavour[f].level != 0 || b.flavour[f].level != 0) return false;   // batched chains: one fermion level
     if (a.n_outer != b.n_outer || a.n_gauge != b.n_gauge || a.tau != b.tau || a.md_prec != b.md_prec ||
         a.n_flavours != b.n_flavours || a.use_surrogate != b.use_surrogate || (a.use_surrogate && a.n_mid != b.n_mid) ||
         (a.ext_phi != nullptr) != (b.ext_phi != nullptr))

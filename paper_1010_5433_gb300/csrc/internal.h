@@ -229,6 +229,13 @@ stag_status ms_core_multi(MsRun* runs, int n, MsStats* stats, stag_status* per_c
 // persistent.cu: the whole iteration loop in one cooperative launch
 bool persistent_fits(stag_ctx* ctx);
 int persistent_ring_slots();        // residual fields the persistent solver cycles through
+// the link formats' instances of the persistent solver (persistent_<format>.cu)
+#define STAG_PERSISTENT_ARGS stag_ctx* ctx, int nrhs, void* ring, size_t rstride, void* p, void* q, void* t, \
+    void* ps, void* x, const double2* b64, double2* x64, double2* t64
+stag_status launch_persistent_f32_18(STAG_PERSISTENT_ARGS);
+stag_status launch_persistent_f32_12(STAG_PERSISTENT_ARGS);
+stag_status launch_persistent_bf16_12(STAG_PERSISTENT_ARGS);
+stag_status launch_persistent_ff(STAG_PERSISTENT_ARGS);
 stag_status launch_persistent(stag_ctx* ctx, stag_prec prec, int nrhs, void* ring, size_t rstride, void* p, void* q,
                               void* t, void* ps, void* x, const double2* b64, double2* x64, double2* t64);
 

@@ -37,10 +37,13 @@ def stats(trajs):
 
 
 def run(trajectories=100, n_outers=(20,), fp64_n_outer=None, md_links="12", warmup=5, log=print, n_pfs=(1,),
-        fp64=True):
+        fp64=True, splits=()):
     """Arms: the mixed path at every n_outer x n_pf (n_pf pseudo-fermions,
     s = 1 / (2 n_pf) each: the paper's multiple pseudo-fermions, Sec. 2), and
-    the fp64 path at fp64_n_outer (default: the first n_outer) with one."""
+    the fp64 path at fp64_n_outer (default: the first n_outer) with one;
+    splits: (n_outer, n_mid, n_gauge) of mixed-path arms with the Hasenbusch
+    mass split of workload.py (ratio term outside, heavy term on the middle
+    level)."""
     import torch
 
     from . import stag, workload as W
@@ -69,6 +72,16 @@ def run(trajectories=100, n_outers=(20,), fp64_n_outer=None, md_links="12", warm
         arms = [("mixed", md_prec, no, npf) for npf in n_pfs for no in n_outers]
         if fp64:
             arms.append(("fp64", stag.STAG_FP64, fp64_n_outer or n_outers[0], 1))
+        if splits:
+            ratio, heavy = W.split_rationals()
+        for no, nm, ng in splits:
+            stag.stag_load_gauge(ctx, start)
+            trajs = [stag.stag_md_trajectory(ctx, W.make_hmc_split(stag, ratio, heavy, md_prec, seed, 30_000 + k, no, nm,
+                                                                   ng)) for k in range(trajectories)]
+            key = f"split_n_outer_{no}_n_mid_{nm}_n_gauge_{ng}"
+            out["arms"][key] = dict(stats(trajs), prec=int(md_prec), n_outer=no, n_mid=nm, n_gauge=ng,
+                                    dH=[round(t.dH, 5) for t in trajs])
+            log(f"{key}: " + json.dumps({k: v for k, v in out["arms"][key].items() if k != "dH"}))
         for name, prec, no, npf in arms:
             stag.stag_load_gauge(ctx, start)
             r_arm = rats if npf == 1 else W.rationals(npf)
@@ -93,6 +106,9 @@ if __name__ == "__main__":
     ap.add_argument("--md-links", default="12")
     ap.add_argument("--n-pf", type=int, nargs="+", default=[1])
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--split", nargs="*", default=[], help="n_outer:n_mid:n_gauge of Hasenbusch-split arms")
+    ap.add_argument("--no-plain", action="store_true", help="only the split arms (and fp64 unless --no-fp64)")
     a = ap.parse_args()
-    print(json.dumps(run(a.trajectories, tuple(a.n_outer), a.fp64_n_outer, a.md_links, n_pfs=tuple(a.n_pf),
-                         fp64=not a.no_fp64)))
+    splits = tuple(tuple(int(v) for v in x.split(":")) for x in a.split)
+    print(json.dumps(run(a.trajectories, () if a.no_plain else tuple(a.n_outer), a.fp64_n_outer or a.n_outer[0],
+                         a.md_links, n_pfs=tuple(a.n_pf), fp64=not a.no_fp64, splits=splits)))

@@ -29,6 +29,7 @@ class RationalApprox:
         self.alpha = [float(a) for a in alpha]
         self.beta = [float(b) for b in beta]
         self.err = float(err)
+        self.delta = 0.0        # > 0: approximates ((x + delta) / x)^s
 
     @property
     def n(self):
@@ -150,17 +151,22 @@ def _extrema(err, tlo, m):
     return alt
 
 
-def remez(s, lo, hi, n, dps=None, max_iter=80):
-    """Relative-minimax r(x) ~ x^(-s) on [lo, hi] with n partial fractions."""
-    if not (0 < lo < hi) or n < 1:
-        raise ValueError("need 0 < lo < hi and n >= 1")
+def remez(s, lo, hi, n, dps=None, max_iter=80, delta=0.0):
+    """Relative-minimax r(x) ~ x^(-s) on [lo, hi] with n partial fractions;
+    with delta > 0, r(x) ~ ((x + delta) / x)^s, the ratio term of a Hasenbusch
+    mass split (x + delta is the spectrum of A at m_h^2 = m^2 + delta)."""
+    if not (0 < lo < hi) or n < 1 or delta < 0:
+        raise ValueError("need 0 < lo < hi, n >= 1 and delta >= 0")
+    if delta > 0:
+        return _ratio_by_moebius(s, lo, hi, n, delta, dps, max_iter)
     dps = dps or (30 + 3 * n)
     with mp.workdps(dps):
-        s_m, hi_m = mp.mpf(s), mp.mpf(hi)
+        s_m, hi_m, d_m = mp.mpf(s), mp.mpf(hi), mp.mpf(delta)
         tlo = mp.mpf(lo) / hi_m
 
         def f(t):
-            return (t * hi_m) ** (-s_m)
+            x = t * hi_m
+            return x ** (-s_m) * (x + d_m) ** s_m if d_m > 0 else x ** (-s_m)
 
         m = 2 * n + 2
         ts = [tlo ** ((1 + mp.cos(mp.pi * j / (m - 1))) / 2) for j in range(m)]
@@ -196,7 +202,34 @@ def remez(s, lo, hi, n, dps=None, max_iter=80):
             alpha.append(_horner(p, t_i) / _horner(dq, t_i) * hi_m)
             beta.append(-t_i * hi_m)
         order = sorted(range(n), key=lambda i: beta[i])
-        return RationalApprox(s, lo, hi, p[n], [alpha[i] for i in order], [beta[i] for i in order], emax)
+        r = RationalApprox(s, lo, hi, p[n], [alpha[i] for i in order], [beta[i] for i in order], emax)
+        r.delta = float(delta)
+        return r
+
+
+def _ratio_by_moebius(s, lo, hi, n, delta, dps, max_iter):
+    """((x + delta) / x)^s on [lo, hi] through the change of variable
+    y = x / (x + delta), under which the function is y^(-s) on
+    [lo / (lo + delta), hi / (hi + delta)].  y is a Moebius function of x, so a
+    type (n, n) rational in y is one in x and the relative minimax error is
+    the same; each partial fraction maps as
+        alpha / (y + beta) = alpha / (1 + beta) (1 + (delta - b) / (x + b)),
+        b = beta delta / (1 + beta)."""
+    with mp.workdps(dps or (30 + 3 * n)):
+        d = mp.mpf(delta)
+        ry = remez(s, float(mp.mpf(lo) / (lo + d)), float(mp.mpf(hi) / (hi + d)), n, dps, max_iter)
+        a0 = mp.mpf(ry.a0)
+        alpha, beta = [], []
+        for a, bt in zip(ry.alpha, ry.beta):
+            a, bt = mp.mpf(a), mp.mpf(bt)
+            b = bt * d / (1 + bt)
+            a0 += a / (1 + bt)
+            alpha.append(a * (d - b) / (1 + bt))
+            beta.append(b)
+        order = sorted(range(n), key=lambda i: beta[i])
+        r = RationalApprox(s, lo, hi, a0, [alpha[i] for i in order], [beta[i] for i in order], ry.err)
+        r.delta = float(delta)
+        return r
 
 
 def rhmc_rationals(n_flavours, n_pf, mass, n_md, n_met, upper=16.0):
@@ -223,8 +256,19 @@ WORKLOADS = {
     "c2_pf2_md": (0.25, 0.02, 12), "c2_pf2_met": (0.25, 0.02, 20), "c2_pf2_hb": (-0.125, 0.02, 20),
     "c2_pf3_md": (1.0 / 6.0, 0.02, 12), "c2_pf3_met": (1.0 / 6.0, 0.02, 20), "c2_pf3_hb": (-1.0 / 12.0, 0.02, 20),
     "c2_pf4_md": (0.125, 0.02, 12), "c2_pf4_met": (0.125, 0.02, 20), "c2_pf4_hb": (-0.0625, 0.02, 20),
+    # the 16^4 workload with a Hasenbusch mass split at m_h = 0.2: the heavy term x^(-1/2) at m_h and the
+    # ratio term ((x + delta) / x)^(1/2) at m = 0.02, delta = m_h^2 - m^2 = 0.0396
+    "c2_heavy_md": (0.5, 0.2, 8), "c2_heavy_met": (0.5, 0.2, 14), "c2_heavy_hb": (-0.25, 0.2, 14),
+    "c2_ratio_md": (0.5, 0.02, 8, 0.0396), "c2_ratio_met": (0.5, 0.02, 12, 0.0396),
+    "c2_ratio_hb": (-0.25, 0.02, 12, 0.0396),
 }
 TABLE_PATH = __import__("os").path.join(__import__("os").path.dirname(__file__), "rational_table.json")
+
+
+def _spec(name):
+    """(s, m, n, delta) of a workload rational (delta 0 unless it is a mass ratio)."""
+    w = WORKLOADS[name]
+    return (w[0], w[1], w[2], w[3] if len(w) > 3 else 0.0)
 
 
 def load(name):
@@ -232,25 +276,30 @@ def load(name):
     or computed now if the table lacks it."""
     import json
     import os
-    s, m, n = WORKLOADS[name]
+    s, m, n, delta = _spec(name)
     if os.path.exists(TABLE_PATH):
         tab = json.load(open(TABLE_PATH))
         if name in tab and tab[name]["n"] == n:
             d = tab[name]
-            return RationalApprox(d["s"], d["lo"], d["hi"], d["a0"], d["alpha"], d["beta"], d["err"])
-    return remez(s, m * m, 16 + m * m, n)
+            r = RationalApprox(d["s"], d["lo"], d["hi"], d["a0"], d["alpha"], d["beta"], d["err"])
+            r.delta = d.get("delta", 0.0)
+            return r
+    return remez(s, m * m, 16 + m * m, n, delta=delta)
 
 
 def write_table(names=None):
     import json
     import os
     tab = json.load(open(TABLE_PATH)) if os.path.exists(TABLE_PATH) else {}
-    for name, (s, m, n) in WORKLOADS.items():
+    for name in WORKLOADS:
+        s, m, n, delta = _spec(name)
         if (names and name not in names) or (name in tab and tab[name]["n"] == n):
             continue
-        r = remez(s, m * m, 16 + m * m, n)
+        r = remez(s, m * m, 16 + m * m, n, delta=delta)
         tab[name] = {"s": r.s, "lo": r.lo, "hi": r.hi, "n": r.n, "a0": r.a0, "alpha": r.alpha, "beta": r.beta,
                      "err": r.err, "mass": m}
+        if delta:
+            tab[name]["delta"] = delta
         json.dump(tab, open(TABLE_PATH, "w"), indent=1)
         print(name, r.n, r.err, flush=True)
 

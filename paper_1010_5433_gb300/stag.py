@@ -42,8 +42,8 @@ class stag_solve_info(C.Structure):
 
 
 class stag_flavour(C.Structure):
-    _fields_ = [("mass", C.c_double), ("n_pf", C.c_int), ("hb", stag_rational), ("md", stag_rational),
-                ("met", stag_rational)]
+    _fields_ = [("mass", C.c_double), ("n_pf", C.c_int), ("level", C.c_int), ("hb", stag_rational),
+                ("md", stag_rational), ("met", stag_rational)]
 
 
 class stag_hmc(C.Structure):

@@ -84,3 +84,34 @@ def thermalise(stag, ctx, rats, seed, md_prec, log=None):
         if log:
             log(f"thermalisation {k}: dH {t.dH:+.4f} accepted {t.accepted} plaquette {t.plaq:.5f}")
     return plaq
+
+
+# Hasenbusch mass split of the flavour (paper Sec. 2's multiple pseudo-fermions,
+# extended by a heavier mass): det(A)^(1/2) = det(A_h)^(1/2) det(A / A_h)^(1/2)
+# with m_h = 0.2; the ratio term at m on the outer level, the heavy term on the
+# middle level.
+HEAVY_MASS = 0.2
+
+
+def split_rationals():
+    from . import rational
+    return ({k: rational.load(f"c2_ratio_{k}") for k in ("md", "met", "hb")},
+            {k: rational.load(f"c2_heavy_{k}") for k in ("md", "met", "hb")})
+
+
+def make_hmc_split(stag, ratio, heavy, prec, seed, counter, n_outer, n_mid, n_gauge=None):
+    """stag_hmc of one trajectory with the mass split: flavour 0 the ratio
+    term (mass m, outer level), flavour 1 the heavy term (mass m_h, middle
+    level, n_mid steps per outer half step)."""
+    w = WORKLOAD
+    p = stag.stag_hmc()
+    p.beta, p.tau, p.n_outer, p.n_gauge = w["beta"], w["tau"], n_outer, n_gauge or w["n_gauge"]
+    p.n_flavours, p.n_mid = 2, n_mid
+    for f, (mass, level, r) in enumerate(((w["mass"], 0, ratio), (HEAVY_MASS, 1, heavy))):
+        fl = p.flavour[f]
+        fl.mass, fl.n_pf, fl.level = mass, 1, level
+        fl.hb, fl.md, fl.met = r["hb"].to_abi(), r["md"].to_abi(), r["met"].to_abi()
+    p.tol_md, p.tol_met, p.max_iter = w["tol_md"], w["tol_met"], 20000
+    p.md_prec = prec
+    p.seed, p.counter = seed, counter
+    return p

@@ -3,7 +3,8 @@ workloads, computed by the oracle's Remez (oracle/rational.py) and nothing
 else.  Run:  python tests/golden/make_rationals.py
 
 Each entry: r(x) = a0 + sum_i alpha_i / (x + beta_i) ~ x^(-s) on [lo, hi] with
-its relative minimax error.  Exponents per pseudo-fermion s = N_f / (4 n_pf)
+its relative minimax error (entries with a "delta": ((x + delta) / x)^s, the
+ratio term of a Hasenbusch mass split).  Exponents per pseudo-fermion s = N_f / (4 n_pf)
 (MD and Metropolis) and -s/2 (heatbath, r_hb ~ x^(+s/2)); ranges
 [m^2, 16 + m^2], the spectrum bound of A = m^2 - D_eo D_oe.
 """
@@ -53,19 +54,29 @@ TABLE = {
     "c2_pf4_md": (0.125, 0.02, 12),
     "c2_pf4_met": (0.125, 0.02, 20),
     "c2_pf4_hb": (-0.0625, 0.02, 20),
+    # Hasenbusch mass split of the 16^4 workload: heavy term at m_h = 0.2, ratio term
+    # ((x + delta) / x)^(1/2) at m = 0.02 with delta = m_h^2 - m^2 = 0.0396
+    "c2_heavy_md": (0.5, 0.2, 8),
+    "c2_heavy_met": (0.5, 0.2, 14),
+    "c2_heavy_hb": (-0.25, 0.2, 14),
+    "c2_ratio_md": (0.5, 0.02, 8, 0.0396),
+    "c2_ratio_met": (0.5, 0.02, 12, 0.0396),
+    "c2_ratio_hb": (-0.25, 0.02, 12, 0.0396),
 }
 
 
 def main(names=None):
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "rationals.json")
     out = json.load(open(path)) if os.path.exists(path) else {}
-    for name, (s, m, n) in TABLE.items():
+    for name, spec in TABLE.items():
+        s, m, n = spec[:3]
+        delta = spec[3] if len(spec) > 3 else 0.0
         if names and name not in names:
             continue
         if name in out and out[name]["n"] == n:
             continue
         t = time.time()
-        r = remez(s, m * m, 16 + m * m, n, dps=60 if n <= 16 else 100)
+        r = remez(s, m * m, 16 + m * m, n, dps=60 if n <= 16 else 100, delta=delta)
         d = r.as_dict()
         d["mass"] = m
         out[name] = d

@@ -412,3 +412,58 @@ def test_fp64_and_mixed_paths_integrate_alike_at_16x4(torch):
         assert du < 1e-4
     finally:
         stag.stag_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec,tol_dh,tol_u", [(0, 1e-7, 1e-10), (2, 5e-3, 1e-5)])
+def test_hasenbusch_split_trajectory_matches_oracle(torch, prec, tol_dh, tol_u):
+    """A Hasenbusch mass split on 4^4: the ratio term ((x + delta) / x)^(1/2)
+    at m = 0.1 on the outer level, the heavy term x^(-1/2) at m_h = 0.4 on
+    a middle level of n_mid = 2 steps around the gauge level, against the
+    oracle's three-level integrator (supplied momenta and sources).  FP64: dH
+    to 1e-7, links to 1e-10; mixed (fp32 MD on 12-real links): the bounds of
+    the other mixed-path trajectory tests."""
+    from oracle import rational as orat
+    from paper_1010_5433_gb300 import stag
+    m, mh = 0.1, 0.4
+    delta = mh * mh - m * m
+    lo, hi, loh, hih = m * m, 16 + m * m, mh * mh, 16 + mh * mh
+    ratio = {"md": orat.remez(0.5, lo, hi, 6, dps=40, delta=delta),
+             "met": orat.remez(0.5, lo, hi, 12, dps=40, delta=delta),
+             "hb": orat.remez(-0.25, lo, hi, 12, dps=40, delta=delta)}
+    heavy = {"md": orat.remez(0.5, loh, hih, 6, dps=40),
+             "met": orat.remez(0.5, loh, hih, 12, dps=40),
+             "hb": orat.remez(-0.25, loh, hih, 12, dps=40)}
+    dims = DIMS
+    u0 = syn.near_identity_gauge(dims, 0x5A0004)
+    mom0 = syn.gaussian_momenta(dims, 401)
+    xis = [[syn.gaussian_fermion(dims, 402, on_parity=0)], [syn.gaussian_fermion(dims, 403, on_parity=0)]]
+    fls = [integrator.Flavour(mass=m, hb=ratio["hb"], md=ratio["md"], met=ratio["met"], level=0),
+           integrator.Flavour(mass=mh, hb=heavy["hb"], md=heavy["md"], met=heavy["met"], level=1)]
+    prm = integrator.HMCParams(dims=dims, beta=5.5, tau=0.5, n_outer=3, n_gauge=2, flavours=fls,
+                               tol_md=1e-13, tol_met=1e-13)
+    want = integrator.trajectory(integrator.Context(prm), u0, mom0, xis, n_mid=2)
+    ctx = stag.stag_create(dims, True)
+    try:
+        stag.stag_load_gauge(ctx, L.gauge_host(u0))
+        d_mom = torch.from_numpy(L.mom_to_abi(mom0, dims)).cuda()
+        d_xi = dev(torch, np.stack([L.to_half(x[0], dims, 0) for x in xis]))
+        p = stag.stag_hmc()
+        p.beta, p.tau, p.n_outer, p.n_gauge, p.n_flavours, p.n_mid = 5.5, 0.5, 3, 2, 2, 2
+        for f, (mass, lev, r) in enumerate(((m, 0, ratio), (mh, 1, heavy))):
+            fl = p.flavour[f]
+            fl.mass, fl.n_pf, fl.level = mass, 1, lev
+            for k in ("hb", "md", "met"):
+                setattr(fl, k, stag.make_rational(r[k].a0, r[k].alpha, r[k].beta))
+        p.tol_md = 1e-12 if prec == 0 else 1e-8
+        p.tol_met, p.max_iter, p.md_prec = 1e-12, 20000, prec
+        p.ext_mom, p.ext_xi, p.no_metropolis = d_mom.data_ptr(), d_xi.data_ptr(), 1
+        res = stag.stag_md_trajectory(ctx, p)
+        buf = np.empty(4 * 256 * 18)
+        stag.stag_store_gauge(ctx, buf)
+        du = np.abs(L.gauge_from_host(buf, dims) - want["u"]).max()
+        print(f"Hasenbusch split prec {prec}: dH gpu {res.dH:.9f} oracle {want['dH']:.9f}, max|dU| {du:.2e}")
+        assert abs(res.H0 - want["H0"]) < 1e-8 * abs(want["H0"])
+        assert abs(res.dH - want["dH"]) < tol_dh
+        assert du < tol_u
+    finally:
+        stag.stag_destroy(ctx)

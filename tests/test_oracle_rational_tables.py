@@ -43,12 +43,18 @@ def _coeffs(d):
     return mp.mpf(d["a0"]), [mp.mpf(a) for a in d["alpha"]], [mp.mpf(b) for b in d["beta"]], mp.mpf(d["s"])
 
 
+def _target_inv(d, x):
+    """1 / the approximated function at x: x^s, or (x / (x + delta))^s for a mass ratio."""
+    s, delta = mp.mpf(d["s"]), mp.mpf(d.get("delta", 0.0))
+    return x ** s if delta == 0 else (x / (x + delta)) ** s
+
+
 def _err_fn(d):
     a0, al, be, s = _coeffs(d)
 
     def e(u):                      # u = log x
         x = mp.e ** u
-        return (a0 + mp.fsum(a / (x + b) for a, b in zip(al, be))) * x ** s - 1
+        return (a0 + mp.fsum(a / (x + b) for a, b in zip(al, be))) * _target_inv(d, x) - 1
     return e
 
 
@@ -64,7 +70,7 @@ def _rounding_band(d, n_grid=800):
             r = a0 + mp.fsum(terms)
             kappa = (abs(a0) + mp.fsum(abs(q) for q in terms)) / abs(r)
             band = max(band, float(kappa) * ROUND * (1 + d["err"]))
-            worst = max(worst, float(abs(r * x ** s - 1)))
+            worst = max(worst, float(abs(r * _target_inv(d, x) - 1)))
         return band, worst
 
 
@@ -100,7 +106,10 @@ def _extrema(d, n_grid=6000):
 
 HIGH = ["c2_md", "c2_met", "c2_hb", "c3_light_md", "c3_light_met", "c3_light_hb", "c3_strange_md",
         "c3_strange_met", "c3_strange_hb", "c4_md", "c4_met", "c4_hb", "c1_met", "c1_hb",
-        "t3_high_md", "t3_high_met", "t3_high_hb", "t3_low_md", "t3_low_met", "t3_low_hb"]
+        "t3_high_md", "t3_high_met", "t3_high_hb", "t3_low_md", "t3_low_met", "t3_low_hb",
+        "c2_pf2_md", "c2_pf2_met", "c2_pf2_hb", "c2_pf3_md", "c2_pf3_met", "c2_pf3_hb",
+        "c2_pf4_md", "c2_pf4_met", "c2_pf4_hb", "c2_heavy_md", "c2_heavy_met", "c2_heavy_hb",
+        "c2_ratio_md", "c2_ratio_met", "c2_ratio_hb"]
 
 
 @pytest.mark.parametrize("name", HIGH)
@@ -136,7 +145,8 @@ def test_inverse_power_rationals_have_positive_partial_fractions(name):
     assert min(d["alpha"]) > 0 and min(d["beta"]) > 0
 
 
-@pytest.mark.parametrize("flavour", ["c1", "c2", "c3_light", "c3_strange", "c4", "t3_high", "t3_low"])
+@pytest.mark.parametrize("flavour", ["c1", "c2", "c3_light", "c3_strange", "c4", "t3_high", "t3_low", "c2_pf2",
+                                     "c2_pf3", "c2_pf4", "c2_heavy", "c2_ratio"])
 def test_heatbath_and_metropolis_rationals_are_inverse(flavour):
     """phi = r_hb(A) xi makes phi^dag r_met(A) phi = xi^dag xi exactly only
     if r_hb^2 r_met = 1; the stored pair meets it within twice the heatbath

@@ -184,7 +184,7 @@ def run_gpu(args, rank, world, local_rank):
         launches = stag.stag_launch_count(ctx) - launches0
         prof = None
         if profile:
-            prof = [stag.stag_profile_read(ctx, kk) for kk in range(4)]
+            prof = [stag.stag_profile_read(ctx, kk) for kk in PROFILE_KINDS]
             stag.stag_profile_begin(ctx, 0)
         return ms, trajs, clk.summary(), launches, prof
 
@@ -218,7 +218,7 @@ def run_gpu(args, rank, world, local_rank):
 
     # ---- roofline of the dominant kernel, from the live sampled events
     hbm, peak_kind = peaks()
-    names = ["dslash_oe", "dslash_eo_A", "update", "persistent_iteration"]
+    names = PROFILE_NAMES
     kern = []
     for nm, pr in zip(names, prof):
         avg_ms = pr.sampled_ms / max(pr.sampled, 1)
@@ -236,7 +236,8 @@ def run_gpu(args, rank, world, local_rank):
                 "note": "unit = one solver iteration; 16^4 fields are L2-resident inside a trajectory; achieved = "
                         "the multi-shift CG iteration's algorithmic bytes (2 link passes + (8 + 4 n_live) spinor "
                         "passes) / CUDA-event time of every persistent launch on the context's stream divided by "
-                        "its iterations",
+                        "its iterations; the fp32 iterations (MD solves) and the float-float ones (heatbath, "
+                        "Metropolis) are timed apart",
                 "kernels": kern}
 
     point = dslash_roofline_point(hbm) if rank == 0 else None
@@ -282,18 +283,32 @@ def run_gpu(args, rank, world, local_rank):
                          "thermalisation": {"plaquette_by_decade": [round(float(np.mean(therm_plaq[i:i + 10])), 5)
                                                                     for i in range(0, len(therm_plaq), 10)],
                                             "seconds": round(t_therm, 1)},
-                         "e2e_replays_timed": all(a.dH == b.dH for a, b in zip(trajs, e2e_trajs))},
+                         "e2e_replays_timed": all(a.dH == b.dH for a, b in zip(trajs, e2e_trajs)),
+                         "e2e_max_abs_dH_difference": max(abs(a.dH - b.dH) for a, b in zip(trajs, e2e_trajs))},
         "dslash_roofline_point": point,
         "batched_chains": chains,
     }
     return out
 
 
+# kernels whose live timing the library records (STAG_PK_*): the three-kernel
+# iteration's kernels, and the persistent solver in fp32 arithmetic (the MD
+# solves) and in float-float (the heatbath and Metropolis solves)
+PROFILE_KINDS = (0, 1, 2, 3, 5)
+PROFILE_NAMES = ("dslash_oe", "dslash_eo_A", "update", "persistent_iteration_fp32", "persistent_iteration_ff")
+
 # DRAM traffic of the dominant kernel per unit (one solver iteration) from an
 # ncu capture of the same kernel on the same 16^4 lattice; empty once the
 # kernel has changed since the capture.  The capture is cold-cache (ncu
 # flushes caches between passes): one read of the working set, then L2 hits.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    "persistent_iteration_fp32": {
+        "bytes_per_unit": 909340,
+        "source": "ncu --set full of k_ms_persistent<float, FMT_F32_12, 1, 1, 256> on 16^4: one whole "
+                  "37-iteration solve of the 12-pole MD rational (solve_bench --prec 2 --tol 0.11), "
+                  "dram__bytes_read.sum 33.18 MB + dram__bytes_write.sum 0.46 MB per launch / 37 iterations",
+    },
+}
 
 
 def batched_chains():

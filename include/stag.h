@@ -342,6 +342,14 @@ stag_status stag_surrogate_add_force_sample(stag_ctx* ctx, const double* exact_f
 stag_status stag_surrogate_add_sample(stag_ctx* ctx, const stag_hmc* p, unsigned long long counter);
 /* Number of training samples (configurations) stored; 0 for a NULL ctx. */
 long long   stag_surrogate_samples(stag_ctx* ctx);
+/* Sets the training store's capacity to exactly n_samples configurations
+ * (896 bytes per link each: 24 features, 24 x 8 generators, 8 target
+ * components in fp32), so that a large training set is allocated once
+ * instead of growing by doubling (which copies and, near the end, needs
+ * twice the memory).  Keeps the samples already stored; STAG_ERR_ARG if
+ * n_samples is smaller than their number, STAG_ERR_ALLOC if the device
+ * cannot hold it.  No counterpart in the paper. */
+stag_status stag_surrogate_reserve(stag_ctx* ctx, long long n_samples);
 /* Mean over stored links of |F^ - F|^2 and its gradient (host, STAG_SUR_PARAMS doubles, may be NULL). */
 stag_status stag_surrogate_loss_grad(stag_ctx* ctx, double* loss, double* grad);
 /* steps full-batch Adam steps (learning rate lr); losses before the first and last step. */
@@ -361,12 +369,15 @@ stag_status stag_selftest_barrier_timeout(stag_ctx* ctx, long long spin_limit);
 #define STAG_PK_DSLASH_OE 0      /* t = D_oe (r + beta p), multi-RHS                             */
 #define STAG_PK_DSLASH_EO_A 1    /* p = r + beta p; q = c0 p - D_eo t; (p, q) and the alpha step */
 #define STAG_PK_UPDATE 2         /* p_i, x_i of the live shifts; r -= alpha q; (r, r), beta step  */
-#define STAG_PK_PERSISTENT 3     /* persistent solver (every volume): units are iterations,
-                                    every launch event-timed, bytes = one whole iteration       */
+#define STAG_PK_PERSISTENT 3     /* persistent solver in fp32 arithmetic (fp32 / 12-real / bf16
+                                    links; every volume): units are iterations, every launch
+                                    event-timed, bytes = one whole iteration                    */
 #define STAG_PK_BATCH 4          /* batched solver (stag_*_batch; profile of the first context):
                                     units are batched iterations (one iteration of every lattice
                                     still iterating), every launch event-timed, bytes = those
                                     iterations of all lattices                                   */
+#define STAG_PK_PERSISTENT_FF 5  /* persistent solver in float-float (the FP64 solves: heatbath,
+                                    Metropolis, the FP64 path's MD), as STAG_PK_PERSISTENT       */
 typedef struct {
     long long launches;       /* launches of this kernel since stag_profile_begin */
     int sampled;              /* of which bracketed by CUDA events on the context's stream */

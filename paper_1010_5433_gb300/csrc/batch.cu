@@ -42,13 +42,23 @@ struct BatchArgs {
     ChainArgs c[MAXC];
 };
 
-// one chain's scalar recurrences (one source)
+// one chain's scalar recurrences (one source), with float-float copies of
+// the coefficients every thread applies, made once per block when they
+// change: a per-thread fp64 load and conversion per site and shift runs on
+// GB300's slow fp64 pipe
 struct ScalM {
     double zeta[NS], zeta_prev[NS], zeta_next[NS], zratio[NS], cx[NS], cpr[NS], cpp[NS], dsig[NS];
     double rr, bb, rr_ref, alpha, alpha_prev, beta_prev, beta, sum, k4_units, c0, tol2, delta2;
+    DF cxD[NS], cprD[NS], cppD[NS], alphaD, betaD, c0D;
     int live[NS], iters_at[NS];
     int rhs_live, k, halt, status, need_reliable, nshift, max_iter, mixed, left, nan;
 };
+
+// a coefficient in the arithmetic of the iteration: the float part for fp32
+// fields, the float-float pair for float-float fields
+template <typename R> __device__ __forceinline__ R coef(const DF& d);
+template <> __device__ __forceinline__ float coef<float>(const DF& d) { return d.hi; }
+template <> __device__ __forceinline__ DF coef<DF>(const DF& d) { return d; }
 
 __device__ void load_scal_m(ScalM* S, const ChainArgs* C, int nc) {
     const int t = threadIdx.x;
@@ -61,6 +71,9 @@ __device__ void load_scal_m(ScalM* S, const ChainArgs* C, int nc) {
         S[c].cx[s] = st->cx[0][s];
         S[c].cpr[s] = st->cpr[0][s];
         S[c].cpp[s] = st->cpp[0][s];
+        S[c].cxD[s] = DF(st->cx[0][s]);
+        S[c].cprD[s] = DF(st->cpr[0][s]);
+        S[c].cppD[s] = DF(st->cpp[0][s]);
         S[c].dsig[s] = st->dsig[s];
         S[c].live[s] = st->live[0][s];
         S[c].iters_at[s] = st->iters_at[0][s];
@@ -72,11 +85,14 @@ __device__ void load_scal_m(ScalM* S, const ChainArgs* C, int nc) {
         s.bb = st->bb[0];
         s.rr_ref = st->rr_ref[0];
         s.alpha = st->alpha[0];
+        s.alphaD = DF(st->alpha[0]);
         s.alpha_prev = st->alpha_prev[0];
         s.beta_prev = st->beta_prev[0];
         s.beta = st->beta[0];
+        s.betaD = DF(st->beta[0]);
         s.k4_units = st->k4_units;
         s.c0 = st->c0;
+        s.c0D = DF(st->c0);
         s.tol2 = st->tol2;
         s.delta2 = st->delta2;
         s.rhs_live = st->rhs_live[0];
@@ -160,6 +176,7 @@ __device__ void alpha_step_m(ScalM* S, int nc, const Pairs& P) {
             a = 0.0;
         }
         S[t].alpha = a;
+        S[t].alphaD = DF(a);
     }
     __syncthreads();
     for (int i = t; i < P.base[nc]; i += blockDim.x) {
@@ -175,6 +192,7 @@ __device__ void alpha_step_m(ScalM* S, int nc, const Pairs& P) {
         C.zeta_next[s] = z * zr;
         C.zratio[s] = zr;
         C.cx[s] = a * zr;
+        C.cxD[s] = DF(C.cx[s]);
     }
     __syncthreads();
 }
@@ -207,6 +225,8 @@ __device__ void beta_step_m(ScalM* S, int nc, const Pairs& P) {
         const double zr = C.zratio[s];
         C.cpr[s] = zn;
         C.cpp[s] = s_beta[c] * zr * zr;
+        C.cprD[s] = DF(zn);
+        C.cppD[s] = DF(C.cpp[s]);
         C.zeta_prev[s] = z;
         C.zeta[s] = zn;
         if (zn * zn * C.sum <= C.tol2 * C.bb) {
@@ -220,6 +240,7 @@ __device__ void beta_step_m(ScalM* S, int nc, const Pairs& P) {
     if (t < nc && active[t]) {
         ScalM& C = S[t];
         C.beta = s_beta[t];
+        C.betaD = DF(s_beta[t]);
         C.alpha_prev = C.alpha;
         C.beta_prev = s_beta[t];
         C.rr = C.sum;
@@ -339,7 +360,7 @@ __device__ __forceinline__ double site_update(const ScalM& S, int h, int Vh, typ
         for (int u = 0; u < 4; ++u) {
             if (!on[u]) continue;
             const int s = s0 + u;
-            const R cx = (R)S.cx[s], cpr = (R)S.cpr[s], cpp = (R)S.cpp[s];
+            const R cx = coef<R>(S.cxD[s]), cpr = coef<R>(S.cprD[s]), cpp = coef<R>(S.cppD[s]);
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 pv[u].c[c].re = cpr * rv.c[c].re + cpp * pv[u].c[c].re;
@@ -351,7 +372,7 @@ __device__ __forceinline__ double site_update(const ScalM& S, int h, int Vh, typ
             store_vec<R>(ps + (size_t)s * rs, h, Vh, pv[u]);
         }
     }
-    const R a = (R)S.alpha;
+    const R a = coef<R>(S.alphaD);
     Vec3<R> qv = load_vec_cg<R>(q, h, Vh);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -411,7 +432,7 @@ __global__ void __launch_bounds__(PB, MB) k_ms_persistent_batch(BatchArgs A, dou
             if (S[c].halt) continue;
             const Geom g = C[c].g;
             const LinkPtrs L = C[c].L;
-            const R bt = (R)S[c].beta;
+            const R bt = coef<R>(S[c].betaD);
             const V *r = (const V*)C[c].r, *p = (const V*)C[c].p;
             V* t = (V*)C[c].t;
             for (int h = first_site(tid, off, nthreads); h < g.Vh; h += (int)nthreads)
@@ -430,7 +451,7 @@ __global__ void __launch_bounds__(PB, MB) k_ms_persistent_batch(BatchArgs A, dou
             if (S[c].halt) continue;
             const Geom g = C[c].g;
             const LinkPtrs L = C[c].L;
-            const R bt = (R)S[c].beta, c0 = (R)S[c].c0;
+            const R bt = coef<R>(S[c].betaD), c0 = coef<R>(S[c].c0D);
             const V *t = (const V*)C[c].t, *r = (const V*)C[c].r;
             V *p = (V*)C[c].p, *q = (V*)C[c].q;
             double d = 0.0;

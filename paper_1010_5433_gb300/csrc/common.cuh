@@ -315,6 +315,18 @@ __device__ __forceinline__ Su3<float> load_link_f(const float* __restrict__ blk,
     return u;
 }
 
+// Two-float split of a double x (Sec. 5): hi = x rounded to float, lo = the
+// remainder rounded to float, then (hi, lo) made canonical, hi = RN(hi + lo).
+// A remainder that rounds up to exactly half an ulp of hi makes hi + lo a
+// tie that a later split of the same double resolves to the even neighbour;
+// the canonical pair is the one that split gives, so a store (hi + lo as a
+// double) followed by a load reproduces (hi, lo) bit for bit.
+__device__ __forceinline__ void hl_canonical(float& hi, float& lo) {
+    const float s = __fadd_rn(hi, lo);
+    lo = __fsub_rn(lo, __fsub_rn(s, hi));
+    hi = s;
+}
+
 __device__ __forceinline__ Su3<double> load_link_d(const float* __restrict__ hi, const float* __restrict__ lo,
                                                    size_t blk, int h, int Vh) {
     const float4* ph = reinterpret_cast<const float4*>(hi + blk);

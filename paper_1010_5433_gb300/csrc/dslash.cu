@@ -41,8 +41,7 @@ static stag_status launch_t(stag_ctx* ctx, int out_par, int nrhs, const void* in
     if ((long long)nblocks(ctx->g.Vh, 16) * nrhs > 0x7fffffffLL) return STAG_ERR_ARG;
     const int nr = dslash_nr_for(nrhs);
     const int tps = dslash_tps(ctx, prec_of(FMT), nr);
-    if (nr == 8) launch_tps<R, FMT, 8>(ctx, ctx->stream, tps, out_par, nrhs, in, epi);
-    else if (nr == 4) launch_tps<R, FMT, 4>(ctx, ctx->stream, tps, out_par, nrhs, in, epi);
+    if (nr == 4) launch_tps<R, FMT, 4>(ctx, ctx->stream, tps, out_par, nrhs, in, epi);
     else launch_tps<R, FMT, 1>(ctx, ctx->stream, tps, out_par, nrhs, in, epi);
     CKL();
     return STAG_OK;

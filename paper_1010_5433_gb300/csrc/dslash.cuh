@@ -88,7 +88,12 @@ __device__ __forceinline__ double df_widen(float f) {
 }
 __device__ __forceinline__ double df_join(DF v) { return df_widen(v.hi) + df_widen(v.lo); }
 
-struct SrcD2DF {
+// CG = false: read-only path (__ldg), for fields no block of the launch
+// writes; CG = true: L2 loads (__ldcg), for fields that other blocks of a
+// persistent launch wrote before a grid barrier (the non-coherent cache may
+// still hold an older copy of those lines).
+template <bool CG>
+struct SrcD2DFT {
     const double2* __restrict__ in;
     template <int NR> __device__ __forceinline__ void prepare(int r0, int nrhs) {}
     __device__ __forceinline__ Vec3<DF> load(int slot, int rhs, int h, int Vh) const {
@@ -96,13 +101,15 @@ struct SrcD2DF {
         Vec3<DF> v;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const double2 d = __ldg(p + (size_t)c * Vh + h);
+            const double2 d = CG ? __ldcg(p + (size_t)c * Vh + h) : __ldg(p + (size_t)c * Vh + h);
             v.c[c].re = df_split(d.x);
             v.c[c].im = df_split(d.y);
         }
         return v;
     }
 };
+typedef SrcD2DFT<false> SrcD2DF;
+typedef SrcD2DFT<true> SrcD2DFcg;
 template <typename R> struct SrcFor { typedef SrcPlain<R> type; typedef typename V2T<R>::T io; };
 template <> struct SrcFor<DF> { typedef SrcD2DF type; typedef double2 io; };
 
@@ -277,10 +284,11 @@ template <typename R> struct EpiAop {
     }
 };
 
-// sources per thread: every link load serves NR of them (the many-source
-// Dslash of the force, Y_i = D_oe X_i over flavours x pseudo-fermions x
-// shifts, takes 8)
-inline int dslash_nr_for(int nrhs) { return nrhs >= 16 ? 8 : nrhs >= 2 ? 4 : 1; }
+// sources per thread: every link load serves NR of them.  Four is the
+// measured optimum for the force's many-source Y_i = D_oe X_i as well (60
+// sources on 32^3 x 8: 311 us at NR = 4, 473 us at NR = 8, whose extra
+// registers halve the resident warps).
+inline int dslash_nr_for(int nrhs) { return nrhs >= 2 ? 4 : 1; }
 
 // Threads per site: enough threads to fill the GPU at small volumes (about
 // 2^19 in flight), one per site once the lattice alone provides them.

@@ -185,16 +185,19 @@ __device__ __forceinline__ double f32_to_f64(float f) {
                                             ((unsigned long long)(u & 0x7FFFFFu) << 29)));
 }
 
-// hi = the double rounded to float, lo = the (exact) remainder rounded to float
+// hi = the double rounded to float, lo = the (exact) remainder rounded to
+// float, the pair made canonical (hl_canonical) as the load makes it
 __device__ __forceinline__ void store_link_hl(float* hi, float* lo, size_t blk, int h, int Vh, const Su3<double>& u) {
     float vh[18], vl[18];
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
         double re = u.e[k / 3][k % 3].re, im = u.e[k / 3][k % 3].im;
         float a = f64_to_f32_rn(re), b = f64_to_f32_rn(im);
+        float la = f64_to_f32_rn(re - f32_to_f64(a)), lb = f64_to_f32_rn(im - f32_to_f64(b));
+        hl_canonical(a, la);
+        hl_canonical(b, lb);
         vh[2 * k] = a; vh[2 * k + 1] = b;
-        vl[2 * k] = f64_to_f32_rn(re - f32_to_f64(a));
-        vl[2 * k + 1] = f64_to_f32_rn(im - f32_to_f64(b));
+        vl[2 * k] = la; vl[2 * k + 1] = lb;
     }
     float4* h4 = reinterpret_cast<float4*>(hi + blk);
     float4* l4 = reinterpret_cast<float4*>(lo + blk);

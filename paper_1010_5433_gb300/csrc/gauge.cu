@@ -20,6 +20,7 @@ __global__ void k_pack_gauge(Geom g, const double* __restrict__ stage, float* hi
         double a = stage[(size_t)idx * 18 + k];
         float b = (float)a;                 // most significant part  (Sec. 5)
         float c = (float)(a - (double)b);   // least significant part
+        hl_canonical(b, c);
         vh[k] = b;
         vl[k] = c;
     }

@@ -37,7 +37,7 @@ enum WsSlot {
 };
 
 // Sampled CUDA-event timing of the solver kernels (stag_profile_*).
-enum ProfKind { PK_DSLASH_OE = 0, PK_DSLASH_EO_A, PK_UPDATE, PK_PERSISTENT, PK_BATCH, PK_COUNT };
+enum ProfKind { PK_DSLASH_OE = 0, PK_DSLASH_EO_A, PK_UPDATE, PK_PERSISTENT, PK_BATCH, PK_PERSISTENT_FF, PK_COUNT };
 struct ProfData {
     bool on = false;
     int every = 16;
@@ -47,8 +47,8 @@ struct ProfData {
     std::vector<std::pair<int, int>> marks[PK_COUNT];
     double bytes_total[PK_COUNT] = {};           // algorithmic bytes over all launches
     long long launches[PK_COUNT] = {};
-    double persist_ms = 0.0;                     // persistent solver: event time of all launches
-    long long persist_iters = 0;                 // and the iterations they ran
+    double persist_ms[2] = {};                   // persistent solver (fp32 / float-float): event time
+    long long persist_iters[2] = {};             // of all launches and the iterations they ran
     double batch_ms = 0.0;                       // batched solver (this context leading): launch time
     long long batch_iters = 0;                   // and batched iterations
 };

@@ -568,7 +568,7 @@ __device__ __noinline__ bool reliable_update(Scal& S, GridSync& gs, const Geom& 
     for (int h = h0 + (int)threadIdx.x; h < h1; h += PB)
         for (int j = 0; j < nrhs; ++j) {
             if (!S.rhs_live[j]) continue;
-            SrcD2DF src{rp.x64 + ((size_t)j * ns + S.base) * rs};
+            SrcD2DFcg src{rp.x64 + ((size_t)j * ns + S.base) * rs};
             Vec3<DF> acc[1];
             dslash_site<DF, FMT_F64, 1, 1>(g, 1, L, src, 0, 1, h, 0, acc);
             double2* o = rp.t64 + (size_t)j * rs;
@@ -588,7 +588,7 @@ __device__ __noinline__ bool reliable_update(Scal& S, GridSync& gs, const Geom& 
 #pragma unroll
         for (int j = 0; j < STAG_MAX_RHS; ++j) {
             if (j >= nrhs || !S.rhs_live[j]) continue;
-            SrcD2DF src{rp.t64 + (size_t)j * rs};
+            SrcD2DFcg src{rp.t64 + (size_t)j * rs};
             Vec3<DF> acc[1];
             dslash_site<DF, FMT_F64, 1, 1>(g, 0, L, src, 0, 1, h, 0, acc);
             const double2* xb = rp.x64 + ((size_t)j * ns + S.base) * rs;

@@ -956,11 +956,12 @@ stag_status ms_core(stag_ctx* ctx, double mass, int nshift, const double* shifts
         const double S = 3.0 * (double)(mixed ? sizeof(float2) : sizeof(double2));
         // one iteration: both Dslash phases (links twice; r, p in, t out / t, p, r in,
         // p, q out) and the updates (r, q in, r out and 96 B per live shift: k4_units)
-        pf.bytes_total[PK_PERSISTENT] += (double)hs->k * g.Vh * (2.0 * link_bytes_site(prec) + 8.0 * S * nrhs) +
-                                         hs->k4_units * g.Vh * (mixed ? 1.0 : 2.0);
-        pf.launches[PK_PERSISTENT] += hs->k;
-        pf.persist_ms += persist_ms;
-        pf.persist_iters += hs->k;
+        const int kind = mixed ? PK_PERSISTENT : PK_PERSISTENT_FF;
+        pf.bytes_total[kind] += (double)hs->k * g.Vh * (2.0 * link_bytes_site(prec) + 8.0 * S * nrhs) +
+                                hs->k4_units * g.Vh * (mixed ? 1.0 : 2.0);
+        pf.launches[kind] += hs->k;
+        pf.persist_ms[mixed ? 0 : 1] += persist_ms;
+        pf.persist_iters[mixed ? 0 : 1] += hs->k;
     } else if (ctx->prof.on) {
         ProfData& pf = ctx->prof;
         const double S = 3.0 * (double)(mixed ? sizeof(float2) : sizeof(double2));   // one spinor at a site
@@ -968,7 +969,7 @@ stag_status ms_core(stag_ctx* ctx, double mass, int nshift, const double* shifts
         // K2 reads t, r, p and writes p, q
         pf.bytes_total[PK_DSLASH_OE] += (double)hs->k * g.Vh * (link_bytes_site(prec) + 3.0 * S * nrhs);
         pf.bytes_total[PK_DSLASH_EO_A] += (double)hs->k * g.Vh * (link_bytes_site(prec) + 5.0 * S * nrhs);
-        for (int kk = 0; kk < PK_COUNT; ++kk) pf.launches[kk] += hs->k;
+        for (int kk = PK_DSLASH_OE; kk <= PK_UPDATE; ++kk) pf.launches[kk] += hs->k;
     }
     CKS(ms_finish(R));
     if (ctx->prof.on && !persistent) ctx->prof.bytes_total[PK_UPDATE] += hs->k4_units * g.Vh * (mixed ? 1.0 : 2.0);
@@ -1143,8 +1144,8 @@ extern "C" stag_status stag_profile_begin(stag_ctx* ctx, int sample_every) {
         pf.bytes_total[k] = 0.0;
         pf.launches[k] = 0;
     }
-    pf.persist_ms = 0.0;
-    pf.persist_iters = 0;
+    pf.persist_ms[0] = pf.persist_ms[1] = 0.0;
+    pf.persist_iters[0] = pf.persist_iters[1] = 0;
     pf.batch_ms = 0.0;
     pf.batch_iters = 0;
     if (ctx->ptime) CK(cudaMemsetAsync(ctx->ptime, 0, PTIME_WORDS * sizeof(unsigned long long), ctx->stream));
@@ -1164,9 +1165,10 @@ extern "C" stag_status stag_profile_read(stag_ctx* ctx, int kind, stag_kernel_pr
     out->launches = pf.launches[kind];
     out->sampled = (int)pf.marks[kind].size();
     out->sampled_ms = ms;
-    if (kind == PK_PERSISTENT) {       // every persistent launch is timed; units are iterations
-        out->sampled = (int)pf.persist_iters;
-        out->sampled_ms = pf.persist_ms;
+    if (kind == PK_PERSISTENT || kind == PK_PERSISTENT_FF) {   // every launch is timed; units are iterations
+        const int w = kind == PK_PERSISTENT ? 0 : 1;
+        out->sampled = (int)pf.persist_iters[w];
+        out->sampled_ms = pf.persist_ms[w];
     }
     if (kind == PK_BATCH) {
         out->sampled = (int)pf.batch_iters;

@@ -649,13 +649,11 @@ stag_status surrogate_check(stag_ctx* ctx) {
     return STAG_ERR_TIMEOUT;
 }
 
-// append (features, generators, exact force) of the current field to the dataset
-stag_status surrogate_append(stag_ctx* ctx, const double* exact_force) {
+// the training store with capacity for exactly cap samples, keeping those held
+static stag_status surrogate_resize(stag_ctx* ctx, long long cap) {
     const long long nl = 8LL * ctx->g.Vh;
     const long long per = (long long)(SUR_NF + SUR_NF * 8 + 8);
-    if (ctx->sur_count >= ctx->sur_cap) {
-        // grow: new buffer of double capacity, copy the samples held so far
-        const long long cap = ctx->sur_cap ? 2 * ctx->sur_cap : 4;
+    {
         float* nb = nullptr;
         CKS(dev_alloc(ctx, (void**)&nb, (size_t)cap * nl * per * sizeof(float)));
         if (ctx->sur_data) {
@@ -671,6 +669,14 @@ stag_status surrogate_append(stag_ctx* ctx, const double* exact_force) {
         ctx->sur_data = nb;
         ctx->sur_cap = cap;
     }
+    return STAG_OK;
+}
+
+// append (features, generators, exact force) of the current field to the dataset
+stag_status surrogate_append(stag_ctx* ctx, const double* exact_force) {
+    const long long nl = 8LL * ctx->g.Vh;
+    // grow by doubling unless the caller reserved the capacity
+    if (ctx->sur_count >= ctx->sur_cap) CKS(surrogate_resize(ctx, ctx->sur_cap ? 2 * ctx->sur_cap : 4));
     const long long stride = ctx->sur_cap * nl;     // one component over all samples
     const long long base = ctx->sur_count * nl;
     float* f = ctx->sur_data + base;
@@ -754,6 +760,12 @@ extern "C" stag_status stag_surrogate_add_force_sample(stag_ctx* ctx, const doub
 }
 
 extern "C" long long stag_surrogate_samples(stag_ctx* ctx) { return ctx ? ctx->sur_count : 0; }
+
+extern "C" stag_status stag_surrogate_reserve(stag_ctx* ctx, long long n_samples) {
+    if (!ctx || n_samples < 1 || n_samples < ctx->sur_count) return STAG_ERR_ARG;
+    if (n_samples == ctx->sur_cap) return STAG_OK;
+    return surrogate_resize(ctx, n_samples);
+}
 
 extern "C" stag_status stag_surrogate_loss_grad(stag_ctx* ctx, double* loss, double* grad) {
     if (!ctx || !loss || !ctx->sur_loaded) return STAG_ERR_ARG;

@@ -52,8 +52,10 @@ def run(dims, prec=1, nrhs=1, max_iter=400, width=0.3, mass=0.02, profile=True, 
         out = {"lattice": "x".join(str(d) for d in dims), "prec": prec, "nrhs": nrhs, "status": st,
                "iterations": info.iterations, "seconds": round(dt, 4), "us_per_iteration": round(dt / max(info.iterations, 1) * 1e6, 2)}
         if profile:
-            names = ["dslash_oe", "dslash_eo_A", "update", "persistent_iteration"]
-            for k, n in enumerate(names):
+            kinds = {"dslash_oe": stag.STAG_PK_DSLASH_OE, "dslash_eo_A": stag.STAG_PK_DSLASH_EO_A,
+                     "update": stag.STAG_PK_UPDATE,
+                     "persistent_iteration": stag.STAG_PK_PERSISTENT if prec else stag.STAG_PK_PERSISTENT_FF}
+            for n, k in kinds.items():
                 pr = stag.stag_profile_read(ctx, k)
                 avg = pr.sampled_ms / max(pr.sampled, 1)
                 out[n] = {"launches": pr.launches, "sampled": pr.sampled, "avg_us": round(avg * 1e3, 2),

@@ -109,6 +109,7 @@ SIGNATURES = {
     "stag_surrogate_add_force_sample": ([_vp, _vp], _i),
     "stag_surrogate_add_sample": ([_vp, C.POINTER(stag_hmc), C.c_ulonglong], _i),
     "stag_surrogate_samples": ([_vp], C.c_longlong),
+    "stag_surrogate_reserve": ([_vp, C.c_longlong], _i),
     "stag_surrogate_loss_grad": ([_vp, C.POINTER(_d), _vp], _i),
     "stag_surrogate_train": ([_vp, _i, _d, C.POINTER(_d), C.POINTER(_d)], _i),
     "stag_draw_momenta": ([_vp, C.c_ulonglong, C.c_ulonglong, _vp], _i),
@@ -301,7 +302,8 @@ def stag_draw_sources(ctx, seed, counter, stream, n, xi):
            "stag_draw_sources", ctx)
 
 
-STAG_PK_DSLASH_OE, STAG_PK_DSLASH_EO_A, STAG_PK_UPDATE, STAG_PK_PERSISTENT, STAG_PK_BATCH = 0, 1, 2, 3, 4
+STAG_PK_DSLASH_OE, STAG_PK_DSLASH_EO_A, STAG_PK_UPDATE, STAG_PK_PERSISTENT, STAG_PK_BATCH, STAG_PK_PERSISTENT_FF = \
+    0, 1, 2, 3, 4, 5
 
 
 def stag_profile_begin(ctx, sample_every):
@@ -374,6 +376,10 @@ def stag_surrogate_add_sample(ctx, hmc, counter):
 
 def stag_surrogate_samples(ctx):
     return lib().stag_surrogate_samples(ctx)
+
+
+def stag_surrogate_reserve(ctx, n_samples):
+    _check(lib().stag_surrogate_reserve(ctx, int(n_samples)), "stag_surrogate_reserve", ctx)
 
 
 def stag_surrogate_loss_grad(ctx, grad=None):

@@ -56,7 +56,9 @@ def force_decomposition(ctx, stag, rats, mass, n_pf, draws, counter0, seed, torc
 
 
 def run(dims=(8, 8, 8, 8), rat_prefix="c4", mass=0.05, beta=5.6, n_outer=8, n_mid=3, n_gauge=4, therm=6,
-        samples=8, train_steps=200, lr=3e-3, pairs=6, decomp_configs=3, draws=6, seed=0x5A0005):
+        samples=8, train_steps=200, lr=3e-3, pairs=6, decomp_configs=3, draws=6, seed=0x5A0005, every=1):
+    """every: chain trajectories between two training samples; the store is
+    reserved for exactly `samples` configurations up front."""
     import torch
 
     import synthetic as syn
@@ -99,15 +101,17 @@ def run(dims=(8, 8, 8, 8), rat_prefix="c4", mass=0.05, beta=5.6, n_outer=8, n_mi
         p0 = np.concatenate([rng.standard_normal(n) * s for n, s in
                              [(768, 0.06), (32, 0.1), (1024, 0.05), (32, 0.1), (768, 0.05), (24, 0.0)]])
         stag.stag_surrogate_load(ctx, p0.astype(np.float32))
+        stag.stag_surrogate_reserve(ctx, samples)
         t0 = time.perf_counter()
         for k in range(samples):
-            stag.stag_md_trajectory(ctx, hmc(100 + k, n_outer))
+            for j in range(every):
+                stag.stag_md_trajectory(ctx, hmc(100_000 + every * k + j, n_outer))
             stag.stag_surrogate_add_sample(ctx, hmc(0, n_outer), 5000 + k)
         t_data = time.perf_counter() - t0
         t0 = time.perf_counter()
         first, last = stag.stag_surrogate_train(ctx, train_steps, lr)
         torch.cuda.synchronize()
-        out["training"] = {"samples": samples, "links": samples * 4 * V, "steps": train_steps,
+        out["training"] = {"samples": samples, "every": every, "links": samples * 4 * V, "steps": train_steps,
                            "loss_first": first, "loss_last": last, "seconds": round(time.perf_counter() - t0, 3),
                            "data_seconds": round(t_data, 3)}
         # what a function of U alone can learn, and what the trained network does learn

@@ -135,3 +135,44 @@ def test_store_gauge_roundtrip(torch):
         assert np.abs(back - u).max() < 1e-13
     finally:
         stag.stag_destroy(ctx)
+
+
+def _tie_field(u):
+    """Every real of u moved to just below the midpoint between its float
+    rounding h and the next float away from zero: x = h + (ulp/2)(1 - 2^-28).
+    Then x rounds to h, and the remainder x - h rounds to exactly half an ulp,
+    so hi + lo is a tie between two floats."""
+    def tie(a):
+        h = a.astype(np.float32).astype(np.float64)
+        ulp = np.spacing(np.abs(h).astype(np.float32)).astype(np.float64)
+        return h + np.sign(h) * ulp * (0.5 - 2.0 ** -29)
+    return tie(u.real) + 1j * tie(u.imag)
+
+
+def test_store_load_roundtrip_is_exact_at_ties(torch):
+    """load, fp32 Dslash, store, load again, fp32 Dslash: the same output bit
+    for bit, and the same stored field, for a field in which every real sits
+    at a float rounding tie of the two-float split (the case where a store and
+    a reload could move the fp32 word by one ulp)."""
+    from paper_1010_5433_gb300 import stag
+    dims = (4, 4, 4, 4)
+    u = _tie_field(syn.near_identity_gauge(dims, 17))
+    inp = syn.gaussian_fermion(dims, 18, on_parity=1)
+    ctx = stag.stag_create(dims, True)
+    try:
+        outs, stores = [], []
+        stag.stag_load_gauge(ctx, L.gauge_host(u))
+        for _ in range(2):
+            for prec in (1, 2):
+                d_in = dev(torch, L.to_half(inp, dims, 1).astype(np.complex64))
+                d_out = torch.empty_like(d_in)
+                stag.stag_dslash(ctx, 0, prec, 1, d_in, d_out)
+                outs.append(d_out.cpu().numpy())
+            buf = np.empty(4 * np.prod(dims) * 18)
+            stag.stag_store_gauge(ctx, buf)
+            stores.append(buf.copy())
+            stag.stag_load_gauge(ctx, buf)
+        assert np.array_equal(stores[0], stores[1])
+        assert np.array_equal(outs[0], outs[2]) and np.array_equal(outs[1], outs[3])
+    finally:
+        stag.stag_destroy(ctx)

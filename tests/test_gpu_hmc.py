@@ -427,9 +427,11 @@ def test_hasenbusch_split_trajectory_matches_oracle(torch, prec, tol_dh, tol_u):
     m, mh = 0.1, 0.4
     delta = mh * mh - m * m
     lo, hi, loh, hih = m * m, 16 + m * m, mh * mh, 16 + mh * mh
+    # the ratio is smooth enough that 8 poles reach ~2e-13: at 12 poles the
+    # levelled-error system of the oracle's Remez becomes singular at 40 digits
     ratio = {"md": orat.remez(0.5, lo, hi, 6, dps=40, delta=delta),
-             "met": orat.remez(0.5, lo, hi, 12, dps=40, delta=delta),
-             "hb": orat.remez(-0.25, lo, hi, 12, dps=40, delta=delta)}
+             "met": orat.remez(0.5, lo, hi, 8, dps=40, delta=delta),
+             "hb": orat.remez(-0.25, lo, hi, 8, dps=40, delta=delta)}
     heavy = {"md": orat.remez(0.5, loh, hih, 6, dps=40),
              "met": orat.remez(0.5, loh, hih, 12, dps=40),
              "hb": orat.remez(-0.25, loh, hih, 12, dps=40)}

@@ -25,7 +25,7 @@ def _setup(dims, seed, hot=True):
     return u, lat.eta(dims), lat.parity(dims)
 
 
-@pytest.mark.parametrize("dims,nrhs", [((4, 4, 4, 4), 1), ((4, 6, 4, 8), 3), ((6, 4, 2, 4), 9)])
+@pytest.mark.parametrize("dims,nrhs", [((4, 4, 4, 4), 1), ((4, 4, 6, 4), 2), ((4, 6, 4, 8), 3), ((6, 4, 2, 4), 9)])
 def test_fp64_multishift_matches_oracle(torch, dims, nrhs):
     from paper_1010_5433_gb300 import stag
     u, eta, par = _setup(dims, 31)
@@ -198,5 +198,38 @@ def test_barrier_wait_gives_up_and_context_stays_usable(torch):
         got = host_complex(d_x).reshape(2, 3, -1)
         for s in range(2):
             assert L.rel_err(got[s], L.to_half(xs[s], dims, 0)) < 1e-10
+    finally:
+        stag.stag_destroy(ctx)
+
+
+def test_persistent_solve_is_reproducible_bit_for_bit(torch):
+    """The same mixed solve with many in-launch reliable updates, three times
+    on one context: the same iterations, residuals and solutions bit for bit
+    (fixed reduction order, and no field that the launch rewrites is read
+    through the non-coherent cache after a grid barrier)."""
+    from paper_1010_5433_gb300 import stag
+    dims = (16, 16, 16, 16)
+    u, eta, par = _setup(dims, 0x5A0003)
+    mass = 0.02
+    shifts = list(np.geomspace(1e-5, 3.0, 11)) + [0.0]
+    b = syn.gaussian_fermion(dims, 93, on_parity=0)
+    ctx = stag.stag_create(dims, True)
+    try:
+        stag.stag_load_gauge(ctx, L.gauge_host(u))
+        d_b = dev(torch, L.to_half(b, dims, 0)[None])
+        runs = []
+        for _ in range(3):
+            d_x = torch.empty((1, len(shifts)) + tuple(d_b.shape[1:]), dtype=torch.float64, device="cuda")
+            info = stag.stag_multishift_solve(ctx, mass, shifts, 2, 1, d_b, d_x, 1e-8, 20000)
+            runs.append((info.iterations, info.reliable_updates,
+                         [info.true_residual[s] for s in range(len(shifts))], d_x.cpu().numpy()))
+        assert runs[0][1] >= 3
+        for it, rel, res, x in runs[1:]:
+            assert (it, rel) == runs[0][:2]
+            assert res == runs[0][2]
+            assert np.array_equal(x, runs[0][3])
+        got = host_complex(torch.from_numpy(runs[0][3])).reshape(len(shifts), 3, -1)
+        for s in (0, 11):
+            assert _oracle_true_residual(u, eta, par, mass, shifts[s], got[s], b, dims) < 1e-8 * 1.05
     finally:
         stag.stag_destroy(ctx)

@@ -241,6 +241,7 @@ def run_gpu(args, rank, world, local_rank):
                 "kernels": kern}
 
     point = dslash_roofline_point(hbm) if rank == 0 else None
+    force_point = force_dslash_point(hbm, clocks.get("sm_max_mhz")) if rank == 0 else None
     stag.stag_destroy(ctx)
     chains = batched_chains() if world == 1 else None
 
@@ -286,6 +287,7 @@ def run_gpu(args, rank, world, local_rank):
                          "e2e_replays_timed": all(a.dH == b.dH for a, b in zip(trajs, e2e_trajs)),
                          "e2e_max_abs_dH_difference": max(abs(a.dH - b.dH) for a, b in zip(trajs, e2e_trajs))},
         "dslash_roofline_point": point,
+        "force_dslash_point": force_point,
         "batched_chains": chains,
     }
     return out
@@ -329,6 +331,41 @@ def dslash_roofline_point(hbm):
     precision, CUDA-event timed over 20 launches after 3 warm-ups."""
     from paper_1010_5433_gb300 import dslash_bench
     return dslash_bench.run(ROOFLINE_POINT_DIMS, (1, 2, 3, 0), 1, 20, hbm)
+
+
+# the many-source force Dslash of the 2+1-flavour workload: Y_i = D_oe X_i for
+# 2 flavours x 2 pseudo-fermions x 15 shifts = 60 sources on 32^3 x 8, bf16
+# 12-real links, fp32 spinors
+FORCE_POINT_DIMS = (32, 32, 32, 8)
+FORCE_POINT_SOURCES = 60
+# algorithmic flops per output site: per source 8 hops of an SU(3) matrix
+# times a colour vector (66 flops each) and their signed sum (7 vector adds,
+# 42 flops); per link the rebuild of row 3 from rows 1-2 (42 flops), once
+FLOPS_PER_SITE_SOURCE = 8 * 66 + 42
+FLOPS_PER_SITE_LINKS = 8 * 42
+# FP32 peak without tensor cores: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x clock
+FP32_LANES = 152 * 128
+
+
+def force_dslash_point(hbm, sm_mhz):
+    """The 60-source bf16-12 Dslash against min(HBM, FP32 ALU): the bound is
+    the longer of the algorithmic bytes at the measured copy bandwidth and
+    the algorithmic flops at the FP32 peak."""
+    from paper_1010_5433_gb300 import dslash_bench
+    r = dslash_bench.run(FORCE_POINT_DIMS, (3,), FORCE_POINT_SOURCES, 10, hbm)
+    b = r["bf16_12"]
+    sites = int(np.prod(FORCE_POINT_DIMS)) // 2
+    flops = sites * (FORCE_POINT_SOURCES * FLOPS_PER_SITE_SOURCE + FLOPS_PER_SITE_LINKS)
+    mhz = sm_mhz or 2070.0
+    fp32_peak = FP32_LANES * 2 * mhz * 1e6
+    t_hbm = sites * b["bytes_per_site"] / (hbm * 1e9)
+    t_alu = flops / fp32_peak
+    t = b["us"] * 1e-6
+    return {"lattice": r["lattice"], "sources": FORCE_POINT_SOURCES, "links": "bf16, 12 reals", "us": b["us"],
+            "achieved_gbs": b["achieved_gbs"], "achieved_tflops": round(flops / t / 1e12, 2),
+            "bound_us": {"hbm": round(t_hbm * 1e6, 2), "fp32_alu": round(t_alu * 1e6, 2)},
+            "fp32_peak_tflops": round(fp32_peak / 1e12, 1), "peak_clock_mhz": mhz,
+            "frac_of_min_bound": round(max(t_hbm, t_alu) / t, 4)}
 
 
 # ---------------------------------------------------------------- CPU baseline (the oracle)

@@ -162,6 +162,10 @@ if __name__ == "__main__":
     ap.add_argument("--pairs", type=int, default=6)
     ap.add_argument("--decomp-configs", type=int, default=3)
     ap.add_argument("--draws", type=int, default=6)
+    ap.add_argument("--n-gauge", type=int, default=4)
+    ap.add_argument("--therm", type=int, default=6)
+    ap.add_argument("--every", type=int, default=1, help="chain trajectories per training sample")
     a = ap.parse_args()
-    print(json.dumps(run(tuple(a.dims), a.rationals, a.mass, n_outer=a.n_outer, n_mid=a.n_mid, samples=a.samples,
-                         train_steps=a.train_steps, pairs=a.pairs, decomp_configs=a.decomp_configs, draws=a.draws)))
+    print(json.dumps(run(tuple(a.dims), a.rationals, a.mass, n_outer=a.n_outer, n_mid=a.n_mid, n_gauge=a.n_gauge,
+                         therm=a.therm, samples=a.samples, train_steps=a.train_steps, pairs=a.pairs,
+                         decomp_configs=a.decomp_configs, draws=a.draws, every=a.every)))

@@ -47,6 +47,19 @@ stag_status ws_get(stag_ctx* ctx, int slot, size_t bytes, void** out) {
     return STAG_OK;
 }
 
+stag_status stage_upload(stag_ctx* ctx, void* dst, const void* src, size_t bytes) {
+    if (bytes > STAGE_SLOT_BYTES || !ctx->stage_host) return STAG_ERR_ARG;
+    const int slot = ctx->stage_next;
+    ctx->stage_next = (slot + 1) % STAGE_SLOTS;
+    // the slot's previous copy has run (long ago, normally: 64 uploads back)
+    CK(cudaEventSynchronize(ctx->stage_ev[slot]));
+    char* h = ctx->stage_host + (size_t)slot * STAGE_SLOT_BYTES;
+    std::memcpy(h, src, bytes);
+    CK(cudaMemcpyAsync(dst, h, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaEventRecord(ctx->stage_ev[slot], ctx->stream));
+    return STAG_OK;
+}
+
 extern "C" const char* stag_strerror(stag_status s) {
     switch (s) {
         case STAG_OK: return "ok";
@@ -102,8 +115,16 @@ extern "C" void stag_destroy(stag_ctx* ctx) {
     if (ctx->sur_data) cudaFree(ctx->sur_data);
     if (ctx->scal) cudaFree(ctx->scal);
     if (ctx->st) cudaFree(ctx->st);
-    if (ctx->scal_host) cudaFreeHost(ctx->scal_host);
     if (ctx->st_host) cudaFreeHost(ctx->st_host);
+    if (ctx->note) cudaFree(ctx->note);
+    for (int w = 0; w < 2; ++w)
+        for (auto& e : ctx->deferred_ev[w]) {
+            cudaEventDestroy(e.first);
+            cudaEventDestroy(e.second);
+        }
+    for (int i = 0; i < STAGE_SLOTS; ++i)
+        if (ctx->stage_ev[i]) cudaEventDestroy(ctx->stage_ev[i]);
+    if (ctx->stage_host) cudaFreeHost(ctx->stage_host);
     delete ctx;
 }
 
@@ -157,16 +178,23 @@ extern "C" stag_status stag_create(const stag_lattice* lat, stag_ctx** out) {
         (s = dev_alloc(ctx, (void**)&ctx->red, sizeof(double) * red_doubles(ctx->g.Vh))) != STAG_OK ||
         (s = dev_alloc(ctx, (void**)&ctx->counters, sizeof(unsigned int) * 16)) != STAG_OK ||
         (s = dev_alloc(ctx, (void**)&ctx->scal, sizeof(double) * 64)) != STAG_OK ||
-        (s = dev_alloc(ctx, (void**)&ctx->st, sizeof(SolverState))) != STAG_OK) {
+        (s = dev_alloc(ctx, (void**)&ctx->st, sizeof(SolverState))) != STAG_OK ||
+        (s = dev_alloc(ctx, (void**)&ctx->note, sizeof(SolveNote))) != STAG_OK) {
         stag_destroy(ctx);
         return s;
     }
-    if (cudaMallocHost((void**)&ctx->scal_host, sizeof(double) * 64) != cudaSuccess ||
-        cudaMallocHost((void**)&ctx->st_host, sizeof(SolverState)) != cudaSuccess) {
+    if (cudaMallocHost((void**)&ctx->st_host, sizeof(SolverState)) != cudaSuccess ||
+        cudaMallocHost((void**)&ctx->stage_host, (size_t)STAGE_SLOTS * STAGE_SLOT_BYTES) != cudaSuccess) {
         cudaGetLastError();
         stag_destroy(ctx);
         return STAG_ERR_ALLOC;
     }
+    for (int i = 0; i < STAGE_SLOTS; ++i)
+        if (cudaEventCreateWithFlags(&ctx->stage_ev[i], cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            stag_destroy(ctx);
+            return STAG_ERR_CUDA;
+        }
     if (cudaMemsetAsync(ctx->counters, 0, sizeof(unsigned int) * 16, ctx->stream) != cudaSuccess ||
         cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
         cudaGetLastError();

@@ -97,13 +97,10 @@ stag_status blas_combine(stag_ctx* ctx, int nrhs, double a0, const double2* phi,
                          const double2* x, double2* out) {
     // coefficients through the small scalar area
     if (nshift > 60) return STAG_ERR_ARG;
-    for (int s = 0; s < nshift; ++s) ctx->scal_host[s] = alpha[s];
-    CK(cudaMemcpyAsync(ctx->scal, ctx->scal_host, nshift * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CKS(stage_upload(ctx, ctx->scal, alpha, nshift * sizeof(double)));
     dim3 grid(nblocks(ctx->g.Vh, BB), nrhs);
     k_combine<<<grid, BB, 0, ctx->stream>>>(ctx->g.Vh, nshift, a0, phi, ctx->scal, x, out);
     CKL();
-    // the pinned coefficients must not be rewritten before the copy ran
-    CK(cudaStreamSynchronize(ctx->stream));
     return STAG_OK;
 }
 

@@ -434,8 +434,7 @@ stag_status sum_partials(stag_ctx* ctx, int nb, double* out) {
 stag_status fermion_force_from_solutions(stag_ctx* ctx, stag_prec prec, int nsrc, int nshift, const double* alpha,
                                          const void* x, const void* y, double* out, double coef, int mode) {
     if (nshift > 60) return STAG_ERR_ARG;
-    for (int s = 0; s < nshift; ++s) ctx->scal_host[s] = alpha[s];
-    CK(cudaMemcpyAsync(ctx->scal, ctx->scal_host, nshift * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CKS(stage_upload(ctx, ctx->scal, alpha, nshift * sizeof(double)));
     long long n = 8LL * ctx->g.Vh;
     LinkPtrs L = link_ptrs(ctx);
     if (prec == STAG_FP64)
@@ -445,7 +444,6 @@ stag_status fermion_force_from_solutions(stag_ctx* ctx, stag_prec prec, int nsrc
         k_fermion_force<float, FMT_F32_18><<<nblocks(n, FB), FB, 0, ctx->stream>>>(
             ctx->g, L, nsrc, nshift, ctx->scal, (const float2*)x, (const float2*)y, out, coef, mode);
     CKL();
-    CK(cudaStreamSynchronize(ctx->stream));   // pinned coefficients are reused by the next call
     return STAG_OK;
 }
 

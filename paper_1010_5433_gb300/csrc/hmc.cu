@@ -497,7 +497,16 @@ extern "C" stag_status stag_md_trajectory(stag_ctx* ctx, const stag_hmc* p, stag
     CKS(timer.begin(0));
     CKS(T.heatbath());
     CKS(timer.end(0));
-    CKS(T.md_evolve());
+    // the MD evolution is enqueued without a host read between its solves
+    // (their iterations and first error are read once, here)
+    CKS(defer_begin(ctx));
+    const stag_status md = T.md_evolve();
+    long long md_iters = 0, md_rel = 0;
+    const stag_status de = defer_end(ctx, &md_iters, &md_rel);
+    T.ts.iters += md_iters;
+    T.ts.reliable += (int)md_rel;
+    CKS(md);
+    CKS(de);
     double sf1 = 0.0;
     CKS(timer.begin(3));
     if (T.npf_total > 0) CKS(T.fermion_action(&sf1));

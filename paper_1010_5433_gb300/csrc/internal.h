@@ -75,6 +75,20 @@ struct BatchTune {
     int iters[4] = {};
 };
 
+// What the host would read after each solve, kept on the device while the
+// MD evolution enqueues solve after solve without waiting (SolveNote's
+// deferred mode); read once after the evolution.
+struct SolveNote {
+    long long iters[2];       // iterations of the persistent solves: [fp32, float-float]
+    long long reliable;       // in-launch residual replacements
+    double bytes[2];          // their algorithmic bytes (the profile's units)
+    int err;                  // first status other than OK / NOT_CONVERGED; TIMEOUT if a launch did not halt
+    int solves;
+};
+// pinned staging slots for host-to-device uploads the host does not wait for
+#define STAGE_SLOTS 64
+#define STAGE_SLOT_BYTES 32768
+
 struct SolverGraphEntry {
     const void* key[8];
     int prec, nrhs;
@@ -96,7 +110,6 @@ struct stag_ctx {
     size_t red_doubles = 0;
     unsigned int* counters = nullptr; // 16 counters, zero between launches
     double* scal = nullptr;           // small device scalar area (64 doubles)
-    double* scal_host = nullptr;      // pinned mirror
     SolverState* st = nullptr;        // device
     SolverState* st_host = nullptr;   // pinned
     // workspace
@@ -128,6 +141,14 @@ struct stag_ctx {
     long long sur_cap = 0, sur_count = 0;
     cudaStream_t cap_stream = nullptr;
     std::vector<SolverGraphEntry> graphs;
+    // deferred solves (inside the MD evolution): no host read between them
+    bool defer = false;
+    SolveNote* note = nullptr;        // device
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> deferred_ev[2];   // profiled persistent launches
+    // staging ring of small uploads (SolverState, coefficients)
+    char* stage_host = nullptr;
+    cudaEvent_t stage_ev[STAGE_SLOTS] = {};
+    int stage_next = 0;
 };
 
 // a single kernel launch: count it and check the launch
@@ -155,6 +176,14 @@ stag_status cuda_fail(stag_ctx* c, cudaError_t e, const char* where);
     } while (0)
 
 stag_status ws_get(stag_ctx* ctx, int slot, size_t bytes, void** out);
+// bytes (<= STAGE_SLOT_BYTES) from host memory to dst on the context's
+// stream, through a pinned slot that is reused only after its copy has run:
+// the caller may change src as soon as this returns, without a sync
+stag_status stage_upload(stag_ctx* ctx, void* dst, const void* src, size_t bytes);
+// deferred solves: begin (the note cleared), end (one sync: the note read,
+// the profile updated, the first error returned)
+stag_status defer_begin(stag_ctx* ctx);
+stag_status defer_end(stag_ctx* ctx, long long* iters, long long* reliable);
 stag_status dev_alloc(stag_ctx* ctx, void** p, size_t bytes);
 
 inline LinkPtrs link_ptrs(const stag_ctx* c) { return LinkPtrs{c->ghi, c->glo, c->g16}; }

@@ -789,7 +789,9 @@ stag_status ms_setup(MsRun& R) {
     hs->c0 = R.mass * R.mass + R.shifts[R.base];
     hs->delta2 = 0.01;   // replace the residual after every factor 10 in ||r||
     for (int s = 0; s < R.nshift; ++s) hs->dsig[s] = R.shifts[s] - R.shifts[R.base];
-    CK(cudaMemcpyAsync(ctx->st, hs, sizeof(SolverState), cudaMemcpyHostToDevice, ctx->stream));
+    // staged: with deferred solves the host fills hs for the next solve before this copy has run
+    static_assert(sizeof(SolverState) <= STAGE_SLOT_BYTES, "the solver state fits a staging slot");
+    CKS(stage_upload(ctx, ctx->st, hs, sizeof(SolverState)));
     dim3 grid_v(nblocks(g.Vh, VB), R.nrhs);
     if (R.mixed)
         k_ms_init<float><<<grid_v, VB, 0, ctx->stream>>>(ctx->st, g.Vh, (const float2*)R.b, (float2*)R.r,
@@ -856,6 +858,60 @@ void ms_stats(const MsRun& R, MsStats* stats) {
 }
 
 stag_status ms_pull_state(stag_ctx* ctx) { return pull_state(ctx); }
+
+// ---------------------------------------------------------------- deferred solves
+// After a persistent launch, on the device: what ms_core would otherwise
+// read on the host (iterations, residual replacements, the algorithmic bytes
+// of the profile, and whether the launch halted with a usable status).
+__global__ void k_solve_note(const SolverState* st, SolveNote* note, int w, double vh, double bytes_iter,
+                             double unit_scale) {
+    const long long k = st->k;
+    note->iters[w] += k;
+    note->reliable += st->n_reliable;
+    note->bytes[w] += (double)k * vh * bytes_iter + st->k4_units * vh * unit_scale;
+    note->solves += 1;
+    if (note->err == 0) {
+        if (!st->halt) note->err = STAG_ERR_TIMEOUT;
+        else if (st->status != STAG_OK && st->status != STAG_ERR_NOT_CONVERGED) note->err = st->status;
+    }
+}
+
+stag_status defer_begin(stag_ctx* ctx) {
+    CK(cudaMemsetAsync(ctx->note, 0, sizeof(SolveNote), ctx->stream));
+    ctx->defer = ctx->use_persistent;
+    return STAG_OK;
+}
+
+stag_status defer_end(stag_ctx* ctx, long long* iters, long long* reliable) {
+    if (!ctx->defer) return STAG_OK;
+    ctx->defer = false;
+    SolveNote n;
+    CK(cudaMemcpyAsync(&n, ctx->note, sizeof(n), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (iters) *iters += n.iters[0] + n.iters[1];
+    if (reliable) *reliable += n.reliable;
+    ProfData& pf = ctx->prof;
+    for (int w = 0; w < 2; ++w) {
+        double ms = 0.0;
+        for (auto& e : ctx->deferred_ev[w]) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, e.first, e.second) == cudaSuccess) ms += t;
+            cudaEventDestroy(e.first);
+            cudaEventDestroy(e.second);
+        }
+        const bool timed = !ctx->deferred_ev[w].empty();
+        ctx->deferred_ev[w].clear();
+        if (pf.on && timed) {
+            const int kind = w == 0 ? PK_PERSISTENT : PK_PERSISTENT_FF;
+            pf.bytes_total[kind] += n.bytes[w];
+            pf.launches[kind] += n.iters[w];
+            pf.persist_ms[w] += ms;
+            pf.persist_iters[w] += n.iters[w];
+        }
+    }
+    cudaGetLastError();
+    return n.err ? (stag_status)n.err : STAG_OK;
+}
 stag_status ms_pull_control_async(stag_ctx* ctx) {
     const size_t off = offsetof(SolverState, k);
     const size_t len = offsetof(SolverState, rhs_live) - off;
@@ -889,6 +945,7 @@ stag_status ms_core(stag_ctx* ctx, double mass, int nshift, const double* shifts
     stag_status status = STAG_OK;
     cudaGraphExec_t gexec = nullptr;
     const bool persistent = persistent_fits(ctx);
+    bool deferred = false;
     if (!persistent) {
         dslash_tps(ctx, prec, dslash_nr_for(nrhs));   // tune before any capture
         if (ctx->use_graphs) CKS(solver_graph(ctx, prec, nrhs, R.tmp, R.r, R.p, R.q, R.ps, R.x, &gexec));
@@ -912,6 +969,21 @@ stag_status ms_core(stag_ctx* ctx, double mass, int nshift, const double* shifts
                                   R.use_rel ? R.b64 : nullptr, R.use_rel ? R.x64 : nullptr,
                                   R.use_rel ? (double2*)R.t64 : nullptr));
             if (pe1) CK(cudaEventRecord(pe1, ctx->stream));
+            if (ctx->defer) {
+                // no host read: the note takes the iterations, the algorithmic
+                // bytes and the first error; the events wait for defer_end
+                const double S = 3.0 * (double)(mixed ? sizeof(float2) : sizeof(double2));
+                k_solve_note<<<1, 1, 0, ctx->stream>>>(ctx->st, ctx->note, mixed ? 0 : 1, (double)g.Vh,
+                                                       2.0 * link_bytes_site(prec) + 8.0 * S * nrhs,
+                                                       mixed ? 1.0 : 2.0);
+                CKL();
+                if (pe0) {
+                    ctx->deferred_ev[mixed ? 0 : 1].push_back({pe0, pe1});
+                    pe0 = pe1 = nullptr;
+                }
+                deferred = true;
+                break;
+            }
             CKS(pull_control(ctx));
             if (pe0) {
                 float ms = 0.f;
@@ -945,6 +1017,11 @@ stag_status ms_core(stag_ctx* ctx, double mass, int nshift, const double* shifts
             continue;
         }
         break;   // converged
+    }
+    if (deferred) {
+        CKS(ms_finish(R));
+        if (stats) std::memset(stats, 0, sizeof(*stats));   // the note has them; defer_end reads it
+        return STAG_OK;
     }
     CKS(pull_state(ctx));
     if (pe0) cudaEventDestroy(pe0);

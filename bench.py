@@ -305,10 +305,10 @@ PROFILE_NAMES = ("dslash_oe", "dslash_eo_A", "update", "persistent_iteration_fp3
 # flushes caches between passes): one read of the working set, then L2 hits.
 NCU_TRAFFIC = {
     "persistent_iteration_fp32": {
-        "bytes_per_unit": 909340,
+        "bytes_per_unit": 840685,
         "source": "ncu --set full of k_ms_persistent<float, FMT_F32_12, 1, 1, 256> on 16^4: one whole "
-                  "37-iteration solve of the 12-pole MD rational (solve_bench --prec 2 --tol 0.11), "
-                  "dram__bytes_read.sum 33.18 MB + dram__bytes_write.sum 0.46 MB per launch / 37 iterations",
+                  "40-iteration solve of the 12-pole MD rational (solve_bench --prec 2 --tol 0.11), "
+                  "dram__bytes_read.sum 33.18 MB + dram__bytes_write.sum 0.44 MB per launch / 40 iterations",
     },
 }
 

@@ -4,6 +4,7 @@
 // update U <- exp(i eps P) U fused with the fp64 reunitarisation, the fp64
 // action sums and the Philox draws of momenta and pseudo-fermion sources.
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "internal.h"
@@ -50,6 +51,32 @@ __device__ __forceinline__ void put_force(double* out, int mu, int par, int h, i
         if (mode) o[(size_t)a * Vh] += coef * f[a];
         else o[(size_t)a * Vh] = coef * f[a];
     }
+}
+
+// Conversions between float and double by integer operations on the IEEE-754
+// bit patterns, with the results of the conversion instructions (round to
+// nearest even): those instructions issue on GB300's FP64 pipe, which is
+// ~1/64 of the FP32 rate, and made up about half of the link update's FP64
+// work.  Zeros, results outside the float normal range, Inf and NaN take the
+// instruction.
+__device__ __forceinline__ float f64_to_f32_rn(double d) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const int e = (int)((b >> 52) & 0x7FF) - 1023 + 127;    // float exponent field
+    if (e <= 0 || e >= 255) return __double2float_rn(d);
+    const unsigned int sign = (unsigned int)(b >> 63) << 31;
+    const unsigned int top = (unsigned int)((b >> 29) & 0x7FFFFFull);   // the 23 kept mantissa bits
+    const unsigned int rest = (unsigned int)(b & 0x1FFFFFFFull);        // the 29 dropped ones
+    const unsigned int up = (rest > 0x10000000u || (rest == 0x10000000u && (top & 1u))) ? 1u : 0u;
+    // a carry out of the mantissa steps the exponent (to Inf past the largest float)
+    return __uint_as_float(sign | ((((unsigned int)e << 23) | top) + up));
+}
+__device__ __forceinline__ double f32_to_f64(float f) {
+    const unsigned int u = __float_as_uint(f);
+    const unsigned int e = (u >> 23) & 0xFFu;
+    if (e == 0u || e == 0xFFu) return (double)f;
+    return __longlong_as_double((long long)(((unsigned long long)(u >> 31) << 63) |
+                                            ((unsigned long long)(e - 127u + 1023u) << 52) |
+                                            ((unsigned long long)(u & 0x7FFFFFu) << 29)));
 }
 
 // ---------------------------------------------------------------- fermion force
@@ -103,9 +130,11 @@ __global__ void __launch_bounds__(FB) k_fermion_force(Geom g, LinkPtrs L, int ns
 }
 
 // ---------------------------------------------------------------- gauge force
-// F_a = -(beta/3) Re tr(i T_a U_mu(x) Sigma_mu(x)), Sigma = sum of upper and lower staples
+// F_a = -(beta/3) Re tr(i T_a U_mu(x) Sigma_mu(x)), Sigma = sum of upper and lower staples.
+// The fp32 instantiation is held to 128 registers (four blocks per SM: its
+// 18 link gathers per thread are L2 latency), the fp64 one would spill there.
 template <typename R, int FMT>
-__global__ void __launch_bounds__(FB) k_gauge_force(Geom g, LinkPtrs L, double beta, double* out, double coef,
+__global__ void __launch_bounds__(FB, std::is_same<R, float>::value ? 4 : 1) k_gauge_force(Geom g, LinkPtrs L, double beta, double* out, double coef,
                                                     int mode) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= 8LL * g.Vh) return;
@@ -153,38 +182,20 @@ __global__ void __launch_bounds__(FB) k_gauge_force(Geom g, LinkPtrs L, double b
     R fr[8];
     re_tr_i_t(w, fr);
     double fd[8];
+    if constexpr (std::is_same<R, float>::value) {
+        // the fp32 force scaled in fp32 and widened by integer operations
+        // (no conversion or multiply on the FP64 pipe but put_force's FMA)
+        const float sb = f64_to_f32_rn(-beta / 3.0);
 #pragma unroll
-    for (int a = 0; a < 8; ++a) fd[a] = -(beta / 3.0) * (double)fr[a];
+        for (int a = 0; a < 8; ++a) fd[a] = f32_to_f64(sb * fr[a]);
+    } else {
+#pragma unroll
+        for (int a = 0; a < 8; ++a) fd[a] = -(beta / 3.0) * (double)fr[a];
+    }
     put_force(out, mu, par, h, g.Vh, fd, coef, mode);
 }
 
 // ---------------------------------------------------------------- link update + reunitarisation
-// Conversions between float and double by integer operations on the IEEE-754
-// bit patterns, with the results of the conversion instructions (round to
-// nearest even): those instructions issue on GB300's FP64 pipe, which is
-// ~1/64 of the FP32 rate, and made up about half of the link update's FP64
-// work.  Zeros, results outside the float normal range, Inf and NaN take the
-// instruction.
-__device__ __forceinline__ float f64_to_f32_rn(double d) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
-    const int e = (int)((b >> 52) & 0x7FF) - 1023 + 127;    // float exponent field
-    if (e <= 0 || e >= 255) return __double2float_rn(d);
-    const unsigned int sign = (unsigned int)(b >> 63) << 31;
-    const unsigned int top = (unsigned int)((b >> 29) & 0x7FFFFFull);   // the 23 kept mantissa bits
-    const unsigned int rest = (unsigned int)(b & 0x1FFFFFFFull);        // the 29 dropped ones
-    const unsigned int up = (rest > 0x10000000u || (rest == 0x10000000u && (top & 1u))) ? 1u : 0u;
-    // a carry out of the mantissa steps the exponent (to Inf past the largest float)
-    return __uint_as_float(sign | ((((unsigned int)e << 23) | top) + up));
-}
-__device__ __forceinline__ double f32_to_f64(float f) {
-    const unsigned int u = __float_as_uint(f);
-    const unsigned int e = (u >> 23) & 0xFFu;
-    if (e == 0u || e == 0xFFu) return (double)f;
-    return __longlong_as_double((long long)(((unsigned long long)(u >> 31) << 63) |
-                                            ((unsigned long long)(e - 127u + 1023u) << 52) |
-                                            ((unsigned long long)(u & 0x7FFFFFu) << 29)));
-}
-
 // hi = the double rounded to float, lo = the (exact) remainder rounded to
 // float, the pair made canonical (hl_canonical) as the load makes it
 __device__ __forceinline__ void store_link_hl(float* hi, float* lo, size_t blk, int h, int Vh, const Su3<double>& u) {
@@ -232,12 +243,91 @@ __device__ __forceinline__ void reunit(Su3<double>& u) {
     rebuild_row2(u);
 }
 
+// 1/sqrt(x) in float-float: the fp32 estimate refined by two Newton steps
+// y <- y + y (1 - x y^2) / 2 (the error squares: about 2^-22, 2^-43, then the
+// float-float rounding)
+__device__ __forceinline__ DF df_rsqrt(const DF& x) {
+    DF y(rsqrtf(x.hi));
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const DF r = DF(1.f) - x * (y * y);
+        y = y + y * r * DF(0.5f);
+    }
+    return y;
+}
+
+// The same Gram-Schmidt in float-float for the fp32 link update (Sec. 4's
+// reunitarisation in double precision, on the fp32 pipes: GB300 issues fp64
+// at ~1/64 of the fp32 rate, and the fp64 version was nearly all of the
+// update's time); the rows come out about 2^-46 from orthonormal.
+__device__ __forceinline__ void reunit_df(Su3<DF>& u) {
+    DF n0(0.f);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) n0 = n0 + u.e[0][j].re * u.e[0][j].re + u.e[0][j].im * u.e[0][j].im;
+    n0 = df_rsqrt(n0);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) u.e[0][j] = n0 * u.e[0][j];
+    Cx<DF> d = mk(DF(0.f), DF(0.f));
+#pragma unroll
+    for (int j = 0; j < 3; ++j) cmacc(d, u.e[0][j], u.e[1][j]);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) u.e[1][j] = u.e[1][j] - d * u.e[0][j];
+    DF n1(0.f);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) n1 = n1 + u.e[1][j].re * u.e[1][j].re + u.e[1][j].im * u.e[1][j].im;
+    n1 = df_rsqrt(n1);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) u.e[1][j] = n1 * u.e[1][j];
+    rebuild_row2(u);
+}
+
+// lo rounded to a multiple of 2^(E - 52), E the exponent of hi: hi + lo is
+// then a double, so storing it (hi + lo as a double) and loading it again
+// gives this pair back bit for bit.  A float-float lo can otherwise hold bits
+// below the double's last place.  hi below 2^-74 (or zero) keeps its lo.
+__device__ __forceinline__ float lo_on_double_grid(float hi, float lo) {
+    const int e = (int)((__float_as_uint(hi) >> 23) & 0xFFu);   // biased exponent of hi
+    if (e < 53 || e == 0xFF) return e == 0 ? 0.f : lo;
+    const float q = __uint_as_float((unsigned int)(e - 52) << 23);        // 2^(E - 52)
+    const float iq = __uint_as_float((unsigned int)(254 - (e - 52)) << 23);   // 1 / q, exact
+    return rintf(lo * iq) * q;
+}
+
+// the float-float link into the two-float store: its value rounded to double
+// precision, split canonically
+__device__ __forceinline__ void store_link_df(float* hi, float* lo, size_t blk, int h, int Vh, const Su3<DF>& u) {
+    float vh[18], vl[18];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        float a = u.e[k / 3][k % 3].re.hi, la = u.e[k / 3][k % 3].re.lo;
+        float b = u.e[k / 3][k % 3].im.hi, lb = u.e[k / 3][k % 3].im.lo;
+        la = lo_on_double_grid(a, la);
+        lb = lo_on_double_grid(b, lb);
+        hl_canonical(a, la);
+        hl_canonical(b, lb);
+        vh[2 * k] = a; vh[2 * k + 1] = b;
+        vl[2 * k] = la; vl[2 * k + 1] = lb;
+    }
+    float4* h4 = reinterpret_cast<float4*>(hi + blk);
+    float4* l4 = reinterpret_cast<float4*>(lo + blk);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        h4[(size_t)k * Vh + h] = make_float4(vh[4 * k], vh[4 * k + 1], vh[4 * k + 2], vh[4 * k + 3]);
+        l4[(size_t)k * Vh + h] = make_float4(vl[4 * k], vl[4 * k + 1], vl[4 * k + 2], vl[4 * k + 3]);
+    }
+    reinterpret_cast<float2*>(hi + blk + 16 * (size_t)Vh)[h] = make_float2(vh[16], vh[17]);
+    reinterpret_cast<float2*>(lo + blk + 16 * (size_t)Vh)[h] = make_float2(vl[16], vl[17]);
+}
+
 // P = sum_a p_a T_a as a Hermitian matrix
 template <typename R>
 __device__ __forceinline__ Su3<R> herm_from_coeffs(const double* p, size_t stride) {
     R c[8];
 #pragma unroll
-    for (int a = 0; a < 8; ++a) c[a] = (R)p[(size_t)a * stride];
+    for (int a = 0; a < 8; ++a) {
+        if constexpr (std::is_same<R, float>::value) c[a] = f64_to_f32_rn(p[(size_t)a * stride]);
+        else c[a] = p[(size_t)a * stride];
+    }
     const R s3 = (R)0.57735026918962576;   // 1/sqrt(3)
     Su3<R> hm;
     hm.e[0][0] = mk<R>((R)0.5 * (c[2] + s3 * c[7]), 0);
@@ -295,7 +385,8 @@ __device__ __forceinline__ double to_f64(float f) { return f32_to_f64(f); }
 __device__ __forceinline__ double to_f64(double d) { return d; }
 
 // U <- reunitarise(exp(i eps P) U): the exponential and the product in R
-// (fp32 in the mixed path, Sec. 4), the reunitarisation always in fp64.
+// (fp32 in the mixed path, Sec. 4), the reunitarisation in double precision:
+// float-float after the fp32 product, fp64 on the fp64 path.
 template <typename R, int FMT, int ORDER>
 __global__ void __launch_bounds__(FB) k_update_links(Geom g, float* hi, float* lo, const double* __restrict__ mom,
                                                      double eps) {
@@ -309,13 +400,23 @@ __global__ void __launch_bounds__(FB) k_update_links(Geom g, float* hi, float* l
     Su3<R> hm = herm_from_coeffs<R>(mom + ((size_t)blk * 8) * g.Vh + h, g.Vh);
     Su3<R> e = expi<R, ORDER>(hm, (R)eps);
     Su3<R> un = mul(e, u);
-    Su3<double> ud;
+    if constexpr (std::is_same<R, float>::value) {
+        Su3<DF> ud;
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+        for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) ud.e[i][j] = mk(to_f64(un.e[i][j].re), to_f64(un.e[i][j].im));
-    reunit(ud);
-    store_link_hl(hi, lo, link_block_f(mu, par, g.Vh), h, g.Vh, ud);
+            for (int j = 0; j < 3; ++j) ud.e[i][j] = mk(DF(un.e[i][j].re), DF(un.e[i][j].im));
+        reunit_df(ud);
+        store_link_df(hi, lo, link_block_f(mu, par, g.Vh), h, g.Vh, ud);
+    } else {
+        Su3<double> ud;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) ud.e[i][j] = mk(to_f64(un.e[i][j].re), to_f64(un.e[i][j].im));
+        reunit(ud);
+        store_link_hl(hi, lo, link_block_f(mu, par, g.Vh), h, g.Vh, ud);
+    }
 }
 
 __global__ void __launch_bounds__(FB) k_reunitarize(Geom g, float* hi, float* lo) {

@@ -390,6 +390,12 @@ __device__ void beta_step(Scal& S, const double* partial, int nb, int off, unsig
         S.left[q] = 0;
         S.units[q] = 0;
     }
+    // the warp's own entries, before the block waits: its closed windows
+    // reset, and zE, zF, 1 / (r, r) of the next alpha step from what lane 0
+    // has just written
+    __syncwarp();
+    if (closed && q < STAG_MAX_RHS) window_reset_one(S, q, s);
+    prep_alpha(S);
     __syncthreads();
     if (fine) {
         const unsigned long long t = gtimer();
@@ -408,9 +414,6 @@ __device__ void beta_step(Scal& S, const double* partial, int nb, int off, unsig
         if (!any) S.halt = 1;
         else if (S.k >= S.max_iter) { S.halt = 1; S.status = STAG_ERR_NOT_CONVERGED; }
     }
-    __syncthreads();
-    if (closed && q < STAG_MAX_RHS) window_reset_one(S, q, s);
-    prep_alpha(S);
     __syncthreads();
     if (fine) fine[5] += gtimer() - tf;
 }

@@ -469,3 +469,60 @@ def test_hasenbusch_split_trajectory_matches_oracle(torch, prec, tol_dh, tol_u):
         assert du < tol_u
     finally:
         stag.stag_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_updated_links_are_special_unitary_to_double_precision(torch, c1, prec):
+    """After a trajectory without Metropolis (so the field is the MD result),
+    every link held in the two-float store (hi + lo) is special unitary to
+    double precision: the fp64 path reunitarises in fp64, the fp32 paths in
+    float-float (about 2^-46 from orthonormal), Sec. 4."""
+    from paper_1010_5433_gb300 import stag
+    u0 = syn.near_identity_gauge(DIMS, 0x5A0001)
+    ctx = stag.stag_create(DIMS, True)
+    try:
+        stag.stag_load_gauge(ctx, L.gauge_host(u0))
+        stag.stag_md_trajectory(ctx, _hmc(stag, c1, prec, counter=7, no_metropolis=1))
+        buf = np.empty(4 * 256 * 18)
+        stag.stag_store_gauge(ctx, buf)
+        u = L.gauge_from_host(buf, DIMS).reshape(-1, 3, 3)
+        assert np.abs(u - u0.reshape(-1, 3, 3)).max() > 1e-3          # the links moved
+        eye = np.eye(3)
+        unit = np.abs(np.einsum("nij,nkj->nik", u, u.conj()) - eye).max()
+        det = np.abs(np.linalg.det(u) - 1.0).max()
+        print(f"prec {prec}: max |U U^dag - 1| {unit:.2e}, max |det U - 1| {det:.2e}")
+        assert unit < 1e-12 and det < 1e-12
+    finally:
+        stag.stag_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_updated_field_survives_store_and_load_bit_for_bit(torch, c1, prec):
+    """The links an MD evolution leaves in the two-float store are exactly
+    the doubles a store returns: store, load, store gives the same doubles,
+    and the fp32 and fp64 Dslash of the reloaded field equal those of the
+    evolved one bit for bit (the end-to-end path reloads the field between
+    trajectories)."""
+    from paper_1010_5433_gb300 import stag
+    u0 = syn.near_identity_gauge(DIMS, 0x5A0001)
+    psi = L.to_half(syn.gaussian_fermion(DIMS, 104, on_parity=1), DIMS, 1)
+    ctx = stag.stag_create(DIMS, True)
+    try:
+        stag.stag_load_gauge(ctx, L.gauge_host(u0))
+        stag.stag_md_trajectory(ctx, _hmc(stag, c1, prec, counter=9, no_metropolis=1))
+        outs, stores = [], []
+        for _ in range(2):
+            for dprec, arr in ((0, psi), (1, psi.astype(np.complex64)), (2, psi.astype(np.complex64))):
+                d_in = dev(torch, arr)
+                d_out = torch.empty_like(d_in)
+                stag.stag_dslash(ctx, 0, dprec, 1, d_in, d_out)
+                outs.append(d_out.cpu().numpy())
+            buf = np.empty(4 * 256 * 18)
+            stag.stag_store_gauge(ctx, buf)
+            stores.append(buf.copy())
+            stag.stag_load_gauge(ctx, buf)
+        assert np.array_equal(stores[0], stores[1])
+        for a, b in zip(outs[:3], outs[3:]):
+            assert np.array_equal(a, b)
+    finally:
+        stag.stag_destroy(ctx)

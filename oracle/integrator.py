@@ -21,6 +21,9 @@ Sint; ref. [hmc] Duane, Kennedy, Pendleton, Roweth).
   * Metropolis on dH = H_f - H_i with H = 1/2 sum p_a^2 + S_g + S_f, where the
     final S_f uses the Metropolis rational (tighter than the MD one, Sec. 2)
     and the initial S_f = xi^dag xi.
+  * the fermion operator is the paper's unimproved one, or (action =
+    "asqtad", not in the paper) the improved operator of oracle/asqtad.py
+    with its fermion force; the gauge action stays Wilson's either way.
 Everything here is float64 (the oracle reference for all precision modes).
 """
 from dataclasses import dataclass, field
@@ -28,7 +31,7 @@ from typing import List
 
 import numpy as np
 
-from . import dirac, lattice as lat, solvers, su3
+from . import asqtad, dirac, lattice as lat, solvers, su3
 from . import surrogate as sur
 from .actions import fermion_action, fermion_force, wilson_action, wilson_force
 
@@ -56,6 +59,8 @@ class HMCParams:
     tol_md: float = 1e-10
     tol_met: float = 1e-14
     antiperiodic_t: bool = True
+    action: str = "unimproved"     # or "asqtad"
+    u0: float = 1.0                # tadpole factor of the asqtad paths
 
 
 class Context:
@@ -65,8 +70,15 @@ class Context:
         self.par = lat.parity(p.dims)
 
     def shifted_solves(self, u, mass, phi, betas, tol):
-        def apply0(v, s0=min(betas)):
-            return dirac.a_op(u, v, mass, self.eta, self.par, s0)
+        if self.p.action == "asqtad":
+            fat, naik = asqtad.fat_long_links(u, self.p.u0, self.p.antiperiodic_t)
+            eta0 = lat.eta(self.p.dims, antiperiodic_t=False)
+
+            def apply0(v, s0=min(betas)):
+                return asqtad.a_op(fat, naik, v, mass, eta0, self.par, s0)
+        else:
+            def apply0(v, s0=min(betas)):
+                return dirac.a_op(u, v, mass, self.eta, self.par, s0)
         xs, _, _ = solvers.multishift_cg(apply0, phi, betas, tol)
         return xs
 
@@ -85,7 +97,10 @@ class Context:
                 continue
             for phi in phi_list:
                 xs = self.shifted_solves(u, fl.mass, phi, fl.md.beta, self.p.tol_md)
-                f += fermion_force(u, xs, fl.md.alpha, self.eta, self.par)
+                if self.p.action == "asqtad":
+                    f += asqtad.fermion_force(u, xs, fl.md.alpha, self.par, self.p.u0, self.p.antiperiodic_t)
+                else:
+                    f += fermion_force(u, xs, fl.md.alpha, self.eta, self.par)
         return f
 
     def fermion_action_total(self, u, phis, tol):

@@ -146,6 +146,39 @@ stag_status stag_apply_a(stag_ctx* ctx, double mass, double shift, stag_prec pre
 stag_status stag_apply_a_noalloc(stag_ctx* ctx, double mass, double shift, stag_prec prec,
                                  int nrhs, const void* in, void* out);
 
+/* ---- improved staggered fermions (not in the paper: its Sec. 2 runs the
+ *      unimproved operator; the improved one is the asqtad action of Lepage,
+ *      PRD 59 (1999) 074502, and Orginos, Toussaint, Sugar, PRD 60 (1999) 054503) */
+
+typedef enum { STAG_ACTION_UNIMPROVED = 0, STAG_ACTION_ASQTAD = 1 } stag_action;
+
+/* Selects the fermion operator every later call of this context uses
+ * (stag_dslash, stag_apply_a, stag_apply_a_noalloc, stag_multishift_solve,
+ * stag_fermion_force, stag_md_trajectory).  STAG_ACTION_UNIMPROVED (the
+ * default) is the paper's operator.  STAG_ACTION_ASQTAD replaces each hop by
+ * a fat link V (1-link 5/8, 6 three-link staples 1/16 u0^-2, 24 five-link
+ * staples 1/64 u0^-4, 48 seven-link staples 1/384 u0^-6, 6 Lepage paths
+ * -1/16 u0^-4) and adds a third-neighbour hop through the Naik link
+ * W = -1/24 u0^-2 U_mu(x) U_mu(x+mu) U_mu(x+2mu):
+ *   D psi(x) = 1/2 sum_mu eta_mu(x) [V_mu(x) psi(x+mu) - V_mu(x-mu)^dag psi(x-mu)
+ *                                  + W_mu(x) psi(x+3mu) - W_mu(x-3mu)^dag psi(x-3mu)],
+ * A = m^2 - D_eo D_oe as before; its spectrum lies in [m^2, m^2 + (4 sum |c|)^2]
+ * (58.8 + m^2 at u0 = 1).  u0: tadpole factor, 0 < u0 <= 1 (1: tree level).
+ * The fat and Naik links are rebuilt on the device (float-float arithmetic
+ * from the two-float store) before the first use after every change of the
+ * thin links.  With the improved operator, prec must be STAG_FP64 or
+ * STAG_FP32 (the fat links are not unitary, so no 12-real or bf16 copy), the
+ * solver takes the three-kernel path, and the batched calls and the force
+ * surrogate return STAG_ERR_ARG.  The gauge action stays Wilson's.
+ * Allocates the two link stores (2 x 4 V x 18 x 8 bytes) on the first switch. */
+stag_status stag_set_action(stag_ctx* ctx, stag_action action, double u0);
+
+/* Fat and Naik links of the current gauge field (after the rebuild, if one is
+ * due) into caller-allocated host buffers of 4*V*18 doubles each, in the host
+ * layout of stag_store_gauge, without eta or boundary signs.  STAG_ERR_ARG
+ * unless the context uses STAG_ACTION_ASQTAD.  Synchronous. */
+stag_status stag_asqtad_links(stag_ctx* ctx, double* host_fat, double* host_naik);
+
 /* ---- solvers (Sec. 6; multi-shift CG after Jegerlehner, hep-lat/9612014) --- */
 
 typedef struct {

@@ -1,0 +1,529 @@
+// Improved (asqtad) staggered fermions: the fat and Naik links built from the
+// thin links, and the fermion force through them (Lepage, PRD 59 (1999)
+// 074502; Orginos, Toussaint, Sugar, PRD 60 (1999) 054503).  The paper runs
+// unimproved staggered fermions (Sec. 2); this is the improved operator on the
+// same even/odd multi-shift machinery (asqtad.cuh holds its Dslash).
+//
+// Fat link of direction mu at x, as nested staples
+//   S_s[A](y) = L(y, s) A(y + s) L(y + mu, s)^dag,   L(y, +nu) = U_nu(y),
+//                                                    L(y, -nu) = U_nu(y - nu)^dag,
+//   V = c1 U_mu + sum_nu S_nu[ c3 U_mu + sum_rho S_rho[ c5 U_mu + c7 sum_sig S_sig[U_mu] ] ]
+//       + cL sum_nu S_nu[S_nu[U_mu]]
+// with nu, rho, sig signed, mutually orthogonal and orthogonal to mu:
+// 1 + 6 + 24 + 48 + 6 paths.  Coefficients (tadpole factor u0): 5/8, 1/16 u0^-2,
+// 1/64 u0^-4, 1/384 u0^-6, -1/16 u0^-4; Naik W = -1/24 u0^-2 U_mu(x) U_mu(x+mu) U_mu(x+2mu).
+// V and W carry neither eta nor the time boundary sign: every path of V_t
+// from the last time slice crosses the boundary an odd number of times and
+// every other path of V an even number, so the Dslash applies the thin
+// links' hop sign to V and the sign of the three t-links to W.
+//
+// Arithmetic: float-float (hi + lo floats, ~48 bits) on the fp32 pipes
+// (GB300's fp64 rate is ~1/64 of fp32), read from the two-float thin-link
+// store and written to two-float stores of the same layout, so the fp32
+// Dslash reads the rounded fat links (hi) and the fp64 one all of them.
+#include <cstring>
+#include <vector>
+
+#include "asqtad.cuh"
+#include "internal.h"
+
+namespace {
+constexpr int AB = 128;
+
+__device__ __forceinline__ int a_hidx(const Geom& g, const int c[4]) {
+    return (c[0] >> 1) + g.Lxh * (c[1] + g.L[1] * (c[2] + g.L[2] * c[3]));
+}
+__device__ __forceinline__ void a_coords(const Geom& g, int par, int h, int c[4]) {
+    int xh = h % g.Lxh, r = h / g.Lxh;
+    c[1] = r % g.L[1]; r /= g.L[1];
+    c[2] = r % g.L[2]; c[3] = r / g.L[2];
+    c[0] = 2 * xh + ((c[1] + c[2] + c[3] + par) & 1);
+}
+// move c by one step along signed direction s (+-(nu+1))
+__device__ __forceinline__ void a_move(const Geom& g, int c[4], int s) {
+    const int nu = (s > 0 ? s : -s) - 1;
+    c[nu] += s > 0 ? 1 : -1;
+    if (c[nu] < 0) c[nu] += g.L[nu];
+    if (c[nu] >= g.L[nu]) c[nu] -= g.L[nu];
+}
+
+template <typename R> __device__ __forceinline__ Su3<R> dagger(const Su3<R>& a) {
+    Su3<R> b;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) b.e[i][j] = conj(a.e[j][i]);
+    return b;
+}
+template <typename R> __device__ __forceinline__ void axpy(Su3<R>& acc, R c, const Su3<R>& a) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            acc.e[i][j].re += c * a.e[i][j].re;
+            acc.e[i][j].im += c * a.e[i][j].im;
+        }
+}
+template <typename R> __device__ __forceinline__ Su3<R> scaled(R c, const Su3<R>& a) {
+    Su3<R> b;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) b.e[i][j] = mk(c * a.e[i][j].re, c * a.e[i][j].im);
+    return b;
+}
+
+// thin link U_nu(c)
+template <typename R, int FMT>
+__device__ __forceinline__ Su3<R> thin(const Geom& g, const LinkPtrs& L, const int c[4], int nu) {
+    return LinkFetch<R, FMT>::get(L, nu, (c[0] + c[1] + c[2] + c[3]) & 1, a_hidx(g, c), g.Vh);
+}
+// the link met on a step from c along s, c moved to the step's end
+template <typename R, int FMT>
+__device__ __forceinline__ Su3<R> walk(const Geom& g, const LinkPtrs& L, int c[4], int s) {
+    if (s > 0) {
+        const Su3<R> u = thin<R, FMT>(g, L, c, s - 1);
+        a_move(g, c, s);
+        return u;
+    }
+    a_move(g, c, s);
+    return dagger(thin<R, FMT>(g, L, c, -s - 1));
+}
+// S_s[A](y) = L(y, s) A L(y + mu, s)^dag, A the value at y + s
+template <typename R, int FMT>
+__device__ __forceinline__ Su3<R> staple(const Geom& g, const LinkPtrs& L, const int y[4], int mu, int s,
+                                         const Su3<R>& a) {
+    int c[4] = {y[0], y[1], y[2], y[3]};
+    const Su3<R> first = walk<R, FMT>(g, L, c, s);
+    int d[4] = {y[0], y[1], y[2], y[3]};
+    a_move(g, d, mu + 1);
+    const Su3<R> last = walk<R, FMT>(g, L, d, s);   // L(y + mu, s)
+    return mul_nd(mul(first, a), last);
+}
+
+struct AsqCoef {
+    float c[6][2];   // one, staple3, staple5, staple7, lepage, naik as float-float (hi, lo)
+};
+__device__ __forceinline__ DF cf(const AsqCoef& k, int i) { return DF(k.c[i][0], k.c[i][1]); }
+
+// float-float -> two-float store (hi, lo canonical, as the thin links)
+__device__ __forceinline__ void store_df(float* hi, float* lo, size_t blk, int h, int Vh, const Su3<DF>& u) {
+    float vh[18], vl[18];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        DF re = u.e[k / 3][k % 3].re, im = u.e[k / 3][k % 3].im;
+        hl_canonical(re.hi, re.lo);
+        hl_canonical(im.hi, im.lo);
+        vh[2 * k] = re.hi; vl[2 * k] = re.lo;
+        vh[2 * k + 1] = im.hi; vl[2 * k + 1] = im.lo;
+    }
+    float4* h4 = reinterpret_cast<float4*>(hi + blk);
+    float4* l4 = reinterpret_cast<float4*>(lo + blk);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        h4[(size_t)k * Vh + h] = make_float4(vh[4 * k], vh[4 * k + 1], vh[4 * k + 2], vh[4 * k + 3]);
+        l4[(size_t)k * Vh + h] = make_float4(vl[4 * k], vl[4 * k + 1], vl[4 * k + 2], vl[4 * k + 3]);
+    }
+    reinterpret_cast<float2*>(hi + blk + 16 * (size_t)Vh)[h] = make_float2(vh[16], vh[17]);
+    reinterpret_cast<float2*>(lo + blk + 16 * (size_t)Vh)[h] = make_float2(vl[16], vl[17]);
+}
+
+// one thread per fat link (mu, x): V and W in float-float
+__global__ void __launch_bounds__(AB) k_fatten(Geom g, LinkPtrs L, AsqCoef k, float* fhi, float* flo, float* lhi,
+                                               float* llo) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 8LL * g.Vh) return;
+    const int blk = (int)(idx / g.Vh), h = (int)(idx % g.Vh);
+    const int mu = blk >> 1, par = blk & 1;
+    int x[4];
+    a_coords(g, par, h, x);
+    Su3<DF> v = scaled(cf(k, 0), thin<DF, FMT_F64>(g, L, x, mu));
+    for (int nu = 0; nu < 4; ++nu) {
+        if (nu == mu) continue;
+        for (int sn = -1; sn <= 1; sn += 2) {
+            const int a = sn * (nu + 1);
+            int y1[4] = {x[0], x[1], x[2], x[3]};
+            a_move(g, y1, a);
+            Su3<DF> q = scaled(cf(k, 1), thin<DF, FMT_F64>(g, L, y1, mu));
+            for (int rho = 0; rho < 4; ++rho) {
+                if (rho == mu || rho == nu) continue;
+                for (int sr = -1; sr <= 1; sr += 2) {
+                    const int b = sr * (rho + 1);
+                    int y2[4] = {y1[0], y1[1], y1[2], y1[3]};
+                    a_move(g, y2, b);
+                    Su3<DF> t = scaled(cf(k, 2), thin<DF, FMT_F64>(g, L, y2, mu));
+                    const int sig = 6 - mu - nu - rho;     // the remaining direction
+                    for (int ss = -1; ss <= 1; ss += 2) {
+                        const int c = ss * (sig + 1);
+                        int y3[4] = {y2[0], y2[1], y2[2], y2[3]};
+                        a_move(g, y3, c);
+                        axpy(t, cf(k, 3), staple<DF, FMT_F64>(g, L, y2, mu, c, thin<DF, FMT_F64>(g, L, y3, mu)));
+                    }
+                    axpy(q, DF(1.f), staple<DF, FMT_F64>(g, L, y1, mu, b, t));
+                }
+            }
+            axpy(v, DF(1.f), staple<DF, FMT_F64>(g, L, x, mu, a, q));
+            // Lepage: the double-width staple in the same direction
+            int y2[4] = {y1[0], y1[1], y1[2], y1[3]};
+            a_move(g, y2, a);
+            const Su3<DF> inner = staple<DF, FMT_F64>(g, L, y1, mu, a, thin<DF, FMT_F64>(g, L, y2, mu));
+            axpy(v, cf(k, 4), staple<DF, FMT_F64>(g, L, x, mu, a, inner));
+        }
+    }
+    store_df(fhi, flo, link_block_f(mu, par, g.Vh), h, g.Vh, v);
+    int c[4] = {x[0], x[1], x[2], x[3]};
+    Su3<DF> w = walk<DF, FMT_F64>(g, L, c, mu + 1);
+    w = mul(w, walk<DF, FMT_F64>(g, L, c, mu + 1));
+    w = mul(w, walk<DF, FMT_F64>(g, L, c, mu + 1));
+    store_df(lhi, llo, link_block_f(mu, par, g.Vh), h, g.Vh, scaled(cf(k, 5), w));
+}
+
+// ---------------------------------------------------------------- force
+// Path incidences of every thin-link direction: each (mu, path of V_mu or
+// W_mu, position k on it) whose k-th step runs along +-nu, listed under nu.
+struct AsqInc {
+    signed char s[7];
+    unsigned char len, k, mu, cls, pad;
+};
+constexpr int ASQ_MAX_INC = 512;
+__constant__ AsqInc c_inc[4][ASQ_MAX_INC];
+__constant__ int c_ninc[4];
+
+template <typename R> __device__ __forceinline__ R from_f64(double d);
+template <> __device__ __forceinline__ float from_f64<float>(double d) { return (float)d; }
+template <> __device__ __forceinline__ DF from_f64<DF>(double d) { return df_split(d); }
+template <typename R> struct FieldT { typedef typename V2T<R>::T T; };
+template <> struct FieldT<DF> { typedef double2 T; };
+
+template <typename R> __device__ __forceinline__ Vec3<R> load_z(const typename FieldT<R>::T* f, int h, int Vh);
+template <> __device__ __forceinline__ Vec3<float> load_z<float>(const float2* f, int h, int Vh) {
+    return load_vec<float>(f, h, Vh);
+}
+template <> __device__ __forceinline__ Vec3<DF> load_z<DF>(const double2* f, int h, int Vh) {
+    Vec3<DF> v;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double2 d = __ldg(f + (size_t)c * Vh + h);
+        v.c[c] = mk(df_split(d.x), df_split(d.y));
+    }
+    return v;
+}
+
+// Xv_mu(x) += sum alpha_s eps(x) (hop sign) Z(x+mu) Z(x)^dag, Xw_mu(x) the
+// same with Z(x+3mu): Z = X on even sites, Y = D_oe X on odd ones.  The
+// fields are [mu][par][18][Vh] reals of R (Xw after Xv).
+template <typename R>
+__global__ void __launch_bounds__(AB) k_asq_outer(Geom g, int nsrc, int nshift, const double* __restrict__ alpha,
+                                                  double coef, const typename FieldT<R>::T* xs,
+                                                  const typename FieldT<R>::T* ys, R* xv, R* xw) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 8LL * g.Vh) return;
+    const int blk = (int)(idx / g.Vh), h = (int)(idx % g.Vh);
+    const int mu = blk >> 1, par = blk & 1;
+    Nbr n;
+    site_neighbours(g, h, par, n);
+    Nbr3 m3;
+    site_neighbours3(g, n, m3);
+    const typename FieldT<R>::T* here = par == 0 ? xs : ys;
+    const typename FieldT<R>::T* there = par == 0 ? ys : xs;
+    const double eps = par == 0 ? 1.0 : -1.0;
+    Su3<R> mv, mw;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) { mv.e[i][j] = mk<R>(R(0), R(0)); mw.e[i][j] = mk<R>(R(0), R(0)); }
+    const size_t rs = (size_t)3 * g.Vh;
+    for (int q = 0; q < nsrc; ++q) {
+        for (int s = 0; s < nshift; ++s) {
+            const size_t off = ((size_t)q * nshift + s) * rs;
+            const Vec3<R> zx = load_z<R>(here + off, h, g.Vh);
+            const Vec3<R> z1 = load_z<R>(there + off, n.fwd[mu], g.Vh);
+            const Vec3<R> z3 = load_z<R>(there + off, m3.fwd[mu], g.Vh);
+            const R a1 = from_f64<R>(coef * alpha[s] * eps * (double)n.sf[mu]);
+            const R a3 = from_f64<R>(coef * alpha[s] * eps * (double)m3.sf[mu]);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const Cx<R> p1 = mk(a1 * z1.c[i].re, a1 * z1.c[i].im);
+                const Cx<R> p3 = mk(a3 * z3.c[i].re, a3 * z3.c[i].im);
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    cmac(mv.e[i][j], p1, conj(zx.c[j]));
+                    cmac(mw.e[i][j], p3, conj(zx.c[j]));
+                }
+            }
+        }
+    }
+    R* ov = xv + (size_t)blk * 18 * g.Vh + h;
+    R* ow = xw + (size_t)blk * 18 * g.Vh + h;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        ov[(size_t)(2 * k) * g.Vh] += mv.e[k / 3][k % 3].re;
+        ov[(size_t)(2 * k + 1) * g.Vh] += mv.e[k / 3][k % 3].im;
+        ow[(size_t)(2 * k) * g.Vh] += mw.e[k / 3][k % 3].re;
+        ow[(size_t)(2 * k + 1) * g.Vh] += mw.e[k / 3][k % 3].im;
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ Su3<R> load_x(const R* f, int mu, const Geom& g, const int c[4]) {
+    const int par = (c[0] + c[1] + c[2] + c[3]) & 1;
+    const R* p = f + (size_t)(2 * mu + par) * 18 * g.Vh + a_hidx(g, c);
+    Su3<R> m;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) m.e[k / 3][k % 3] = mk(p[(size_t)(2 * k) * g.Vh], p[(size_t)(2 * k + 1) * g.Vh]);
+    return m;
+}
+
+template <typename R> __device__ __forceinline__ R coef_as(const AsqCoef& k, int i);
+template <> __device__ __forceinline__ float coef_as<float>(const AsqCoef& k, int i) { return k.c[i][0] + k.c[i][1]; }
+template <> __device__ __forceinline__ DF coef_as<DF>(const AsqCoef& k, int i) { return cf(k, i); }
+
+// One thread per thin link (nu, y): over every incidence of nu, the rest of
+// the path's loop R = A_{k+1} .. A_n X_mu(x) A_1 .. A_{k-1} (x the path's
+// start), summed with the path coefficient into Gf (link met forward) or Gb
+// (met backward); then F_a = Re tr[i T_a (U Gf - Gb U^dag)], which is
+// d S / d omega_a under U -> exp(i omega_a T_a) U.
+template <typename R, int FMT>
+__global__ void __launch_bounds__(AB) k_asq_force(Geom g, LinkPtrs L, AsqCoef k, const R* __restrict__ xv,
+                                                  const R* __restrict__ xw, double* out, int mode) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 8LL * g.Vh) return;
+    const int blk = (int)(idx / g.Vh), h = (int)(idx % g.Vh);
+    const int nu = blk >> 1, par = blk & 1;
+    int y[4];
+    a_coords(g, par, h, y);
+    Su3<R> gf, gb;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) { gf.e[i][j] = mk<R>(R(0), R(0)); gb.e[i][j] = mk<R>(R(0), R(0)); }
+    const int ninc = c_ninc[nu];
+    for (int e = 0; e < ninc; ++e) {
+        const AsqInc& in = c_inc[nu][e];
+        const int len = in.len, kk = in.k, mu = in.mu;
+        const bool fwd = in.s[kk] > 0;
+        // start of the path: undo the steps before k from the link's near end
+        int x[4] = {y[0], y[1], y[2], y[3]};
+        if (!fwd) a_move(g, x, -in.s[kk]);
+        for (int j = kk - 1; j >= 0; --j) a_move(g, x, -in.s[j]);
+        // the far end of link k, where the rest of the path goes on
+        int c[4] = {y[0], y[1], y[2], y[3]};
+        if (fwd) a_move(g, c, in.s[kk]);
+        Su3<R> m;
+        bool have = false;
+        for (int j = kk + 1; j < len; ++j) {
+            const Su3<R> a = walk<R, FMT>(g, L, c, in.s[j]);
+            m = have ? mul(m, a) : a;
+            have = true;
+        }
+        const Su3<R> xm = load_x<R>(in.cls == 5 ? xw : xv, mu, g, x);
+        m = have ? mul(m, xm) : xm;
+        for (int j = 0; j < kk; ++j) m = mul(m, walk<R, FMT>(g, L, x, in.s[j]));
+        axpy(fwd ? gf : gb, coef_as<R>(k, in.cls), m);
+    }
+    const Su3<R> u = thin<R, FMT>(g, L, y, nu);
+    Su3<R> w = mul(u, gf);
+    const Su3<R> b = mul_nd(gb, u);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            w.e[i][j].re -= b.e[i][j].re;
+            w.e[i][j].im -= b.e[i][j].im;
+        }
+    // Re tr(i T_a W), T_a = lambda_a / 2
+    const R hf = R(0.5f);
+    R f[8];
+    f[0] = -hf * (w.e[1][0].im + w.e[0][1].im);
+    f[1] = -hf * (w.e[0][1].re - w.e[1][0].re);
+    f[2] = -hf * (w.e[0][0].im - w.e[1][1].im);
+    f[3] = -hf * (w.e[2][0].im + w.e[0][2].im);
+    f[4] = -hf * (w.e[0][2].re - w.e[2][0].re);
+    f[5] = -hf * (w.e[2][1].im + w.e[1][2].im);
+    f[6] = -hf * (w.e[1][2].re - w.e[2][1].re);
+    f[7] = -(w.e[0][0].im + w.e[1][1].im - R(2.f) * w.e[2][2].im) * R(0.28867513459481287);   // 1/(2 sqrt 3)
+    double* o = out + ((size_t)blk * 8) * g.Vh + h;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        const double fa = (double)f[a];
+        if (mode) o[(size_t)a * g.Vh] += fa;
+        else o[(size_t)a * g.Vh] = fa;
+    }
+}
+
+// host: the incidence table of every direction
+struct IncTable {
+    AsqInc inc[4][ASQ_MAX_INC];
+    int n[4];
+};
+void build_incidences(IncTable* t) {
+    std::memset(t, 0, sizeof(*t));
+    for (int mu = 0; mu < 4; ++mu) {
+        const int m = mu + 1;
+        std::vector<std::pair<int, std::vector<int>>> paths;   // (class, steps)
+        paths.push_back({0, {m}});
+        for (int nu = 0; nu < 4; ++nu) {
+            if (nu == mu) continue;
+            for (int sn = -1; sn <= 1; sn += 2) {
+                const int a = sn * (nu + 1);
+                paths.push_back({1, {a, m, -a}});
+                paths.push_back({4, {a, a, m, -a, -a}});
+                for (int rho = 0; rho < 4; ++rho) {
+                    if (rho == mu || rho == nu) continue;
+                    for (int sr = -1; sr <= 1; sr += 2) {
+                        const int b = sr * (rho + 1);
+                        paths.push_back({2, {a, b, m, -b, -a}});
+                        const int sig = 6 - mu - nu - rho;
+                        for (int ss = -1; ss <= 1; ss += 2) {
+                            const int c = ss * (sig + 1);
+                            paths.push_back({3, {a, b, c, m, -c, -b, -a}});
+                        }
+                    }
+                }
+            }
+        }
+        paths.push_back({5, {m, m, m}});
+        for (auto& p : paths) {
+            const int len = (int)p.second.size();
+            for (int k = 0; k < len; ++k) {
+                const int d = (p.second[k] > 0 ? p.second[k] : -p.second[k]) - 1;
+                AsqInc& e = t->inc[d][t->n[d]++];
+                for (int j = 0; j < len; ++j) e.s[j] = (signed char)p.second[j];
+                e.len = (unsigned char)len;
+                e.k = (unsigned char)k;
+                e.mu = (unsigned char)mu;
+                e.cls = (unsigned char)p.first;
+            }
+        }
+    }
+}
+
+AsqCoef make_coef(const double (&c)[6]) {
+    AsqCoef k;
+    for (int i = 0; i < 6; ++i) {
+        k.c[i][0] = (float)c[i];
+        k.c[i][1] = (float)(c[i] - (double)k.c[i][0]);
+    }
+    return k;
+}
+
+size_t link_store_floats(const stag_ctx* ctx) { return (size_t)4 * 2 * 18 * ctx->g.Vh; }
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+AsqLinks asq_links(const stag_ctx* ctx) {
+    const size_t n = link_store_floats(ctx);
+    float* base = ctx->asq_store;
+    return AsqLinks{LinkPtrs{base, base + n, nullptr}, LinkPtrs{base + 2 * n, base + 3 * n, nullptr}};
+}
+
+int asq_tps(const stag_ctx* ctx) {
+    if (ctx->tps_force == 1 || ctx->tps_force == 2 || ctx->tps_force == 4 || ctx->tps_force == 8) return ctx->tps_force;
+    return dslash_tps_for(ctx->g.Vh);
+}
+
+stag_status asq_ensure(stag_ctx* ctx) {
+    if (!ctx->asqtad) return STAG_OK;
+    if (!ctx->has_gauge) return STAG_ERR_NO_GAUGE;
+    if (!ctx->asq_stale) return STAG_OK;
+    const AsqLinks A = asq_links(ctx);
+    const long long n = 8LL * ctx->g.Vh;
+    k_fatten<<<nblocks(n, AB), AB, 0, ctx->stream>>>(ctx->g, link_ptrs(ctx), make_coef(ctx->asq_coef),
+                                                     const_cast<float*>(A.fat.hi), const_cast<float*>(A.fat.lo),
+                                                     const_cast<float*>(A.lng.hi), const_cast<float*>(A.lng.lo));
+    CKL();
+    ctx->asq_stale = false;
+    return STAG_OK;
+}
+
+stag_status asq_outer_begin(stag_ctx* ctx, stag_prec prec) {
+    const size_t rs = prec == STAG_FP64 ? sizeof(DF) : sizeof(float);
+    const size_t bytes = 2 * link_store_floats(ctx) * rs;
+    void* p;
+    CKS(ws_get(ctx, WS_ASQ_X, bytes, &p));
+    CK(cudaMemsetAsync(p, 0, bytes, ctx->stream));
+    return STAG_OK;
+}
+
+stag_status asq_outer_add(stag_ctx* ctx, stag_prec prec, int nsrc, int nshift, const double* alpha, const void* x,
+                          const void* y, double coef) {
+    if (nshift > 60) return STAG_ERR_ARG;
+    CKS(stage_upload(ctx, ctx->scal, alpha, nshift * sizeof(double)));
+    const long long n = 8LL * ctx->g.Vh;
+    const size_t nl = link_store_floats(ctx);
+    if (prec == STAG_FP64) {
+        DF* xv = (DF*)ctx->ws[WS_ASQ_X];
+        k_asq_outer<DF><<<nblocks(n, AB), AB, 0, ctx->stream>>>(ctx->g, nsrc, nshift, ctx->scal, coef,
+                                                                (const double2*)x, (const double2*)y, xv, xv + nl);
+    } else {
+        float* xv = (float*)ctx->ws[WS_ASQ_X];
+        k_asq_outer<float><<<nblocks(n, AB), AB, 0, ctx->stream>>>(ctx->g, nsrc, nshift, ctx->scal, coef,
+                                                                   (const float2*)x, (const float2*)y, xv, xv + nl);
+    }
+    CKL();
+    return STAG_OK;
+}
+
+stag_status asq_force_finish(stag_ctx* ctx, stag_prec prec, double* out, int mode) {
+    CKS(asq_ensure(ctx));
+    const long long n = 8LL * ctx->g.Vh;
+    const size_t nl = link_store_floats(ctx);
+    const AsqCoef k = make_coef(ctx->asq_coef);
+    if (prec == STAG_FP64) {
+        const DF* xv = (const DF*)ctx->ws[WS_ASQ_X];
+        k_asq_force<DF, FMT_F64><<<nblocks(n, AB), AB, 0, ctx->stream>>>(ctx->g, link_ptrs(ctx), k, xv, xv + nl,
+                                                                         out, mode);
+    } else {
+        const float* xv = (const float*)ctx->ws[WS_ASQ_X];
+        k_asq_force<float, FMT_F32_18><<<nblocks(n, AB), AB, 0, ctx->stream>>>(ctx->g, link_ptrs(ctx), k, xv,
+                                                                               xv + nl, out, mode);
+    }
+    CKL();
+    return STAG_OK;
+}
+
+extern "C" stag_status stag_set_action(stag_ctx* ctx, stag_action action, double u0) {
+    if (!ctx) return STAG_ERR_ARG;
+    if (action == STAG_ACTION_UNIMPROVED) {
+        ctx->asqtad = false;
+        return STAG_OK;
+    }
+    if (action != STAG_ACTION_ASQTAD || !(u0 > 0.0) || !(u0 <= 1.0)) return STAG_ERR_ARG;
+    void* p;
+    CKS(ws_get(ctx, WS_ASQ_LINKS, 4 * link_store_floats(ctx) * sizeof(float), &p));
+    ctx->asq_store = (float*)p;
+    const double u2 = u0 * u0, u4 = u2 * u2, u6 = u4 * u2;
+    const double c[6] = {5.0 / 8.0, 1.0 / 16.0 / u2, 1.0 / 64.0 / u4, 1.0 / 384.0 / u6, -1.0 / 16.0 / u4,
+                         -1.0 / 24.0 / u2};
+    for (int i = 0; i < 6; ++i) ctx->asq_coef[i] = c[i];
+    static IncTable table;      // the same for every context; built once
+    static bool built = false;
+    if (!built) {
+        build_incidences(&table);
+        built = true;
+    }
+    for (int d = 0; d < 4; ++d)
+        if (table.n[d] > ASQ_MAX_INC) return STAG_ERR_ARG;
+    CK(cudaMemcpyToSymbolAsync(c_inc, table.inc, sizeof(table.inc), 0, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyToSymbolAsync(c_ninc, table.n, sizeof(table.n), 0, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->asqtad = true;
+    ctx->asq_stale = true;
+    return STAG_OK;
+}
+
+extern "C" stag_status stag_asqtad_links(stag_ctx* ctx, double* host_fat, double* host_naik) {
+    if (!ctx || !host_fat || !host_naik || !ctx->asqtad) return STAG_ERR_ARG;
+    CKS(asq_ensure(ctx));
+    const AsqLinks A = asq_links(ctx);
+    const size_t bytes = (size_t)4 * ctx->g.V * 18 * sizeof(double);
+    void* stage;
+    CKS(ws_get(ctx, WS_STAGE, bytes, &stage));
+    for (int which = 0; which < 2; ++which) {
+        const LinkPtrs& l = which == 0 ? A.fat : A.lng;
+        CKS(unpack_links(ctx, l.hi, l.lo, (double*)stage));
+        CK(cudaMemcpyAsync(which == 0 ? host_fat : host_naik, stage, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    return STAG_OK;
+}

@@ -24,6 +24,24 @@ static void launch_tps(stag_ctx* ctx, cudaStream_t stream, int tps, int out_par,
     }
 }
 
+// the same for the improved operator (asqtad.cuh): fat and Naik links
+template <typename R, int FMT, int NR, class Epi>
+static void launch_tps_asq(stag_ctx* ctx, cudaStream_t stream, int tps, int out_par, int nrhs, const void* in,
+                           Epi epi) {
+    typedef typename SrcFor<R>::type Src;
+    const int bs = STAG_DSLASH_BLOCK;
+    const int nchunk = (nrhs + NR - 1) / NR;
+    const int grid = nblocks(ctx->g.Vh, bs / tps) * nchunk;
+    Src src{(const typename SrcFor<R>::io*)in};
+    const AsqLinks A = asq_links(ctx);
+    switch (tps) {
+        case 8: k_dslash_asq<R, FMT, NR, 8, Src, Epi><<<grid, bs, 0, stream>>>(ctx->g, out_par, A, src, nrhs, nchunk, epi); break;
+        case 4: k_dslash_asq<R, FMT, NR, 4, Src, Epi><<<grid, bs, 0, stream>>>(ctx->g, out_par, A, src, nrhs, nchunk, epi); break;
+        case 2: k_dslash_asq<R, FMT, NR, 2, Src, Epi><<<grid, bs, 0, stream>>>(ctx->g, out_par, A, src, nrhs, nchunk, epi); break;
+        default: k_dslash_asq<R, FMT, NR, 1, Src, Epi><<<grid, bs, 0, stream>>>(ctx->g, out_par, A, src, nrhs, nchunk, epi); break;
+    }
+}
+
 // out = scale * D in: the plain-store epilogue of each arithmetic
 template <typename R> struct StoreEpi {
     static EpiStore<R> make(void* out, double scale) { return EpiStore<R>{(typename V2T<R>::T*)out, (R)scale}; }
@@ -40,6 +58,15 @@ template <typename R, int FMT, class Epi>
 static stag_status launch_t(stag_ctx* ctx, int out_par, int nrhs, const void* in, Epi epi) {
     if ((long long)nblocks(ctx->g.Vh, 16) * nrhs > 0x7fffffffLL) return STAG_ERR_ARG;
     const int nr = dslash_nr_for(nrhs);
+    if constexpr (FMT == FMT_F64 || FMT == FMT_F32_18) {
+        if (ctx->asqtad) {
+            const int tps = asq_tps(ctx);
+            if (nr == 4) launch_tps_asq<R, FMT, 4>(ctx, ctx->stream, tps, out_par, nrhs, in, epi);
+            else launch_tps_asq<R, FMT, 1>(ctx, ctx->stream, tps, out_par, nrhs, in, epi);
+            CKL();
+            return STAG_OK;
+        }
+    }
     const int tps = dslash_tps(ctx, prec_of(FMT), nr);
     if (nr == 4) launch_tps<R, FMT, 4>(ctx, ctx->stream, tps, out_par, nrhs, in, epi);
     else launch_tps<R, FMT, 1>(ctx, ctx->stream, tps, out_par, nrhs, in, epi);
@@ -200,6 +227,7 @@ static stag_status check_prec(stag_ctx* ctx, stag_prec prec) {
     if (!ctx->has_gauge) return STAG_ERR_NO_GAUGE;
     if (prec == STAG_BF16_12 && ctx->b16_stale) CKS(refresh_bf16(ctx));
     if (prec < STAG_FP64 || prec > STAG_BF16_12) return STAG_ERR_ARG;
+    if (ctx->asqtad && prec != STAG_FP64 && prec != STAG_FP32) return STAG_ERR_ARG;   // fat links are not unitary
     return STAG_OK;
 }
 
@@ -256,12 +284,14 @@ static size_t real_size(stag_prec p) { return p == STAG_FP64 ? sizeof(double) : 
 extern "C" stag_status stag_dslash(stag_ctx* ctx, int out_parity, stag_prec prec, int nrhs, const void* in,
                                    void* out) {
     if (!ctx || !in || !out || nrhs < 1 || (out_parity != 0 && out_parity != 1)) return STAG_ERR_ARG;
+    CKS(asq_ensure(ctx));
     return launch_dslash(ctx, out_parity, prec, nrhs, in, out, 0.5);
 }
 
 extern "C" stag_status stag_apply_a(stag_ctx* ctx, double mass, double shift, stag_prec prec, int nrhs,
                                     const void* in, void* out) {
     if (!ctx || !in || !out || nrhs < 1) return STAG_ERR_ARG;
+    CKS(asq_ensure(ctx));
     void* tmp;
     CKS(ws_get(ctx, WS_APPLY_TMP, (size_t)nrhs * 3 * ctx->g.Vh * 2 * real_size(prec), &tmp));
     return launch_apply_a(ctx, mass * mass + shift, prec, nrhs, in, out, tmp);

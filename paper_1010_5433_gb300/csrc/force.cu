@@ -569,6 +569,7 @@ stag_status update_links(stag_ctx* ctx, const double* mom, double eps, stag_prec
                                                                                      eps);
     CKL();
     ctx->b16_stale = true;
+    ctx->asq_stale = true;
     return STAG_OK;
 }
 
@@ -577,6 +578,7 @@ stag_status reunitarize(stag_ctx* ctx) {
     k_reunitarize<<<nblocks(n, FB), FB, 0, ctx->stream>>>(ctx->g, ctx->ghi, ctx->glo);
     CKL();
     ctx->b16_stale = true;
+    ctx->asq_stale = true;
     return STAG_OK;
 }
 

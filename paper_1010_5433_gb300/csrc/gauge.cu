@@ -89,11 +89,19 @@ stag_status gauge_copy(stag_ctx* ctx, float* dh, float* dl, const float* sh, con
     return STAG_OK;
 }
 
+stag_status unpack_links(stag_ctx* ctx, const float* hi, const float* lo, double* stage) {
+    long long n = 4LL * ctx->g.V;
+    k_unpack_gauge<<<nblocks(n, 128), 128, 0, ctx->stream>>>(ctx->g, hi, lo, stage);
+    CKL();
+    return STAG_OK;
+}
+
 static stag_status pack_from_device(stag_ctx* ctx, const double* dev_u) {
     long long n = 4LL * ctx->g.V;
     k_pack_gauge<<<nblocks(n, 128), 128, 0, ctx->stream>>>(ctx->g, dev_u, ctx->ghi, ctx->glo);
     CKL();
     ctx->has_gauge = true;
+    ctx->asq_stale = true;
     return refresh_bf16(ctx);
 }
 

@@ -102,6 +102,20 @@ stag_status force_from_buffers(stag_ctx* ctx, const ForceTerm* terms, int nterms
     const stag_prec py = prec == STAG_FP64 ? STAG_FP64 : STAG_FP32;
     const size_t cs = prec == STAG_FP64 ? sizeof(double2) : sizeof(float2);
     CKS(launch_dslash(ctx, 1, py, (int)B.total, B.x, B.y, 0.5));
+    if (ctx->asqtad) {
+        // the outer products of every term and pseudo-fermion first, then one
+        // pass through the fat and Naik paths (asqtad.cu)
+        CKS(asq_outer_begin(ctx, py));
+        size_t off = 0;
+        for (int t = 0; t < nterms; ++t) {
+            const ForceTerm& T = terms[t];
+            const int ns = T.r->n;
+            CKS(asq_outer_add(ctx, py, T.n, ns, T.r->alpha, (const char*)B.x + off * hc * cs,
+                              (const char*)B.y + off * hc * cs, coef));
+            off += (size_t)T.n * ns;
+        }
+        return asq_force_finish(ctx, py, out, mode);
+    }
     size_t off = 0;
     for (int t = 0; t < nterms; ++t) {
         const ForceTerm& T = terms[t];
@@ -320,6 +334,7 @@ struct Traj {
         if (!accept && !p->no_metropolis) {
             CKS(gauge_copy(ctx, ctx->ghi, ctx->glo, save_hi, save_lo));
             ctx->b16_stale = true;
+            ctx->asq_stale = true;
         }
         CK(cudaEventRecord(e1, ctx->stream));
         double plaq;
@@ -446,6 +461,8 @@ stag_status check_hmc(stag_ctx* ctx, const stag_hmc* p) {
     if (!ctx || !p) return STAG_ERR_ARG;
     if (!ctx->has_gauge) return STAG_ERR_NO_GAUGE;
     if (p->use_surrogate && (p->n_mid < 1 || !ctx->sur_loaded)) return STAG_ERR_ARG;
+    if (ctx->asqtad && (p->use_surrogate || (p->md_prec != STAG_FP64 && p->md_prec != STAG_FP32)))
+        return STAG_ERR_ARG;
     for (int f = 0; f < p->n_flavours && f < STAG_MAX_FLAVOURS; ++f)
         if (p->flavour[f].level < 0 || p->flavour[f].level > 1 || (p->flavour[f].level == 1 && p->n_mid < 1))
             return STAG_ERR_ARG;
@@ -690,6 +707,7 @@ extern "C" stag_status stag_md_trajectory_batch(stag_ctx* const* ctxs, int n, co
         for (int j = 0; j < i; ++j)
             if (ctxs[j] == ctxs[i]) return STAG_ERR_ARG;
         CKS(check_hmc(ctxs[i], &ps[i]));
+        if (ctxs[i]->asqtad) return STAG_ERR_ARG;   // batched chains run the unimproved operator
         if (!same_schedule(ps[0], ps[i])) return STAG_ERR_ARG;
     }
     if (n == 1) return stag_md_trajectory(ctxs[0], &ps[0], &outs[0]);

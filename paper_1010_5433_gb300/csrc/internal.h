@@ -9,6 +9,7 @@
 
 #include "common.cuh"
 #include "dslash.cuh"
+#include "asqtad.cuh"
 
 // Device state of one multi-shift solve (see solver.cu).
 struct SolverState;
@@ -33,6 +34,8 @@ enum WsSlot {
     WS_B_DF, WS_X_DF,  // fp64 solves: float-float copies of b and x
     WS_SUR_GRAD_PART, WS_SUR_LOSS_PART, WS_SUR_GRAD,   // surrogate training
     WS_BATCH_RED,      // batched solves: per-block partial sums of all chains
+    WS_ASQ_LINKS,      // improved staggered: fat and Naik links (two-float stores)
+    WS_ASQ_X,          // improved staggered force: the outer-product fields of V and W
     WS_COUNT
 };
 
@@ -124,6 +127,11 @@ struct stag_ctx {
     float tps_us[4][2] = {};          // the winner's time per launch (us)
     int tps_force = 0;                // STAG_DSLASH_TPS: force a value (0 = tune)
     bool no_alloc_call = false;       // inside stag_apply_a_noalloc: nothing may allocate
+    // improved (asqtad) operator: fat and Naik links rebuilt after every change of the thin links
+    bool asqtad = false;
+    bool asq_stale = true;
+    double asq_coef[6] = {};          // 1-link, 3-, 5-, 7-staple, Lepage, Naik
+    float* asq_store = nullptr;       // fat hi, fat lo, Naik hi, Naik lo (WS_ASQ_LINKS)
     bool use_persistent = true;       // persistent cooperative solver (STAG_PERSISTENT=0: the three-kernel path)
     void* bar = nullptr;              // grid-barrier words of the persistent solver
     void* ptime = nullptr;            // per-phase ns counters of the persistent kernels while profiling
@@ -192,6 +200,20 @@ inline int nblocks(long long n, int bs) { return (int)((n + bs - 1) / bs); }
 // gauge.cu
 stag_status refresh_bf16(stag_ctx* ctx);
 stag_status gauge_copy(stag_ctx* ctx, float* dst_hi, float* dst_lo, const float* src_hi, const float* src_lo);
+
+// asqtad.cu: the improved operator.  asq_ensure rebuilds the fat and Naik
+// links if the thin links changed since (a no-op for the unimproved operator);
+// the force accumulates the outer products of every term, then one pass
+// through the paths writes (mode 0) or adds (mode 1) the force into out.
+AsqLinks asq_links(const stag_ctx* ctx);
+int asq_tps(const stag_ctx* ctx);
+stag_status asq_ensure(stag_ctx* ctx);
+stag_status asq_outer_begin(stag_ctx* ctx, stag_prec prec);
+stag_status asq_outer_add(stag_ctx* ctx, stag_prec prec, int nsrc, int nshift, const double* alpha, const void* x,
+                          const void* y, double coef);
+stag_status asq_force_finish(stag_ctx* ctx, stag_prec prec, double* out, int mode);
+// gauge.cu: a two-float link store to the host layout (double, [mu][site][3][3] complex) on the device
+stag_status unpack_links(stag_ctx* ctx, const float* hi, const float* lo, double* stage);
 
 // dslash.cu: threads per site for a Dslash of this precision and sources per
 // thread, autotuned on first use (never call it first inside a stream capture)

@@ -67,6 +67,7 @@ extern "C" stag_status stag_apply_a_noalloc(stag_ctx* ctx, double mass, double s
     // them, so nothing left there by an earlier call needs clearing.  The
     // flag keeps the Dslash autotuner (which allocates test fields) from
     // running inside this call; an untuned precision uses one thread per site.
+    CKS(asq_ensure(ctx));   // the improved operator's links, if due: a kernel, no allocation
     ctx->no_alloc_call = true;
     stag_status s = launch_apply_a(ctx, mass * mass + shift, prec, nrhs, in, out, tmp);
     ctx->no_alloc_call = false;

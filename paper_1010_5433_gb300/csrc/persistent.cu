@@ -10,7 +10,8 @@ bool persistent_fits(stag_ctx* ctx) {
     // the three-kernel iteration at 16^4 (launch- and latency-bound) and at
     // 32^4 and 48^4 alike (fp32-12: 194 against 429 us and 990 against 2062 us
     // per iteration), the deferred shift updates moving a third of the bytes
-    return ctx->use_persistent;
+    // (the improved operator takes the three-kernel path)
+    return ctx->use_persistent && !ctx->asqtad;
 }
 
 int persistent_ring_slots() { return RING; }

@@ -591,6 +591,37 @@ static void ms_dslash_pair(cudaStream_t stream, int grid, const Geom& g, const L
     k_dslash<R, FMT, NR, TPS, SrcPlain<R>, EpiMsA<R>><<<grid, bs, 0, stream>>>(g, 0, L, s2, nrhs, nchunk, e2);
 }
 
+// the same pair for the improved operator (fat and Naik links)
+template <typename R, int FMT, int NR, int TPS>
+static void ms_dslash_pair_asq(cudaStream_t stream, int grid, const Geom& g, const AsqLinks& A, const SrcRp<R>& s1,
+                               const SrcPlain<R>& s2, const EpiMsOdd<R>& e1, const EpiMsA<R>& e2, int nrhs,
+                               int nchunk, cudaEvent_t mid) {
+    const int bs = STAG_DSLASH_BLOCK;
+    k_dslash_asq<R, FMT, NR, TPS, SrcRp<R>, EpiMsOdd<R>><<<grid, bs, 0, stream>>>(g, 1, A, s1, nrhs, nchunk, e1);
+    if (mid) cudaEventRecord(mid, stream);
+    k_dslash_asq<R, FMT, NR, TPS, SrcPlain<R>, EpiMsA<R>><<<grid, bs, 0, stream>>>(g, 0, A, s2, nrhs, nchunk, e2);
+}
+
+template <typename R, int FMT, int NR>
+static void ms_dslash_asq_tps(int tps, cudaStream_t stream, int grid, const Geom& g, const AsqLinks& A,
+                              const SrcRp<R>& s1, const SrcPlain<R>& s2, const EpiMsOdd<R>& e1, const EpiMsA<R>& e2,
+                              int nrhs, int nchunk, cudaEvent_t mid) {
+    switch (tps) {
+        case 8: ms_dslash_pair_asq<R, FMT, NR, 8>(stream, grid, g, A, s1, s2, e1, e2, nrhs, nchunk, mid); break;
+        case 4: ms_dslash_pair_asq<R, FMT, NR, 4>(stream, grid, g, A, s1, s2, e1, e2, nrhs, nchunk, mid); break;
+        case 2: ms_dslash_pair_asq<R, FMT, NR, 2>(stream, grid, g, A, s1, s2, e1, e2, nrhs, nchunk, mid); break;
+        default: ms_dslash_pair_asq<R, FMT, NR, 1>(stream, grid, g, A, s1, s2, e1, e2, nrhs, nchunk, mid); break;
+    }
+}
+
+template <typename R, int FMT>
+static void ms_dslash_asq(int nr, int tps, cudaStream_t stream, int grid, const Geom& g, const AsqLinks& A,
+                          const SrcRp<R>& s1, const SrcPlain<R>& s2, const EpiMsOdd<R>& e1, const EpiMsA<R>& e2,
+                          int nrhs, int nchunk, cudaEvent_t mid) {
+    if (nr == 4) ms_dslash_asq_tps<R, FMT, 4>(tps, stream, grid, g, A, s1, s2, e1, e2, nrhs, nchunk, mid);
+    else ms_dslash_asq_tps<R, FMT, 1>(tps, stream, grid, g, A, s1, s2, e1, e2, nrhs, nchunk, mid);
+}
+
 template <typename R, int FMT, int NR>
 static void ms_dslash_tps(int tps, cudaStream_t stream, int grid, const Geom& g, const LinkPtrs& L,
                           const SrcRp<R>& s1, const SrcPlain<R>& s2, const EpiMsOdd<R>& e1, const EpiMsA<R>& e2,
@@ -620,7 +651,7 @@ static stag_status ms_iterations(stag_ctx* ctx, cudaStream_t stream, stag_prec p
     typedef typename V2T<R>::T V;
     const Geom& g = ctx->g;
     const int nr = dslash_nr_for(nrhs);
-    const int tps = dslash_tps(ctx, prec, nr);
+    const int tps = ctx->asqtad ? asq_tps(ctx) : dslash_tps(ctx, prec, nr);
     const int nchunk = (nrhs + nr - 1) / nr;
     const int grid_d = nblocks(g.Vh, STAG_DSLASH_BLOCK / tps) * nchunk;
     dim3 grid_u(nblocks(g.Vh, VB / UPDATE_GROUPS), nrhs);
@@ -638,7 +669,11 @@ static stag_status ms_iterations(stag_ctx* ctx, cudaStream_t stream, stag_prec p
             CK(cudaEventRecord(pf.pool[ev[0]], stream));
         }
         cudaEvent_t mid = smp ? pf.pool[ev[1]] : nullptr;
-        if constexpr (sizeof(R) == 8) {
+        if (ctx->asqtad) {
+            const AsqLinks A = asq_links(ctx);
+            if constexpr (sizeof(R) == 8) ms_dslash_asq<R, FMT_F64>(nr, tps, stream, grid_d, g, A, src1, src2, e1, e2, nrhs, nchunk, mid);
+            else ms_dslash_asq<R, FMT_F32_18>(nr, tps, stream, grid_d, g, A, src1, src2, e1, e2, nrhs, nchunk, mid);
+        } else if constexpr (sizeof(R) == 8) {
             ms_dslash<R, FMT_F64>(nr, tps, stream, grid_d, g, L, src1, src2, e1, e2, nrhs, nchunk, mid);
         } else {
             if (prec == STAG_FP32) ms_dslash<R, FMT_F32_18>(nr, tps, stream, grid_d, g, L, src1, src2, e1, e2, nrhs, nchunk, mid);
@@ -668,9 +703,10 @@ static size_t rsize(stag_prec p) { return p == STAG_FP64 ? sizeof(double) : size
 static stag_status solver_graph(stag_ctx* ctx, stag_prec prec, int nrhs, void* tmp, void* r, void* p, void* q,
                                 void* ps, void* x, cudaGraphExec_t* out) {
     const void* key[8] = {tmp, r, p, q, ps, x, ctx->st, ctx->red};
+    const int pkey = (int)prec + (ctx->asqtad ? 16 : 0);    // the operator is part of the captured launches
     auto& cache = ctx->graphs;
     for (auto& e : cache) {
-        if (e.prec == (int)prec && e.nrhs == nrhs && std::memcmp(e.key, key, sizeof(key)) == 0) {
+        if (e.prec == pkey && e.nrhs == nrhs && std::memcmp(e.key, key, sizeof(key)) == 0) {
             *out = e.exec;
             return STAG_OK;
         }
@@ -678,7 +714,7 @@ static stag_status solver_graph(stag_ctx* ctx, stag_prec prec, int nrhs, void* t
     if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
     SolverGraphEntry sg = {};
     std::memcpy(sg.key, key, sizeof(key));
-    sg.prec = (int)prec;
+    sg.prec = pkey;
     sg.nrhs = nrhs;
     CK(cudaGraphCreate(&sg.graph, 0));
     cudaGraphConditionalHandle h;
@@ -741,6 +777,8 @@ stag_status ms_setup(MsRun& R) {
     const Geom& g = ctx->g;
     R.mixed = R.prec != STAG_FP64;
     if (R.nrhs < 1 || R.nrhs > STAG_MAX_RHS || R.nshift < 1 || R.nshift > STAG_MAX_SHIFTS) return STAG_ERR_ARG;
+    if (ctx->asqtad && R.prec != STAG_FP64 && R.prec != STAG_FP32) return STAG_ERR_ARG;
+    CKS(asq_ensure(ctx));
     if (R.mixed && R.reliable && (!R.b64 || !R.x64)) return STAG_ERR_ARG;
     // the bf16 copy must follow every link update before a bf16 iteration
     if (R.prec == STAG_BF16_12 && ctx->b16_stale) CKS(refresh_bf16(ctx));
@@ -878,7 +916,7 @@ __global__ void k_solve_note(const SolverState* st, SolveNote* note, int w, doub
 
 stag_status defer_begin(stag_ctx* ctx) {
     CK(cudaMemsetAsync(ctx->note, 0, sizeof(SolveNote), ctx->stream));
-    ctx->defer = ctx->use_persistent;
+    ctx->defer = persistent_fits(ctx);
     return STAG_OK;
 }
 
@@ -947,7 +985,7 @@ stag_status ms_core(stag_ctx* ctx, double mass, int nshift, const double* shifts
     const bool persistent = persistent_fits(ctx);
     bool deferred = false;
     if (!persistent) {
-        dslash_tps(ctx, prec, dslash_nr_for(nrhs));   // tune before any capture
+        if (!ctx->asqtad) dslash_tps(ctx, prec, dslash_nr_for(nrhs));   // tune before any capture
         if (ctx->use_graphs) CKS(solver_graph(ctx, prec, nrhs, R.tmp, R.r, R.p, R.q, R.ps, R.x, &gexec));
     }
     cudaEvent_t pe0 = nullptr, pe1 = nullptr;
@@ -1044,8 +1082,9 @@ stag_status ms_core(stag_ctx* ctx, double mass, int nshift, const double* shifts
         const double S = 3.0 * (double)(mixed ? sizeof(float2) : sizeof(double2));   // one spinor at a site
         // K1 reads r and p (the direction is formed on the fly) and writes t;
         // K2 reads t, r, p and writes p, q
-        pf.bytes_total[PK_DSLASH_OE] += (double)hs->k * g.Vh * (link_bytes_site(prec) + 3.0 * S * nrhs);
-        pf.bytes_total[PK_DSLASH_EO_A] += (double)hs->k * g.Vh * (link_bytes_site(prec) + 5.0 * S * nrhs);
+        const double lb = (ctx->asqtad ? 2.0 : 1.0) * link_bytes_site(prec);   // fat + Naik links: twice the thin ones
+        pf.bytes_total[PK_DSLASH_OE] += (double)hs->k * g.Vh * (lb + 3.0 * S * nrhs);
+        pf.bytes_total[PK_DSLASH_EO_A] += (double)hs->k * g.Vh * (lb + 5.0 * S * nrhs);
         for (int kk = PK_DSLASH_OE; kk <= PK_UPDATE; ++kk) pf.launches[kk] += hs->k;
     }
     CKS(ms_finish(R));
@@ -1268,6 +1307,7 @@ extern "C" stag_status stag_multishift_solve_batch(stag_ctx* const* ctxs, int n,
     for (int i = 0; i < n; ++i) {
         if (!ctxs[i] || !b[i] || !x[i]) return STAG_ERR_ARG;
         if (!ctxs[i]->has_gauge) return STAG_ERR_NO_GAUGE;
+        if (ctxs[i]->asqtad) return STAG_ERR_ARG;   // batched solves run the unimproved operator
         for (int j = 0; j < i; ++j)
             if (ctxs[j] == ctxs[i]) return STAG_ERR_ARG;
     }

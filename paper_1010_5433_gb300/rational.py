@@ -261,14 +261,19 @@ WORKLOADS = {
     "c2_heavy_md": (0.5, 0.2, 8), "c2_heavy_met": (0.5, 0.2, 14), "c2_heavy_hb": (-0.25, 0.2, 14),
     "c2_ratio_md": (0.5, 0.02, 8, 0.0396), "c2_ratio_met": (0.5, 0.02, 12, 0.0396),
     "c2_ratio_hb": (-0.25, 0.02, 12, 0.0396),
+    # the improved (asqtad, tree level) 16^4 N_f = 2 workload at m = 0.02: its A has a wider spectrum,
+    # bounded by m^2 + (4 sum |c|)^2 = m^2 + 58.8, so these approximate on [m^2, m^2 + 64]
+    "asqtad_md": (0.5, 0.02, 14, 0.0, 64.0), "asqtad_met": (0.5, 0.02, 24, 0.0, 64.0),
+    "asqtad_hb": (-0.25, 0.02, 24, 0.0, 64.0),
 }
 TABLE_PATH = __import__("os").path.join(__import__("os").path.dirname(__file__), "rational_table.json")
 
 
 def _spec(name):
-    """(s, m, n, delta) of a workload rational (delta 0 unless it is a mass ratio)."""
+    """(s, m, n, delta, upper) of a workload rational (delta 0 unless it is a
+    mass ratio; the interval is [m^2, m^2 + upper], upper 16 unless given)."""
     w = WORKLOADS[name]
-    return (w[0], w[1], w[2], w[3] if len(w) > 3 else 0.0)
+    return (w[0], w[1], w[2], w[3] if len(w) > 3 else 0.0, w[4] if len(w) > 4 else 16.0)
 
 
 def load(name):
@@ -276,7 +281,7 @@ def load(name):
     or computed now if the table lacks it."""
     import json
     import os
-    s, m, n, delta = _spec(name)
+    s, m, n, delta, upper = _spec(name)
     if os.path.exists(TABLE_PATH):
         tab = json.load(open(TABLE_PATH))
         if name in tab and tab[name]["n"] == n:
@@ -284,7 +289,7 @@ def load(name):
             r = RationalApprox(d["s"], d["lo"], d["hi"], d["a0"], d["alpha"], d["beta"], d["err"])
             r.delta = d.get("delta", 0.0)
             return r
-    return remez(s, m * m, 16 + m * m, n, delta=delta)
+    return remez(s, m * m, upper + m * m, n, delta=delta)
 
 
 def write_table(names=None):
@@ -292,10 +297,10 @@ def write_table(names=None):
     import os
     tab = json.load(open(TABLE_PATH)) if os.path.exists(TABLE_PATH) else {}
     for name in WORKLOADS:
-        s, m, n, delta = _spec(name)
+        s, m, n, delta, upper = _spec(name)
         if (names and name not in names) or (name in tab and tab[name]["n"] == n):
             continue
-        r = remez(s, m * m, 16 + m * m, n, delta=delta)
+        r = remez(s, m * m, upper + m * m, n, delta=delta)
         tab[name] = {"s": r.s, "lo": r.lo, "hi": r.hi, "n": r.n, "a0": r.a0, "alpha": r.alpha, "beta": r.beta,
                      "err": r.err, "mass": m}
         if delta:

@@ -15,6 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "libstag.so")
 
 STAG_FP64, STAG_FP32, STAG_FP32_12, STAG_BF16_12 = 0, 1, 2, 3
+STAG_ACTION_UNIMPROVED, STAG_ACTION_ASQTAD = 0, 1
 STAG_MAX_SHIFTS = 32
 STAG_MAX_FLAVOURS = 2
 STATUS = {0: "ok", 1: "invalid argument", 2: "allocation failed", 3: "CUDA error",
@@ -85,6 +86,8 @@ SIGNATURES = {
     "stag_dslash": ([_vp, _i, _i, _i, _vp, _vp], _i),
     "stag_apply_a": ([_vp, _d, _d, _i, _i, _vp, _vp], _i),
     "stag_apply_a_noalloc": ([_vp, _d, _d, _i, _i, _vp, _vp], _i),
+    "stag_set_action": ([_vp, _i, _d], _i),
+    "stag_asqtad_links": ([_vp, _vp, _vp], _i),
     "stag_multishift_solve": ([_vp, _d, _i, _vp, _i, _i, _vp, _vp, _d, _i, C.POINTER(stag_solve_info)], _i),
     "stag_fermion_force": ([_vp, _d, C.POINTER(stag_rational), _i, _i, _vp, _vp, _d, _i,
                             C.POINTER(stag_solve_info)], _i),
@@ -225,6 +228,16 @@ def stag_apply_a_noalloc(ctx, mass, shift, prec, nrhs, inp, out):
     st = lib().stag_apply_a_noalloc(ctx, float(mass), float(shift), int(prec), int(nrhs), _ptr(inp), _ptr(out))
     if st != 0:
         raise StagError(st, "stag_apply_a_noalloc", lib().stag_last_cuda_error(ctx).decode())
+
+
+def stag_set_action(ctx, action, u0=1.0):
+    """STAG_ACTION_UNIMPROVED (the paper's operator) or STAG_ACTION_ASQTAD with tadpole factor u0."""
+    _check(lib().stag_set_action(ctx, int(action), float(u0)), "stag_set_action", ctx)
+
+
+def stag_asqtad_links(ctx, host_fat, host_naik):
+    """Fat and Naik links into float64 host arrays of 4*V*18 values each (host gauge layout)."""
+    _check(lib().stag_asqtad_links(ctx, _ptr(host_fat), _ptr(host_naik)), "stag_asqtad_links", ctx)
 
 
 def stag_multishift_solve(ctx, mass, shifts, prec, nrhs, b, x, tol, max_iter, info=True, check=True):

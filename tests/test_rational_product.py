@@ -24,7 +24,7 @@ def _close(r, g, tol):
 @pytest.mark.parametrize("name", ["c1_md", "c2_md", "c4_md"])
 def test_product_remez_matches_oracle(name):
     g = json.load(open(GOLDEN))[name]
-    s, m, n = rational.WORKLOADS[name]
+    s, m, n = rational.WORKLOADS[name][:3]
     _close(rational.remez(s, m * m, 16 + m * m, n), g, 1e-9)
 
 

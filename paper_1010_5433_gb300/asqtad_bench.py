@@ -10,7 +10,7 @@ output spinor once: 16 x 72 + 2 x 24 = 1200 B (fp32), 16 x 144 + 2 x 48 =
 2400 B (fp64).  Times are CUDA events on the launching stream.
 
   python -m paper_1010_5433_gb300.asqtad_bench [--dslash-dims 48 48 48 48] [--solve-dims 16 16 16 16 32 32 32 32]
-         [--trajectories 10] [--warmup 5] [--skip-hmc]
+         [--trajectories 10] [--warmup 5] [--skip-hmc] [--skip-solve]
 """
 import argparse
 import json
@@ -95,9 +95,11 @@ def dslash_point(dims, reps=20, hbm_gbs=None):
     return res
 
 
-def solve_point(dims, nshift=12, mass=0.02, reps=3):
-    """fp32 multi-shift solves (fp64 reliable updates) and the force at the
-    same shifts: time per iteration, and the force's share beyond its solve."""
+def solve_point(dims, mass=0.02, reps=3):
+    """fp32 multi-shift solves (fp64 reliable updates) at the MD rational's
+    shifts, and the force of that rational: time per iteration, and the
+    force's time beyond its solve (the Y = D_oe X Dslash, outer products and
+    the fat-link path gather)."""
     import torch
 
     from . import rational, stag
@@ -106,7 +108,7 @@ def solve_point(dims, nshift=12, mass=0.02, reps=3):
     V = int(np.prod(dims))
     vh = V // 2
     md = rational.load("asqtad_md")
-    shifts = list(md.beta[:nshift])
+    shifts = list(md.beta)
     ctx = stag.stag_create(dims, True, stream.cuda_stream)
     res = {"lattice": "x".join(str(d) for d in dims), "shifts": len(shifts), "mass": mass}
     try:
@@ -219,6 +221,7 @@ if __name__ == "__main__":
     ap.add_argument("--trajectories", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--skip-hmc", action="store_true")
+    ap.add_argument("--skip-solve", action="store_true")
     a = ap.parse_args()
     peak = None
     try:
@@ -226,7 +229,7 @@ if __name__ == "__main__":
     except (OSError, ValueError):
         pass
     print(json.dumps({"asqtad_dslash": dslash_point(tuple(a.dslash_dims), hbm_gbs=peak)}), flush=True)
-    for k in range(0, len(a.solve_dims), 4):
+    for k in range(0, 0 if a.skip_solve else len(a.solve_dims), 4):
         print(json.dumps({"asqtad_solve": solve_point(tuple(a.solve_dims[k:k + 4]))}), flush=True)
     if not a.skip_hmc:
         hmc_run(a.trajectories, a.warmup, log=lambda s: print(json.dumps({"asqtad_hmc": json.loads(s)}), flush=True))

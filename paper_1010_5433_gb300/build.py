@@ -13,7 +13,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libstag.so")
 SOURCES = ["api.cu", "gauge.cu", "dslash.cu", "solver.cu", "blas.cu", "force.cu", "hmc.cu", "noalloc.cu", "persistent.cu", "persistent_f32_18.cu",
-           "persistent_f32_12.cu", "persistent_bf16_12.cu", "persistent_ff.cu", "surrogate.cu", "batch.cu", "asqtad.cu"]
+           "persistent_f32_12.cu", "persistent_bf16_12.cu", "persistent_ff.cu", "surrogate.cu", "batch.cu", "asqtad.cu",
+           "persistent_asq_f32.cu", "persistent_asq_ff.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -73,6 +73,53 @@ template <typename R> __device__ __forceinline__ Su3<R> scaled(R c, const Su3<R>
     return b;
 }
 
+// 3x3 products a b and a b^dag.  In float-float each entry's six real
+// products are summed with error-free products and a compensated running sum
+// (df_mac, Ogita-Rump-Oishi) and renormalised once, about half the work of
+// chained float-float multiplies and adds.
+__device__ __forceinline__ Su3<float> mm(const Su3<float>& a, const Su3<float>& b) { return mul(a, b); }
+__device__ __forceinline__ Su3<float> mm_nd(const Su3<float>& a, const Su3<float>& b) { return mul_nd(a, b); }
+__device__ __forceinline__ Su3<DF> mm(const Su3<DF>& a, const Su3<DF>& b) {
+    Su3<DF> c;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            DF re(0.f), im(0.f);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                df_mac(re, a.e[i][k].re, b.e[k][j].re);
+                df_mac(re, -a.e[i][k].im, b.e[k][j].im);
+                df_mac(im, a.e[i][k].re, b.e[k][j].im);
+                df_mac(im, a.e[i][k].im, b.e[k][j].re);
+            }
+            df_renorm(re);
+            df_renorm(im);
+            c.e[i][j] = mk(re, im);
+        }
+    return c;
+}
+__device__ __forceinline__ Su3<DF> mm_nd(const Su3<DF>& a, const Su3<DF>& b) {
+    Su3<DF> c;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            DF re(0.f), im(0.f);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {   // a_ik conj(b_jk)
+                df_mac(re, a.e[i][k].re, b.e[j][k].re);
+                df_mac(re, a.e[i][k].im, b.e[j][k].im);
+                df_mac(im, a.e[i][k].im, b.e[j][k].re);
+                df_mac(im, -a.e[i][k].re, b.e[j][k].im);
+            }
+            df_renorm(re);
+            df_renorm(im);
+            c.e[i][j] = mk(re, im);
+        }
+    return c;
+}
+
 // thin link U_nu(c)
 template <typename R, int FMT>
 __device__ __forceinline__ Su3<R> thin(const Geom& g, const LinkPtrs& L, const int c[4], int nu) {
@@ -98,7 +145,7 @@ __device__ __forceinline__ Su3<R> staple(const Geom& g, const LinkPtrs& L, const
     int d[4] = {y[0], y[1], y[2], y[3]};
     a_move(g, d, mu + 1);
     const Su3<R> last = walk<R, FMT>(g, L, d, s);   // L(y + mu, s)
-    return mul_nd(mul(first, a), last);
+    return mm_nd(mm(first, a), last);
 }
 
 struct AsqCoef {
@@ -128,7 +175,24 @@ __device__ __forceinline__ void store_df(float* hi, float* lo, size_t blk, int h
     reinterpret_cast<float2*>(lo + blk + 16 * (size_t)Vh)[h] = make_float2(vl[16], vl[17]);
 }
 
-// one thread per fat link (mu, x): V and W in float-float
+template <typename R> __device__ __forceinline__ R coef_as(const AsqCoef& k, int i);
+template <> __device__ __forceinline__ float coef_as<float>(const AsqCoef& k, int i) { return k.c[i][0] + k.c[i][1]; }
+template <> __device__ __forceinline__ DF coef_as<DF>(const AsqCoef& k, int i) { return cf(k, i); }
+
+__device__ __forceinline__ Su3<DF> as_df(const Su3<DF>& u) { return u; }
+__device__ __forceinline__ Su3<DF> as_df(const Su3<float>& u) {
+    Su3<DF> d;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) d.e[i][j] = mk(DF(u.e[i][j].re), DF(u.e[i][j].im));
+    return d;
+}
+
+// one thread per fat link (mu, x): V and W in float-float (R = DF, from the
+// two-float thin links) or in fp32 (R = float, from their hi words; stored
+// with zero lo words)
+template <typename R, int FMT>
 __global__ void __launch_bounds__(AB) k_fatten(Geom g, LinkPtrs L, AsqCoef k, float* fhi, float* flo, float* lhi,
                                                float* llo) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -137,45 +201,45 @@ __global__ void __launch_bounds__(AB) k_fatten(Geom g, LinkPtrs L, AsqCoef k, fl
     const int mu = blk >> 1, par = blk & 1;
     int x[4];
     a_coords(g, par, h, x);
-    Su3<DF> v = scaled(cf(k, 0), thin<DF, FMT_F64>(g, L, x, mu));
+    Su3<R> v = scaled(coef_as<R>(k, 0), thin<R, FMT>(g, L, x, mu));
     for (int nu = 0; nu < 4; ++nu) {
         if (nu == mu) continue;
         for (int sn = -1; sn <= 1; sn += 2) {
             const int a = sn * (nu + 1);
             int y1[4] = {x[0], x[1], x[2], x[3]};
             a_move(g, y1, a);
-            Su3<DF> q = scaled(cf(k, 1), thin<DF, FMT_F64>(g, L, y1, mu));
+            Su3<R> q = scaled(coef_as<R>(k, 1), thin<R, FMT>(g, L, y1, mu));
             for (int rho = 0; rho < 4; ++rho) {
                 if (rho == mu || rho == nu) continue;
                 for (int sr = -1; sr <= 1; sr += 2) {
                     const int b = sr * (rho + 1);
                     int y2[4] = {y1[0], y1[1], y1[2], y1[3]};
                     a_move(g, y2, b);
-                    Su3<DF> t = scaled(cf(k, 2), thin<DF, FMT_F64>(g, L, y2, mu));
+                    Su3<R> t = scaled(coef_as<R>(k, 2), thin<R, FMT>(g, L, y2, mu));
                     const int sig = 6 - mu - nu - rho;     // the remaining direction
                     for (int ss = -1; ss <= 1; ss += 2) {
                         const int c = ss * (sig + 1);
                         int y3[4] = {y2[0], y2[1], y2[2], y2[3]};
                         a_move(g, y3, c);
-                        axpy(t, cf(k, 3), staple<DF, FMT_F64>(g, L, y2, mu, c, thin<DF, FMT_F64>(g, L, y3, mu)));
+                        axpy(t, coef_as<R>(k, 3), staple<R, FMT>(g, L, y2, mu, c, thin<R, FMT>(g, L, y3, mu)));
                     }
-                    axpy(q, DF(1.f), staple<DF, FMT_F64>(g, L, y1, mu, b, t));
+                    axpy(q, R(1.f), staple<R, FMT>(g, L, y1, mu, b, t));
                 }
             }
-            axpy(v, DF(1.f), staple<DF, FMT_F64>(g, L, x, mu, a, q));
+            axpy(v, R(1.f), staple<R, FMT>(g, L, x, mu, a, q));
             // Lepage: the double-width staple in the same direction
             int y2[4] = {y1[0], y1[1], y1[2], y1[3]};
             a_move(g, y2, a);
-            const Su3<DF> inner = staple<DF, FMT_F64>(g, L, y1, mu, a, thin<DF, FMT_F64>(g, L, y2, mu));
-            axpy(v, cf(k, 4), staple<DF, FMT_F64>(g, L, x, mu, a, inner));
+            const Su3<R> inner = staple<R, FMT>(g, L, y1, mu, a, thin<R, FMT>(g, L, y2, mu));
+            axpy(v, coef_as<R>(k, 4), staple<R, FMT>(g, L, x, mu, a, inner));
         }
     }
-    store_df(fhi, flo, link_block_f(mu, par, g.Vh), h, g.Vh, v);
+    store_df(fhi, flo, link_block_f(mu, par, g.Vh), h, g.Vh, as_df(v));
     int c[4] = {x[0], x[1], x[2], x[3]};
-    Su3<DF> w = walk<DF, FMT_F64>(g, L, c, mu + 1);
-    w = mul(w, walk<DF, FMT_F64>(g, L, c, mu + 1));
-    w = mul(w, walk<DF, FMT_F64>(g, L, c, mu + 1));
-    store_df(lhi, llo, link_block_f(mu, par, g.Vh), h, g.Vh, scaled(cf(k, 5), w));
+    Su3<R> w = walk<R, FMT>(g, L, c, mu + 1);
+    w = mm(w, walk<R, FMT>(g, L, c, mu + 1));
+    w = mm(w, walk<R, FMT>(g, L, c, mu + 1));
+    store_df(lhi, llo, link_block_f(mu, par, g.Vh), h, g.Vh, as_df(scaled(coef_as<R>(k, 5), w)));
 }
 
 // ---------------------------------------------------------------- force
@@ -274,10 +338,6 @@ __device__ __forceinline__ Su3<R> load_x(const R* f, int mu, const Geom& g, cons
     return m;
 }
 
-template <typename R> __device__ __forceinline__ R coef_as(const AsqCoef& k, int i);
-template <> __device__ __forceinline__ float coef_as<float>(const AsqCoef& k, int i) { return k.c[i][0] + k.c[i][1]; }
-template <> __device__ __forceinline__ DF coef_as<DF>(const AsqCoef& k, int i) { return cf(k, i); }
-
 // One thread per thin link (nu, y): over every incidence of nu, the rest of
 // the path's loop R = A_{k+1} .. A_n X_mu(x) A_1 .. A_{k-1} (x the path's
 // start), summed with the path coefficient into Gf (link met forward) or Gb
@@ -313,17 +373,17 @@ __global__ void __launch_bounds__(AB) k_asq_force(Geom g, LinkPtrs L, AsqCoef k,
         bool have = false;
         for (int j = kk + 1; j < len; ++j) {
             const Su3<R> a = walk<R, FMT>(g, L, c, in.s[j]);
-            m = have ? mul(m, a) : a;
+            m = have ? mm(m, a) : a;
             have = true;
         }
         const Su3<R> xm = load_x<R>(in.cls == 5 ? xw : xv, mu, g, x);
-        m = have ? mul(m, xm) : xm;
-        for (int j = 0; j < kk; ++j) m = mul(m, walk<R, FMT>(g, L, x, in.s[j]));
+        m = have ? mm(m, xm) : xm;
+        for (int j = 0; j < kk; ++j) m = mm(m, walk<R, FMT>(g, L, x, in.s[j]));
         axpy(fwd ? gf : gb, coef_as<R>(k, in.cls), m);
     }
     const Su3<R> u = thin<R, FMT>(g, L, y, nu);
-    Su3<R> w = mul(u, gf);
-    const Su3<R> b = mul_nd(gb, u);
+    Su3<R> w = mm(u, gf);
+    const Su3<R> b = mm_nd(gb, u);
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -425,14 +485,21 @@ int asq_tps(const stag_ctx* ctx) {
 stag_status asq_ensure(stag_ctx* ctx) {
     if (!ctx->asqtad) return STAG_OK;
     if (!ctx->has_gauge) return STAG_ERR_NO_GAUGE;
-    if (!ctx->asq_stale) return STAG_OK;
+    const int want = ctx->asq_fp32_build ? 1 : 2;
+    if (!ctx->asq_stale && ctx->asq_built == want) return STAG_OK;
     const AsqLinks A = asq_links(ctx);
     const long long n = 8LL * ctx->g.Vh;
-    k_fatten<<<nblocks(n, AB), AB, 0, ctx->stream>>>(ctx->g, link_ptrs(ctx), make_coef(ctx->asq_coef),
-                                                     const_cast<float*>(A.fat.hi), const_cast<float*>(A.fat.lo),
-                                                     const_cast<float*>(A.lng.hi), const_cast<float*>(A.lng.lo));
+    float *fh = const_cast<float*>(A.fat.hi), *fl = const_cast<float*>(A.fat.lo);
+    float *lh = const_cast<float*>(A.lng.hi), *ll = const_cast<float*>(A.lng.lo);
+    if (want == 2)
+        k_fatten<DF, FMT_F64><<<nblocks(n, AB), AB, 0, ctx->stream>>>(ctx->g, link_ptrs(ctx), make_coef(ctx->asq_coef),
+                                                                      fh, fl, lh, ll);
+    else
+        k_fatten<float, FMT_F32_18><<<nblocks(n, AB), AB, 0, ctx->stream>>>(ctx->g, link_ptrs(ctx),
+                                                                            make_coef(ctx->asq_coef), fh, fl, lh, ll);
     CKL();
     ctx->asq_stale = false;
+    ctx->asq_built = want;
     return STAG_OK;
 }
 

@@ -136,6 +136,15 @@ stag_status force_from_buffers(stag_ctx* ctx, const ForceTerm* terms, int nterms
 // force kernel runs once per term.
 stag_status fermion_force_terms(stag_ctx* ctx, const ForceTerm* terms, int nterms, stag_prec prec, double* out,
                                 double coef, int mode, double tol, int max_iter, TrajStats* ts) {
+    // an fp32 force of the improved operator uses fat links built in fp32 (a
+    // deterministic function of the thin links, as the MD needs); the fp64
+    // solves of the heatbath and the Metropolis step use float-float ones
+    struct Fp32Build {
+        stag_ctx* c;
+        bool old;
+        ~Fp32Build() { c->asq_fp32_build = old; }
+    } guard{ctx, ctx->asq_fp32_build};
+    ctx->asq_fp32_build = prec != STAG_FP64;
     ForceBufs B;
     CKS(force_buffers(ctx, terms, nterms, prec, &B));
     for (int t = 0; t < nterms; ++t) {

@@ -130,6 +130,8 @@ struct stag_ctx {
     // improved (asqtad) operator: fat and Naik links rebuilt after every change of the thin links
     bool asqtad = false;
     bool asq_stale = true;
+    int asq_built = 0;                // arithmetic of the current fat links: 1 fp32, 2 float-float
+    bool asq_fp32_build = false;      // set while fp32 MD forces run: their solves take fp32-built fat links
     double asq_coef[6] = {};          // 1-link, 3-, 5-, 7-staple, Lepage, Naik
     float* asq_store = nullptr;       // fat hi, fat lo, Naik hi, Naik lo (WS_ASQ_LINKS)
     bool use_persistent = true;       // persistent cooperative solver (STAG_PERSISTENT=0: the three-kernel path)
@@ -168,6 +170,10 @@ struct stag_ctx {
 // bytes of the eight links of one site in a Dslash of this precision
 inline double link_bytes_site(stag_prec p) {
     return p == STAG_FP64 ? 1152.0 : p == STAG_FP32 ? 576.0 : p == STAG_FP32_12 ? 384.0 : 192.0;
+}
+// the same for the context's operator: the improved one reads a fat and a Naik link per hop
+inline double op_link_bytes_site(const stag_ctx* ctx, stag_prec p) {
+    return (ctx->asqtad ? 2.0 : 1.0) * link_bytes_site(p);
 }
 
 // error plumbing
@@ -287,6 +293,8 @@ stag_status launch_persistent_f32_18(STAG_PERSISTENT_ARGS);
 stag_status launch_persistent_f32_12(STAG_PERSISTENT_ARGS);
 stag_status launch_persistent_bf16_12(STAG_PERSISTENT_ARGS);
 stag_status launch_persistent_ff(STAG_PERSISTENT_ARGS);
+stag_status launch_persistent_asq_f32(STAG_PERSISTENT_ARGS);
+stag_status launch_persistent_asq_ff(STAG_PERSISTENT_ARGS);
 stag_status launch_persistent(stag_ctx* ctx, stag_prec prec, int nrhs, void* ring, size_t rstride, void* p, void* q,
                               void* t, void* ps, void* x, const double2* b64, double2* x64, double2* t64);
 

@@ -10,8 +10,7 @@ bool persistent_fits(stag_ctx* ctx) {
     // the three-kernel iteration at 16^4 (launch- and latency-bound) and at
     // 32^4 and 48^4 alike (fp32-12: 194 against 429 us and 990 against 2062 us
     // per iteration), the deferred shift updates moving a third of the bytes
-    // (the improved operator takes the three-kernel path)
-    return ctx->use_persistent && !ctx->asqtad;
+    return ctx->use_persistent;
 }
 
 int persistent_ring_slots() { return RING; }
@@ -22,6 +21,10 @@ stag_status launch_persistent(stag_ctx* ctx, stag_prec prec, int nrhs, void* rin
     if (!ctx->ptime) {
         CKS(dev_alloc(ctx, &ctx->ptime, PTIME_WORDS * sizeof(unsigned long long)));
         CK(cudaMemsetAsync(ctx->ptime, 0, PTIME_WORDS * sizeof(unsigned long long), ctx->stream));
+    }
+    if (ctx->asqtad) {
+        if (prec == STAG_FP64) return launch_persistent_asq_ff(ctx, nrhs, ring, rstride, p, q, t, ps, x, b64, x64, t64);
+        return launch_persistent_asq_f32(ctx, nrhs, ring, rstride, p, q, t, ps, x, b64, x64, t64);
     }
     switch (prec) {
         case STAG_FP64: return launch_persistent_ff(ctx, nrhs, ring, rstride, p, q, t, ps, x, b64, x64, t64);

@@ -541,8 +541,9 @@ __device__ __noinline__ void flush_block(Scal& S, int h0, int h1, int PB, size_t
 // with fp64 sums (even sites), (r, r) = rr = rr_ref.  Three grid barriers.
 // The fp64 operator runs in float-float on the two-float link store, as the
 // standalone fp64 A does.  false if a barrier wait gave up.
-template <typename R>
-__device__ __noinline__ bool reliable_update(Scal& S, GridSync& gs, const Geom& g, const LinkPtrs& L, int h0, int h1, int PB,
+template <typename R, bool ASQ>
+__device__ __noinline__ bool reliable_update(Scal& S, GridSync& gs, const Geom& g, const LinkPtrs& L, const AsqLinks& A,
+                                int h0, int h1, int PB,
                                 typename V2T<R>::T* ring, size_t rstride, typename V2T<R>::T* ps,
                                 typename V2T<R>::T* x, const RelPtrs& rp, double* partial, unsigned int nb) {
     const size_t rs = (size_t)3 * g.Vh;
@@ -573,7 +574,8 @@ __device__ __noinline__ bool reliable_update(Scal& S, GridSync& gs, const Geom& 
             if (!S.rhs_live[j]) continue;
             SrcD2DFcg src{rp.x64 + ((size_t)j * ns + S.base) * rs};
             Vec3<DF> acc[1];
-            dslash_site<DF, FMT_F64, 1, 1>(g, 1, L, src, 0, 1, h, 0, acc);
+            if constexpr (ASQ) dslash_site_asq<DF, FMT_F64, 1, 1>(g, 1, A, src, 0, 1, h, 0, acc);
+            else dslash_site<DF, FMT_F64, 1, 1>(g, 1, L, src, 0, 1, h, 0, acc);
             double2* o = rp.t64 + (size_t)j * rs;
             const DF half(0.5f);
 #pragma unroll
@@ -593,7 +595,8 @@ __device__ __noinline__ bool reliable_update(Scal& S, GridSync& gs, const Geom& 
             if (j >= nrhs || !S.rhs_live[j]) continue;
             SrcD2DFcg src{rp.t64 + (size_t)j * rs};
             Vec3<DF> acc[1];
-            dslash_site<DF, FMT_F64, 1, 1>(g, 0, L, src, 0, 1, h, 0, acc);
+            if constexpr (ASQ) dslash_site_asq<DF, FMT_F64, 1, 1>(g, 0, A, src, 0, 1, h, 0, acc);
+            else dslash_site<DF, FMT_F64, 1, 1>(g, 0, L, src, 0, 1, h, 0, acc);
             const double2* xb = rp.x64 + ((size_t)j * ns + S.base) * rs;
             const double2* bb = rp.b64 + (size_t)j * rs;
             float2* ro = (float2*)rcur + (size_t)j * rs;
@@ -637,13 +640,15 @@ __device__ __noinline__ bool reliable_update(Scal& S, GridSync& gs, const Geom& 
     return true;
 }
 
+// ASQ: the improved operator (asqtad.cuh): every hop through the fat link
+// plus a third-neighbour hop through the Naik link, A holding both stores.
 // NRP: sources per pass of the Dslash phases; ND: sources the per-thread sums
 // and the update phase cover (1 and 1 for one source, 2 and 2 for two -- a
 // flavour split over two pseudo-fermions --, 4 and STAG_MAX_RHS otherwise);
 // PB: threads per block.  r is a ring of RING residual fields, rstride
 // elements apart.
-template <typename R, int FMT, int NRP, int ND, int PB>
-__global__ void __launch_bounds__(PB) k_ms_persistent(Geom g, LinkPtrs L, SolverState* st,
+template <typename R, int FMT, bool ASQ, int NRP, int ND, int PB>
+__global__ void __launch_bounds__(PB) k_ms_persistent(Geom g, LinkPtrs L, AsqLinks A, SolverState* st,
                                                       typename V2T<R>::T* ring, size_t rstride,
                                                       typename V2T<R>::T* p, typename V2T<R>::T* q,
                                                       typename V2T<R>::T* t, typename V2T<R>::T* ps,
@@ -682,7 +687,8 @@ __global__ void __launch_bounds__(PB) k_ms_persistent(Geom g, LinkPtrs L, Solver
     static_assert(ND % NRP == 0 && ND <= STAG_MAX_RHS, "sources per pass divide the sources covered");
     // float-float hops are long (compensated products): unrolled over the four
     // directions the kernel outgrows the instruction cache, so they loop
-    constexpr int MU_UNROLL = std::is_same<R, DF>::value ? 1 : 4;
+    // (and so do the improved operator's sixteen hops)
+    constexpr int MU_UNROLL = (std::is_same<R, DF>::value || ASQ) ? 1 : 4;
     bool ok = true;
     while (!S.halt && ok) {
         const V* r = ring + (size_t)(S.k % RING) * rstride;          // r_k
@@ -691,6 +697,8 @@ __global__ void __launch_bounds__(PB) k_ms_persistent(Geom g, LinkPtrs L, Solver
         for (int h = h0 + (int)threadIdx.x; h < h1; h += PB) {
             Nbr n;
             site_neighbours(g, h, 1, n);
+            Nbr3 m3;
+            if constexpr (ASQ) site_neighbours3(g, n, m3);
             for (int r0 = 0; r0 < nrhs; r0 += NRP) {
                 Vec3<R> acc[NRP];
                 R bt[NRP];
@@ -703,9 +711,13 @@ __global__ void __launch_bounds__(PB) k_ms_persistent(Geom g, LinkPtrs L, Solver
                 for (int mu = 0; mu < 4; ++mu) {
 #pragma unroll
                     for (int dir = 0; dir < 2; ++dir) {
-                        const int nb_h = dir == 0 ? n.fwd[mu] : n.bwd[mu];
-                        Su3<R> u = dir == 0 ? LinkFetch<R, FMT>::get(L, mu, 1, h, g.Vh)
-                                            : LinkFetch<R, FMT>::get(L, mu, 0, nb_h, g.Vh);
+#pragma unroll
+                        for (int hop = 0; hop < (ASQ ? 2 : 1); ++hop) {
+                        const int nb_h = hop == 0 ? (dir == 0 ? n.fwd[mu] : n.bwd[mu]) : (dir == 0 ? m3.fwd[mu] : m3.bwd[mu]);
+                        const LinkPtrs& LH = ASQ ? (hop == 0 ? A.fat : A.lng) : L;
+                        Su3<R> u = dir == 0 ? LinkFetch<R, FMT>::get(LH, mu, 1, h, g.Vh)
+                                            : LinkFetch<R, FMT>::get(LH, mu, 0, nb_h, g.Vh);
+                        const float sgn = hop == 0 ? (dir == 0 ? n.sf[mu] : -n.sb[mu]) : (dir == 0 ? m3.sf[mu] : -m3.sb[mu]);
 #pragma unroll
                         for (int j = 0; j < NRP; ++j) {
                             if (r0 + j >= nrhs) continue;
@@ -717,8 +729,9 @@ __global__ void __launch_bounds__(PB) k_ms_persistent(Geom g, LinkPtrs L, Solver
                                 a.c[c].re += bt[j] * b.c[c].re;
                                 a.c[c].im += bt[j] * b.c[c].im;
                             }
-                            if (dir == 0) mac_uv(acc[j], (R)n.sf[mu], u, a);
-                            else mac_udv(acc[j], -(R)n.sb[mu], u, a);
+                            if (dir == 0) mac_uv(acc[j], (R)sgn, u, a);
+                            else mac_udv(acc[j], (R)sgn, u, a);
+                        }
                         }
                     }
                 }
@@ -738,6 +751,8 @@ __global__ void __launch_bounds__(PB) k_ms_persistent(Geom g, LinkPtrs L, Solver
         for (int h = h0 + (int)threadIdx.x; h < h1; h += PB) {
             Nbr n;
             site_neighbours(g, h, 0, n);
+            Nbr3 m3;
+            if constexpr (ASQ) site_neighbours3(g, n, m3);
 #pragma unroll
             for (int r0 = 0; r0 < ND; r0 += NRP) {
                 if (r0 >= nrhs) break;
@@ -748,15 +763,20 @@ __global__ void __launch_bounds__(PB) k_ms_persistent(Geom g, LinkPtrs L, Solver
                 for (int mu = 0; mu < 4; ++mu) {
 #pragma unroll
                     for (int dir = 0; dir < 2; ++dir) {
-                        const int nb_h = dir == 0 ? n.fwd[mu] : n.bwd[mu];
-                        Su3<R> u = dir == 0 ? LinkFetch<R, FMT>::get(L, mu, 0, h, g.Vh)
-                                            : LinkFetch<R, FMT>::get(L, mu, 1, nb_h, g.Vh);
+#pragma unroll
+                        for (int hop = 0; hop < (ASQ ? 2 : 1); ++hop) {
+                        const int nb_h = hop == 0 ? (dir == 0 ? n.fwd[mu] : n.bwd[mu]) : (dir == 0 ? m3.fwd[mu] : m3.bwd[mu]);
+                        const LinkPtrs& LH = ASQ ? (hop == 0 ? A.fat : A.lng) : L;
+                        Su3<R> u = dir == 0 ? LinkFetch<R, FMT>::get(LH, mu, 0, h, g.Vh)
+                                            : LinkFetch<R, FMT>::get(LH, mu, 1, nb_h, g.Vh);
+                        const float sgn = hop == 0 ? (dir == 0 ? n.sf[mu] : -n.sb[mu]) : (dir == 0 ? m3.sf[mu] : -m3.sb[mu]);
 #pragma unroll
                         for (int j = 0; j < NRP; ++j) {
                             if (r0 + j >= nrhs) continue;
                             Vec3<R> a = load_vec_cg<R>(t + (size_t)(r0 + j) * rs, nb_h, g.Vh);
-                            if (dir == 0) mac_uv(acc[j], (R)n.sf[mu], u, a);
-                            else mac_udv(acc[j], -(R)n.sb[mu], u, a);
+                            if (dir == 0) mac_uv(acc[j], (R)sgn, u, a);
+                            else mac_udv(acc[j], (R)sgn, u, a);
+                        }
                         }
                     }
                 }
@@ -827,7 +847,7 @@ __global__ void __launch_bounds__(PB) k_ms_persistent(Geom g, LinkPtrs L, Solver
         PHASE_MARK(7)
         if constexpr (std::is_same<R, float>::value) {
             if (S.need_reliable && !S.halt) {
-                ok = reliable_update<R>(S, gs, g, L, h0, h1, PB, ring, rstride, ps, x, rp, partial, nb);
+                ok = reliable_update<R, ASQ>(S, gs, g, L, A, h0, h1, PB, ring, rstride, ps, x, rp, partial, nb);
                 PHASE_MARK(8)
             }
         }
@@ -846,11 +866,11 @@ __global__ void __launch_bounds__(PB) k_ms_persistent(Geom g, LinkPtrs L, Solver
     if (blockIdx.x == 0) store_scal(S, st);
 }
 
-template <typename R, int FMT, int NRP, int ND, int PB>
+template <typename R, int FMT, bool ASQ, int NRP, int ND, int PB>
 stag_status launch_persistent_pb(stag_ctx* ctx, void* ring, size_t rstride, void* p, void* q, void* t, void* ps,
                                  void* x, RelPtrs rp) {
     typedef typename V2T<R>::T V;
-    auto kern = k_ms_persistent<R, FMT, NRP, ND, PB>;
+    auto kern = k_ms_persistent<R, FMT, ASQ, NRP, ND, PB>;
     int per_sm = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, PB, 0));
     if (per_sm < 1) return STAG_ERR_ARG;
@@ -869,24 +889,26 @@ stag_status launch_persistent_pb(stag_ctx* ctx, void* ring, size_t rstride, void
     CK(cudaMemsetAsync(ctx->bar, 0, sizeof(GridBar), ctx->stream));
     Geom g = ctx->g;
     LinkPtrs L = link_ptrs(ctx);
+    AsqLinks A{};
+    if (ASQ) A = asq_links(ctx);
     SolverState* st = ctx->st;
     V *vr = (V*)ring, *vp = (V*)p, *vq = (V*)q, *vt = (V*)t, *vps = (V*)ps, *vx = (V*)x;
     double* part = ctx->red;
     GridBar* bar = (GridBar*)ctx->bar;
     unsigned long long* pt = ctx->prof.on ? (unsigned long long*)ctx->ptime : nullptr;
-    void* args[] = {&g, &L, &st, &vr, &rstride, &vp, &vq, &vt, &vps, &vx, &rp, &part, &bar, &pt};
+    void* args[] = {&g, &L, &A, &st, &vr, &rstride, &vp, &vq, &vt, &vps, &vx, &rp, &part, &bar, &pt};
     CK(cudaLaunchCooperativeKernel((const void*)kern, grid, PB, args, 0, ctx->stream));
     ++ctx->launches;
     return STAG_OK;
 }
 // One link format's solve: the kernel variant by the number of sources
-template <typename R, int FMT>
+template <typename R, int FMT, bool ASQ = false>
 stag_status launch_persistent_fmt(stag_ctx* ctx, int nrhs, void* ring, size_t rstride, void* p, void* q, void* t,
                                   void* ps, void* x, const double2* b64, double2* x64, double2* t64) {
     RelPtrs rp{b64, x64, t64};
     // 256 threads per block: one block per SM at these register counts
-    if (nrhs == 1) return launch_persistent_pb<R, FMT, 1, 1, 256>(ctx, ring, rstride, p, q, t, ps, x, rp);
-    if (nrhs == 2) return launch_persistent_pb<R, FMT, 2, 2, 256>(ctx, ring, rstride, p, q, t, ps, x, rp);
-    return launch_persistent_pb<R, FMT, 4, STAG_MAX_RHS, 256>(ctx, ring, rstride, p, q, t, ps, x, rp);
+    if (nrhs == 1) return launch_persistent_pb<R, FMT, ASQ, 1, 1, 256>(ctx, ring, rstride, p, q, t, ps, x, rp);
+    if (nrhs == 2) return launch_persistent_pb<R, FMT, ASQ, 2, 2, 256>(ctx, ring, rstride, p, q, t, ps, x, rp);
+    return launch_persistent_pb<R, FMT, ASQ, 4, STAG_MAX_RHS, 256>(ctx, ring, rstride, p, q, t, ps, x, rp);
 }
 }  // namespace

@@ -1012,7 +1012,7 @@ stag_status ms_core(stag_ctx* ctx, double mass, int nshift, const double* shifts
                 // bytes and the first error; the events wait for defer_end
                 const double S = 3.0 * (double)(mixed ? sizeof(float2) : sizeof(double2));
                 k_solve_note<<<1, 1, 0, ctx->stream>>>(ctx->st, ctx->note, mixed ? 0 : 1, (double)g.Vh,
-                                                       2.0 * link_bytes_site(prec) + 8.0 * S * nrhs,
+                                                       2.0 * op_link_bytes_site(ctx, prec) + 8.0 * S * nrhs,
                                                        mixed ? 1.0 : 2.0);
                 CKL();
                 if (pe0) {
@@ -1072,7 +1072,7 @@ stag_status ms_core(stag_ctx* ctx, double mass, int nshift, const double* shifts
         // one iteration: both Dslash phases (links twice; r, p in, t out / t, p, r in,
         // p, q out) and the updates (r, q in, r out and 96 B per live shift: k4_units)
         const int kind = mixed ? PK_PERSISTENT : PK_PERSISTENT_FF;
-        pf.bytes_total[kind] += (double)hs->k * g.Vh * (2.0 * link_bytes_site(prec) + 8.0 * S * nrhs) +
+        pf.bytes_total[kind] += (double)hs->k * g.Vh * (2.0 * op_link_bytes_site(ctx, prec) + 8.0 * S * nrhs) +
                                 hs->k4_units * g.Vh * (mixed ? 1.0 : 2.0);
         pf.launches[kind] += hs->k;
         pf.persist_ms[mixed ? 0 : 1] += persist_ms;
@@ -1082,7 +1082,7 @@ stag_status ms_core(stag_ctx* ctx, double mass, int nshift, const double* shifts
         const double S = 3.0 * (double)(mixed ? sizeof(float2) : sizeof(double2));   // one spinor at a site
         // K1 reads r and p (the direction is formed on the fly) and writes t;
         // K2 reads t, r, p and writes p, q
-        const double lb = (ctx->asqtad ? 2.0 : 1.0) * link_bytes_site(prec);   // fat + Naik links: twice the thin ones
+        const double lb = op_link_bytes_site(ctx, prec);
         pf.bytes_total[PK_DSLASH_OE] += (double)hs->k * g.Vh * (lb + 3.0 * S * nrhs);
         pf.bytes_total[PK_DSLASH_EO_A] += (double)hs->k * g.Vh * (lb + 5.0 * S * nrhs);
         for (int kk = PK_DSLASH_OE; kk <= PK_UPDATE; ++kk) pf.launches[kk] += hs->k;

@@ -91,7 +91,10 @@ typedef struct {
  *   STAG_BATCH_SHAPE=k     launch shape k (0, 1, 2) of the batched solver
  *                          instead of the tuned one
  *   STAG_PERSIST_SITES=n   at least n sites per block of the persistent
- *                          solver (default: one site per thread) */
+ *                          solver (default: one site per thread)
+ *   STAG_ASQ_FORCE=gather  the improved operator's force as a per-link gather
+ *                          over the path incidences instead of the reverse
+ *                          pass through the nested staples (same sum, other order) */
 stag_status stag_create(const stag_lattice* lat, stag_ctx** out);
 /* Frees every device and pinned buffer of the context (NULL is a no-op);
  * the caller's buffers are untouched.  Synchronises the context's stream. */

@@ -10,7 +10,7 @@ output spinor once: 16 x 72 + 2 x 24 = 1200 B (fp32), 16 x 144 + 2 x 48 =
 2400 B (fp64).  Times are CUDA events on the launching stream.
 
   python -m paper_1010_5433_gb300.asqtad_bench [--dslash-dims 48 48 48 48] [--solve-dims 16 16 16 16 32 32 32 32]
-         [--trajectories 10] [--warmup 5] [--skip-hmc] [--skip-solve]
+         [--trajectories 10] [--warmup 5] [--skip-hmc] [--skip-solve] [--skip-dslash]
 """
 import argparse
 import json
@@ -222,13 +222,15 @@ if __name__ == "__main__":
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--skip-hmc", action="store_true")
     ap.add_argument("--skip-solve", action="store_true")
+    ap.add_argument("--skip-dslash", action="store_true")
     a = ap.parse_args()
     peak = None
     try:
         peak = json.load(open("MEASURED_PEAKS.json")).get("hbm_gbs")
     except (OSError, ValueError):
         pass
-    print(json.dumps({"asqtad_dslash": dslash_point(tuple(a.dslash_dims), hbm_gbs=peak)}), flush=True)
+    if not a.skip_dslash:
+        print(json.dumps({"asqtad_dslash": dslash_point(tuple(a.dslash_dims), hbm_gbs=peak)}), flush=True)
     for k in range(0, 0 if a.skip_solve else len(a.solve_dims), 4):
         print(json.dumps({"asqtad_solve": solve_point(tuple(a.solve_dims[k:k + 4]))}), flush=True)
     if not a.skip_hmc:

@@ -168,6 +168,10 @@ extern "C" stag_status stag_create(const stag_lattice* lat, stag_ctx** out) {
     // STAG_PERSIST_SITES=n: the persistent solver gives every block at least n sites
     const char* ps = std::getenv("STAG_PERSIST_SITES");
     ctx->persist_sites = ps ? std::atoi(ps) : 0;
+    // STAG_ASQ_FORCE=gather: the improved operator's force as the per-link
+    // gather over path incidences instead of the reverse pass
+    const char* af = std::getenv("STAG_ASQ_FORCE");
+    ctx->asq_gather = af && std::strcmp(af, "gather") == 0;
     stag_status s = STAG_OK;
     size_t gbytes = (size_t)4 * 2 * 18 * ctx->g.Vh * sizeof(float);
     size_t bbytes = (size_t)4 * 2 * 12 * ctx->g.Vh * sizeof(uint16_t);

@@ -338,6 +338,40 @@ __device__ __forceinline__ Su3<R> load_x(const R* f, int mu, const Geom& g, cons
     return m;
 }
 
+// F_a = Re tr[i T_a (U Gf - Gb U^dag)] of thin link (blk = 2 nu + par, h),
+// written (mode 0) or added (mode 1) in the momentum layout
+template <typename R>
+__device__ __forceinline__ void put_asq_force(const Geom& g, const Su3<R>& u, const Su3<R>& gf, const Su3<R>& gb,
+                                              double* out, int blk, int h, int mode) {
+    Su3<R> w = mm(u, gf);
+    const Su3<R> b = mm_nd(gb, u);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            w.e[i][j].re -= b.e[i][j].re;
+            w.e[i][j].im -= b.e[i][j].im;
+        }
+    // Re tr(i T_a W), T_a = lambda_a / 2
+    const R hf = R(0.5f);
+    R f[8];
+    f[0] = -hf * (w.e[1][0].im + w.e[0][1].im);
+    f[1] = -hf * (w.e[0][1].re - w.e[1][0].re);
+    f[2] = -hf * (w.e[0][0].im - w.e[1][1].im);
+    f[3] = -hf * (w.e[2][0].im + w.e[0][2].im);
+    f[4] = -hf * (w.e[0][2].re - w.e[2][0].re);
+    f[5] = -hf * (w.e[2][1].im + w.e[1][2].im);
+    f[6] = -hf * (w.e[1][2].re - w.e[2][1].re);
+    f[7] = -(w.e[0][0].im + w.e[1][1].im - R(2.f) * w.e[2][2].im) * R(0.28867513459481287);   // 1/(2 sqrt 3)
+    double* o = out + ((size_t)blk * 8) * g.Vh + h;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        const double fa = (double)f[a];
+        if (mode) o[(size_t)a * g.Vh] += fa;
+        else o[(size_t)a * g.Vh] = fa;
+    }
+}
+
 // One thread per thin link (nu, y): over every incidence of nu, the rest of
 // the path's loop R = A_{k+1} .. A_n X_mu(x) A_1 .. A_{k-1} (x the path's
 // start), summed with the path coefficient into Gf (link met forward) or Gb
@@ -381,34 +415,290 @@ __global__ void __launch_bounds__(AB) k_asq_force(Geom g, LinkPtrs L, AsqCoef k,
         for (int j = 0; j < kk; ++j) m = mm(m, walk<R, FMT>(g, L, x, in.s[j]));
         axpy(fwd ? gf : gb, coef_as<R>(k, in.cls), m);
     }
-    const Su3<R> u = thin<R, FMT>(g, L, y, nu);
-    Su3<R> w = mm(u, gf);
-    const Su3<R> b = mm_nd(gb, u);
+    put_asq_force(g, thin<R, FMT>(g, L, y, nu), gf, gb, out, blk, h, mode);
+}
+
+
+// ---------------------------------------------------------------- force by reverse mode
+// The force as the reverse pass of the nested staples of the fat link
+// (the rebuild's structure), with every intermediate kept as a field:
+//   T_{mu sig}(y) = c5 U_mu(y) + c7 sum_{s = +-sig} S_s[U_mu](y)            (sig unsigned, 12 fields)
+//   Q_{mu nu}(y)  = c3 U_mu(y) + sum_rho S_rho[T_{mu, sig(nu, rho)}](y)      (nu signed, 24)
+//   P_{mu nu}(y)  = S_nu[U_mu](y)                                           (the Lepage path's inner staple, 24)
+//   V_mu(x) = c1 U_mu(x) + sum_nu S_nu[Q_{mu nu} + cL P_{mu nu}](x)
+// with sig(nu, rho) the direction orthogonal to mu, nu and rho.  Cotangents
+// (Re tr[C dA] for each intermediate A), from Xv = dS/dV:
+//   CQ_{mu nu}(y) = L(x + mu, nu)^dag Xv_mu(x) L(x, nu),  x = y - nu    (that of P is cL CQ)
+//   CT_{mu sig}(z) = sum over nu, rho with sig(nu, rho) = sig of L(y + mu, rho)^dag CQ_{mu nu}(y) L(y, rho), y = z - rho
+// and the thin link U_al(z) collects: the direct terms of the 1-link,
+// c3 U and c5 U pieces (al = mu), the inner U_mu of the seven-link and inner
+// Lepage staples, the Naik products, and as a leg of every staple S_s with
+// |s| = al: for a staple L1 A L2^dag with cotangent C, Re tr[(A L2^dag C) dL1]
+// and Re tr[(C L1 A) d(L2^dag)], turned into Gf (link met forward) or Gb
+// (met backward).  About 460 3x3 products per link against ~3000 for the
+// per-link gather over the path incidences.
+// Matrix fields: slot f, [f][par][18][Vh] reals of R; T at slot mu*4 + sig,
+// Q, P and CQ at mu*8 + 2*dir(nu) + (nu < 0), CT at mu*4 + sig.
+template <typename R>
+__device__ __forceinline__ Su3<R> ld_f(const R* base, int slot, const Geom& g, const int c[4]) {
+    const int par = (c[0] + c[1] + c[2] + c[3]) & 1;
+    const R* p = base + ((size_t)(2 * slot + par) * 18) * g.Vh + a_hidx(g, c);
+    Su3<R> m;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) m.e[k / 3][k % 3] = mk(p[(size_t)(2 * k) * g.Vh], p[(size_t)(2 * k + 1) * g.Vh]);
+    return m;
+}
+template <typename R>
+__device__ __forceinline__ void st_f(R* base, int slot, int par, int h, int Vh, const Su3<R>& m) {
+    R* p = base + ((size_t)(2 * slot + par) * 18) * Vh + h;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        p[(size_t)(2 * k) * Vh] = m.e[k / 3][k % 3].re;
+        p[(size_t)(2 * k + 1) * Vh] = m.e[k / 3][k % 3].im;
+    }
+}
+// a link-layout field of R at (direction mu, parity, half index)
+template <typename R>
+__device__ __forceinline__ Su3<R> ld_half(const R* f, int mu, int par, int h, int Vh) {
+    const R* p = f + (size_t)(2 * mu + par) * 18 * Vh + h;
+    Su3<R> m;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) m.e[e / 3][e % 3] = mk(p[(size_t)(2 * e) * Vh], p[(size_t)(2 * e + 1) * Vh]);
+    return m;
+}
+// a staple leg's matrix cotangent: A L2^dag C for the first leg, C L1 A for
+// the second (other = the staple's other leg)
+template <typename R>
+__device__ __forceinline__ Su3<R> leg_term(int leg, const Su3<R>& A, const Su3<R>& C, const Su3<R>& other) {
+    return leg == 1 ? mm(mm_nd(A, other), C) : mm(mm(C, other), A);
+}
+__device__ __forceinline__ int slot8(int mu, int s) { return mu * 8 + 2 * ((s > 0 ? s : -s) - 1) + (s < 0); }
+// L(y, s) without moving y
+template <typename R, int FMT>
+__device__ __forceinline__ Su3<R> lnk(const Geom& g, const LinkPtrs& L, const int y[4], int s) {
+    int c[4] = {y[0], y[1], y[2], y[3]};
+    return walk<R, FMT>(g, L, c, s);
+}
+template <typename R> __device__ __forceinline__ Su3<R> zero_m() {
+    Su3<R> m;
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            w.e[i][j].re -= b.e[i][j].re;
-            w.e[i][j].im -= b.e[i][j].im;
+        for (int j = 0; j < 3; ++j) m.e[i][j] = mk<R>(R(0), R(0));
+    return m;
+}
+template <typename R> __device__ __forceinline__ Su3<R> add_m(const Su3<R>& a, R c, const Su3<R>& b) {
+    Su3<R> m = a;
+    axpy(m, c, b);
+    return m;
+}
+
+struct FwdArgs {
+    Geom g;
+    LinkPtrs L;
+    AsqCoef k;
+};
+
+// T and then Q, P: one thread per (mu, site)
+template <typename R, int FMT>
+__global__ void __launch_bounds__(AB) k_asq_fwd_t(FwdArgs a, R* T) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 8LL * a.g.Vh) return;
+    const Geom& g = a.g;
+    const int blk = (int)(idx / g.Vh), h = (int)(idx % g.Vh);
+    const int mu = blk >> 1, par = blk & 1;
+    int x[4];
+    a_coords(g, par, h, x);
+    const Su3<R> umu = thin<R, FMT>(g, a.L, x, mu);
+    for (int sig = 0; sig < 4; ++sig) {
+        if (sig == mu) continue;
+        Su3<R> t = scaled(coef_as<R>(a.k, 2), umu);
+        for (int sg = -1; sg <= 1; sg += 2) {
+            const int s = sg * (sig + 1);
+            int y[4] = {x[0], x[1], x[2], x[3]};
+            a_move(g, y, s);
+            axpy(t, coef_as<R>(a.k, 3), staple<R, FMT>(g, a.L, x, mu, s, thin<R, FMT>(g, a.L, y, mu)));
         }
-    // Re tr(i T_a W), T_a = lambda_a / 2
-    const R hf = R(0.5f);
-    R f[8];
-    f[0] = -hf * (w.e[1][0].im + w.e[0][1].im);
-    f[1] = -hf * (w.e[0][1].re - w.e[1][0].re);
-    f[2] = -hf * (w.e[0][0].im - w.e[1][1].im);
-    f[3] = -hf * (w.e[2][0].im + w.e[0][2].im);
-    f[4] = -hf * (w.e[0][2].re - w.e[2][0].re);
-    f[5] = -hf * (w.e[2][1].im + w.e[1][2].im);
-    f[6] = -hf * (w.e[1][2].re - w.e[2][1].re);
-    f[7] = -(w.e[0][0].im + w.e[1][1].im - R(2.f) * w.e[2][2].im) * R(0.28867513459481287);   // 1/(2 sqrt 3)
-    double* o = out + ((size_t)blk * 8) * g.Vh + h;
-#pragma unroll
-    for (int a = 0; a < 8; ++a) {
-        const double fa = (double)f[a];
-        if (mode) o[(size_t)a * g.Vh] += fa;
-        else o[(size_t)a * g.Vh] = fa;
+        st_f(T, mu * 4 + sig, par, h, g.Vh, t);
     }
+}
+template <typename R, int FMT>
+__global__ void __launch_bounds__(AB) k_asq_fwd_qp(FwdArgs a, const R* __restrict__ T, R* Q, R* P) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 8LL * a.g.Vh) return;
+    const Geom& g = a.g;
+    const int blk = (int)(idx / g.Vh), h = (int)(idx % g.Vh);
+    const int mu = blk >> 1, par = blk & 1;
+    int x[4];
+    a_coords(g, par, h, x);
+    const Su3<R> umu = thin<R, FMT>(g, a.L, x, mu);
+    for (int nd = 0; nd < 4; ++nd) {
+        if (nd == mu) continue;
+        for (int sn = -1; sn <= 1; sn += 2) {
+            const int nu = sn * (nd + 1);
+            Su3<R> q = scaled(coef_as<R>(a.k, 1), umu);
+            for (int rd = 0; rd < 4; ++rd) {
+                if (rd == mu || rd == nd) continue;
+                const int sig = 6 - mu - nd - rd;
+                for (int sr = -1; sr <= 1; sr += 2) {
+                    const int rho = sr * (rd + 1);
+                    int y[4] = {x[0], x[1], x[2], x[3]};
+                    a_move(g, y, rho);
+                    axpy(q, R(1.f), staple<R, FMT>(g, a.L, x, mu, rho, ld_f(T, mu * 4 + sig, g, y)));
+                }
+            }
+            st_f(Q, slot8(mu, nu), par, h, g.Vh, q);
+            int y[4] = {x[0], x[1], x[2], x[3]};
+            a_move(g, y, nu);
+            st_f(P, slot8(mu, nu), par, h, g.Vh, staple<R, FMT>(g, a.L, x, mu, nu, thin<R, FMT>(g, a.L, y, mu)));
+        }
+    }
+}
+// CQ, then CT: one thread per (mu, site)
+template <typename R, int FMT>
+__global__ void __launch_bounds__(AB) k_asq_bwd_cq(FwdArgs a, const R* __restrict__ xv, R* CQ) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 8LL * a.g.Vh) return;
+    const Geom& g = a.g;
+    const int blk = (int)(idx / g.Vh), h = (int)(idx % g.Vh);
+    const int mu = blk >> 1, par = blk & 1;
+    int y[4];
+    a_coords(g, par, h, y);
+    for (int nd = 0; nd < 4; ++nd) {
+        if (nd == mu) continue;
+        for (int sn = -1; sn <= 1; sn += 2) {
+            const int nu = sn * (nd + 1);
+            int x[4] = {y[0], y[1], y[2], y[3]};
+            a_move(g, x, -nu);
+            int xm[4] = {x[0], x[1], x[2], x[3]};
+            a_move(g, xm, mu + 1);
+            const Su3<R> c = mm(mm(dagger(lnk<R, FMT>(g, a.L, xm, nu)), load_x<R>(xv, mu, g, x)), lnk<R, FMT>(g, a.L, x, nu));
+            st_f(CQ, slot8(mu, nu), par, h, g.Vh, c);
+        }
+    }
+}
+template <typename R, int FMT>
+__global__ void __launch_bounds__(AB) k_asq_bwd_ct(FwdArgs a, const R* __restrict__ CQ, R* CT) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 8LL * a.g.Vh) return;
+    const Geom& g = a.g;
+    const int blk = (int)(idx / g.Vh), h = (int)(idx % g.Vh);
+    const int mu = blk >> 1, par = blk & 1;
+    int z[4];
+    a_coords(g, par, h, z);
+    for (int sig = 0; sig < 4; ++sig) {
+        if (sig == mu) continue;
+        Su3<R> acc = zero_m<R>();
+        for (int nd = 0; nd < 4; ++nd) {
+            if (nd == mu || nd == sig) continue;
+            const int rd = 6 - mu - sig - nd;
+            for (int sn = -1; sn <= 1; sn += 2)
+                for (int sr = -1; sr <= 1; sr += 2) {
+                    const int nu = sn * (nd + 1), rho = sr * (rd + 1);
+                    int y[4] = {z[0], z[1], z[2], z[3]};
+                    a_move(g, y, -rho);
+                    int ym[4] = {y[0], y[1], y[2], y[3]};
+                    a_move(g, ym, mu + 1);
+                    axpy(acc, R(1.f), mm(mm(dagger(lnk<R, FMT>(g, a.L, ym, rho)), ld_f(CQ, slot8(mu, nu), g, y)),
+                                         lnk<R, FMT>(g, a.L, y, rho)));
+                }
+        }
+        st_f(CT, mu * 4 + sig, par, h, g.Vh, acc);
+    }
+}
+// the thin link U_al(z): direct terms, Naik, and every staple leg on it
+template <typename R, int FMT>
+__global__ void __launch_bounds__(AB) k_asq_bwd_links(FwdArgs a, const R* __restrict__ xv, const R* __restrict__ xw,
+                                                      const R* __restrict__ T, const R* __restrict__ Q,
+                                                      const R* __restrict__ P, const R* __restrict__ CQ,
+                                                      const R* __restrict__ CT, double* out, int mode) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 8LL * a.g.Vh) return;
+    const Geom& g = a.g;
+    const LinkPtrs& L = a.L;
+    const int blk = (int)(idx / g.Vh), h = (int)(idx % g.Vh);
+    const int al = blk >> 1, par = blk & 1;
+    int z[4];
+    a_coords(g, par, h, z);
+    const R c1 = coef_as<R>(a.k, 0), c3 = coef_as<R>(a.k, 1), c5 = coef_as<R>(a.k, 2), c7 = coef_as<R>(a.k, 3);
+    const R cl = coef_as<R>(a.k, 4), cn = coef_as<R>(a.k, 5);
+    Su3<R> gf = scaled(c1, load_x<R>(xv, al, g, z)), gb = zero_m<R>();
+    // direct terms: U_al(z) as the c3 and c5 pieces, and as the inner link of
+    // the seven-link and inner Lepage staples based at z - s
+    for (int d = 0; d < 4; ++d) {
+        if (d == al) continue;
+        axpy(gf, c5, ld_f(CT, al * 4 + d, g, z));
+        for (int sg = -1; sg <= 1; sg += 2) {
+            const int s = sg * (d + 1);
+            axpy(gf, c3, ld_f(CQ, slot8(al, s), g, z));
+            int y[4] = {z[0], z[1], z[2], z[3]};
+            a_move(g, y, -s);
+            int ym[4] = {y[0], y[1], y[2], y[3]};
+            a_move(g, ym, al + 1);
+            const Su3<R> c = add_m(scaled(c7, ld_f(CT, al * 4 + d, g, y)), cl, ld_f(CQ, slot8(al, s), g, y));
+            axpy(gf, R(1.f), mm(mm(dagger(lnk<R, FMT>(g, L, ym, s)), c), lnk<R, FMT>(g, L, y, s)));
+        }
+    }
+    // Naik: W_al(x) = cN U(x) U(x+al) U(x+2al) with U_al(z) first, second, third;
+    // the sites z + k al (k = 2, 1, -1, -2) as half-lattice indices computed
+    // from scalars
+    {
+        const int La = g.L[al], za = z[al];
+        int hk[4], pk[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int k = q == 0 ? 2 : q == 1 ? 1 : q == 2 ? -1 : -2;
+            const int ca = (za + k + 2 * La) % La;
+            const int c0 = al == 0 ? ca : z[0], c1 = al == 1 ? ca : z[1];
+            const int c2 = al == 2 ? ca : z[2], c3 = al == 3 ? ca : z[3];
+            hk[q] = (c0 >> 1) + g.Lxh * (c1 + g.L[1] * (c2 + g.L[2] * c3));
+            pk[q] = (c0 + c1 + c2 + c3) & 1;
+        }
+        const Su3<R> up2 = LinkFetch<R, FMT>::get(L, al, pk[0], hk[0], g.Vh);
+        const Su3<R> up1 = LinkFetch<R, FMT>::get(L, al, pk[1], hk[1], g.Vh);
+        const Su3<R> um1 = LinkFetch<R, FMT>::get(L, al, pk[2], hk[2], g.Vh);
+        const Su3<R> um2 = LinkFetch<R, FMT>::get(L, al, pk[3], hk[3], g.Vh);
+        axpy(gf, cn, mm(mm(up1, up2), load_x<R>(xw, al, g, z)));
+        axpy(gf, cn, mm(mm(up1, ld_half<R>(xw, al, pk[2], hk[2], g.Vh)), um1));
+        axpy(gf, cn, mm(mm(ld_half<R>(xw, al, pk[3], hk[3], g.Vh), um2), um1));
+    }
+    // legs: U_al(z) in the staples S_s, |s| = al, of every outer direction mu
+    for (int mu = 0; mu < 4; ++mu) {
+        if (mu == al) continue;
+        for (int sg = -1; sg <= 1; sg += 2) {
+            const int s = sg * (al + 1);
+            for (int leg = 1; leg <= 2; ++leg) {
+                // the staple's base y: leg 1 starts at y, leg 2 starts at y + mu
+                int y[4] = {z[0], z[1], z[2], z[3]};
+                if (leg == 2) a_move(g, y, -(mu + 1));
+                if (s < 0) a_move(g, y, -s);
+                int ys[4] = {y[0], y[1], y[2], y[3]};
+                a_move(g, ys, s);
+                int ym[4] = {y[0], y[1], y[2], y[3]};
+                a_move(g, ym, mu + 1);
+                // the other leg of the staple
+                const Su3<R> other = leg == 1 ? lnk<R, FMT>(g, L, ym, s) : lnk<R, FMT>(g, L, y, s);
+                // (inner value, cotangent) pairs of every staple of this geometry,
+                // the leg's matrix cotangents summed in acc
+                Su3<R> acc = leg_term(leg, add_m(ld_f(Q, slot8(mu, s), g, ys), cl, ld_f(P, slot8(mu, s), g, ys)),
+                                      load_x<R>(xv, mu, g, y), other);
+                for (int nd = 0; nd < 4; ++nd) {
+                    if (nd == mu || nd == al) continue;
+                    const int sig = 6 - mu - nd - al;
+                    for (int sn = -1; sn <= 1; sn += 2)
+                        axpy(acc, R(1.f), leg_term(leg, ld_f(T, mu * 4 + sig, g, ys),
+                                                   ld_f(CQ, slot8(mu, sn * (nd + 1)), g, y), other));
+                }
+                axpy(acc, R(1.f), leg_term(leg, thin<R, FMT>(g, L, ys, mu),
+                                           add_m(scaled(cl, ld_f(CQ, slot8(mu, s), g, y)), c7,
+                                                 ld_f(CT, mu * 4 + al, g, y)), other));
+                // leg 1 with s > 0 and leg 2 with s < 0 meet U_al(z) forward
+                if ((leg == 1) == (s > 0)) axpy(gf, R(1.f), acc);
+                else axpy(gb, R(1.f), acc);
+            }
+        }
+    }
+    put_asq_force(g, thin<R, FMT>(g, L, z, al), gf, gb, out, blk, h, mode);
 }
 
 // host: the incidence table of every direction
@@ -531,6 +821,28 @@ stag_status asq_outer_add(stag_ctx* ctx, stag_prec prec, int nsrc, int nshift, c
     return STAG_OK;
 }
 
+template <typename R, int FMT>
+static stag_status asq_force_reverse(stag_ctx* ctx, const R* xv, const R* xw, double* out, int mode) {
+    const size_t slot = (size_t)2 * 18 * ctx->g.Vh;     // reals of one matrix field
+    void* p;
+    CKS(ws_get(ctx, WS_ASQ_F, 128 * slot * sizeof(R), &p));
+    R* T = (R*)p;
+    R* Q = T + 16 * slot;
+    R* P = Q + 32 * slot;
+    R* CQ = P + 32 * slot;
+    R* CT = CQ + 32 * slot;
+    const FwdArgs a{ctx->g, link_ptrs(ctx), make_coef(ctx->asq_coef)};
+    const int nb = nblocks(8LL * ctx->g.Vh, AB);
+    k_asq_fwd_t<R, FMT><<<nb, AB, 0, ctx->stream>>>(a, T);
+    k_asq_fwd_qp<R, FMT><<<nb, AB, 0, ctx->stream>>>(a, T, Q, P);
+    k_asq_bwd_cq<R, FMT><<<nb, AB, 0, ctx->stream>>>(a, xv, CQ);
+    k_asq_bwd_ct<R, FMT><<<nb, AB, 0, ctx->stream>>>(a, CQ, CT);
+    k_asq_bwd_links<R, FMT><<<nb, AB, 0, ctx->stream>>>(a, xv, xw, T, Q, P, CQ, CT, out, mode);
+    ctx->launches += 4;
+    CKL();
+    return STAG_OK;
+}
+
 stag_status asq_force_finish(stag_ctx* ctx, stag_prec prec, double* out, int mode) {
     CKS(asq_ensure(ctx));
     const long long n = 8LL * ctx->g.Vh;
@@ -538,10 +850,12 @@ stag_status asq_force_finish(stag_ctx* ctx, stag_prec prec, double* out, int mod
     const AsqCoef k = make_coef(ctx->asq_coef);
     if (prec == STAG_FP64) {
         const DF* xv = (const DF*)ctx->ws[WS_ASQ_X];
+        if (!ctx->asq_gather) return asq_force_reverse<DF, FMT_F64>(ctx, xv, xv + nl, out, mode);
         k_asq_force<DF, FMT_F64><<<nblocks(n, AB), AB, 0, ctx->stream>>>(ctx->g, link_ptrs(ctx), k, xv, xv + nl,
                                                                          out, mode);
     } else {
         const float* xv = (const float*)ctx->ws[WS_ASQ_X];
+        if (!ctx->asq_gather) return asq_force_reverse<float, FMT_F32_18>(ctx, xv, xv + nl, out, mode);
         k_asq_force<float, FMT_F32_18><<<nblocks(n, AB), AB, 0, ctx->stream>>>(ctx->g, link_ptrs(ctx), k, xv,
                                                                                xv + nl, out, mode);
     }

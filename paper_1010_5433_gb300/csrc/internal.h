@@ -36,6 +36,7 @@ enum WsSlot {
     WS_BATCH_RED,      // batched solves: per-block partial sums of all chains
     WS_ASQ_LINKS,      // improved staggered: fat and Naik links (two-float stores)
     WS_ASQ_X,          // improved staggered force: the outer-product fields of V and W
+    WS_ASQ_F,          // improved staggered force: the staple and cotangent fields of the reverse pass
     WS_COUNT
 };
 
@@ -132,6 +133,7 @@ struct stag_ctx {
     bool asq_stale = true;
     int asq_built = 0;                // arithmetic of the current fat links: 1 fp32, 2 float-float
     bool asq_fp32_build = false;      // set while fp32 MD forces run: their solves take fp32-built fat links
+    bool asq_gather = false;          // STAG_ASQ_FORCE=gather: the force as a per-link gather over path incidences
     double asq_coef[6] = {};          // 1-link, 3-, 5-, 7-staple, Lepage, Naik
     float* asq_store = nullptr;       // fat hi, fat lo, Naik hi, Naik lo (WS_ASQ_LINKS)
     bool use_persistent = true;       // persistent cooperative solver (STAG_PERSISTENT=0: the three-kernel path)

@@ -340,3 +340,32 @@ def test_unsupported_combinations_are_refused(torch):
         assert L.rel_err(host_complex(d_out).reshape(3, -1), want) < 2e-6
     finally:
         stag.stag_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 1e-5)])
+def test_force_reverse_pass_equals_gather(torch, prec, tol):
+    """The force as the reverse pass through the nested staples (the default)
+    and as the per-link gather over the 508 path incidences of each direction
+    (STAG_ASQ_FORCE=gather) are the same sum in two orders."""
+    from paper_1010_5433_gb300 import stag
+    dims = (4, 6, 4, 4)
+    u = _gauge(dims, 21)
+    rat = json.load(open(GOLDEN))["c1_md"]
+    phi = syn.gaussian_fermion(dims, 210, on_parity=0)
+    r = stag.make_rational(rat["a0"], rat["alpha"], rat["beta"])
+    d_phi = dev(torch, L.to_half(phi, dims, 0)[None])
+    forces = []
+    for mode in ("", "gather"):
+        os.environ["STAG_ASQ_FORCE"] = mode
+        try:
+            ctx = _ctx(stag, dims, u, 0.87)
+        finally:
+            os.environ.pop("STAG_ASQ_FORCE", None)
+        try:
+            f = torch.empty((4, 2, 8, int(np.prod(dims)) // 2), dtype=torch.float64, device="cuda")
+            stag.stag_fermion_force(ctx, 0.1, r, prec, 1, d_phi, f, 1e-12 if prec == 0 else 1e-8, 10000)
+            forces.append(f.cpu().numpy())
+        finally:
+            stag.stag_destroy(ctx)
+    err = np.linalg.norm(forces[0] - forces[1]) / np.linalg.norm(forces[1])
+    assert err < tol, err

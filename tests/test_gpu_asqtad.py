@@ -369,3 +369,60 @@ def test_force_reverse_pass_equals_gather(torch, prec, tol):
             stag.stag_destroy(ctx)
     err = np.linalg.norm(forces[0] - forces[1]) / np.linalg.norm(forces[1])
     assert err < tol, err
+
+
+def _golden_8x4_asqtad():
+    import importlib.util
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    spec = importlib.util.spec_from_file_location("make_traj_8x4_asqtad",
+                                                  os.path.join(here, "make_traj_8x4_asqtad.py"))
+    mk = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mk)
+    return mk, json.load(open(os.path.join(here, "traj_8x4_asqtad.json")))
+
+
+@pytest.mark.parametrize("prec,tol_dh,tol_u", [(0, 1e-7, 1e-10), (1, 5e-3, 1e-5)])
+def test_trajectory_at_the_workload_settings_matches_oracle_on_8x4(torch, prec, tol_dh, tol_u):
+    """One improved-operator trajectory on 8^4 with the 16^4 workload's
+    rationals (14-pole MD, 24-pole heatbath and Metropolis on [m^2, m^2 + 64]),
+    mass 0.02 and integrator (10 x 5 minimum-norm steps, tau = 1) against the
+    oracle's, stored by tests/golden/make_traj_8x4_asqtad.py from the same
+    seeded links, momenta and heatbath source.  FP64: dH to 1e-7, links to
+    1e-10; mixed (fp32 MD inversions with fp64 reliable updates on fp32-built
+    fat links, fp32 link updates): 5e-3 and 1e-5."""
+    from paper_1010_5433_gb300 import stag
+    mk, gold = _golden_8x4_asqtad()
+    s = gold["setup"]
+    dims, u0, mom0, xi = mk.inputs(s)
+    g = json.load(open(GOLDEN))
+    rats = {k: g["asqtad_" + k] for k in ("md", "met", "hb")}
+    ctx = _ctx(stag, dims, u0, s["u0"])
+    try:
+        d_mom = torch.from_numpy(L.mom_to_abi(mom0, dims)).cuda()
+        d_xi = dev(torch, L.to_half(xi, dims, 0)[None])
+        p = stag.stag_hmc()
+        p.beta, p.tau, p.n_outer, p.n_gauge = s["beta"], s["tau"], s["n_outer"], s["n_gauge"]
+        p.n_flavours = 1
+        fl = p.flavour[0]
+        fl.mass, fl.n_pf = s["mass"], 1
+        for k in ("hb", "md", "met"):
+            setattr(fl, k, stag.make_rational(rats[k]["a0"], rats[k]["alpha"], rats[k]["beta"]))
+        p.tol_md = 1e-12 if prec == 0 else 1e-8
+        p.tol_met = 1e-12
+        p.max_iter = 40000
+        p.md_prec = prec
+        p.ext_mom, p.ext_xi, p.no_metropolis = d_mom.data_ptr(), d_xi.data_ptr(), 1
+        res = stag.stag_md_trajectory(ctx, p)
+        buf = np.empty(4 * int(np.prod(dims)) * 18)
+        stag.stag_store_gauge(ctx, buf)
+        u1 = L.gauge_from_host(buf, dims)
+        got = np.array([u1[tuple(q)].reshape(-1) for q in gold["u_sample_pos"]])
+        want = np.array([[complex(*v) for v in row] for row in gold["u_sample"]])
+        du = np.abs(got - want).max()
+        print(f"asqtad 8^4 at the workload settings, prec {prec}: dH gpu {res.dH:.9f} oracle {gold['dH']:.9f}, "
+              f"max|dU| {du:.2e}, CG iterations {res.cg_iterations}")
+        assert abs(res.H0 - gold["H0"]) < 1e-10 * abs(gold["H0"])
+        assert abs(res.dH - gold["dH"]) < tol_dh
+        assert du < tol_u
+    finally:
+        stag.stag_destroy(ctx)

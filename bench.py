@@ -242,6 +242,7 @@ def run_gpu(args, rank, world, local_rank):
 
     point = dslash_roofline_point(hbm) if rank == 0 else None
     force_point = force_dslash_point(hbm, clocks.get("sm_max_mhz")) if rank == 0 else None
+    asq_point = asqtad_dslash_point(hbm) if rank == 0 else None
     stag.stag_destroy(ctx)
     chains = batched_chains() if world == 1 else None
 
@@ -288,6 +289,7 @@ def run_gpu(args, rank, world, local_rank):
                          "e2e_max_abs_dH_difference": max(abs(a.dH - b.dH) for a, b in zip(trajs, e2e_trajs))},
         "dslash_roofline_point": point,
         "force_dslash_point": force_point,
+        "asqtad_dslash_point": asq_point,
         "batched_chains": chains,
     }
     return out
@@ -331,6 +333,13 @@ def dslash_roofline_point(hbm):
     precision, CUDA-event timed over 20 launches after 3 warm-ups."""
     from paper_1010_5433_gb300 import dslash_bench
     return dslash_bench.run(ROOFLINE_POINT_DIMS, (1, 2, 3, 0), 1, 20, hbm)
+
+
+def asqtad_dslash_point(hbm):
+    """The improved (asqtad) operator's D_oe at 48^4, fp32 fat and Naik
+    links: 8 + 8 links of 72 B and the two spinors, 1200 B per site."""
+    from paper_1010_5433_gb300 import asqtad_bench
+    return asqtad_bench.dslash_point(ROOFLINE_POINT_DIMS, 20, hbm, precs=(1,), rebuild=False)
 
 
 # the many-source force Dslash of the 2+1-flavour workload: Y_i = D_oe X_i for

@@ -38,8 +38,9 @@ def _near_identity_device(torch, dev, V, scale=0.05):
     return g
 
 
-def dslash_point(dims, reps=20, hbm_gbs=None):
-    """D_oe with the improved operator, fp32 and fp64, back-to-back launches."""
+def dslash_point(dims, reps=20, hbm_gbs=None, precs=(1, 0), rebuild=True):
+    """D_oe with the improved operator in the given precisions (1 fp32, 0
+    fp64), back-to-back launches; with rebuild, also the fat-link rebuild."""
     import torch
 
     from . import stag
@@ -54,7 +55,7 @@ def dslash_point(dims, reps=20, hbm_gbs=None):
         stag.stag_load_gauge_device(ctx, g)
         stag.stag_set_action(ctx, stag.STAG_ACTION_ASQTAD, 1.0)
         e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-        for prec in (1, 0):
+        for prec in precs:
             dt = torch.float64 if prec == 0 else torch.float32
             s = 48 if prec == 0 else 24
             inp = torch.randn(3 * 2 * vh, dtype=dt, device=dev)
@@ -74,6 +75,8 @@ def dslash_point(dims, reps=20, hbm_gbs=None):
                 r["frac"] = round(gbs / hbm_gbs, 4)
             res[NAMES[prec]] = r
             del inp, out
+        if not rebuild:
+            return res
         # the fat-link rebuild: a reload marks the links stale, the next Dslash rebuilds them
         inp = torch.randn(3 * 2 * vh, dtype=torch.float32, device=dev)
         out = torch.empty_like(inp)

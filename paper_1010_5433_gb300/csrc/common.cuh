@@ -352,17 +352,19 @@ __device__ __forceinline__ Su3<double> load_link_d(const float* __restrict__ hi,
 __device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
 
-__device__ __forceinline__ Su3<float> load_link_bf(const uint16_t* __restrict__ blk, int h, int Vh) {
-    const uint4* p4 = reinterpret_cast<const uint4*>(blk);
-    const uint2* p2 = reinterpret_cast<const uint2*>(blk + 8 * (size_t)Vh);
-    uint4 a = __ldg(p4 + h);
-    uint2 b = __ldg(p2 + h);
+// rows 0-1 of a bf16 link from its two words (uint4: u00 u01 u02 u10, uint2: u11 u12), row 2 rebuilt
+__device__ __forceinline__ Su3<float> unpack_link_bf(const uint4 a, const uint2 b) {
     Su3<float> u;
     u.e[0][0] = mk(bf_lo(a.x), bf_hi(a.x)); u.e[0][1] = mk(bf_lo(a.y), bf_hi(a.y));
     u.e[0][2] = mk(bf_lo(a.z), bf_hi(a.z)); u.e[1][0] = mk(bf_lo(a.w), bf_hi(a.w));
     u.e[1][1] = mk(bf_lo(b.x), bf_hi(b.x)); u.e[1][2] = mk(bf_lo(b.y), bf_hi(b.y));
     rebuild_row2(u);
     return u;
+}
+__device__ __forceinline__ Su3<float> load_link_bf(const uint16_t* __restrict__ blk, int h, int Vh) {
+    const uint4* p4 = reinterpret_cast<const uint4*>(blk);
+    const uint2* p2 = reinterpret_cast<const uint2*>(blk + 8 * (size_t)Vh);
+    return unpack_link_bf(__ldg(p4 + h), __ldg(p2 + h));
 }
 
 // ---------------------------------------------------------------- spinors

@@ -119,9 +119,46 @@ template <> struct SrcFor<DF> { typedef SrcD2DF type; typedef double2 io; };
 // `sub` takes the hops of mu = sub, sub + TPS, ... (TPS <= 4), or, for TPS = 8,
 // the forward (even sub) or backward (odd sub) hop of mu = sub / 2; the TPS
 // partial sums are then added with warp shuffles.
+// bf16 links, one thread per site and source: every load of the site (eight
+// links' raw words, eight neighbour spinors) is issued before the first
+// product, so a warp keeps ~12 KB in flight instead of one hop's worth
+template <class Src>
+__device__ __forceinline__ void dslash_site_bf16_prefetch(const Geom& g, int out_par, const LinkPtrs& L,
+                                                          const Src& src, int r0, int h, Vec3<float>& acc) {
+    Nbr n;
+    site_neighbours(g, h, out_par, n);
+    uint4 la[8];
+    uint2 lb[8];
+    Vec3<float> v[8];
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+        const uint16_t* bf = L.b16 + link_block_b(mu, out_par, g.Vh);
+        const uint16_t* bb = L.b16 + link_block_b(mu, 1 - out_par, g.Vh);
+        la[2 * mu] = __ldg(reinterpret_cast<const uint4*>(bf) + h);
+        lb[2 * mu] = __ldg(reinterpret_cast<const uint2*>(bf + 8 * (size_t)g.Vh) + h);
+        la[2 * mu + 1] = __ldg(reinterpret_cast<const uint4*>(bb) + n.bwd[mu]);
+        lb[2 * mu + 1] = __ldg(reinterpret_cast<const uint2*>(bb + 8 * (size_t)g.Vh) + n.bwd[mu]);
+    }
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+        v[2 * mu] = src.load(0, r0, n.fwd[mu], g.Vh);
+        v[2 * mu + 1] = src.load(0, r0, n.bwd[mu], g.Vh);
+    }
+    zero(acc);
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+        mac_uv(acc, n.sf[mu], unpack_link_bf(la[2 * mu], lb[2 * mu]), v[2 * mu]);
+        mac_udv(acc, -n.sb[mu], unpack_link_bf(la[2 * mu + 1], lb[2 * mu + 1]), v[2 * mu + 1]);
+    }
+}
+
 template <typename R, int FMT, int NR, int TPS, class Src>
 __device__ __forceinline__ void dslash_site(const Geom& g, int out_par, const LinkPtrs& L, const Src& src,
                                             int r0, int nrhs, int h, int sub, Vec3<R> (&acc)[NR]) {
+    if constexpr (FMT == FMT_BF16_12 && TPS == 1 && NR == 1) {
+        dslash_site_bf16_prefetch(g, out_par, L, src, r0, h, acc[0]);
+        return;
+    }
     Nbr n;
     site_neighbours(g, h, out_par, n);
 #pragma unroll

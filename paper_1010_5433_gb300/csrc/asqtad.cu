@@ -17,10 +17,17 @@
 // every other path of V an even number, so the Dslash applies the thin
 // links' hop sign to V and the sign of the three t-links to W.
 //
-// Arithmetic: float-float (hi + lo floats, ~48 bits) on the fp32 pipes
-// (GB300's fp64 rate is ~1/64 of fp32), read from the two-float thin-link
-// store and written to two-float stores of the same layout, so the fp32
-// Dslash reads the rounded fat links (hi) and the fp64 one all of them.
+// Arithmetic of the rebuild: float-float (hi + lo floats, ~48 bits) on the
+// fp32 pipes (GB300's fp64 rate is ~1/64 of fp32), read from the two-float
+// thin-link store and written to two-float stores of the same layout, so the
+// fp32 Dslash reads the rounded fat links (hi) and the fp64 one all of them;
+// before an fp32 MD force the rebuild runs in fp32 from the hi words.
+//
+// Force: dS = sum Re tr[dV Xv + dW Xw] with the outer-product fields Xv, Xw
+// of the solutions (k_asq_outer), differentiated through the nested staples
+// by a reverse pass (k_asq_fwd_*, k_asq_bwd_*); k_asq_force, one gather per
+// thin link over the path incidences of its direction, is the same sum in
+// another order, kept as a cross-check (STAG_ASQ_FORCE=gather).
 #include <cstring>
 #include <vector>
 

@@ -444,8 +444,9 @@ __global__ void __launch_bounds__(AB) k_asq_force(Geom g, LinkPtrs L, AsqCoef k,
 // and Re tr[(C L1 A) d(L2^dag)], turned into Gf (link met forward) or Gb
 // (met backward).  About 460 3x3 products per link against ~3000 for the
 // per-link gather over the path incidences.
-// Matrix fields: slot f, [f][par][18][Vh] reals of R; T at slot mu*4 + sig,
-// Q, P and CQ at mu*8 + 2*dir(nu) + (nu < 0), CT at mu*4 + sig.
+// Matrix fields: slot f, [f][par][18][Vh] reals of R.  Q and P enter the
+// pass only as Q + cL P, which is stored instead of the two: 72 slots,
+// T and CT at slot3(mu, sig), Q + cL P and CQ at slot6(mu, nu).
 template <typename R>
 __device__ __forceinline__ Su3<R> ld_f(const R* base, int slot, const Geom& g, const int c[4]) {
     const int par = (c[0] + c[1] + c[2] + c[3]) & 1;
@@ -479,7 +480,12 @@ template <typename R>
 __device__ __forceinline__ Su3<R> leg_term(int leg, const Su3<R>& A, const Su3<R>& C, const Su3<R>& other) {
     return leg == 1 ? mm(mm_nd(A, other), C) : mm(mm(C, other), A);
 }
-__device__ __forceinline__ int slot8(int mu, int s) { return mu * 8 + 2 * ((s > 0 ? s : -s) - 1) + (s < 0); }
+// direction sig != mu (unsigned) and signed nu orthogonal to mu, numbered densely per mu
+__device__ __forceinline__ int slot3(int mu, int sig) { return mu * 3 + sig - (sig > mu); }
+__device__ __forceinline__ int slot6(int mu, int s) {
+    const int d = (s > 0 ? s : -s) - 1;
+    return mu * 6 + 2 * (d - (d > mu)) + (s < 0);
+}
 // L(y, s) without moving y
 template <typename R, int FMT>
 __device__ __forceinline__ Su3<R> lnk(const Geom& g, const LinkPtrs& L, const int y[4], int s) {
@@ -526,11 +532,11 @@ __global__ void __launch_bounds__(AB) k_asq_fwd_t(FwdArgs a, R* T) {
             a_move(g, y, s);
             axpy(t, coef_as<R>(a.k, 3), staple<R, FMT>(g, a.L, x, mu, s, thin<R, FMT>(g, a.L, y, mu)));
         }
-        st_f(T, mu * 4 + sig, par, h, g.Vh, t);
+        st_f(T, slot3(mu, sig), par, h, g.Vh, t);
     }
 }
 template <typename R, int FMT>
-__global__ void __launch_bounds__(AB) k_asq_fwd_qp(FwdArgs a, const R* __restrict__ T, R* Q, R* P) {
+__global__ void __launch_bounds__(AB) k_asq_fwd_qp(FwdArgs a, const R* __restrict__ T, R* QP) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= 8LL * a.g.Vh) return;
     const Geom& g = a.g;
@@ -551,13 +557,13 @@ __global__ void __launch_bounds__(AB) k_asq_fwd_qp(FwdArgs a, const R* __restric
                     const int rho = sr * (rd + 1);
                     int y[4] = {x[0], x[1], x[2], x[3]};
                     a_move(g, y, rho);
-                    axpy(q, R(1.f), staple<R, FMT>(g, a.L, x, mu, rho, ld_f(T, mu * 4 + sig, g, y)));
+                    axpy(q, R(1.f), staple<R, FMT>(g, a.L, x, mu, rho, ld_f(T, slot3(mu, sig), g, y)));
                 }
             }
-            st_f(Q, slot8(mu, nu), par, h, g.Vh, q);
             int y[4] = {x[0], x[1], x[2], x[3]};
             a_move(g, y, nu);
-            st_f(P, slot8(mu, nu), par, h, g.Vh, staple<R, FMT>(g, a.L, x, mu, nu, thin<R, FMT>(g, a.L, y, mu)));
+            axpy(q, coef_as<R>(a.k, 4), staple<R, FMT>(g, a.L, x, mu, nu, thin<R, FMT>(g, a.L, y, mu)));
+            st_f(QP, slot6(mu, nu), par, h, g.Vh, q);
         }
     }
 }
@@ -580,7 +586,7 @@ __global__ void __launch_bounds__(AB) k_asq_bwd_cq(FwdArgs a, const R* __restric
             int xm[4] = {x[0], x[1], x[2], x[3]};
             a_move(g, xm, mu + 1);
             const Su3<R> c = mm(mm(dagger(lnk<R, FMT>(g, a.L, xm, nu)), load_x<R>(xv, mu, g, x)), lnk<R, FMT>(g, a.L, x, nu));
-            st_f(CQ, slot8(mu, nu), par, h, g.Vh, c);
+            st_f(CQ, slot6(mu, nu), par, h, g.Vh, c);
         }
     }
 }
@@ -606,18 +612,18 @@ __global__ void __launch_bounds__(AB) k_asq_bwd_ct(FwdArgs a, const R* __restric
                     a_move(g, y, -rho);
                     int ym[4] = {y[0], y[1], y[2], y[3]};
                     a_move(g, ym, mu + 1);
-                    axpy(acc, R(1.f), mm(mm(dagger(lnk<R, FMT>(g, a.L, ym, rho)), ld_f(CQ, slot8(mu, nu), g, y)),
+                    axpy(acc, R(1.f), mm(mm(dagger(lnk<R, FMT>(g, a.L, ym, rho)), ld_f(CQ, slot6(mu, nu), g, y)),
                                          lnk<R, FMT>(g, a.L, y, rho)));
                 }
         }
-        st_f(CT, mu * 4 + sig, par, h, g.Vh, acc);
+        st_f(CT, slot3(mu, sig), par, h, g.Vh, acc);
     }
 }
 // the thin link U_al(z): direct terms, Naik, and every staple leg on it
 template <typename R, int FMT>
 __global__ void __launch_bounds__(AB) k_asq_bwd_links(FwdArgs a, const R* __restrict__ xv, const R* __restrict__ xw,
-                                                      const R* __restrict__ T, const R* __restrict__ Q,
-                                                      const R* __restrict__ P, const R* __restrict__ CQ,
+                                                      const R* __restrict__ T, const R* __restrict__ QP,
+                                                      const R* __restrict__ CQ,
                                                       const R* __restrict__ CT, double* out, int mode) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= 8LL * a.g.Vh) return;
@@ -634,15 +640,15 @@ __global__ void __launch_bounds__(AB) k_asq_bwd_links(FwdArgs a, const R* __rest
     // the seven-link and inner Lepage staples based at z - s
     for (int d = 0; d < 4; ++d) {
         if (d == al) continue;
-        axpy(gf, c5, ld_f(CT, al * 4 + d, g, z));
+        axpy(gf, c5, ld_f(CT, slot3(al, d), g, z));
         for (int sg = -1; sg <= 1; sg += 2) {
             const int s = sg * (d + 1);
-            axpy(gf, c3, ld_f(CQ, slot8(al, s), g, z));
+            axpy(gf, c3, ld_f(CQ, slot6(al, s), g, z));
             int y[4] = {z[0], z[1], z[2], z[3]};
             a_move(g, y, -s);
             int ym[4] = {y[0], y[1], y[2], y[3]};
             a_move(g, ym, al + 1);
-            const Su3<R> c = add_m(scaled(c7, ld_f(CT, al * 4 + d, g, y)), cl, ld_f(CQ, slot8(al, s), g, y));
+            const Su3<R> c = add_m(scaled(c7, ld_f(CT, slot3(al, d), g, y)), cl, ld_f(CQ, slot6(al, s), g, y));
             axpy(gf, R(1.f), mm(mm(dagger(lnk<R, FMT>(g, L, ym, s)), c), lnk<R, FMT>(g, L, y, s)));
         }
     }
@@ -687,18 +693,17 @@ __global__ void __launch_bounds__(AB) k_asq_bwd_links(FwdArgs a, const R* __rest
                 const Su3<R> other = leg == 1 ? lnk<R, FMT>(g, L, ym, s) : lnk<R, FMT>(g, L, y, s);
                 // (inner value, cotangent) pairs of every staple of this geometry,
                 // the leg's matrix cotangents summed in acc
-                Su3<R> acc = leg_term(leg, add_m(ld_f(Q, slot8(mu, s), g, ys), cl, ld_f(P, slot8(mu, s), g, ys)),
-                                      load_x<R>(xv, mu, g, y), other);
+                Su3<R> acc = leg_term(leg, ld_f(QP, slot6(mu, s), g, ys), load_x<R>(xv, mu, g, y), other);
                 for (int nd = 0; nd < 4; ++nd) {
                     if (nd == mu || nd == al) continue;
                     const int sig = 6 - mu - nd - al;
                     for (int sn = -1; sn <= 1; sn += 2)
-                        axpy(acc, R(1.f), leg_term(leg, ld_f(T, mu * 4 + sig, g, ys),
-                                                   ld_f(CQ, slot8(mu, sn * (nd + 1)), g, y), other));
+                        axpy(acc, R(1.f), leg_term(leg, ld_f(T, slot3(mu, sig), g, ys),
+                                                   ld_f(CQ, slot6(mu, sn * (nd + 1)), g, y), other));
                 }
                 axpy(acc, R(1.f), leg_term(leg, thin<R, FMT>(g, L, ys, mu),
-                                           add_m(scaled(cl, ld_f(CQ, slot8(mu, s), g, y)), c7,
-                                                 ld_f(CT, mu * 4 + al, g, y)), other));
+                                           add_m(scaled(cl, ld_f(CQ, slot6(mu, s), g, y)), c7,
+                                                 ld_f(CT, slot3(mu, al), g, y)), other));
                 // leg 1 with s > 0 and leg 2 with s < 0 meet U_al(z) forward
                 if ((leg == 1) == (s > 0)) axpy(gf, R(1.f), acc);
                 else axpy(gb, R(1.f), acc);
@@ -832,19 +837,18 @@ template <typename R, int FMT>
 static stag_status asq_force_reverse(stag_ctx* ctx, const R* xv, const R* xw, double* out, int mode) {
     const size_t slot = (size_t)2 * 18 * ctx->g.Vh;     // reals of one matrix field
     void* p;
-    CKS(ws_get(ctx, WS_ASQ_F, 128 * slot * sizeof(R), &p));
+    CKS(ws_get(ctx, WS_ASQ_F, 72 * slot * sizeof(R), &p));
     R* T = (R*)p;
-    R* Q = T + 16 * slot;
-    R* P = Q + 32 * slot;
-    R* CQ = P + 32 * slot;
-    R* CT = CQ + 32 * slot;
+    R* QP = T + 12 * slot;
+    R* CQ = QP + 24 * slot;
+    R* CT = CQ + 24 * slot;
     const FwdArgs a{ctx->g, link_ptrs(ctx), make_coef(ctx->asq_coef)};
     const int nb = nblocks(8LL * ctx->g.Vh, AB);
     k_asq_fwd_t<R, FMT><<<nb, AB, 0, ctx->stream>>>(a, T);
-    k_asq_fwd_qp<R, FMT><<<nb, AB, 0, ctx->stream>>>(a, T, Q, P);
+    k_asq_fwd_qp<R, FMT><<<nb, AB, 0, ctx->stream>>>(a, T, QP);
     k_asq_bwd_cq<R, FMT><<<nb, AB, 0, ctx->stream>>>(a, xv, CQ);
     k_asq_bwd_ct<R, FMT><<<nb, AB, 0, ctx->stream>>>(a, CQ, CT);
-    k_asq_bwd_links<R, FMT><<<nb, AB, 0, ctx->stream>>>(a, xv, xw, T, Q, P, CQ, CT, out, mode);
+    k_asq_bwd_links<R, FMT><<<nb, AB, 0, ctx->stream>>>(a, xv, xw, T, QP, CQ, CT, out, mode);
     ctx->launches += 4;
     CKL();
     return STAG_OK;

@@ -421,6 +421,41 @@ def _oracle_sample_job(seed):
     return oracle_sample(seed)
 
 
+# lattices of the oracle's Dslash rate: the 4^4, 16^4 and 32^3 x 8 workloads
+ORACLE_DSLASH_DIMS = ((4, 4, 4, 4), (16, 16, 16, 16), (32, 32, 32, 8))
+
+
+def oracle_dslash_rate(reps=3):
+    """The oracle's D_oe (numpy, fp64, whole-lattice arrays, as it stands) on
+    one core: milliseconds per application and the equivalent GB/s of the
+    FP64 Dslash's algorithmic bytes (8 links x 144 B + 2 spinors x 48 B =
+    1248 B per output site), best of reps."""
+    import synthetic as syn
+    from oracle import dirac, lattice as lat
+    try:
+        from threadpoolctl import threadpool_limits
+        limit = threadpool_limits(1)
+    except ImportError:
+        limit = None
+    out = []
+    for dims in ORACLE_DSLASH_DIMS:
+        u = syn.near_identity_gauge(dims, 3)
+        eta, par = lat.eta(dims), lat.parity(dims)
+        psi = syn.gaussian_fermion(dims, 4, on_parity=0)
+        best = None
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            dirac.d_block(u, psi, eta, par, 1)
+            t = time.perf_counter() - t0
+            best = t if best is None else min(best, t)
+        vh = int(np.prod(dims)) // 2
+        out.append({"lattice": "x".join(str(d) for d in dims), "ms": round(best * 1e3, 3),
+                    "equivalent_gbs": round(vh * 1248 / best / 1e9, 4)})
+    if limit is not None:
+        limit.restore_original_limits()
+    return out
+
+
 def traj_seconds(t, per_traj):
     return (per_traj["cg_iterations"] * t["cg_iteration"] + per_traj["fermion_forces"] * t["fermion_force"]
             + per_traj["gauge_forces"] * t["gauge_force"] + per_traj["link_updates"] * t["link_update"])
@@ -442,7 +477,8 @@ def cpu_baseline(per_traj, all_cores=True):
               "sample": f"16^4: 4 multi-shift CG iterations (12 shifts), 1 fermion force, 1 Wilson force, 1 link "
                         f"update ({one['sample_s']:.1f} s), scaled by {work}"}
     out = {"value": single["value"], "unit": "trajectories/hour", "cores": single["cores"], "kind": "oracle",
-           "sample": single["sample"], "seconds_per_traj": single["seconds_per_traj"], "single_core": single}
+           "sample": single["sample"], "seconds_per_traj": single["seconds_per_traj"], "single_core": single,
+           "dslash_single_core": oracle_dslash_rate()}
     nproc = os.cpu_count() or 1
     if all_cores and nproc > 1:
         import multiprocessing as mp

@@ -50,10 +50,16 @@ def peaks():
 
 # ---------------------------------------------------------------- clocks
 class ClockSampler:
+    """nvidia-smi sampling clocks and throttle reasons every 200 ms.  The
+    tool's start-up (NVML initialisation) can hold the driver for a few
+    hundred ms, so the caller waits for the first sample before it starts the
+    timed region and then keeps only the samples taken inside it."""
+
     def __init__(self, index):
         self.index = index
-        self.lines = []
+        self.lines = []                  # (host time, csv line)
         self.proc = None
+        self.window = None
 
     def __enter__(self):
         try:
@@ -72,7 +78,12 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def wait_first(self, timeout=5.0):
+        t0 = time.perf_counter()
+        while self.proc and not self.lines and time.perf_counter() - t0 < timeout:
+            time.sleep(0.02)
 
     def __exit__(self, *a):
         if self.proc:
@@ -85,7 +96,11 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        lines = self.lines
+        if self.window:
+            inside = [x for x in lines if self.window[0] <= x[0] <= self.window[1]]
+            lines = inside or lines
+        for _, ln in lines:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 7:
                 continue
@@ -170,13 +185,17 @@ def run_gpu(args, rank, world, local_rank):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         with ClockSampler(local_rank) as clk:
+            clk.wait_first()                  # the sampler's start-up stays outside the timed region
+            torch.cuda.synchronize()
             torch.cuda.nvtx.range_push(f"timed_{'fp64' if prec == 0 else 'mixed'}")
+            t_in = time.perf_counter()
             e0.record(stream)
             for k in range(steps):
                 flush.zero_()                 # inputs fit in L2: flush between trajectories
                 trajs.append(stag.stag_md_trajectory(ctx, make_hmc(stag, rats, prec, seed, c0 + k)))
             e1.record(stream)
             torch.cuda.synchronize()
+            clk.window = (t_in, time.perf_counter())
             torch.cuda.nvtx.range_pop()
         if world > 1:
             torch.distributed.barrier()

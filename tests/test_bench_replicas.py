@@ -93,3 +93,18 @@ def test_fewer_than_three_warmup_steps_are_refused():
     p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--warmup", "2"],
                        capture_output=True, text=True, timeout=300)
     assert p.returncode == 2 and "--warmup" in p.stderr
+
+
+def test_clock_summary_keeps_the_timed_window():
+    """Samples taken before the timed region (the sampler's start-up) are left
+    out when the window holds any; throttle reasons are those seen inside."""
+    import bench
+    c = bench.ClockSampler(0)
+    c.lines = [(0.5, "900, 2070, 0x0, Not Active, Not Active, Not Active, Not Active"),
+               (1.0, "2070, 2070, 0x0, Not Active, Not Active, Not Active, Active"),
+               (2.0, "2070, 2070, 0x0, Not Active, Not Active, Not Active, Not Active")]
+    c.window = (0.9, 2.5)
+    s = c.summary()
+    assert s["sm_mhz"] == 2070.0 and s["samples"] == 2 and s["reasons"] == ["sw_power_cap"]
+    c.window = (5.0, 6.0)        # no sample inside: all of them
+    assert c.summary()["samples"] == 3

@@ -268,3 +268,16 @@ def test_dh_scales_as_step_squared():
         dh.append(abs(r["dH"]))
     ratio = dh[0] / dh[1]
     assert 3.0 < ratio < 5.5, (dh, ratio)
+
+
+def test_one_hop_skeleton_is_the_unimproved_operator():
+    """With the boundary-signed thin links as fat links and no Naik term the
+    improved operator's hop structure is the paper's unimproved D (pinned
+    separately by its own free-field spectrum and dense solves)."""
+    from oracle import dirac
+    dims = (4, 2, 4, 6)
+    u = syn.haar_gauge(dims, 71)
+    psi = syn.gaussian_fermion(dims, 72, on_parity=None)
+    v = asqtad.boundary_signed_links(u, True)
+    got = asqtad.dslash(v, np.zeros_like(u), psi, lat.eta(dims, antiperiodic_t=False))
+    np.testing.assert_allclose(got, dirac.dslash(u, psi, lat.eta(dims, True)), atol=1e-14)

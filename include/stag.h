@@ -170,9 +170,11 @@ typedef enum { STAG_ACTION_UNIMPROVED = 0, STAG_ACTION_ASQTAD = 1 } stag_action;
  * The fat and Naik links are rebuilt on the device (float-float arithmetic
  * from the two-float store) before the first use after every change of the
  * thin links.  With the improved operator, prec must be STAG_FP64 or
- * STAG_FP32 (the fat links are not unitary, so no 12-real or bf16 copy), the
- * solver takes the three-kernel path, and the batched calls and the force
- * surrogate return STAG_ERR_ARG.  The gauge action stays Wilson's.
+ * STAG_FP32 (the fat links are not unitary, so no 12-real or bf16 copy), and
+ * the batched calls and the force surrogate return STAG_ERR_ARG.  fp32
+ * forces (the MD) build the fat links in fp32 from the thin links' hi words;
+ * every other use builds them in float-float.  The gauge action stays
+ * Wilson's.
  * Allocates the two link stores (2 x 4 V x 18 x 8 bytes) on the first switch. */
 stag_status stag_set_action(stag_ctx* ctx, stag_action action, double u0);
 

@@ -66,3 +66,16 @@ def test_golden_entry_is_what_the_committed_script_writes():
     np.testing.assert_allclose(r.beta, g["beta"], rtol=1e-13)
     np.testing.assert_allclose(r.alpha, g["alpha"], rtol=1e-13)
     assert abs(r.a0 - g["a0"]) <= 1e-13 * abs(g["a0"])
+
+
+def test_improved_operator_rationals_cover_its_spectrum_bound():
+    """The improved operator's workload rationals approximate on [m^2, m^2 + 64],
+    which contains its A's spectrum bound m^2 + 58.8 (u0 = 1), and the shipped
+    table agrees with the oracle's Remez there too."""
+    import json as _json
+    gold = _json.load(open(GOLDEN))
+    for k in ("asqtad_md", "asqtad_met", "asqtad_hb"):
+        r = rational.load(k)
+        assert abs(r.lo - 0.02 ** 2) < 1e-15 and abs(r.hi - (64.0 + 0.02 ** 2)) < 1e-12
+        assert r.hi - r.lo >= (4 * (5 / 8 + 6 / 16 + 24 / 64 + 48 / 384 + 6 / 16 + 1 / 24)) ** 2
+        _close(r, gold[k], 1e-8)

@@ -12,6 +12,7 @@ Modules
   su3         SU(3) algebra: generators, exp, projections, reunitarise (Sec. 4)
   dirac       unimproved staggered D, even/odd blocks, A = m^2 - D_eo D_oe (Sec. 2)
   asqtad      improved (asqtad) staggered D: fat and Naik links, its force (not in the paper)
+  hisq        HISQ links (fat7, U(3) projection, fat7 + Lepage, Naik) and force (not in the paper)
   solvers     CG and multi-shift CG (Jegerlehner, hep-lat/9612014)     (Sec. 6)
   rational    Remez minimax rational approximation, partial fractions  (Sec. 2)
   actions     Wilson gauge action and force; fermion action and force (Sec. 2, 4)

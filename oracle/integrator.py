@@ -22,8 +22,9 @@ Sint; ref. [hmc] Duane, Kennedy, Pendleton, Roweth).
     final S_f uses the Metropolis rational (tighter than the MD one, Sec. 2)
     and the initial S_f = xi^dag xi.
   * the fermion operator is the paper's unimproved one, or (action =
-    "asqtad", not in the paper) the improved operator of oracle/asqtad.py
-    with its fermion force; the gauge action stays Wilson's either way.
+    "asqtad" or "hisq", not in the paper) the improved operators of
+    oracle/asqtad.py and oracle/hisq.py with their fermion forces; the gauge
+    action stays Wilson's either way.
 Everything here is float64 (the oracle reference for all precision modes).
 """
 from dataclasses import dataclass, field
@@ -31,7 +32,7 @@ from typing import List
 
 import numpy as np
 
-from . import asqtad, dirac, lattice as lat, solvers, su3
+from . import asqtad, dirac, hisq, lattice as lat, solvers, su3
 from . import surrogate as sur
 from .actions import fermion_action, fermion_force, wilson_action, wilson_force
 
@@ -59,7 +60,7 @@ class HMCParams:
     tol_md: float = 1e-10
     tol_met: float = 1e-14
     antiperiodic_t: bool = True
-    action: str = "unimproved"     # or "asqtad"
+    action: str = "unimproved"     # or "asqtad", "hisq"
     u0: float = 1.0                # tadpole factor of the asqtad paths
 
 
@@ -70,8 +71,11 @@ class Context:
         self.par = lat.parity(p.dims)
 
     def shifted_solves(self, u, mass, phi, betas, tol):
-        if self.p.action == "asqtad":
-            fat, naik = asqtad.fat_long_links(u, self.p.u0, self.p.antiperiodic_t)
+        if self.p.action in ("asqtad", "hisq"):
+            if self.p.action == "asqtad":
+                fat, naik = asqtad.fat_long_links(u, self.p.u0, self.p.antiperiodic_t)
+            else:
+                fat, naik, _, _ = hisq.hisq_links(u, self.p.antiperiodic_t)
             eta0 = lat.eta(self.p.dims, antiperiodic_t=False)
 
             def apply0(v, s0=min(betas)):
@@ -99,6 +103,8 @@ class Context:
                 xs = self.shifted_solves(u, fl.mass, phi, fl.md.beta, self.p.tol_md)
                 if self.p.action == "asqtad":
                     f += asqtad.fermion_force(u, xs, fl.md.alpha, self.par, self.p.u0, self.p.antiperiodic_t)
+                elif self.p.action == "hisq":
+                    f += hisq.fermion_force(u, xs, fl.md.alpha, self.par, self.p.antiperiodic_t)
                 else:
                     f += fermion_force(u, xs, fl.md.alpha, self.eta, self.par)
         return f

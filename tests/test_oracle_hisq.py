@@ -139,3 +139,15 @@ def test_trajectory_reversible():
     u2, m2 = itg.md_evolve(ctx, u1, -m1, phis, p.tau, p.n_outer, p.n_gauge)
     assert np.max(np.abs(u2 - u0)) < 1e-12
     assert np.max(np.abs(m2 + mom)) < 1e-11
+
+
+def test_projection_equals_newton_polar_iteration():
+    """The polar factor by the eigen-decomposition of V^dag V (the oracle's)
+    equals Newton's iteration W <- (W + W^(-dag)) / 2 from W = V, an
+    independent method, on the level-1 links of a hot field."""
+    dims = (4, 2, 4, 2)
+    _, _, w, v = hisq.hisq_links(syn.haar_gauge(dims, 13))
+    x = v.copy()
+    for _ in range(30):
+        x = 0.5 * (x + su3.dag(np.linalg.inv(x)))
+    np.testing.assert_allclose(x, w, atol=1e-12)
